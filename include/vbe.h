@@ -1,0 +1,298 @@
+/*
+ * vbe.h -- C ABI of libvbe, a single-GPU executor for vector bytecode.
+ *
+ * The interface follows the paper's component protocol (Kristensen et al.,
+ * "cphVB: A System for Automated Runtime Optimization and Parallelization of
+ * Vectorized Applications", SciPy 2012):
+ *
+ *   - section "Interface": the Vector Engine and its manager expose
+ *     initialisation, finalisation, execution of a list of bytecodes, and
+ *     creation of arrays           -> vbe_init, vbe_finalize, vbe_submit,
+ *                                     vbe_base_create / vbe_view_create;
+ *   - section "Numerical Python": an array-base is a contiguous allocation,
+ *     an array-view selects / re-orders its elements -> vbe_view_create;
+ *   - section "Bytecode": one opcode per mnemonic, the opcode fixes the
+ *     operand count, operands are multidimensional arrays -> vbe_instr;
+ *   - section "Vector Engine Manager": late allocation (metadata first,
+ *     memory on first write) and the sync / discard / release ownership
+ *     instructions -> vbe_base_create, vbe_sync, vbe_discard, vbe_free and
+ *     the SYNC / DISCARD / FREE opcodes;
+ *   - section "Vector Engine" (implementation): instructions are grouped
+ *     into kernels while they are "blockable" (they share no data with the
+ *     kernel, or exactly the same data) -> the fusion analysis behind
+ *     vbe_submit (VBE_FUSE), described by vbe_plan.
+ *
+ * Conventions. Every call returns VBE_OK (0) or a negative VBE_ERR_* code;
+ * no C++ exception crosses the boundary. vbe_last_error() gives a message
+ * for the most recent failure on a context. Handles (vbe_base, vbe_view,
+ * vbe_ticket) are opaque positive 64-bit ids; 0 means "none". Offsets,
+ * shapes and strides count ELEMENTS, not bytes. Host pointers passed in are
+ * only read during the call unless stated otherwise. The library owns the
+ * device memory it allocates; memory registered with vbe_base_register
+ * stays owned by the caller. A context is not thread-safe: use one context
+ * per client thread, or lock around calls (the server API below does this
+ * internally).
+ */
+#ifndef VBE_H
+#define VBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+enum {
+  VBE_OK = 0,
+  VBE_ERR_INVALID = -1,      /* bad argument, unknown handle or opcode      */
+  VBE_ERR_OUT_OF_BOUNDS = -2,/* a view reaches outside its base             */
+  VBE_ERR_DTYPE = -3,        /* dtype rule of an opcode violated            */
+  VBE_ERR_SHAPE = -4,        /* operand shapes disagree                     */
+  VBE_ERR_OOM = -5,          /* device allocation failed                    */
+  VBE_ERR_ADMISSION = -6,    /* request larger than the memory cap          */
+  VBE_ERR_COMPILE = -7,      /* NVRTC rejected a generated kernel           */
+  VBE_ERR_TIMEOUT = -8,      /* a wait ran out of time                      */
+  VBE_ERR_CUDA = -9,         /* a CUDA runtime call failed                  */
+  VBE_ERR_UNINIT = -10,      /* read of a base that was never written       */
+  VBE_ERR_NO_DEVICE = -11,   /* call needs a device; context is host-only   */
+  VBE_ERR_OVERLAP = -12,     /* an output view overlaps itself              */
+  VBE_ERR_BUSY = -13         /* server queue full / shutting down           */
+};
+
+/* --------------------------------------------------------------- dtypes */
+enum { VBE_BOOL = 0, VBE_INT64 = 1, VBE_FLOAT32 = 2, VBE_FLOAT64 = 3 };
+
+/* -------------------------------------------------------------- opcodes */
+/* Arity in brackets. Elementwise ops require every view operand to have
+ * the output's shape (broadcasting is expressed by stride-0 views).
+ * Arithmetic inputs share one dtype equal to the output's.               */
+enum {
+  VBE_OP_ADD = 1,         /* [2] int64/f32/f64; int64 wraps modulo 2^64   */
+  VBE_OP_SUBTRACT = 2,    /* [2]                                          */
+  VBE_OP_MULTIPLY = 3,    /* [2]                                          */
+  VBE_OP_DIVIDE = 4,      /* [2] f32/f64 only, IEEE round-to-nearest      */
+  VBE_OP_MAXIMUM = 5,     /* [2] a if (a > b or a is NaN) else b          */
+  VBE_OP_MINIMUM = 6,     /* [2] a if (a < b or a is NaN) else b          */
+  VBE_OP_SQRT = 7,        /* [1] f32/f64, correctly rounded               */
+  VBE_OP_EXP = 8,         /* [1] f32/f64, CUDA exp/expf                   */
+  VBE_OP_LOG = 9,         /* [1] f32/f64, CUDA log/logf                   */
+  VBE_OP_ABSOLUTE = 10,   /* [1] int64/f32/f64                            */
+  VBE_OP_NEGATIVE = 11,   /* [1] int64/f32/f64                            */
+  VBE_OP_LESS = 12,       /* [2] same-dtype inputs, bool output           */
+  VBE_OP_LESS_EQUAL = 13,
+  VBE_OP_GREATER = 14,
+  VBE_OP_GREATER_EQUAL = 15,
+  VBE_OP_EQUAL = 16,
+  VBE_OP_NOT_EQUAL = 17,
+  VBE_OP_SELECT = 18,     /* [3] out = in0 ? in1 : in2; in0 bool          */
+  VBE_OP_CAST = 19,       /* [1] any -> any; float->int64 truncates; ->bool is (x != 0) */
+  VBE_OP_COPY = 20,       /* [1] same dtype; with a constant: fill        */
+  VBE_OP_RANDOM = 21,     /* [0] f64 out; element m (row-major index over the
+                             output view) = splitmix64 finaliser of
+                             seed + (key + step*m + 1) * 0x9e3779b97f4a7c15,
+                             top 53 bits scaled by 2^-53                  */
+  VBE_OP_ADD_REDUCE = 22, /* [1] out = in with dimension `axis` summed    */
+  VBE_OP_MIN_REDUCE = 23, /* [1] NaN propagates; empty axis is an error   */
+  VBE_OP_MAX_REDUCE = 24,
+  VBE_OP_SYNC = 25,       /* [0] out's base must hold its current value in
+                             device memory here (a fusion barrier)        */
+  VBE_OP_DISCARD = 26,    /* [0] out's base contents are dead until written
+                             again; the handle stays valid                */
+  VBE_OP_FREE = 27        /* [0] out's base is released after the batch   */
+};
+#define VBE_MAX_NDIM 8
+
+/* ------------------------------------------------------------- handles */
+typedef int64_t vbe_base;
+typedef int64_t vbe_view;
+typedef int64_t vbe_ticket;
+typedef struct vbe_ctx vbe_ctx;
+
+/* ----------------------------------------------------------- instruction */
+typedef struct vbe_instr {
+  int32_t op;          /* VBE_OP_*                                          */
+  int32_t const_slot;  /* -1, or k: input k is the scalar `konst` instead of
+                          in[k]; the constant takes the dtype of the other
+                          inputs (SELECT: bool for slot 0, else the output's) */
+  vbe_view out;        /* output view (SYNC/DISCARD/FREE: any view of the base) */
+  vbe_view in[3];      /* input views; unused slots 0                        */
+  int32_t axis;        /* reductions: dimension of in[0] to reduce           */
+  int32_t reserved;
+  union { double f64; int64_t i64; } konst; /* int64/bool constants use i64 */
+  uint64_t seed;       /* RANDOM */
+  uint64_t key;        /* RANDOM */
+  int64_t step;        /* RANDOM */
+} vbe_instr;
+
+/* ---------------------------------------------------------------- config */
+enum {
+  VBE_FUSE = 1u << 0,      /* form kernels from blockable runs (else one launch per bytecode) */
+  VBE_GRAPHS = 1u << 1,    /* capture repeated identical batches as CUDA graphs              */
+  VBE_AUTOTUNE = 1u << 2,  /* time launch shapes per kernel signature and keep the fastest  */
+  VBE_PACK = 1u << 3,      /* pack consecutive independent same-signature runs in one launch */
+  VBE_HOST_ONLY = 1u << 4, /* no device: analysis, planning and code generation only        */
+  VBE_RECORD = 1u << 5     /* host-only context whose bases live in host memory and whose
+                              launches are recorded (vbe_debug_take_launches) instead of run,
+                              so tests can execute the generated kernels on a CPU; implies
+                              VBE_HOST_ONLY. Not an execution path: nothing runs the kernels. */
+};
+
+typedef struct vbe_config {
+  int32_t device;          /* CUDA device ordinal                                   */
+  uint32_t flags;          /* VBE_* flags above                                     */
+  uint64_t mem_cap_bytes;  /* 0 = unlimited; library allocations beyond it fail OOM */
+  void* stream;            /* cudaStream_t to launch on, or NULL for a private one   */
+  const char* cache_dir;   /* directory for compiled kernels and tuning choices, or NULL */
+} vbe_config;
+
+/* Create a context. On VBE_HOST_ONLY no CUDA call is made.
+ * Errors: VBE_ERR_INVALID (null args), VBE_ERR_CUDA (device unusable). */
+int vbe_init(const vbe_config* cfg, vbe_ctx** out);
+/* Wait for all work, release every library allocation, destroy the context. */
+int vbe_finalize(vbe_ctx* ctx);
+
+/* Array-base creation: metadata only; device memory is allocated when the
+ * base is first written (late allocation, section "Vector Engine Manager").
+ * nelem >= 0. Errors: VBE_ERR_INVALID (dtype, nelem). */
+int vbe_base_create(vbe_ctx* ctx, int32_t dtype, int64_t nelem, vbe_base* out);
+/* Wrap caller-owned device memory (e.g. a framework tensor) as a base.
+ * device_ptr must hold nelem elements and stay valid until vbe_free. The
+ * library never frees it. */
+int vbe_base_register(vbe_ctx* ctx, int32_t dtype, int64_t nelem, void* device_ptr, vbe_base* out);
+/* Copy nbytes (== nelem * itemsize) from host into the base, allocating it
+ * if needed. Ordered after all earlier submits; returns when the copy has
+ * been read from host memory. */
+int vbe_base_upload(vbe_ctx* ctx, vbe_base base, const void* host, int64_t nbytes);
+/* Device address of the base, or NULL if it has no memory yet. */
+int vbe_base_device_ptr(vbe_ctx* ctx, vbe_base base, void** out);
+
+/* Describe a view: element (i_0..i_{ndim-1}) is base[offset + sum i_k*strides[k]].
+ * ndim in [0, VBE_MAX_NDIM]; shape[k] >= 0; strides may be 0 or negative.
+ * Every reachable element must lie in the base (VBE_ERR_OUT_OF_BOUNDS). */
+int vbe_view_create(vbe_ctx* ctx, vbe_base base, int64_t offset, int32_t ndim,
+                    const int64_t* shape, const int64_t* strides, vbe_view* out);
+int vbe_view_destroy(vbe_ctx* ctx, vbe_view view);
+
+/* Execute a batch of n bytecodes, in order semantics (section "Vector
+ * Engine": the engine obeys the serialisation dependencies). Returns after
+ * the work is enqueued on the context's stream; *ticket identifies it.
+ * The batch is validated first; on any error nothing is enqueued. */
+int vbe_submit(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, vbe_ticket* ticket);
+/* Wait for a ticket. timeout_ns < 0 waits forever; VBE_ERR_TIMEOUT when the
+ * limit passes (the work continues). */
+int vbe_wait(vbe_ctx* ctx, vbe_ticket ticket, int64_t timeout_ns);
+/* Read access (section "Vector Engine Manager", sync): wait for all work
+ * enqueued so far, then copy nbytes of the base into host_dst. */
+int vbe_sync(vbe_ctx* ctx, vbe_base base, void* host_dst, int64_t nbytes);
+/* Mark a base's contents dead (discard); its memory may be reused. */
+int vbe_discard(vbe_ctx* ctx, vbe_base base);
+/* Release a base (and its views) after the work enqueued so far. */
+int vbe_free(vbe_ctx* ctx, vbe_base base);
+
+/* Describe, as JSON, how vbe_submit would execute a batch: the kernels
+ * (runs) it forms, the instructions of each, which values stay in registers
+ * and which are stored, and the generated CUDA source when
+ * want_source != 0. Writes at most cap bytes (NUL-terminated) and the full
+ * length to *needed. Works on host-only contexts. */
+int vbe_plan(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, int32_t want_source,
+             char* buf, int64_t cap, int64_t* needed);
+
+/* Generate and compile (without loading) every kernel the batch would
+ * use: a host-side check of the code generator. *nkernels = runs compiled. */
+int vbe_plan_compile(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, int64_t* nkernels);
+/* Diagnostic: *out = 0 when the two views provably share no element, else
+ * 1. This is the overlap test the fusion analysis uses (exact for views
+ * whose strides form a divisibility chain, conservative otherwise). */
+int vbe_views_may_overlap(vbe_ctx* ctx, vbe_view a, vbe_view b, int32_t* out);
+
+/* VBE_RECORD contexts: move the launches recorded so far into buf as JSON
+ * {"allocs": [[addr, bytes], ...], "launches": [...], "sources": {key: text}}
+ * (addresses are host addresses of the context's allocations). Same size
+ * protocol as vbe_plan. */
+int vbe_debug_take_launches(vbe_ctx* ctx, char* buf, int64_t cap, int64_t* needed);
+
+typedef struct vbe_stats {
+  int64_t kernel_launches;   /* launches of generated kernels                 */
+  int64_t graph_launches;    /* CUDA graph replays                            */
+  int64_t graph_captures;
+  int64_t compiles;          /* NVRTC compilations (cache misses)             */
+  int64_t autotunes;         /* signatures tuned                              */
+  int64_t batches;
+  int64_t bytes_allocated;   /* live library allocations                      */
+  int64_t peak_bytes;
+} vbe_stats;
+int vbe_get_stats(vbe_ctx* ctx, vbe_stats* out);
+
+const char* vbe_strerror(int code);
+const char* vbe_last_error(vbe_ctx* ctx);
+
+/* ------------------------------------------------------------ serving */
+/* A request is a self-contained program executed by the server loop:
+ * bases (with optional host input and result buffers), views over them
+ * (base = index into bases[]), and instructions whose view fields hold
+ * 1-based indices into views[] (0 = none). Host buffers must stay valid
+ * until the request completes. */
+typedef struct vbe_req_base {
+  int32_t dtype;
+  int32_t reserved;
+  int64_t nelem;
+  const void* init;   /* host data uploaded on admission, or NULL          */
+  void* result;       /* host buffer receiving the final contents, or NULL */
+} vbe_req_base;
+
+typedef struct vbe_req_view {
+  int32_t base;       /* index into bases[] */
+  int32_t ndim;
+  int64_t offset;
+  int64_t shape[VBE_MAX_NDIM];
+  int64_t strides[VBE_MAX_NDIM];
+} vbe_req_view;
+
+typedef struct vbe_request {
+  const vbe_req_base* bases;
+  int32_t nbases;
+  int32_t nviews;
+  const vbe_req_view* views;
+  const vbe_instr* instrs;
+  int64_t ninstrs;
+} vbe_request;
+
+typedef struct vbe_server_config {
+  int32_t slots;          /* requests in flight at once (one stream each) */
+  int32_t max_queue;      /* pending requests accepted before VBE_ERR_BUSY */
+  uint64_t mem_cap_bytes; /* admission cap on the sum of request footprints */
+  uint32_t flags;         /* VBE_FUSE etc. for request execution             */
+} vbe_server_config;
+
+typedef struct vbe_request_result {
+  int32_t status;         /* VBE_OK or the request's error code             */
+  int32_t reserved;
+  int64_t footprint_bytes;
+  double t_arrive_ns;     /* submit time (steady clock)                     */
+  double t_admit_ns;      /* admitted (slot + memory available)             */
+  double t_done_ns;       /* results copied to the host buffers             */
+} vbe_request_result;
+
+typedef struct vbe_server vbe_server;
+
+/* Start a server on a context (which it then owns for execution; do not
+ * submit on the context directly while the server runs). A scheduler
+ * thread admits queued requests while a slot is free and the admitted
+ * footprints fit mem_cap_bytes (continuous batching: a request is admitted
+ * as soon as another completes), executes each on its slot's stream, and
+ * completes it when its results are on the host. */
+int vbe_server_create(vbe_ctx* ctx, const vbe_server_config* cfg, vbe_server** out);
+/* Enqueue a request; *id identifies it. VBE_ERR_ADMISSION if its footprint
+ * alone exceeds the cap, VBE_ERR_BUSY if the queue is full. */
+int vbe_server_submit(vbe_server* srv, const vbe_request* req, int64_t* id);
+/* Wait for a request (timeout_ns < 0: forever) and fetch its result record. */
+int vbe_server_wait(vbe_server* srv, int64_t id, int64_t timeout_ns, vbe_request_result* out);
+/* Drain, stop the scheduler, release everything. */
+int vbe_server_destroy(vbe_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VBE_H */

@@ -1,0 +1,419 @@
+// extern "C" entry points of libvbe (declared in include/vbe.h).
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+
+#include "vbe_core.h"
+
+using vbe::Ctx;
+using vbe::Error;
+
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int record(vbe_ctx* ctx, const Error& e) {
+  if (ctx) ctx->c.last_error = e.msg;
+  g_last_error = e.msg;
+  return e.code;
+}
+
+}  // namespace
+
+#define API_BEGIN try {
+#define API_END                                                   \
+  }                                                               \
+  catch (const Error& e) {                                        \
+    return record(ctx, e);                                        \
+  }                                                               \
+  catch (const std::exception& e) {                               \
+    return record(ctx, Error{VBE_ERR_INVALID, e.what()});         \
+  }                                                               \
+  return VBE_OK;
+
+namespace vbe {
+std::vector<char> compile_cached(Ctx* c, const std::string& src, bool* compiled);
+}
+
+extern "C" {
+
+const char* vbe_strerror(int code) {
+  switch (code) {
+    case VBE_OK: return "ok";
+    case VBE_ERR_INVALID: return "invalid argument";
+    case VBE_ERR_OUT_OF_BOUNDS: return "view out of bounds";
+    case VBE_ERR_DTYPE: return "dtype rule violated";
+    case VBE_ERR_SHAPE: return "shape mismatch";
+    case VBE_ERR_OOM: return "out of device memory";
+    case VBE_ERR_ADMISSION: return "request exceeds the memory cap";
+    case VBE_ERR_COMPILE: return "kernel compilation failed";
+    case VBE_ERR_TIMEOUT: return "timed out";
+    case VBE_ERR_CUDA: return "CUDA error";
+    case VBE_ERR_UNINIT: return "read of a base that was never written";
+    case VBE_ERR_NO_DEVICE: return "no device (host-only context)";
+    case VBE_ERR_OVERLAP: return "output view overlaps itself";
+    case VBE_ERR_BUSY: return "server busy";
+  }
+  return "unknown error";
+}
+
+const char* vbe_last_error(vbe_ctx* ctx) { return ctx ? ctx->c.last_error.c_str() : g_last_error.c_str(); }
+
+int vbe_init(const vbe_config* cfg, vbe_ctx** out) {
+  vbe_ctx* ctx = nullptr;
+  API_BEGIN
+  if (!cfg || !out) vbe::fail(VBE_ERR_INVALID, "null config or output");
+  std::unique_ptr<vbe_ctx> h(new vbe_ctx());
+  Ctx& c = h->c;
+  c.cfg = *cfg;
+  c.cfg.cache_dir = nullptr;
+  c.record = (cfg->flags & VBE_RECORD) != 0;
+  c.host_only = (cfg->flags & VBE_HOST_ONLY) != 0 || c.record;
+  if (c.record) {
+    // launch shapes of recorded runs (small, so a CPU can execute them)
+    if (const char* e = getenv("VBE_RECORD_BLOCK")) c.rec_block = atoi(e);
+    if (const char* e = getenv("VBE_RECORD_U")) c.rec_U = atoi(e);
+    c.sm_count = 2;
+    if (const char* e = getenv("VBE_RECORD_SMS")) c.sm_count = atoi(e);
+  }
+  c.device = cfg->device;
+  if (cfg->cache_dir) {
+    // the context keeps its own copy of the path
+    c.cache_dir_s = cfg->cache_dir;
+    c.cfg.cache_dir = c.cache_dir_s.c_str();
+  }
+  if (!c.host_only) {
+    vbe::cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
+    int sms = 0;
+    vbe::cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device), "device attribute");
+    c.sm_count = sms;
+    if (cfg->stream) {
+      c.exec.stream = (cudaStream_t)cfg->stream;
+    } else {
+      vbe::cuda_check(cudaStreamCreateWithFlags(&c.exec.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+      c.own_stream = true;
+    }
+    vbe::cuda_check(cudaDeviceGetDefaultMemPool(&c.pool, c.device), "default mem pool");
+    uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool
+    cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  *out = h.release();
+  API_END
+}
+
+int vbe_finalize(vbe_ctx* ctx) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  if (c.record) {
+    vbe::release_exec(&c, &c.exec);
+    for (auto& kv : c.host_allocs) free((void*)kv.first);
+    c.host_allocs.clear();
+  }
+  if (!c.host_only) {
+    cudaStreamSynchronize(c.exec.stream);
+    for (auto& kv : c.bases)
+      if (kv.second.dptr && !kv.second.external) cudaFreeAsync(kv.second.dptr, c.exec.stream);
+    for (auto& kv : c.batches) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+      for (void* p : kv.second.keep) cudaFree(p);
+    }
+    for (auto& kv : c.tickets) cudaEventDestroy(kv.second);
+    cudaStreamSynchronize(c.exec.stream);
+    vbe::release_exec(&c, &c.exec);
+    for (auto& kv : c.kernels)
+      if (kv.second->lib) cudaLibraryUnload(kv.second->lib);
+    if (c.own_stream) cudaStreamDestroy(c.exec.stream);
+  }
+  delete ctx;
+  ctx = nullptr;
+  API_END
+}
+
+int vbe_base_create(vbe_ctx* ctx, int32_t dtype, int64_t nelem, vbe_base* out) {
+  API_BEGIN
+  if (!ctx || !out) vbe::fail(VBE_ERR_INVALID, "null argument");
+  vbe::itemsize(dtype);
+  if (nelem < 0) vbe::fail(VBE_ERR_INVALID, "negative size");
+  vbe::BaseRec b;
+  b.dtype = dtype;
+  b.nelem = nelem;
+  int64_t h = ctx->c.next_handle++;
+  ctx->c.bases[h] = b;
+  *out = h;
+  API_END
+}
+
+int vbe_base_register(vbe_ctx* ctx, int32_t dtype, int64_t nelem, void* device_ptr, vbe_base* out) {
+  API_BEGIN
+  if (!ctx || !out) vbe::fail(VBE_ERR_INVALID, "null argument");
+  vbe::itemsize(dtype);
+  if (nelem < 0) vbe::fail(VBE_ERR_INVALID, "negative size");
+  if (!device_ptr && nelem > 0) vbe::fail(VBE_ERR_INVALID, "null device pointer");
+  vbe::BaseRec b;
+  b.dtype = dtype;
+  b.nelem = nelem;
+  b.dptr = device_ptr;
+  b.external = true;
+  b.written = true;
+  int64_t h = ctx->c.next_handle++;
+  ctx->c.bases[h] = b;
+  *out = h;
+  API_END
+}
+
+int vbe_base_upload(vbe_ctx* ctx, vbe_base base, const void* host, int64_t nbytes) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  if (c.host_only && !c.record) vbe::fail(VBE_ERR_NO_DEVICE, "host-only context");
+  auto it = c.bases.find(base);
+  if (it == c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
+  if (nbytes != it->second.bytes()) vbe::fail(VBE_ERR_INVALID, "upload size must equal the base size");
+  if (nbytes > 0 && !host) vbe::fail(VBE_ERR_INVALID, "null host pointer");
+  if (!it->second.dptr) it->second.dptr = vbe::dev_alloc(&c, &c.exec, it->second.bytes());
+  it->second.written = true;
+  if (c.record) {
+    if (nbytes > 0) memcpy(it->second.dptr, host, (size_t)nbytes);
+    return VBE_OK;
+  }
+  if (nbytes > 0)
+    vbe::cuda_check(cudaMemcpyAsync(it->second.dptr, host, (size_t)nbytes, cudaMemcpyHostToDevice, c.exec.stream),
+                    "upload");
+  vbe::cuda_check(cudaStreamSynchronize(c.exec.stream), "upload sync");
+  API_END
+}
+
+int vbe_base_device_ptr(vbe_ctx* ctx, vbe_base base, void** out) {
+  API_BEGIN
+  if (!ctx || !out) vbe::fail(VBE_ERR_INVALID, "null argument");
+  auto it = ctx->c.bases.find(base);
+  if (it == ctx->c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
+  *out = it->second.dptr;
+  API_END
+}
+
+int vbe_view_create(vbe_ctx* ctx, vbe_base base, int64_t offset, int32_t ndim, const int64_t* shape,
+                    const int64_t* strides, vbe_view* out) {
+  API_BEGIN
+  if (!ctx || !out) vbe::fail(VBE_ERR_INVALID, "null argument");
+  if (ndim < 0 || ndim > VBE_MAX_NDIM) vbe::fail(VBE_ERR_INVALID, "ndim out of range");
+  if (ndim > 0 && (!shape || !strides)) vbe::fail(VBE_ERR_INVALID, "null shape or strides");
+  auto it = ctx->c.bases.find(base);
+  if (it == ctx->c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
+  vbe::ViewDesc v;
+  v.base = base;
+  v.offset = offset;
+  v.ndim = ndim;
+  for (int k = 0; k < ndim; ++k) {
+    if (shape[k] < 0) vbe::fail(VBE_ERR_INVALID, "negative extent");
+    v.shape[k] = shape[k];
+    v.strides[k] = strides[k];
+  }
+  v.finish();
+  if (v.size() > 0 && (v.lo < 0 || v.hi >= it->second.nelem))
+    vbe::fail(VBE_ERR_OUT_OF_BOUNDS, "view reaches [" + std::to_string(v.lo) + ", " + std::to_string(v.hi) +
+                                         "] outside a base of " + std::to_string(it->second.nelem) + " elements");
+  int64_t h = ctx->c.next_handle++;
+  ctx->c.views[h] = v;
+  *out = h;
+  API_END
+}
+
+int vbe_view_destroy(vbe_ctx* ctx, vbe_view view) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  if (!ctx->c.views.erase(view)) vbe::fail(VBE_ERR_INVALID, "unknown view");
+  API_END
+}
+
+int vbe_submit(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, vbe_ticket* ticket) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  vbe::exec_batch(&c, &c.exec, prog, n, true);
+  if (ticket && c.record) *ticket = 0;
+  if (ticket && !c.record) {
+    cudaEvent_t ev;
+    vbe::cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    vbe::cuda_check(cudaEventRecord(ev, c.exec.stream), "event record");
+    int64_t t = c.next_ticket++;
+    c.tickets[t] = ev;
+    *ticket = t;
+  }
+  API_END
+}
+
+int vbe_wait(vbe_ctx* ctx, vbe_ticket ticket, int64_t timeout_ns) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  if (c.record && ticket == 0) return VBE_OK;
+  auto it = c.tickets.find(ticket);
+  if (it == c.tickets.end()) vbe::fail(VBE_ERR_INVALID, "unknown ticket");
+  if (timeout_ns < 0) {
+    vbe::cuda_check(cudaEventSynchronize(it->second), "wait");
+  } else {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      cudaError_t e = cudaEventQuery(it->second);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) vbe::cuda_check(e, "wait");
+      auto el = std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
+      if (el >= timeout_ns) vbe::fail(VBE_ERR_TIMEOUT, "ticket not complete within the limit");
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+  cudaEventDestroy(it->second);
+  c.tickets.erase(it);
+  API_END
+}
+
+int vbe_sync(vbe_ctx* ctx, vbe_base base, void* host_dst, int64_t nbytes) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  if (c.host_only && !c.record) vbe::fail(VBE_ERR_NO_DEVICE, "host-only context");
+  auto it = c.bases.find(base);
+  if (it == c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
+  if (nbytes < 0 || nbytes > it->second.bytes()) vbe::fail(VBE_ERR_INVALID, "bad size");
+  if (nbytes > 0 && !it->second.dptr) vbe::fail(VBE_ERR_UNINIT, "base was never written");
+  if (c.record) {
+    if (nbytes > 0) memcpy(host_dst, it->second.dptr, (size_t)nbytes);
+    return VBE_OK;
+  }
+  if (nbytes > 0) {
+    if (!host_dst) vbe::fail(VBE_ERR_INVALID, "null host pointer");
+    vbe::cuda_check(cudaMemcpyAsync(host_dst, it->second.dptr, (size_t)nbytes, cudaMemcpyDeviceToHost, c.exec.stream),
+                    "sync copy");
+  }
+  vbe::cuda_check(cudaStreamSynchronize(c.exec.stream), "sync");
+  API_END
+}
+
+int vbe_discard(vbe_ctx* ctx, vbe_base base) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  auto it = ctx->c.bases.find(base);
+  if (it == ctx->c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
+  it->second.written = false;
+  API_END
+}
+
+int vbe_free(vbe_ctx* ctx, vbe_base base) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  auto it = c.bases.find(base);
+  if (it == c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
+  if (it->second.dptr && !it->second.external) vbe::dev_free(&c, &c.exec, it->second.dptr, it->second.bytes());
+  for (auto v = c.views.begin(); v != c.views.end();) {
+    if (v->second.base == base) v = c.views.erase(v);
+    else ++v;
+  }
+  c.bases.erase(it);
+  API_END
+}
+
+int vbe_plan(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, int32_t want_source, char* buf, int64_t cap,
+             int64_t* needed) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  std::vector<vbe::RInstr> rp = vbe::resolve_batch(&c, prog, n);
+  size_t nb = c.bases.size();
+  (void)nb;
+  std::vector<int64_t> before;
+  for (auto& kv : c.bases) before.push_back(kv.first);
+  vbe::Plan p = vbe::make_plan(&c, rp, (c.cfg.flags & VBE_FUSE) != 0, (c.cfg.flags & VBE_PACK) != 0);
+  std::string js = vbe::plan_json(&c, rp, p, want_source != 0);
+  for (auto& st : p.staging) c.bases.erase(st.first);
+  if (needed) *needed = (int64_t)js.size() + 1;
+  if (buf && cap > 0) {
+    size_t k = std::min<size_t>((size_t)cap - 1, js.size());
+    memcpy(buf, js.data(), k);
+    buf[k] = '\0';
+  }
+  API_END
+}
+
+// Compile (without loading) the kernels a batch would use: a host-side
+// check that the generated sources are valid CUDA for sm_103a.
+int vbe_plan_compile(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, int64_t* nkernels) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  std::vector<vbe::RInstr> rp = vbe::resolve_batch(&c, prog, n);
+  vbe::Plan p = vbe::make_plan(&c, rp, (c.cfg.flags & VBE_FUSE) != 0, (c.cfg.flags & VBE_PACK) != 0);
+  int64_t k = 0;
+  std::vector<std::string> srcs;
+  for (auto& it : p.items) {
+    if (it.kind != 0) continue;
+    std::vector<uintptr_t> lp(it.run.loads.size(), 0), sp(it.run.stores.size(), 0);
+    vbe::Canon cn = vbe::canonicalize(it.run, true, lp, sp, 0);
+    srcs.push_back(vbe::generate_source(it.run, cn, nullptr));
+    ++k;
+  }
+  if (srcs.size() == 1) vbe::compile_cached(&c, srcs[0], nullptr);
+  else vbe::precompile(&c, srcs);
+  for (auto& st : p.staging) c.bases.erase(st.first);
+  if (nkernels) *nkernels = k;
+  API_END
+}
+
+int vbe_views_may_overlap(vbe_ctx* ctx, vbe_view a, vbe_view b, int32_t* out) {
+  API_BEGIN
+  if (!ctx || !out) vbe::fail(VBE_ERR_INVALID, "null argument");
+  auto ia = ctx->c.views.find(a), ib = ctx->c.views.find(b);
+  if (ia == ctx->c.views.end() || ib == ctx->c.views.end()) vbe::fail(VBE_ERR_INVALID, "unknown view");
+  *out = vbe::may_overlap(ia->second, ib->second) ? 1 : 0;
+  API_END
+}
+
+int vbe_debug_take_launches(vbe_ctx* ctx, char* buf, int64_t cap, int64_t* needed) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  if (!c.record) vbe::fail(VBE_ERR_INVALID, "not a recording context");
+  std::string js = "{\"allocs\":[";
+  bool first = true;
+  for (auto& kv : c.host_allocs) {
+    js += (first ? "[" : ",[") + std::to_string(kv.first) + "," + std::to_string(kv.second) + "]";
+    first = false;
+  }
+  js += "],\"launches\":[";
+  for (size_t i = 0; i < c.rec_launches.size(); ++i) js += (i ? "," : "") + c.rec_launches[i];
+  js += "],\"sources\":{";
+  first = true;
+  for (auto& kv : c.rec_sources) {
+    std::string esc;
+    for (char ch : kv.second) {
+      if (ch == '"') esc += "\\\"";
+      else if (ch == '\\') esc += "\\\\";
+      else if (ch == '\n') esc += "\\n";
+      else esc += ch;
+    }
+    js += (first ? "\"" : ",\"") + kv.first + "\":\"" + esc + "\"";
+    first = false;
+  }
+  js += "}}";
+  if (needed) *needed = (int64_t)js.size() + 1;
+  if (buf && cap >= (int64_t)js.size() + 1) {
+    memcpy(buf, js.data(), js.size());
+    buf[js.size()] = '\0';
+    c.rec_launches.clear();
+  }
+  API_END
+}
+
+int vbe_get_stats(vbe_ctx* ctx, vbe_stats* out) {
+  API_BEGIN
+  if (!ctx || !out) vbe::fail(VBE_ERR_INVALID, "null argument");
+  *out = ctx->c.stats;
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,853 @@
+// Code generator: one CUDA kernel per run, compiled by NVRTC for sm_103a.
+//
+// The paper proposes JIT compilation of instruction kernels as the remedy
+// for memory-bound bytecode execution (section "Future Work"). Each run is
+// rendered as straight-line CUDA: the run's instructions become a chain of
+// register operations evaluated once per element; loads and stores touch
+// only the run's live-in and live-out views. Iteration patterns:
+//
+//   elementwise / full reduction ("tile" kernels): the coalesced iteration
+//     space is walked in tiles of blockDim.x * U elements of the innermost
+//     dimension; a one-dimensional run whose views are unit-stride and
+//     aligned uses 16-byte vector loads and stores. A full reduction keeps a
+//     per-thread accumulator, reduces it in the block (warp shuffles, then
+//     shared memory), writes one partial per block, and the last block to
+//     finish sums the partials in block order.
+//   axis reduction: one thread per output element looping over the reduced
+//     dimensions (reduced dimensions outer in memory), or one block per
+//     output element with the threads striding the reduced dimensions and a
+//     block tree (reduced dimension inner in memory).
+//   packed: many independent one-dimensional runs of one signature in one
+//     persistent launch; blocks take fixed-size chunks from an atomic
+//     counter, and the last chunk of an instance to finish sums that
+//     instance's chunk partials in chunk order.
+//
+// Every reduction order depends only on the launch shape, never on timing,
+// so a result is reproducible for a given signature and size.
+#include <algorithm>
+#include <cstring>
+#include <sstream>
+
+#include "vbe_core.h"
+
+namespace vbe {
+
+namespace {
+
+struct Layout {
+  int nwords = 0;
+  int dims0 = 0;
+  int nouter = -1, inner = -1;
+  int nout = -1, nred = -1;
+  std::vector<int> lptr, lst, sptr, sst;
+  int red_ptr = -1, red_st = -1, partials = -1, counter = -1;
+  int idx_st = -1;
+  std::vector<int> rnd;
+  int consts = -1;
+};
+
+bool tile_mode(Mode m) { return m == Mode::ELEM || m == Mode::FULL; }
+
+Layout layout_of(const Run& r, const Canon& c) {
+  Layout L;
+  int w = 0;
+  int nst;  // strides per slot
+  L.dims0 = w;
+  if (tile_mode(c.spec.mode)) {
+    w += c.spec.nd;
+    L.nouter = w++;
+    L.inner = w++;
+    nst = c.spec.nd;
+  } else {
+    w += c.spec.ndk + c.spec.ndr;
+    L.nout = w++;
+    L.nred = w++;
+    nst = c.spec.ndk + c.spec.ndr;
+  }
+  for (size_t s = 0; s < r.loads.size(); ++s) {
+    L.lptr.push_back(w++);
+    L.lst.push_back(w);
+    w += nst;
+  }
+  for (size_t s = 0; s < r.stores.size(); ++s) {
+    L.sptr.push_back(w++);
+    L.sst.push_back(w);
+    w += nst;
+  }
+  if (r.has_red) {
+    L.red_ptr = w++;
+    if (!tile_mode(c.spec.mode)) {
+      L.red_st = w;
+      w += c.spec.ndk;
+    } else {
+      L.partials = w++;
+      L.counter = w++;
+    }
+  }
+  if (r.nrandom > 0 && !tile_mode(c.spec.mode)) {
+    L.idx_st = w;
+    w += c.spec.ndk + c.spec.ndr;
+  }
+  for (int k = 0; k < r.nrandom; ++k) {
+    L.rnd.push_back(w);
+    w += 3;
+  }
+  L.consts = w;
+  w += (int)r.consts.size();
+  L.nwords = std::max(w, 1);
+  return L;
+}
+
+// merge consecutive dims (in the given order) when every stride list agrees
+void coalesce(std::vector<int64_t>& dims, std::vector<std::vector<int64_t>*> lists) {
+  std::vector<int64_t> nd;
+  std::vector<std::vector<int64_t>> nl(lists.size());
+  for (size_t k = 0; k < dims.size(); ++k) {
+    if (dims[k] == 1) continue;
+    if (!nd.empty()) {
+      bool ok = true;
+      for (size_t s = 0; s < lists.size(); ++s)
+        if (nl[s].back() != (*lists[s])[k] * dims[k]) ok = false;
+      if (ok) {
+        nd.back() *= dims[k];
+        for (size_t s = 0; s < lists.size(); ++s) nl[s].back() = (*lists[s])[k];
+        continue;
+      }
+    }
+    nd.push_back(dims[k]);
+    for (size_t s = 0; s < lists.size(); ++s) nl[s].push_back((*lists[s])[k]);
+  }
+  dims = nd;
+  for (size_t s = 0; s < lists.size(); ++s) *lists[s] = nl[s];
+}
+
+std::vector<int64_t> c_strides(const std::vector<int64_t>& shape) {
+  std::vector<int64_t> st(shape.size());
+  int64_t acc = 1;
+  for (int k = (int)shape.size() - 1; k >= 0; --k) {
+    st[k] = acc;
+    acc *= std::max<int64_t>(1, shape[k]);
+  }
+  return st;
+}
+
+int cls_of(int64_t s) { return s == 0 ? 0 : (s == 1 ? 1 : 2); }
+
+}  // namespace
+
+Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& load_ptrs,
+                   const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr) {
+  Canon c;
+  int D = (int)r.shape.size();
+  c.total = r.elements();
+  // every slot must describe the run's iteration space (internal invariant)
+  for (auto& s : r.loads)
+    if ((int)s.st.size() != D) fail(VBE_ERR_INVALID, "internal: load slot rank differs from the run's");
+  for (auto& s : r.stores)
+    if ((int)s.st.size() != D) fail(VBE_ERR_INVALID, "internal: store slot rank differs from the run's");
+  if (r.has_red && (int)r.red_out.st.size() != D - (int)r.red_axes.size())
+    fail(VBE_ERR_INVALID, "internal: reduction output rank");
+  bool full = r.has_red && (int)r.red_axes.size() == D;
+  if (!r.has_red || full) {
+    c.spec.mode = r.has_red ? Mode::FULL : Mode::ELEM;
+    std::vector<int64_t> dims = r.shape;
+    c.lst.clear();
+    for (auto& s : r.loads) c.lst.push_back(s.st);
+    for (auto& s : r.stores) c.sst.push_back(s.st);
+    std::vector<std::vector<int64_t>*> lists;
+    for (auto& v : c.lst) lists.push_back(&v);
+    for (auto& v : c.sst) lists.push_back(&v);
+    coalesce(dims, lists);
+    if (dims.empty()) {
+      dims.push_back(1);
+      for (auto* l : lists) l->assign(1, 0);
+    }
+    c.dims = dims;
+    c.spec.nd = (int)dims.size();
+    for (auto& v : c.lst) c.spec.load_cls.push_back(cls_of(v.back()));
+    for (auto& v : c.sst) c.spec.store_cls.push_back(cls_of(v.back()));
+    // vector path: one dimension, unit or zero strides, aligned pointers
+    if (allow_vec && c.spec.nd == 1) {
+      int maxsz = 0;
+      bool ok = true;
+      for (size_t s = 0; s < r.loads.size(); ++s) {
+        if (c.spec.load_cls[s] == 2) ok = false;
+        if (c.spec.load_cls[s] == 1) maxsz = std::max(maxsz, itemsize(r.loads[s].dtype));
+      }
+      for (size_t s = 0; s < r.stores.size(); ++s) {
+        if (c.spec.store_cls[s] != 1) ok = false;
+        maxsz = std::max(maxsz, itemsize(r.stores[s].dtype));
+      }
+      if (ok && maxsz > 0) {
+        int E = 16 / maxsz;
+        for (size_t s = 0; s < r.loads.size(); ++s) {
+          if (c.spec.load_cls[s] != 1) continue;
+          int b = E * itemsize(r.loads[s].dtype);
+          uintptr_t p = load_ptrs[s] + (uintptr_t)(r.loads[s].offset * itemsize(r.loads[s].dtype));
+          if (p % b) ok = false;
+        }
+        for (size_t s = 0; s < r.stores.size(); ++s) {
+          int b = E * itemsize(r.stores[s].dtype);
+          uintptr_t p = store_ptrs[s] + (uintptr_t)(r.stores[s].offset * itemsize(r.stores[s].dtype));
+          if (p % b) ok = false;
+        }
+        if (ok) {
+          c.spec.vec = true;
+          c.spec.E = E;
+        }
+      }
+    }
+    (void)red_ptr;
+    return c;
+  }
+  // axis reduction: kept dims (in order) then reduced dims
+  std::vector<int> kept, red = r.red_axes;
+  for (int d = 0; d < D; ++d)
+    if (!std::binary_search(red.begin(), red.end(), d)) kept.push_back(d);
+  std::vector<int64_t> cst = c_strides(r.shape);
+  auto pick = [](const std::vector<int64_t>& v, const std::vector<int>& idx) {
+    std::vector<int64_t> o;
+    for (int i : idx) o.push_back(v[i]);
+    return o;
+  };
+  std::vector<int64_t> kd = pick(r.shape, kept), rd = pick(r.shape, red);
+  std::vector<std::vector<int64_t>> lk, lr, sk, sr;
+  for (auto& s : r.loads) {
+    lk.push_back(pick(s.st, kept));
+    lr.push_back(pick(s.st, red));
+  }
+  for (auto& s : r.stores) {
+    sk.push_back(pick(s.st, kept));
+    sr.push_back(pick(s.st, red));
+  }
+  std::vector<int64_t> outk = r.red_out.st;  // already over the kept dims
+  std::vector<int64_t> ik = pick(cst, kept), ir = pick(cst, red);
+  {
+    std::vector<std::vector<int64_t>*> L;
+    for (auto& v : lk) L.push_back(&v);
+    for (auto& v : sk) L.push_back(&v);
+    L.push_back(&outk);
+    if (r.nrandom) L.push_back(&ik);
+    coalesce(kd, L);
+  }
+  {
+    std::vector<std::vector<int64_t>*> L;
+    for (auto& v : lr) L.push_back(&v);
+    for (auto& v : sr) L.push_back(&v);
+    if (r.nrandom) L.push_back(&ir);
+    coalesce(rd, L);
+  }
+  if (rd.empty()) {  // reducing extent-1 dims only
+    rd.push_back(1);
+    for (auto& v : lr) v.assign(1, 0);
+    for (auto& v : sr) v.assign(1, 0);
+    ir.assign(1, 0);
+  }
+  c.spec.ndk = (int)kd.size();
+  c.spec.ndr = (int)rd.size();
+  c.dims = kd;
+  c.dims.insert(c.dims.end(), rd.begin(), rd.end());
+  for (size_t s = 0; s < lk.size(); ++s) {
+    std::vector<int64_t> v = lk[s];
+    v.insert(v.end(), lr[s].begin(), lr[s].end());
+    c.lst.push_back(v);
+    c.spec.load_cls.push_back(cls_of(lr[s].back()));
+  }
+  for (size_t s = 0; s < sk.size(); ++s) {
+    std::vector<int64_t> v = sk[s];
+    v.insert(v.end(), sr[s].begin(), sr[s].end());
+    c.sst.push_back(v);
+    c.spec.store_cls.push_back(cls_of(sr[s].back()));
+  }
+  c.red_st = outk;
+  c.idx_st = ik;
+  c.idx_st.insert(c.idx_st.end(), ir.begin(), ir.end());
+  int64_t nred = 1, nout = 1;
+  for (auto v : rd) nred *= v;
+  for (auto v : kd) nout *= v;
+  // one block per output when the reduced dimension is inner in memory
+  bool inner_unit = !r.loads.empty() && lr[0].back() == 1;
+  c.spec.mode = (nred >= 64 && (inner_unit || nout < 4 * 148)) ? Mode::AXIS_BLOCK : Mode::AXIS_THREAD;
+  return c;
+}
+
+int words_count(const Run& r, const Canon& c) { return layout_of(r, c).nwords; }
+
+void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load_ptrs,
+                const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr, uintptr_t partials,
+                uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out) {
+  (void)block;
+  (void)U;
+  Layout L = layout_of(r, c);
+  std::vector<int64_t>& w = out->w;
+  w.assign(L.nwords, 0);
+  for (size_t k = 0; k < c.dims.size(); ++k) w[L.dims0 + k] = c.dims[k];
+  if (tile_mode(c.spec.mode)) {
+    int64_t no = 1;
+    for (int k = 0; k + 1 < c.spec.nd; ++k) no *= c.dims[k];
+    w[L.nouter] = no;
+    w[L.inner] = c.dims[c.spec.nd - 1];
+  } else {
+    int64_t no = 1, nr = 1;
+    for (int k = 0; k < c.spec.ndk; ++k) no *= c.dims[k];
+    for (int k = 0; k < c.spec.ndr; ++k) nr *= c.dims[c.spec.ndk + k];
+    w[L.nout] = no;
+    w[L.nred] = nr;
+  }
+  for (size_t s = 0; s < r.loads.size(); ++s) {
+    w[L.lptr[s]] = (int64_t)(load_ptrs[s] + (uintptr_t)(r.loads[s].offset * itemsize(r.loads[s].dtype)));
+    for (size_t k = 0; k < c.lst[s].size(); ++k) w[L.lst[s] + k] = c.lst[s][k];
+  }
+  for (size_t s = 0; s < r.stores.size(); ++s) {
+    w[L.sptr[s]] = (int64_t)(store_ptrs[s] + (uintptr_t)(r.stores[s].offset * itemsize(r.stores[s].dtype)));
+    for (size_t k = 0; k < c.sst[s].size(); ++k) w[L.sst[s] + k] = c.sst[s][k];
+  }
+  if (r.has_red) {
+    w[L.red_ptr] = (int64_t)(red_ptr + (uintptr_t)(r.red_out.offset * itemsize(r.red_dtype)));
+    if (L.red_st >= 0)
+      for (size_t k = 0; k < c.red_st.size(); ++k) w[L.red_st + k] = c.red_st[k];
+    if (L.partials >= 0) {
+      w[L.partials] = (int64_t)partials;
+      w[L.counter] = (int64_t)counter;
+    }
+  }
+  if (L.idx_st >= 0)
+    for (size_t k = 0; k < c.idx_st.size(); ++k) w[L.idx_st + k] = c.idx_st[k];
+  for (size_t k = 0; k < r.consts.size(); ++k) {
+    const Operand& o = r.consts[k];
+    int64_t bits = o.i;
+    if (o.dtype == VBE_FLOAT64) {
+      memcpy(&bits, &o.f, 8);
+    } else if (o.dtype == VBE_FLOAT32) {
+      float g = (float)o.f;
+      uint32_t b32;
+      memcpy(&b32, &g, 4);
+      bits = (int64_t)b32;
+    }
+    w[L.consts + k] = bits;
+  }
+  int ri = 0;
+  for (auto& s : r.steps) {
+    if (s.op != VBE_OP_RANDOM) continue;
+    w[L.rnd[ri]] = (int64_t)s.seed;
+    w[L.rnd[ri] + 1] = (int64_t)s.key;
+    w[L.rnd[ri] + 2] = s.rstep;
+    ++ri;
+  }
+}
+
+// ---------------------------------------------------------------- source
+
+namespace {
+
+const char* kPrelude = R"CUDA(
+typedef long long i64;
+typedef unsigned long long u64;
+__device__ __forceinline__ i64 vbe_iadd(i64 a, i64 b) { return (i64)((u64)a + (u64)b); }
+__device__ __forceinline__ i64 vbe_isub(i64 a, i64 b) { return (i64)((u64)a - (u64)b); }
+__device__ __forceinline__ i64 vbe_imul(i64 a, i64 b) { return (i64)((u64)a * (u64)b); }
+__device__ __forceinline__ i64 vbe_ineg(i64 a) { return (i64)(0ull - (u64)a); }
+__device__ __forceinline__ i64 vbe_iabs(i64 a) { return a < 0 ? vbe_ineg(a) : a; }
+template <class T> __device__ __forceinline__ T vbe_max(T a, T b) { return (a > b || a != a) ? a : b; }
+template <class T> __device__ __forceinline__ T vbe_min(T a, T b) { return (a < b || a != a) ? a : b; }
+// RANDOM: splitmix64 finaliser of seed + (key + step*m + 1) * golden gamma,
+// top 53 bits scaled to [0, 1)
+__device__ __forceinline__ double vbe_u01(u64 seed, u64 key, u64 step, u64 m) {
+  u64 z = seed + (key + step * m + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 1.1102230246251565404236316680908203125e-16;
+}
+#ifndef VBE_EMU
+template <class T> __device__ __forceinline__ T* vbe_ptr(i64 v) { return reinterpret_cast<T*>(v); }
+template <int B> struct vbe_vec;
+template <> struct vbe_vec<16> { typedef uint4 t; };
+template <> struct vbe_vec<8> { typedef uint2 t; };
+template <> struct vbe_vec<4> { typedef unsigned int t; };
+template <> struct vbe_vec<2> { typedef unsigned short t; };
+template <> struct vbe_vec<1> { typedef unsigned char t; };
+template <class T, int E> __device__ __forceinline__ void vbe_vload(const T* p, T (&o)[E]) {
+  typedef typename vbe_vec<sizeof(T) * E>::t V;
+  union { V v; T t[E]; } u;
+  u.v = *reinterpret_cast<const V*>(p);
+#pragma unroll
+  for (int e = 0; e < E; ++e) o[e] = u.t[e];
+}
+template <class T, int E> __device__ __forceinline__ void vbe_vstore(T* p, const T (&o)[E]) {
+  typedef typename vbe_vec<sizeof(T) * E>::t V;
+  union { V v; T t[E]; } u;
+#pragma unroll
+  for (int e = 0; e < E; ++e) u.t[e] = o[e];
+  *reinterpret_cast<V*>(p) = u.v;
+}
+#endif
+)CUDA";
+
+struct Gen {
+  const Run& r;
+  const Canon& c;
+  Layout L;
+  std::ostringstream o;
+  const char* rt() const { return ctype(r.red_dtype); }
+  bool kahan() const { return r.has_red && r.red_op == VBE_OP_ADD_REDUCE && r.red_dtype == VBE_FLOAT32; }
+
+  Gen(const Run& r_, const Canon& c_) : r(r_), c(c_), L(layout_of(r_, c_)) {}
+
+  std::string opnd(const Operand& a) {
+    if (a.kind == 0) return "l" + std::to_string(a.idx);
+    if (a.kind == 2) return "v" + std::to_string(a.idx);
+    // constants are parameter words (so kernels that differ only in their
+    // constants share one compiled module)
+    std::string w = "p.w[" + std::to_string(L.consts + a.idx) + "]";
+    switch (a.dtype) {
+      case VBE_FLOAT64: return "__longlong_as_double(" + w + ")";
+      case VBE_FLOAT32: return "__int_as_float((int)" + w + ")";
+      case VBE_BOOL: return "(" + w + " != 0)";
+      default: return w;
+    }
+  }
+
+  std::string expr(const Step& s) {
+    std::string a = s.nin > 0 ? opnd(s.a[0]) : "", b = s.nin > 1 ? opnd(s.a[1]) : "",
+                d = s.nin > 2 ? opnd(s.a[2]) : "";
+    bool i64t = s.dt_in == VBE_INT64;
+    bool f32 = s.dt_in == VBE_FLOAT32;
+    switch (s.op) {
+      case VBE_OP_ADD: return i64t ? "vbe_iadd(" + a + "," + b + ")" : "(" + a + " + " + b + ")";
+      case VBE_OP_SUBTRACT: return i64t ? "vbe_isub(" + a + "," + b + ")" : "(" + a + " - " + b + ")";
+      case VBE_OP_MULTIPLY: return i64t ? "vbe_imul(" + a + "," + b + ")" : "(" + a + " * " + b + ")";
+      case VBE_OP_DIVIDE: return "(" + a + " / " + b + ")";
+      case VBE_OP_MAXIMUM: return "vbe_max(" + a + "," + b + ")";
+      case VBE_OP_MINIMUM: return "vbe_min(" + a + "," + b + ")";
+      case VBE_OP_SQRT: return std::string(f32 ? "sqrtf(" : "sqrt(") + a + ")";
+      case VBE_OP_EXP: return std::string(f32 ? "expf(" : "exp(") + a + ")";
+      case VBE_OP_LOG: return std::string(f32 ? "logf(" : "log(") + a + ")";
+      case VBE_OP_ABSOLUTE:
+        return i64t ? "vbe_iabs(" + a + ")" : std::string(f32 ? "fabsf(" : "fabs(") + a + ")";
+      case VBE_OP_NEGATIVE: return i64t ? "vbe_ineg(" + a + ")" : "(-" + a + ")";
+      case VBE_OP_LESS: return "(" + a + " < " + b + ")";
+      case VBE_OP_LESS_EQUAL: return "(" + a + " <= " + b + ")";
+      case VBE_OP_GREATER: return "(" + a + " > " + b + ")";
+      case VBE_OP_GREATER_EQUAL: return "(" + a + " >= " + b + ")";
+      case VBE_OP_EQUAL: return "(" + a + " == " + b + ")";
+      case VBE_OP_NOT_EQUAL: return "(" + a + " != " + b + ")";
+      case VBE_OP_SELECT: return "(" + a + " ? " + b + " : " + d + ")";
+      case VBE_OP_CAST:
+        if (s.dt_out == VBE_BOOL) return "(" + a + " != 0)";
+        return "((" + std::string(ctype(s.dt_out)) + ")" + a + ")";
+      case VBE_OP_COPY: return a;
+      case VBE_OP_RANDOM: {
+        int w = L.rnd[s.random_idx];
+        return "vbe_u01((u64)p.w[" + std::to_string(w) + "], (u64)p.w[" + std::to_string(w + 1) +
+               "], (u64)p.w[" + std::to_string(w + 2) + "], (u64)m)";
+      }
+    }
+    fail(VBE_ERR_INVALID, "codegen: unsupported opcode");
+  }
+
+  std::string red_id() {
+    int dt = r.red_dtype;
+    switch (r.red_op) {
+      case VBE_OP_ADD_REDUCE: return dt == VBE_INT64 ? "((i64)0)" : (dt == VBE_FLOAT32 ? "0.0f" : "0.0");
+      case VBE_OP_MIN_REDUCE:
+        return dt == VBE_INT64 ? "((i64)0x7fffffffffffffffll)"
+                               : (dt == VBE_FLOAT32 ? "__int_as_float(0x7f800000)"
+                                                    : "__longlong_as_double(0x7ff0000000000000ll)");
+      case VBE_OP_MAX_REDUCE:
+        return dt == VBE_INT64 ? "((i64)0x8000000000000000ull)"
+                               : (dt == VBE_FLOAT32 ? "__int_as_float(0xff800000)"
+                                                    : "__longlong_as_double(0xfff0000000000000ll)");
+    }
+    return "0";
+  }
+
+  std::string comb(const std::string& a, const std::string& b) {
+    switch (r.red_op) {
+      case VBE_OP_ADD_REDUCE:
+        return r.red_dtype == VBE_INT64 ? "vbe_iadd(" + a + "," + b + ")" : "(" + a + " + " + b + ")";
+      case VBE_OP_MIN_REDUCE: return "vbe_min(" + a + "," + b + ")";
+      case VBE_OP_MAX_REDUCE: return "vbe_max(" + a + "," + b + ")";
+    }
+    return a;
+  }
+
+  // the per-element function: loaded values in, values to store out
+  void emit_elem() {
+    o << "struct P { i64 w[" << L.nwords << "]; };\n";
+    o << "__device__ __forceinline__ void vbe_elem(const P& p, i64 m";
+    for (size_t s = 0; s < r.loads.size(); ++s) o << ", const " << ctype(r.loads[s].dtype) << " l" << s;
+    for (size_t s = 0; s < r.stores.size(); ++s) o << ", " << ctype(r.stores[s].dtype) << "& o" << s;
+    if (r.has_red) {
+      o << ", " << rt() << "& acc";
+      if (kahan()) o << ", float& kc";
+    }
+    o << ") {\n  (void)m; (void)p;\n";
+    for (auto& s : r.steps) o << "  const " << ctype(s.dt_out) << " v" << s.value << " = " << expr(s) << ";\n";
+    for (size_t s = 0; s < r.stores.size(); ++s) o << "  o" << s << " = v" << r.store_value[s] << ";\n";
+    if (r.has_red) {
+      std::string x = "v" + std::to_string(r.red_value);
+      if (kahan()) {
+        o << "  { const float y = " << x << " - kc; const float t = acc + y; kc = (t - acc) - y; acc = t; }\n";
+      } else {
+        o << "  acc = " << comb("acc", x) << ";\n";
+      }
+    }
+    o << "}\n";
+  }
+
+  void emit_block_reduce() {
+    if (!r.has_red) return;
+    o << "__device__ __forceinline__ " << rt() << " vbe_block_reduce(" << rt() << " v) {\n"
+      << "  __shared__ " << rt() << " sh[32];\n"
+      << "  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;\n"
+      << "  for (int off = 16; off > 0; off >>= 1) { " << rt() << " t = __shfl_down_sync(0xffffffffu, v, off); v = "
+      << comb("v", "t") << "; }\n"
+      << "  if (lane == 0) sh[wid] = v;\n  __syncthreads();\n"
+      << "  if (wid == 0) {\n    v = lane < nw ? sh[lane] : " << red_id() << ";\n"
+      << "    for (int off = 16; off > 0; off >>= 1) { " << rt()
+      << " t = __shfl_down_sync(0xffffffffu, v, off); v = " << comb("v", "t") << "; }\n  }\n"
+      << "  __syncthreads();\n  return v;\n}\n";
+  }
+
+  std::string T(int dt) { return ctype(dt); }
+  std::string W(int k) { return "p.w[" + std::to_string(k) + "]"; }
+
+  // argument list for vbe_elem given per-slot value expressions
+  std::string call(const std::string& m, const std::vector<std::string>& lv, const std::vector<std::string>& sv) {
+    std::string s = "vbe_elem(p, " + m;
+    for (auto& x : lv) s += ", " + x;
+    for (auto& x : sv) s += ", " + x;
+    if (r.has_red) s += kahan() ? ", acc, kc" : ", acc";
+    return s + ");";
+  }
+
+  void emit_pointers(const std::string& pfx) {
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      o << pfx << "const auto lp" << s << " = vbe_ptr<const " << T(r.loads[s].dtype) << ">(" << W(L.lptr[s])
+        << ");\n";
+    for (size_t s = 0; s < r.stores.size(); ++s)
+      o << pfx << "const auto sp" << s << " = vbe_ptr<" << T(r.stores[s].dtype) << ">(" << W(L.sptr[s]) << ");\n";
+  }
+
+  void emit_acc_init(const std::string& pfx) {
+    if (!r.has_red) return;
+    o << pfx << rt() << " acc = " << red_id() << ";\n";
+    if (kahan()) o << pfx << "float kc = 0.0f;\n";
+  }
+
+  std::string acc_final() { return kahan() ? "(acc - kc)" : "acc"; }
+
+  // full-reduction epilogue: block partial, last block sums partials
+  void emit_full_epilogue(const std::string& pfx, const std::string& part, const std::string& slot,
+                          const std::string& count, const std::string& nparts, const std::string& out) {
+    o << pfx << "{\n"
+      << pfx << "  " << rt() << " bsum = vbe_block_reduce(" << acc_final() << ");\n"
+      << pfx << "  __shared__ int s_last;\n"
+      << pfx << "  if (threadIdx.x == 0) {\n"
+      << pfx << "    vbe_ptr<" << rt() << ">(" << part << ")[" << slot << "] = bsum;\n"
+      << pfx << "    __threadfence();\n"
+      << pfx << "    unsigned prev = atomicAdd(vbe_ptr<unsigned>(" << count << "), 1u);\n"
+      << pfx << "    s_last = (prev == (unsigned)(" << nparts << ") - 1u);\n"
+      << pfx << "  }\n"
+      << pfx << "  __syncthreads();\n"
+      << pfx << "  if (s_last) {\n"
+      << pfx << "    __threadfence();\n"
+      << pfx << "    " << rt() << " v = " << red_id() << ";\n"
+      << pfx << "    const auto pp = vbe_ptr<const volatile " << rt() << ">(" << part << ");\n"
+      << pfx << "    for (i64 i = threadIdx.x; i < (i64)(" << nparts << "); i += blockDim.x) { " << rt()
+      << " x = pp[i]; v = " << comb("v", "x") << "; }\n"
+      << pfx << "    v = vbe_block_reduce(v);\n"
+      << pfx << "    if (threadIdx.x == 0) { vbe_ptr<" << rt() << ">(" << out << ")[0] = v; vbe_ptr<unsigned>(" << count
+      << ")[0] = 0u; }\n"
+      << pfx << "  }\n"
+      << pfx << "}\n";
+  }
+
+  // --------------------------------------------------------- tile kernels
+  void emit_tile_kernel(int U) {
+    const int nd = c.spec.nd;
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_u" << U << "(const P p) {\n";
+    emit_pointers("  ");
+    emit_acc_init("  ");
+    // inner strides
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      if (c.spec.load_cls[s] == 2) o << "  const i64 li" << s << " = " << W(L.lst[s] + nd - 1) << ";\n";
+    for (size_t s = 0; s < r.stores.size(); ++s)
+      if (c.spec.store_cls[s] == 2) o << "  const i64 si" << s << " = " << W(L.sst[s] + nd - 1) << ";\n";
+    if (c.spec.vec) {
+      emit_vec_body(U);
+    } else {
+      o << "  const i64 inner = " << W(L.inner) << ";\n"
+        << "  const i64 bsu = (i64)blockDim.x * " << U << ";\n"
+        << "  const i64 tpr = (inner + bsu - 1) / bsu;\n"
+        << "  const i64 ntiles = " << W(L.nouter) << " * tpr;\n"
+        << "  i64 t = blockIdx.x;\n"
+        << "  i64 row = tpr ? t / tpr : 0, ct = t - row * tpr;\n"
+        << "  const i64 rstep = tpr ? (i64)gridDim.x / tpr : 0, cstep = (i64)gridDim.x - rstep * tpr;\n"
+        << "  for (; t < ntiles; t += gridDim.x) {\n";
+      // row offsets
+      auto rowoff = [&](const std::string& name, int stw) {
+        if (nd == 1) {
+          o << "    const i64 " << name << " = 0;\n";
+        } else if (nd == 2) {
+          o << "    const i64 " << name << " = row * " << W(stw) << ";\n";
+        } else {
+          o << "    i64 " << name << " = 0;\n    { i64 rr = row;\n";
+          for (int k = nd - 2; k >= 0; --k)
+            o << "      { const i64 ik = rr % " << W(L.dims0 + k) << "; rr /= " << W(L.dims0 + k) << "; " << name
+              << " += ik * " << W(stw + k) << "; }\n";
+          o << "    }\n";
+        }
+      };
+      for (size_t s = 0; s < r.loads.size(); ++s) rowoff("lr" + std::to_string(s), L.lst[s]);
+      for (size_t s = 0; s < r.stores.size(); ++s) rowoff("sr" + std::to_string(s), L.sst[s]);
+      o << "    const i64 c0 = ct * bsu + threadIdx.x;\n";
+      auto laddr = [&](size_t s, const std::string& col) {
+        int cl = c.spec.load_cls[s];
+        std::string b = "lr" + std::to_string(s);
+        if (cl == 0) return "lp" + std::to_string(s) + "[" + b + "]";
+        if (cl == 1) return "lp" + std::to_string(s) + "[" + b + " + " + col + "]";
+        return "lp" + std::to_string(s) + "[" + b + " + " + col + " * li" + std::to_string(s) + "]";
+      };
+      auto saddr = [&](size_t s, const std::string& col) {
+        int cl = c.spec.store_cls[s];
+        std::string b = "sr" + std::to_string(s);
+        if (cl == 0) return "sp" + std::to_string(s) + "[" + b + "]";
+        if (cl == 1) return "sp" + std::to_string(s) + "[" + b + " + " + col + "]";
+        return "sp" + std::to_string(s) + "[" + b + " + " + col + " * si" + std::to_string(s) + "]";
+      };
+      // full tile: all loads first
+      o << "    if (ct * bsu + bsu <= inner) {\n";
+      for (size_t s = 0; s < r.loads.size(); ++s) o << "      " << T(r.loads[s].dtype) << " a" << s << "[" << U << "];\n";
+      for (size_t s = 0; s < r.stores.size(); ++s) o << "      " << T(r.stores[s].dtype) << " b" << s << "[" << U << "];\n";
+      o << "#pragma unroll\n      for (int u = 0; u < " << U << "; ++u) {\n        const i64 col = c0 + (i64)u * blockDim.x;\n";
+      for (size_t s = 0; s < r.loads.size(); ++s) o << "        a" << s << "[u] = " << laddr(s, "col") << ";\n";
+      o << "      }\n#pragma unroll\n      for (int u = 0; u < " << U << "; ++u) {\n        const i64 col = c0 + (i64)u * blockDim.x;\n        (void)col;\n";
+      {
+        std::vector<std::string> lv, sv;
+        for (size_t s = 0; s < r.loads.size(); ++s) lv.push_back("a" + std::to_string(s) + "[u]");
+        for (size_t s = 0; s < r.stores.size(); ++s) sv.push_back("b" + std::to_string(s) + "[u]");
+        o << "        " << call("row * inner + col", lv, sv) << "\n";
+      }
+      o << "      }\n#pragma unroll\n      for (int u = 0; u < " << U << "; ++u) {\n        const i64 col = c0 + (i64)u * blockDim.x;\n        (void)col;\n";
+      for (size_t s = 0; s < r.stores.size(); ++s) o << "        " << saddr(s, "col") << " = b" << s << "[u];\n";
+      o << "      }\n    } else {\n";
+      o << "#pragma unroll\n      for (int u = 0; u < " << U << "; ++u) {\n        const i64 col = c0 + (i64)u * blockDim.x;\n        if (col < inner) {\n";
+      {
+        std::vector<std::string> lv, sv;
+        for (size_t s = 0; s < r.loads.size(); ++s) lv.push_back(laddr(s, "col"));
+        for (size_t s = 0; s < r.stores.size(); ++s) {
+          o << "          " << T(r.stores[s].dtype) << " b" << s << ";\n";
+          sv.push_back("b" + std::to_string(s));
+        }
+        o << "          " << call("row * inner + col", lv, sv) << "\n";
+        for (size_t s = 0; s < r.stores.size(); ++s) o << "          " << saddr(s, "col") << " = b" << s << ";\n";
+      }
+      o << "        }\n      }\n    }\n";
+      o << "    ct += cstep; row += rstep; if (ct >= tpr) { ct -= tpr; ++row; }\n  }\n";
+    }
+    if (c.spec.mode == Mode::FULL)
+      emit_full_epilogue("  ", W(L.partials), "blockIdx.x", W(L.counter), "gridDim.x", W(L.red_ptr));
+    o << "}\n";
+  }
+
+  void emit_vec_body(int U) {
+    const int E = c.spec.E;
+    o << "  const i64 n = " << W(L.inner) << ";\n"
+      << "  const i64 nvec = n / " << E << ";\n"
+      << "  const i64 bd = blockDim.x;\n";
+    // broadcast (stride-0) loads are read once
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      if (c.spec.load_cls[s] == 0) o << "  const " << T(r.loads[s].dtype) << " z" << s << " = lp" << s << "[0];\n";
+    o << "  for (i64 v0 = (i64)blockIdx.x * bd * " << U << "; v0 < nvec; v0 += (i64)gridDim.x * bd * " << U << ") {\n";
+    auto body = [&](const std::string& pfx, bool guard) {
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        if (c.spec.load_cls[s] == 1)
+          o << pfx << T(r.loads[s].dtype) << " a" << s << "[" << (guard ? 1 : U) << "][" << E << "];\n";
+      for (size_t s = 0; s < r.stores.size(); ++s)
+        o << pfx << T(r.stores[s].dtype) << " b" << s << "[" << (guard ? 1 : U) << "][" << E << "];\n";
+      int UU = guard ? 1 : U;
+      std::string uidx = guard ? "0" : "u";
+      if (!guard) o << "#pragma unroll\n";
+      o << pfx << "for (int u = 0; u < " << UU << "; ++u) {\n";
+      o << pfx << "  const i64 vi = " << (guard ? "vg" : "v0 + (i64)u * bd + threadIdx.x") << ";\n";
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        if (c.spec.load_cls[s] == 1) o << pfx << "  vbe_vload(lp" << s << " + vi * " << E << ", a" << s << "[u]);\n";
+      o << pfx << "}\n";
+      if (!guard) o << "#pragma unroll\n";
+      o << pfx << "for (int u = 0; u < " << UU << "; ++u) {\n";
+      o << pfx << "  const i64 vi = " << (guard ? "vg" : "v0 + (i64)u * bd + threadIdx.x") << ";\n  (void)vi;\n";
+      o << "#pragma unroll\n" << pfx << "  for (int e = 0; e < " << E << "; ++e) {\n";
+      std::vector<std::string> lv, sv;
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        lv.push_back(c.spec.load_cls[s] == 1 ? "a" + std::to_string(s) + "[u][e]" : "z" + std::to_string(s));
+      for (size_t s = 0; s < r.stores.size(); ++s) sv.push_back("b" + std::to_string(s) + "[u][e]");
+      o << pfx << "    " << call("vi * " + std::to_string(E) + " + e", lv, sv) << "\n";
+      o << pfx << "  }\n";
+      for (size_t s = 0; s < r.stores.size(); ++s) o << pfx << "  vbe_vstore(sp" << s << " + vi * " << E << ", b" << s << "[u]);\n";
+      o << pfx << "}\n";
+      (void)uidx;
+    };
+    o << "    if (v0 + bd * " << U << " <= nvec) {\n";
+    body("      ", false);
+    o << "    } else {\n"
+      << "      for (int uu = 0; uu < " << U << "; ++uu) {\n"
+      << "        const i64 vg = v0 + (i64)uu * bd + threadIdx.x;\n"
+      << "        if (vg < nvec) {\n";
+    body("          ", true);
+    o << "        }\n      }\n    }\n  }\n";
+    // scalar tail
+    o << "  for (i64 e = nvec * " << E << " + (i64)blockIdx.x * bd + threadIdx.x; e < n; e += (i64)gridDim.x * bd) {\n";
+    std::vector<std::string> lv, sv;
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      lv.push_back(c.spec.load_cls[s] == 1 ? "lp" + std::to_string(s) + "[e]" : "z" + std::to_string(s));
+    for (size_t s = 0; s < r.stores.size(); ++s) {
+      o << "    " << T(r.stores[s].dtype) << " b" << s << ";\n";
+      sv.push_back("b" + std::to_string(s));
+    }
+    o << "    " << call("e", lv, sv) << "\n";
+    for (size_t s = 0; s < r.stores.size(); ++s) o << "    sp" << s << "[e] = b" << s << ";\n";
+    o << "  }\n";
+  }
+
+  // ---------------------------------------------------- packed 1-D kernel
+  void emit_packed_kernel(int U) {
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_pack_u" << U
+      << "(const P* __restrict__ descs, const i64* __restrict__ prefix, int ninst, i64 total, i64 chunk, unsigned* work) {\n"
+      << "  __shared__ i64 s_c;\n"
+      << "  for (;;) {\n"
+      << "    if (threadIdx.x == 0) s_c = (i64)atomicAdd(work, 1u);\n"
+      << "    __syncthreads();\n"
+      << "    const i64 cidx = s_c;\n"
+      << "    __syncthreads();\n"
+      << "    if (cidx >= total) break;\n"
+      << "    int lo = 0, hi = ninst;\n"
+      << "    while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (prefix[mid] <= cidx) lo = mid; else hi = mid; }\n"
+      << "    const P& p = descs[lo];\n"
+      << "    const i64 lc = cidx - prefix[lo];\n"
+      << "    const i64 n = " << W(L.inner) << ";\n"
+      << "    const i64 e0 = lc * chunk, e1 = min(n, e0 + chunk);\n";
+    emit_pointers("    ");
+    emit_acc_init("    ");
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      if (c.spec.load_cls[s] == 2) o << "    const i64 li" << s << " = " << W(L.lst[s]) << ";\n";
+    for (size_t s = 0; s < r.stores.size(); ++s)
+      if (c.spec.store_cls[s] == 2) o << "    const i64 si" << s << " = " << W(L.sst[s]) << ";\n";
+    o << "    for (i64 eb = e0 + threadIdx.x; eb < e1; eb += (i64)blockDim.x * " << U << ") {\n"
+      << "#pragma unroll\n      for (int u = 0; u < " << U << "; ++u) {\n"
+      << "        const i64 e = eb + (i64)u * blockDim.x;\n"
+      << "        if (e < e1) {\n";
+    std::vector<std::string> lv, sv;
+    for (size_t s = 0; s < r.loads.size(); ++s) {
+      int cl = c.spec.load_cls[s];
+      lv.push_back("lp" + std::to_string(s) + (cl == 0 ? "[0]" : (cl == 1 ? "[e]" : "[e * li" + std::to_string(s) + "]")));
+    }
+    for (size_t s = 0; s < r.stores.size(); ++s) {
+      o << "          " << T(r.stores[s].dtype) << " b" << s << ";\n";
+      sv.push_back("b" + std::to_string(s));
+    }
+    o << "          " << call("e", lv, sv) << "\n";
+    for (size_t s = 0; s < r.stores.size(); ++s) {
+      int cl = c.spec.store_cls[s];
+      o << "          sp" << s << (cl == 0 ? "[0]" : (cl == 1 ? "[e]" : "[e * si" + std::to_string(s) + "]")) << " = b"
+        << s << ";\n";
+    }
+    o << "        }\n      }\n    }\n";
+    if (r.has_red) {
+      o << "    const i64 nch = n > 0 ? (n + chunk - 1) / chunk : 1;\n";
+      emit_full_epilogue("    ", W(L.partials), "lc", W(L.counter), "nch", W(L.red_ptr));
+    }
+    o << "  }\n}\n";
+  }
+
+  // ------------------------------------------------------- axis kernels
+  void emit_axis_kernel() {
+    const int ndk = c.spec.ndk, ndr = c.spec.ndr;
+    bool block = c.spec.mode == Mode::AXIS_BLOCK;
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_axis(const P p) {\n";
+    emit_pointers("  ");
+    o << "  const auto rp = vbe_ptr<" << rt() << ">(" << W(L.red_ptr) << ");\n"
+      << "  const i64 nout = " << W(L.nout) << ", nred = " << W(L.nred) << ";\n";
+    if (block)
+      o << "  for (i64 oi = blockIdx.x; oi < nout; oi += gridDim.x) {\n";
+    else
+      o << "  for (i64 oi = (i64)blockIdx.x * blockDim.x + threadIdx.x; oi < nout; oi += (i64)gridDim.x * blockDim.x) {\n";
+    // kept offsets
+    std::vector<std::pair<std::string, int>> ks;  // name, first stride word
+    for (size_t s = 0; s < r.loads.size(); ++s) ks.push_back({"lk" + std::to_string(s), L.lst[s]});
+    for (size_t s = 0; s < r.stores.size(); ++s) ks.push_back({"sk" + std::to_string(s), L.sst[s]});
+    ks.push_back({"rk", L.red_st});
+    if (L.idx_st >= 0) ks.push_back({"ik", L.idx_st});
+    for (auto& k : ks) o << "    i64 " << k.first << " = 0;\n";
+    o << "    { i64 rr = oi;\n";
+    for (int k = ndk - 1; k >= 0; --k) {
+      o << "      { const i64 ix = rr % " << W(L.dims0 + k) << "; rr /= " << W(L.dims0 + k) << ";";
+      for (auto& kk : ks) o << " " << kk.first << " += ix * " << W(kk.second + k) << ";";
+      o << " }\n";
+    }
+    o << "    }\n";
+    emit_acc_init("    ");
+    if (block)
+      o << "    for (i64 ri = threadIdx.x; ri < nred; ri += blockDim.x) {\n";
+    else
+      o << "    for (i64 ri = 0; ri < nred; ++ri) {\n";
+    // reduced offsets
+    std::vector<std::pair<std::string, int>> rs;
+    for (size_t s = 0; s < r.loads.size(); ++s) rs.push_back({"lr" + std::to_string(s), L.lst[s] + ndk});
+    for (size_t s = 0; s < r.stores.size(); ++s) rs.push_back({"sr" + std::to_string(s), L.sst[s] + ndk});
+    if (L.idx_st >= 0) rs.push_back({"ir", L.idx_st + ndk});
+    for (auto& k : rs) o << "      i64 " << k.first << " = 0;\n";
+    if (ndr == 1) {
+      for (auto& k : rs) o << "      " << k.first << " = ri * " << W(k.second) << ";\n";
+    } else {
+      o << "      { i64 rr = ri;\n";
+      for (int k = ndr - 1; k >= 0; --k) {
+        o << "        { const i64 ix = rr % " << W(L.dims0 + ndk + k) << "; rr /= " << W(L.dims0 + ndk + k) << ";";
+        for (auto& kk : rs) o << " " << kk.first << " += ix * " << W(kk.second + k) << ";";
+        o << " }\n";
+      }
+      o << "      }\n";
+    }
+    std::vector<std::string> lv, sv;
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      lv.push_back("lp" + std::to_string(s) + "[lk" + std::to_string(s) + " + lr" + std::to_string(s) + "]");
+    for (size_t s = 0; s < r.stores.size(); ++s) {
+      o << "      " << T(r.stores[s].dtype) << " b" << s << ";\n";
+      sv.push_back("b" + std::to_string(s));
+    }
+    o << "      " << call(L.idx_st >= 0 ? "ik + ir" : "0", lv, sv) << "\n";
+    for (size_t s = 0; s < r.stores.size(); ++s)
+      o << "      sp" << s << "[sk" << s << " + sr" << s << "] = b" << s << ";\n";
+    o << "    }\n";
+    if (block) {
+      o << "    { " << rt() << " v = vbe_block_reduce(" << acc_final() << "); if (threadIdx.x == 0) rp[rk] = v; }\n";
+    } else {
+      o << "    rp[rk] = " << acc_final() << ";\n";
+    }
+    o << "  }\n}\n";
+  }
+};
+
+}  // namespace
+
+std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix) {
+  Gen g(r, c);
+  g.o << "// generated by libvbe: " << r.steps.size() << " operations, " << r.loads.size() << " loads, "
+      << r.stores.size() << " stores\n";
+  g.o << kPrelude;
+  g.emit_elem();
+  g.emit_block_reduce();
+  if (tile_mode(c.spec.mode)) {
+    for (int U : {1, 2, 4}) g.emit_tile_kernel(U);
+    if (c.spec.nd == 1)
+      for (int U : {1, 4}) g.emit_packed_kernel(U);
+    if (entry_prefix) *entry_prefix = "vbe_u";
+  } else {
+    g.emit_axis_kernel();
+    if (entry_prefix) *entry_prefix = "vbe_axis";
+  }
+  return g.o.str();
+}
+
+}  // namespace vbe

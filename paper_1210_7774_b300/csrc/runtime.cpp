@@ -1,0 +1,837 @@
+// Runtime: NVRTC compilation and module cache, device memory, launch
+// shapes and their autotuning, batch execution, CUDA-graph replay of
+// repeated batches and packing of independent runs into one launch.
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <set>
+#include <sstream>
+
+#include "vbe_core.h"
+
+namespace vbe {
+
+// ------------------------------------------------------------------ NVRTC
+
+static std::vector<char> nvrtc_compile(const std::string& src, std::string* log) {
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "vbe_run.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+    fail(VBE_ERR_COMPILE, "nvrtcCreateProgram failed");
+  // IEEE arithmetic: no contraction into FMA, no flush to zero, correctly
+  // rounded division and square root
+  const char* opts[] = {"-arch=sm_103a", "--fmad=false", "-ftz=false", "-prec-div=true",
+                        "-prec-sqrt=true", "-std=c++17", "-lineinfo"};
+  nvrtcResult res = nvrtcCompileProgram(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
+  size_t ls = 0;
+  nvrtcGetProgramLogSize(prog, &ls);
+  std::string lg(ls, '\0');
+  if (ls) nvrtcGetProgramLog(prog, &lg[0]);
+  if (log) *log = lg;
+  if (res != NVRTC_SUCCESS) {
+    nvrtcDestroyProgram(&prog);
+    fail(VBE_ERR_COMPILE, "NVRTC: " + std::string(nvrtcGetErrorString(res)) + "\n" + lg);
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(prog, &n);
+  std::vector<char> cubin(n);
+  nvrtcGetCUBIN(prog, cubin.data());
+  nvrtcDestroyProgram(&prog);
+  return cubin;
+}
+
+static std::string src_key(const std::string& src) {
+  return hex64(fnv1a(src.data(), src.size())) + hex64(fnv1a(src.data(), src.size(), 7ull));
+}
+
+std::vector<char> compile_cached(Ctx* c, const std::string& src, bool* compiled) {
+  std::string key = src_key(src);
+  std::string path;
+  if (c->cfg.cache_dir && *c->cfg.cache_dir) {
+    path = std::string(c->cfg.cache_dir) + "/" + key + ".cubin";
+    std::ifstream f(path, std::ios::binary);
+    if (f) {
+      std::vector<char> b((std::istreambuf_iterator<char>(f)), std::istreambuf_iterator<char>());
+      if (!b.empty()) {
+        if (compiled) *compiled = false;
+        return b;
+      }
+    }
+  }
+  std::vector<char> cubin = nvrtc_compile(src, nullptr);
+  c->stats.compiles++;
+  if (compiled) *compiled = true;
+  if (!path.empty()) {
+    mkdir(c->cfg.cache_dir, 0755);
+    std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+    std::ofstream f(tmp, std::ios::binary);
+    f.write(cubin.data(), (std::streamsize)cubin.size());
+    f.close();
+    rename(tmp.c_str(), path.c_str());
+  }
+  return cubin;
+}
+
+// Compile, in parallel threads, every source not loaded yet (first sight
+// of a batch), then load the modules.
+void precompile(Ctx* c, const std::vector<std::string>& srcs) {
+  std::vector<std::string> todo;
+  std::set<std::string> seen;
+  for (auto& s : srcs) {
+    std::string k = src_key(s);
+    if (c->kernels.count(k) || seen.count(k)) continue;
+    seen.insert(k);
+    todo.push_back(s);
+  }
+  if (todo.size() <= 1) return;
+  std::vector<std::vector<char>> bins(todo.size());
+  std::vector<std::string> errs(todo.size());
+  std::atomic<size_t> next{0};
+  int nt = (int)std::min<size_t>(todo.size(), std::max(1u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  std::mutex mu;
+  for (int t = 0; t < nt; ++t) {
+    th.emplace_back([&]() {
+      for (;;) {
+        size_t i = next++;
+        if (i >= todo.size()) return;
+        try {
+          bool compiled = false;
+          Ctx tmp_view;  // only cfg.cache_dir is read
+          tmp_view.cfg.cache_dir = c->cfg.cache_dir;
+          bins[i] = compile_cached(&tmp_view, todo[i], &compiled);
+          if (compiled) {
+            std::lock_guard<std::mutex> lk(mu);
+            c->stats.compiles++;
+          }
+        } catch (const Error& e) {
+          errs[i] = e.msg;
+        }
+      }
+    });
+  }
+  for (auto& t : th) t.join();
+  for (size_t i = 0; i < todo.size(); ++i) {
+    if (!errs[i].empty()) fail(VBE_ERR_COMPILE, errs[i]);
+    if (c->host_only) continue;
+    auto k = std::make_shared<Kernel>();
+    cuda_check(cudaLibraryLoadData(&k->lib, bins[i].data(), nullptr, nullptr, 0, nullptr, nullptr, 0),
+               "cudaLibraryLoadData");
+    c->kernels[src_key(todo[i])] = k;
+  }
+}
+
+std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src) {
+  std::string key = src_key(src);
+  auto it = c->kernels.find(key);
+  if (it != c->kernels.end()) return it->second;
+  if (c->record) {
+    c->rec_sources[key] = src;
+    auto k = std::make_shared<Kernel>();
+    c->kernels[key] = k;
+    return k;
+  }
+  std::vector<char> cubin = compile_cached(c, src, nullptr);
+  auto k = std::make_shared<Kernel>();
+  if (c->host_only) fail(VBE_ERR_NO_DEVICE, "host-only context cannot load kernels");
+  cuda_check(cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0),
+             "cudaLibraryLoadData");
+  c->kernels[key] = k;
+  return k;
+}
+
+static cudaKernel_t kernel_fn(Kernel* k, const std::string& name) {
+  if (!k->lib) return (cudaKernel_t)(uintptr_t)1;  // recording: never launched
+  auto it = k->fn.find(name);
+  if (it != k->fn.end()) return it->second;
+  cudaKernel_t f;
+  cuda_check(cudaLibraryGetKernel(&f, k->lib, name.c_str()), "cudaLibraryGetKernel");
+  k->fn[name] = f;
+  return f;
+}
+
+// ----------------------------------------------------------------- memory
+
+static void* host_alloc(Ctx* c, int64_t bytes) {
+  size_t n = ((size_t)bytes + 255) / 256 * 256;
+  void* p = aligned_alloc(256, n);
+  if (!p) fail(VBE_ERR_OOM, "host allocation failed");
+  memset(p, 0, n);
+  c->host_allocs[(uintptr_t)p] = (size_t)bytes;
+  return p;
+}
+
+static void host_free(Ctx* c, void* p) {
+  c->host_allocs.erase((uintptr_t)p);
+  free(p);
+}
+
+void* dev_alloc(Ctx* c, Exec* ex, int64_t bytes) {
+  if (bytes <= 0) bytes = 16;
+  if (c->record) {
+    void* p = host_alloc(c, bytes);
+    c->stats.bytes_allocated += bytes;
+    c->stats.peak_bytes = std::max(c->stats.peak_bytes, c->stats.bytes_allocated);
+    return p;
+  }
+  if (c->cfg.mem_cap_bytes && c->stats.bytes_allocated + bytes > (int64_t)c->cfg.mem_cap_bytes)
+    fail(VBE_ERR_OOM, "allocation of " + std::to_string(bytes) + " bytes exceeds the memory cap");
+  void* p = nullptr;
+  cuda_check(cudaMallocAsync(&p, (size_t)bytes, ex->stream), "cudaMallocAsync");
+  c->stats.bytes_allocated += bytes;
+  c->stats.peak_bytes = std::max(c->stats.peak_bytes, c->stats.bytes_allocated);
+  return p;
+}
+
+void dev_free(Ctx* c, Exec* ex, void* p, int64_t bytes) {
+  if (!p) return;
+  if (bytes <= 0) bytes = 16;
+  c->stats.bytes_allocated -= bytes;
+  if (c->record) {
+    // recorded launches run later, so a freed block stays allocated (and
+    // addressable) until the context ends, like a stream-ordered free
+    return;
+  }
+  cudaFreeAsync(p, ex->stream);
+}
+
+void ensure_scratch(Ctx* c, Exec* ex, int64_t partials, int64_t counters) {
+  Scratch& s = ex->scratch;
+  if (s.n_partials >= partials && s.n_counters >= counters) return;
+  if (c->record) {
+    s.n_partials = std::max<int64_t>(partials, 1 << 20);
+    s.n_counters = std::max<int64_t>(counters, 1 << 16);
+    s.partials = host_alloc(c, s.n_partials * 8);
+    s.counters = (unsigned int*)host_alloc(c, s.n_counters * 4);
+    return;
+  }
+  // grow: wait for users of the old buffers, then replace them
+  cuda_check(cudaStreamSynchronize(ex->stream), "cudaStreamSynchronize");
+  if (s.partials) cudaFree(s.partials);
+  if (s.counters) cudaFree(s.counters);
+  // cached graphs may reference the old buffers
+  for (auto& kv : c->batches) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    for (void* p : kv.second.keep) cudaFree(p);
+    kv.second.exec = nullptr;
+    kv.second.graph = nullptr;
+    kv.second.keep.clear();
+  }
+  s.n_partials = std::max<int64_t>(partials, 1 << 20);
+  s.n_counters = std::max<int64_t>(counters, 1 << 16);
+  cuda_check(cudaMalloc(&s.partials, (size_t)s.n_partials * 8), "cudaMalloc(partials)");
+  cuda_check(cudaMalloc((void**)&s.counters, (size_t)s.n_counters * 4), "cudaMalloc(counters)");
+  cuda_check(cudaMemset(s.counters, 0, (size_t)s.n_counters * 4), "cudaMemset(counters)");
+}
+
+void release_exec(Ctx* c, Exec* ex) {
+  if (c->record) {
+    if (ex->scratch.partials) host_free(c, ex->scratch.partials);
+    if (ex->scratch.counters) host_free(c, ex->scratch.counters);
+    ex->scratch = Scratch();
+    return;
+  }
+  if (ex->scratch.partials) cudaFree(ex->scratch.partials);
+  if (ex->scratch.counters) cudaFree(ex->scratch.counters);
+  ex->scratch = Scratch();
+  if (ex->ev0) cudaEventDestroy(ex->ev0);
+  if (ex->ev1) cudaEventDestroy(ex->ev1);
+  ex->ev0 = ex->ev1 = nullptr;
+}
+
+// --------------------------------------------------------------- launches
+
+namespace {
+
+struct Launch {
+  cudaKernel_t fn = nullptr;
+  std::string key, entry;          // module and kernel name (recorded launches)
+  unsigned grid = 1, block = 256;
+  std::vector<int64_t> words;      // by-value parameter block (single runs)
+  bool packed = false;
+  std::vector<int64_t> descs;      // packed: words of every instance
+  std::vector<int64_t> prefix;     // packed: chunk prefix sums
+  int ninst = 0;
+  int64_t total = 0, chunk = 0;
+  void* d_descs = nullptr;         // device copies (packed)
+  void* d_prefix = nullptr;
+  int64_t d_bytes = 0;
+};
+
+int occupancy(cudaKernel_t fn, int block) {
+  int n = 0;
+  if (fn == (cudaKernel_t)(uintptr_t)1) return 2;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)fn, block, 0) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = std::max(1, 2048 / block);
+  }
+  return n;
+}
+
+uintptr_t base_ptr(Ctx* c, int64_t b) {
+  auto it = c->bases.find(b);
+  if (it == c->bases.end()) fail(VBE_ERR_INVALID, "base vanished during execution");
+  return (uintptr_t)it->second.dptr;
+}
+
+std::string words_json(const std::vector<int64_t>& w) {
+  std::string s = "[";
+  for (size_t i = 0; i < w.size(); ++i) s += (i ? "," : "") + std::to_string(w[i]);
+  return s + "]";
+}
+
+void record_launch(Ctx* c, Exec* ex, Launch& L) {
+  std::string j = "{\"key\":\"" + L.key + "\",\"entry\":\"" + L.entry + "\",\"grid\":" +
+                  std::to_string(L.grid) + ",\"block\":" + std::to_string(L.block);
+  if (L.packed) {
+    int64_t db = (int64_t)(L.descs.size() * 8), pb = (int64_t)(L.prefix.size() * 8);
+    char* d = (char*)dev_alloc(c, ex, db + pb);  // kept until the context ends
+    memcpy(d, L.descs.data(), db);
+    memcpy(d + db, L.prefix.data(), pb);
+    unsigned* work = ex->scratch.counters + (ex->scratch.n_counters - 1);
+    j += ",\"packed\":true,\"descs\":" + std::to_string((uintptr_t)d) + ",\"prefix\":" +
+         std::to_string((uintptr_t)(d + db)) + ",\"ninst\":" + std::to_string(L.ninst) + ",\"total\":" +
+         std::to_string(L.total) + ",\"chunk\":" + std::to_string(L.chunk) + ",\"work\":" +
+         std::to_string((uintptr_t)work);
+  } else {
+    j += ",\"words\":" + words_json(L.words);
+  }
+  c->rec_launches.push_back(j + "}");
+  c->stats.kernel_launches++;
+}
+
+void issue(Ctx* c, Exec* ex, Launch& L, bool capturing) {
+  if (c->record) {
+    record_launch(c, ex, L);
+    return;
+  }
+  cudaStream_t s = ex->stream;
+  if (L.packed) {
+    if (!capturing) {
+      int64_t db = (int64_t)(L.descs.size() * 8), pb = (int64_t)(L.prefix.size() * 8);
+      char* d = (char*)dev_alloc(c, ex, db + pb);
+      cuda_check(cudaMemcpyAsync(d, L.descs.data(), db, cudaMemcpyHostToDevice, s), "upload descriptors");
+      cuda_check(cudaMemcpyAsync(d + db, L.prefix.data(), pb, cudaMemcpyHostToDevice, s), "upload prefix");
+      L.d_descs = d;
+      L.d_prefix = d + db;
+      L.d_bytes = db + pb;
+    }
+    unsigned* work = ex->scratch.counters + (ex->scratch.n_counters - 1);
+    cuda_check(cudaMemsetAsync(work, 0, 4, s), "cudaMemsetAsync(work)");
+    void* a0 = L.d_descs;
+    void* a1 = L.d_prefix;
+    int a2 = L.ninst;
+    long long a3 = L.total, a4 = L.chunk;
+    void* a5 = work;
+    void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
+    cuda_check(cudaLaunchKernel((const void*)L.fn, dim3(L.grid), dim3(L.block), args, 0, s), "launch (packed)");
+    if (!capturing) {
+      dev_free(c, ex, L.d_descs, L.d_bytes);
+      L.d_descs = L.d_prefix = nullptr;
+    }
+  } else {
+    void* args[] = {(void*)L.words.data()};
+    cuda_check(cudaLaunchKernel((const void*)L.fn, dim3(L.grid), dim3(L.block), args, 0, s), "launch");
+  }
+  if (!capturing) c->stats.kernel_launches++;
+}
+
+struct RunPtrs {
+  std::vector<uintptr_t> lp, sp;
+  uintptr_t rp = 0;
+};
+
+RunPtrs run_ptrs(Ctx* c, const Run& r) {
+  RunPtrs p;
+  for (auto& s : r.loads) p.lp.push_back(base_ptr(c, s.base));
+  for (auto& s : r.stores) p.sp.push_back(base_ptr(c, s.base));
+  if (r.has_red) p.rp = base_ptr(c, r.red_out.base);
+  return p;
+}
+
+// late allocation (section "Vector Engine Manager"): a base gets memory
+// when a run first stores into it
+void allocate_outputs(Ctx* c, Exec* ex, const Run& r) {
+  auto need = [&](int64_t b) {
+    BaseRec& br = c->bases[b];
+    if (!br.dptr) br.dptr = dev_alloc(c, ex, br.bytes());
+    br.written = true;
+  };
+  for (auto& s : r.stores) need(s.base);
+  if (r.has_red) need(r.red_out.base);
+  for (auto& s : r.loads) {
+    BaseRec& br = c->bases[s.base];
+    if (!br.dptr) fail(VBE_ERR_UNINIT, "a run reads base " + std::to_string(s.base) + " which was never written");
+  }
+}
+
+int64_t tiles_of(const Canon& cn, int block, int U) {
+  int64_t bsu = (int64_t)block * U;
+  if (cn.spec.vec) {
+    int64_t nvec = cn.dims[0] / cn.spec.E;
+    return std::max<int64_t>(1, (nvec + bsu - 1) / bsu);
+  }
+  int64_t inner = cn.dims.back(), outer = 1;
+  for (int k = 0; k + 1 < cn.spec.nd; ++k) outer *= cn.dims[k];
+  return std::max<int64_t>(1, outer * ((inner + bsu - 1) / bsu));
+}
+
+struct Prepared {
+  Run* run = nullptr;
+  Canon canon;
+  std::string src;
+  std::shared_ptr<Kernel> kern;
+  std::string key;
+};
+
+std::string tune_key(const std::string& src, const Canon& cn) {
+  // tuned per signature and per size class (log2 of the element count)
+  int lg = 0;
+  int64_t n = std::max<int64_t>(1, cn.total);
+  while (n > 1) {
+    n >>= 1;
+    ++lg;
+  }
+  return src_key(src) + ":" + std::to_string(lg);
+}
+
+Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const RunPtrs& ptr) {
+  Launch L;
+  const Run& r = *P.run;
+  const Canon& cn = P.canon;
+  LaunchArgs a;
+  if (cn.spec.mode == Mode::ELEM || cn.spec.mode == Mode::FULL) {
+    L.entry = "vbe_u" + std::to_string(tc.U);
+    L.key = P.key;
+    L.fn = kernel_fn(P.kern.get(), L.entry);
+    L.block = tc.block;
+    int64_t tiles = tiles_of(cn, tc.block, tc.U);
+    int64_t cap = (int64_t)occupancy(L.fn, tc.block) * c->sm_count;
+    if (tc.grid_mult > 0) cap = std::min<int64_t>(cap, (int64_t)tc.grid_mult * c->sm_count);
+    int64_t g = std::min(tiles, cap);
+    if (cn.spec.mode == Mode::FULL) g = std::min<int64_t>(g, ex->scratch.n_partials);
+    L.grid = (unsigned)std::max<int64_t>(1, g);
+    fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, (uintptr_t)ex->scratch.partials, (uintptr_t)ex->scratch.counters,
+               tc.block, tc.U, &a);
+  } else {
+    L.entry = "vbe_axis";
+    L.key = P.key;
+    L.fn = kernel_fn(P.kern.get(), L.entry);
+    int64_t nout = 1, nred = 1;
+    for (int k = 0; k < cn.spec.ndk; ++k) nout *= cn.dims[k];
+    for (int k = 0; k < cn.spec.ndr; ++k) nred *= cn.dims[cn.spec.ndk + k];
+    if (cn.spec.mode == Mode::AXIS_BLOCK) {
+      int b = 32;
+      while (b < 256 && b * 8 < nred) b *= 2;
+      L.block = b;
+      int64_t cap = (int64_t)occupancy(L.fn, b) * c->sm_count;
+      L.grid = (unsigned)std::max<int64_t>(1, std::min(nout, cap));
+    } else {
+      L.block = 128;
+      int64_t cap = (int64_t)occupancy(L.fn, 128) * c->sm_count;
+      L.grid = (unsigned)std::max<int64_t>(1, std::min((nout + 127) / 128, cap));
+    }
+    fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, 0, 0, L.block, 1, &a);
+  }
+  L.words = std::move(a.w);
+  return L;
+}
+
+// time the launch shapes of a tile kernel with its outputs redirected to
+// scratch buffers (so in-place runs are not disturbed) and keep the fastest
+TuneChoice autotune(Ctx* c, Exec* ex, Prepared& P, const RunPtrs& real) {
+  const Run& r = *P.run;
+  RunPtrs ptr = real;
+  std::vector<std::pair<void*, int64_t>> bufs;
+  auto redirect = [&](const Slot& s, const std::vector<int64_t>& shape_st, int64_t nshape_dims,
+                      const std::vector<int64_t>& shape, uintptr_t* p) {
+    (void)shape_st;
+    (void)nshape_dims;
+    int isz = itemsize(s.dtype);
+    int64_t lo = s.offset, hi = s.offset;
+    for (size_t k = 0; k < s.st.size() && k < shape.size(); ++k) {
+      int64_t e = (shape[k] - 1) * s.st[k];
+      if (e < 0) lo += e; else hi += e;
+    }
+    int64_t bytes = (hi - lo + 1) * isz;
+    void* b = dev_alloc(c, ex, bytes);
+    bufs.push_back({b, bytes});
+    *p = (uintptr_t)b - (uintptr_t)(lo * isz);
+  };
+  for (size_t s = 0; s < r.stores.size(); ++s) redirect(r.stores[s], {}, 0, r.shape, &ptr.sp[s]);
+  if (r.has_red) {
+    std::vector<int64_t> kshape;
+    for (int d = 0; d < (int)r.shape.size(); ++d)
+      if (!std::binary_search(r.red_axes.begin(), r.red_axes.end(), d)) kshape.push_back(r.shape[d]);
+    redirect(r.red_out, {}, 0, kshape, &ptr.rp);
+  }
+  TuneChoice best;
+  float best_ms = 1e30f;
+  if (!ex->ev0) {
+    cudaEventCreate(&ex->ev0);
+    cudaEventCreate(&ex->ev1);
+  }
+  for (int block : {128, 256, 512}) {
+    for (int U : {1, 2, 4}) {
+      TuneChoice tc;
+      tc.block = block;
+      tc.U = U;
+      Launch L = build_single(c, ex, P, tc, ptr);
+      issue(c, ex, L, false);  // warm
+      c->stats.kernel_launches--;
+      cuda_check(cudaEventRecord(ex->ev0, ex->stream), "event");
+      for (int rep = 0; rep < 3; ++rep) {
+        issue(c, ex, L, false);
+        c->stats.kernel_launches--;
+      }
+      cuda_check(cudaEventRecord(ex->ev1, ex->stream), "event");
+      cuda_check(cudaEventSynchronize(ex->ev1), "event sync");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ex->ev0, ex->ev1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = tc;
+      }
+    }
+  }
+  for (auto& b : bufs) dev_free(c, ex, b.first, b.second);
+  c->stats.autotunes++;
+  return best;
+}
+
+TuneChoice choose(Ctx* c, Exec* ex, Prepared& P, const RunPtrs& ptr, bool may_tune) {
+  bool tile = P.canon.spec.mode == Mode::ELEM || P.canon.spec.mode == Mode::FULL;
+  if (c->record) {
+    TuneChoice tc;
+    tc.block = c->rec_block;
+    tc.U = c->rec_U;
+    return tc;
+  }
+  std::string tk = tune_key(P.src, P.canon);
+  auto it = c->tune.find(tk);
+  if (it != c->tune.end()) return it->second;
+  TuneChoice tc;
+  tc.block = 256;
+  tc.U = P.canon.total >= (1 << 16) ? 2 : 1;
+  if (c->record) {
+    tc.block = c->rec_block;
+    tc.U = c->rec_U;
+    return tc;
+  }
+  if (tile && may_tune && (c->cfg.flags & VBE_AUTOTUNE) && P.canon.total >= (1 << 20)) {
+    tc = autotune(c, ex, P, ptr);
+    c->tune[tk] = tc;
+  }
+  return tc;
+}
+
+bool independent(const Run& a, const Run& b, Ctx* c) {
+  auto view_of = [&](const Slot& s, const std::vector<int64_t>& shape) {
+    ViewDesc v;
+    v.base = s.base;
+    v.offset = s.offset;
+    v.ndim = (int)shape.size();
+    for (int k = 0; k < v.ndim; ++k) {
+      v.shape[k] = shape[k];
+      v.strides[k] = s.st[k];
+    }
+    v.finish();
+    return v;
+  };
+  (void)c;
+  std::vector<ViewDesc> ra, wa, rb, wb;
+  for (auto& s : a.loads) ra.push_back(view_of(s, a.shape));
+  for (auto& s : a.stores) wa.push_back(view_of(s, a.shape));
+  for (auto& s : b.loads) rb.push_back(view_of(s, b.shape));
+  for (auto& s : b.stores) wb.push_back(view_of(s, b.shape));
+  auto kept = [](const Run& r) {
+    std::vector<int64_t> k;
+    for (int d = 0; d < (int)r.shape.size(); ++d)
+      if (!std::binary_search(r.red_axes.begin(), r.red_axes.end(), d)) k.push_back(r.shape[d]);
+    return k;
+  };
+  if (a.has_red) wa.push_back(view_of(a.red_out, kept(a)));
+  if (b.has_red) wb.push_back(view_of(b.red_out, kept(b)));
+  for (auto& x : wb) {
+    for (auto& y : ra) if (may_overlap(x, y)) return false;
+    for (auto& y : wa) if (may_overlap(x, y)) return false;
+  }
+  for (auto& x : rb)
+    for (auto& y : wa) if (may_overlap(x, y)) return false;
+  return true;
+}
+
+uint64_t batch_key(const vbe_instr* prog, int64_t n) {
+  uint64_t h = fnv1a(&n, sizeof n);
+  return fnv1a(prog, (size_t)n * sizeof(vbe_instr), h);
+}
+
+std::vector<std::pair<int64_t, uintptr_t>> fingerprint(Ctx* c, const std::vector<RInstr>& rp) {
+  std::vector<int64_t> ids;
+  for (auto& r : rp) {
+    ids.push_back(r.out.base);
+    for (int k = 0; k < r.nin; ++k)
+      if (k != r.const_slot) ids.push_back(r.in[k].base);
+  }
+  std::sort(ids.begin(), ids.end());
+  ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+  std::vector<std::pair<int64_t, uintptr_t>> f;
+  for (auto b : ids) {
+    auto it = c->bases.find(b);
+    f.push_back({b, it == c->bases.end() ? 0 : (uintptr_t)it->second.dptr});
+  }
+  return f;
+}
+
+void do_action(Ctx* c, Exec* ex, const HostAction& a) {
+  auto it = c->bases.find(a.base);
+  if (it == c->bases.end()) return;
+  if (a.kind == 0) {  // FREE
+    if (it->second.dptr && !it->second.external) dev_free(c, ex, it->second.dptr, it->second.bytes());
+    for (auto v = c->views.begin(); v != c->views.end();) {
+      if (v->second.base == a.base) v = c->views.erase(v);
+      else ++v;
+    }
+    c->bases.erase(it);
+  }
+}
+
+}  // namespace
+
+// Execute one batch on ex's stream. Eager the first time a batch is seen;
+// with VBE_GRAPHS, a batch seen again (same instructions, same views, same
+// base addresses, no FREE) is captured into a CUDA graph and later replayed.
+void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_graph) {
+  if (c->host_only && !c->record) fail(VBE_ERR_NO_DEVICE, "host-only context");
+  std::vector<RInstr> rp = resolve_batch(c, prog, n);
+  c->stats.batches++;
+  bool has_free = false;
+  for (auto& r : rp)
+    if (r.op == VBE_OP_FREE) has_free = true;
+  bool graphs = allow_graph && (c->cfg.flags & VBE_GRAPHS) && !has_free && !c->record;
+  uint64_t key = graphs ? batch_key(prog, n) : 0;
+  CachedBatch* cb = nullptr;
+  if (graphs) {
+    cb = &c->batches[key];
+    cb->key = key;
+    if (cb->exec && cb->fingerprint == fingerprint(c, rp)) {
+      cuda_check(cudaGraphLaunch(cb->exec, ex->stream), "cudaGraphLaunch");
+      c->stats.graph_launches++;
+      c->stats.kernel_launches += cb->launches;
+      return;
+    }
+  }
+  bool fuse = (c->cfg.flags & VBE_FUSE) != 0;
+  bool pack = (c->cfg.flags & VBE_PACK) != 0;
+  std::vector<RInstr> staged = rp;
+  Plan plan = make_plan(c, staged, fuse, pack);
+  ensure_scratch(c, ex, 1 << 20, 1 << 16);
+  bool capture = graphs && cb->seen >= 1;
+  if (graphs) cb->seen++;
+
+  // compile the batch's kernels in parallel on first sight
+  {
+    std::vector<std::string> srcs;
+    for (auto& it : plan.items) {
+      if (it.kind != 0) continue;
+      RunPtrs pp;
+      for (auto& s : it.run.loads) pp.lp.push_back((uintptr_t)c->bases[s.base].dptr);
+      for (auto& s : it.run.stores) pp.sp.push_back((uintptr_t)c->bases[s.base].dptr);
+      Canon cn = canonicalize(it.run, true, pp.lp, pp.sp, 0);
+      srcs.push_back(generate_source(it.run, cn, nullptr));
+    }
+    if (!c->record) precompile(c, srcs);
+  }
+  // first pass: allocation order and reads of never-written bases
+  {
+    std::set<int64_t> avail;
+    for (auto& kv : c->bases)
+      if (kv.second.dptr) avail.insert(kv.first);
+    for (auto& it : plan.items) {
+      if (it.kind != 0) continue;
+      for (auto& s : it.run.loads)
+        if (!avail.count(s.base))
+          fail(VBE_ERR_UNINIT, "the batch reads base " + std::to_string(s.base) + " before anything wrote it");
+      for (auto& s : it.run.stores) avail.insert(s.base);
+      if (it.run.has_red) avail.insert(it.run.red_out.base);
+    }
+  }
+  // capture needs every store target allocated already
+  if (capture) {
+    for (auto& it : plan.items) {
+      if (it.kind != 0) continue;
+      for (auto& s : it.run.stores)
+        if (!c->bases[s.base].dptr) capture = false;
+      if (it.run.has_red && !c->bases[it.run.red_out.base].dptr) capture = false;
+    }
+  }
+
+  std::vector<Launch> recorded;
+  std::vector<HostAction> deferred;
+  auto flush_deferred = [&]() {
+    for (auto& a : deferred) do_action(c, ex, a);
+    deferred.clear();
+  };
+  size_t i = 0;
+  while (i < plan.items.size()) {
+    PlanItem& it = plan.items[i];
+    if (it.kind == 1) {
+      if (capture) {
+        ++i;
+        continue;  // capture never has FREE; DISCARD/SYNC are no-ops on the device
+      }
+      deferred.push_back(it.act);
+      ++i;
+      if (it.act.kind == 2) flush_deferred();
+      continue;
+    }
+    Run& r = it.run;
+    if (!r.has_red && r.elements() == 0) {
+      ++i;
+      continue;
+    }
+    allocate_outputs(c, ex, r);
+    Prepared P;
+    P.run = &r;
+    RunPtrs ptr = run_ptrs(c, r);
+    P.canon = canonicalize(r, true, ptr.lp, ptr.sp, ptr.rp);
+    P.src = generate_source(r, P.canon, nullptr);
+    P.key = src_key(P.src);
+    P.kern = get_kernel(c, P.src);
+    bool tile = P.canon.spec.mode == Mode::ELEM || P.canon.spec.mode == Mode::FULL;
+    // packing: following runs with the same kernel that share no data
+    std::vector<size_t> group{i};
+    size_t j = i + 1;
+    if (pack && tile && P.canon.spec.nd == 1) {
+      std::vector<size_t> skipped;
+      while (j < plan.items.size()) {
+        PlanItem& nx = plan.items[j];
+        if (nx.kind == 1) {
+          if (nx.act.kind == 2) break;  // SYNC
+          ++j;
+          continue;
+        }
+        Run& r2 = nx.run;
+        if (r2.shape.size() != r.shape.size() && !(r2.shape.size() <= 1 && r.shape.size() <= 1)) break;
+        bool ok = true;
+        for (size_t g : group)
+          if (!independent(plan.items[g].run, r2, c)) ok = false;
+        if (!ok) break;
+        allocate_outputs(c, ex, r2);
+        RunPtrs p2 = run_ptrs(c, r2);
+        Canon c2 = canonicalize(r2, true, p2.lp, p2.sp, p2.rp);
+        if (c2.spec.nd != 1 || generate_source(r2, c2, nullptr) != P.src) break;
+        group.push_back(j);
+        ++j;
+      }
+      if (group.size() == 1) j = i + 1;
+    }
+    if (group.size() > 1 && (int64_t)group.size() < ex->scratch.n_counters - 1) {
+      // one persistent launch over all instances
+      Launch L;
+      L.packed = true;
+      int U = 4;
+      L.entry = "vbe_pack_u" + std::to_string(U);
+      L.key = P.key;
+      L.fn = kernel_fn(P.kern.get(), L.entry);
+      L.block = 256;
+      int64_t total_elems = 0;
+      for (size_t g : group) total_elems += plan.items[g].run.elements();
+      int64_t chunk = std::max<int64_t>(L.block * U * 4, (total_elems / (ex->scratch.n_partials / 2)) + 1);
+      chunk = ((chunk + 1023) / 1024) * 1024;
+      L.chunk = chunk;
+      L.ninst = (int)group.size();
+      int64_t poff = 0;
+      L.prefix.push_back(0);
+      for (size_t gi = 0; gi < group.size(); ++gi) {
+        Run& rg = plan.items[group[gi]].run;
+        RunPtrs pg = run_ptrs(c, rg);
+        Canon cg = canonicalize(rg, true, pg.lp, pg.sp, pg.rp);
+        int64_t ne = rg.elements();
+        int64_t nch = ne > 0 ? (ne + chunk - 1) / chunk : 1;
+        LaunchArgs a;
+        fill_words(rg, cg, pg.lp, pg.sp, pg.rp,
+                   (uintptr_t)((char*)ex->scratch.partials + poff * 8),
+                   (uintptr_t)(ex->scratch.counters + gi), L.block, U, &a);
+        L.descs.insert(L.descs.end(), a.w.begin(), a.w.end());
+        poff += nch;
+        L.prefix.push_back(L.prefix.back() + nch);
+      }
+      L.total = L.prefix.back();
+      if (poff > ex->scratch.n_partials) fail(VBE_ERR_INVALID, "packed launch needs too many partials");
+      L.grid = (unsigned)std::min<int64_t>(L.total, (int64_t)occupancy(L.fn, L.block) * c->sm_count);
+      if (capture) {
+        recorded.push_back(std::move(L));
+      } else {
+        issue(c, ex, L, false);
+      }
+      // host actions skipped over while packing run after the pack
+      for (size_t k = i + 1; k < j; ++k)
+        if (plan.items[k].kind == 1) deferred.push_back(plan.items[k].act);
+      i = j;
+      if (!capture) flush_deferred();
+      continue;
+    }
+    TuneChoice tc = choose(c, ex, P, ptr, !capture);
+    Launch L = build_single(c, ex, P, tc, ptr);
+    if (capture) recorded.push_back(std::move(L));
+    else issue(c, ex, L, false);
+    ++i;
+    if (!capture) flush_deferred();
+  }
+  if (!capture) {
+    flush_deferred();
+    return;
+  }
+  // capture the recorded launches into a graph and replay it
+  std::vector<void*> keep;
+  for (auto& L : recorded) {
+    if (!L.packed) continue;
+    int64_t db = (int64_t)(L.descs.size() * 8), pb = (int64_t)(L.prefix.size() * 8);
+    char* d = nullptr;
+    cuda_check(cudaMalloc((void**)&d, db + pb), "cudaMalloc(descriptors)");
+    cuda_check(cudaMemcpy(d, L.descs.data(), db, cudaMemcpyHostToDevice), "descriptors");
+    cuda_check(cudaMemcpy(d + db, L.prefix.data(), pb, cudaMemcpyHostToDevice), "prefix");
+    L.d_descs = d;
+    L.d_prefix = d + db;
+    keep.push_back(d);
+  }
+  static thread_local cudaStream_t cap = nullptr;
+  if (!cap) cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+  Exec cex = *ex;
+  cex.stream = cap;
+  cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  try {
+    for (auto& L : recorded) issue(c, &cex, L, true);
+  } catch (...) {
+    cudaGraph_t g;
+    cudaStreamEndCapture(cap, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  cudaGraph_t graph;
+  cuda_check(cudaStreamEndCapture(cap, &graph), "cudaStreamEndCapture");
+  cudaGraphExec_t gexec;
+  cuda_check(cudaGraphInstantiate(&gexec, graph, 0), "cudaGraphInstantiate");
+  if (cb->exec) cudaGraphExecDestroy(cb->exec);
+  if (cb->graph) cudaGraphDestroy(cb->graph);
+  for (void* p : cb->keep) cudaFree(p);
+  cb->exec = gexec;
+  cb->graph = graph;
+  cb->keep = keep;
+  cb->launches = (int64_t)recorded.size();
+  cb->fingerprint = fingerprint(c, rp);
+  c->stats.graph_captures++;
+  cuda_check(cudaGraphLaunch(gexec, ex->stream), "cudaGraphLaunch");
+  c->stats.graph_launches++;
+  c->stats.kernel_launches += cb->launches;
+}
+
+}  // namespace vbe

@@ -1,0 +1,276 @@
+// Internal declarations of libvbe (see include/vbe.h for the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/vbe.h"
+
+namespace vbe {
+
+// ----------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+
+// ----------------------------------------------------------------- dtypes
+int itemsize(int dtype);
+const char* ctype(int dtype);
+const char* dtype_name(int dtype);
+bool is_float(int dtype);
+
+// ------------------------------------------------------------------ views
+struct ViewDesc {
+  int64_t base = 0;
+  int64_t offset = 0;
+  int ndim = 0;
+  int64_t shape[VBE_MAX_NDIM] = {};
+  int64_t strides[VBE_MAX_NDIM] = {};
+  int64_t lo = 0, hi = -1;  // reachable element range; hi < lo when empty
+
+  int64_t size() const;
+  bool same_shape(const ViewDesc& o) const;
+  // identical element mapping: same base, offset, shape and strides
+  bool identical(const ViewDesc& o) const;
+  void finish();  // computes lo/hi
+  bool self_overlapping() const;
+};
+
+// false only when the two views provably reach no common element
+bool may_overlap(const ViewDesc& a, const ViewDesc& b);
+
+// ------------------------------------------------------------ instructions
+enum OpKind { K_ARITH, K_DIV, K_FUNARY, K_SUNARY, K_CMP, K_SELECT, K_CAST, K_COPY, K_RANDOM,
+              K_REDUCE, K_CONTROL };
+OpKind op_kind(int op);
+int op_arity(int op);
+const char* op_name(int op);
+
+struct RInstr {  // a validated, resolved instruction
+  int op = 0;
+  int nin = 0;
+  int const_slot = -1;
+  bool has_out = false;
+  ViewDesc out;
+  ViewDesc in[3];
+  int64_t h_out = 0, h_in[3] = {0, 0, 0};  // view handles
+  double kf = 0;
+  int64_t ki = 0;
+  int axis = 0;
+  uint64_t seed = 0, key = 0;
+  int64_t step = 0;
+  int dt_out = 0;
+  int dt_in[3] = {0, 0, 0};
+  int dt_const = 0;
+};
+
+// -------------------------------------------------------------- run plan
+enum class Mode { ELEM = 0, FULL = 1, AXIS_THREAD = 2, AXIS_BLOCK = 3 };
+
+struct Slot {  // a view over the run's iteration space
+  int64_t base = 0;
+  int64_t offset = 0;
+  int dtype = 0;
+  std::vector<int64_t> st;  // stride per run dimension (kept dims only for reduction outputs)
+};
+
+struct Operand {
+  int kind = 0;  // 0: load slot, 1: constant, 2: value
+  int idx = 0;
+  double f = 0;
+  int64_t i = 0;
+  int dtype = 0;
+};
+
+struct Step {
+  int op = 0;
+  int dt_out = 0;
+  int dt_in = 0;
+  int nin = 0;
+  Operand a[3];
+  int value = 0;  // SSA id of the result
+  uint64_t seed = 0, key = 0;
+  int64_t rstep = 0;
+  int random_idx = -1;  // index among the run's RANDOM steps
+  int instr = 0;
+};
+
+struct Run {
+  std::vector<int64_t> shape;
+  std::vector<Slot> loads;
+  std::vector<Slot> stores;
+  std::vector<int> store_value;
+  std::vector<Step> steps;
+  std::vector<int> value_dtype;
+  bool has_red = false;
+  int red_op = 0, red_dtype = 0, red_value = -1;
+  std::vector<int> red_axes;  // run dims that are reduced (sorted)
+  Slot red_out;               // strides over the kept dims, in order
+  std::vector<int> instrs;    // batch indices
+  int nrandom = 0;
+  std::vector<Operand> consts;  // constant operands, passed as parameter words
+  int64_t elements() const;
+};
+
+// host-side effects between runs
+struct HostAction {
+  int kind = 0;  // 0 FREE, 1 DISCARD, 2 SYNC
+  int64_t base = 0;
+};
+
+struct PlanItem {
+  int kind = 0;  // 0 run, 1 host action
+  Run run;
+  HostAction act;
+  int pack_with_next = 0;  // >0: this run starts a pack of that many runs
+};
+
+struct Plan {
+  std::vector<PlanItem> items;
+  std::vector<std::pair<int64_t, int64_t>> staging;  // internal temps: (base handle, src instr)
+};
+
+// --------------------------------------------------------------- codegen
+struct Spec {  // the launch-independent shape of a generated kernel
+  Mode mode = Mode::ELEM;
+  int nd = 0;         // ELEM/FULL: iteration dims after coalescing
+  int ndk = 0, ndr = 0;
+  bool vec = false;   // 1-D contiguous path with vector loads
+  int E = 1;          // elements per vector chunk
+  std::vector<int> load_cls, store_cls;  // inner-dim stride class: 0 zero, 1 unit, 2 general
+  int red_cls = 0;
+  bool packed = false;
+};
+
+struct Canon {  // a run in the form the generated kernel consumes
+  Spec spec;
+  std::vector<int64_t> dims;          // ELEM/FULL dims, or kept dims then reduced dims
+  std::vector<std::vector<int64_t>> lst, sst;  // per slot strides over dims
+  std::vector<int64_t> red_st;        // reduction output strides over kept dims
+  std::vector<int64_t> idx_st;        // RANDOM linear index strides over dims
+  int64_t total = 0;
+};
+
+Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& load_ptrs,
+                   const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr);
+std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix);
+
+// words of the kernel parameter block, in the order the generated code reads them
+struct LaunchArgs {
+  std::vector<int64_t> w;
+};
+void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load_ptrs,
+                const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr, uintptr_t partials,
+                uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out);
+int words_count(const Run& r, const Canon& c);
+
+// ----------------------------------------------------------------- context
+struct BaseRec {
+  int dtype = 0;
+  int64_t nelem = 0;
+  void* dptr = nullptr;
+  bool external = false;
+  bool written = false;
+  bool internal = false;  // created by the library (staging)
+  int64_t bytes() const { return nelem * itemsize(dtype); }
+};
+
+struct Kernel {
+  cudaLibrary_t lib = nullptr;
+  std::map<std::string, cudaKernel_t> fn;
+};
+
+struct TuneChoice {
+  int block = 256;
+  int U = 2;
+  int grid_mult = 0;  // 0: enough CTAs for the work (capped by residency)
+};
+
+struct Scratch {  // per stream: reduction partials and counters
+  void* partials = nullptr;
+  unsigned int* counters = nullptr;
+  int64_t n_partials = 0, n_counters = 0;
+};
+
+struct Exec {
+  cudaStream_t stream = nullptr;
+  Scratch scratch;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+struct CachedBatch {
+  uint64_t key = 0;
+  int seen = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::vector<std::pair<int64_t, uintptr_t>> fingerprint;
+  std::vector<void*> keep;  // device buffers the graph references
+  int64_t launches = 0;
+};
+
+struct Ctx {
+  vbe_config cfg{};
+  std::string cache_dir_s;
+  bool host_only = false;
+  int device = 0;
+  int sm_count = 148;
+  Exec exec;
+  bool own_stream = false;
+  std::mutex mu;  // guards handles and caches when a server thread shares the context
+  std::unordered_map<int64_t, BaseRec> bases;
+  std::unordered_map<int64_t, ViewDesc> views;
+  int64_t next_handle = 1;
+  std::string last_error;
+  // caches
+  std::unordered_map<std::string, std::shared_ptr<Kernel>> kernels;  // by source hash
+  std::unordered_map<std::string, TuneChoice> tune;                  // by source hash
+  std::unordered_map<uint64_t, CachedBatch> batches;
+  // tickets
+  std::unordered_map<int64_t, cudaEvent_t> tickets;
+  int64_t next_ticket = 1;
+  vbe_stats stats{};
+  cudaMemPool_t pool = nullptr;
+  // VBE_RECORD: host allocations and recorded launches
+  bool record = false;
+  int rec_block = 64, rec_U = 1;
+  std::map<uintptr_t, size_t> host_allocs;
+  std::vector<std::string> rec_launches;
+  std::unordered_map<std::string, std::string> rec_sources;
+};
+
+// analysis
+std::vector<RInstr> resolve_batch(Ctx* c, const vbe_instr* prog, int64_t n);
+Plan make_plan(Ctx* c, std::vector<RInstr>& prog, bool fuse, bool pack);
+std::string plan_json(Ctx* c, const std::vector<RInstr>& prog, const Plan& p, bool want_source);
+
+// runtime
+void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_graph);
+std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src);
+void precompile(Ctx* c, const std::vector<std::string>& srcs);
+void* dev_alloc(Ctx* c, Exec* ex, int64_t bytes);
+void dev_free(Ctx* c, Exec* ex, void* p, int64_t bytes);
+void ensure_scratch(Ctx* c, Exec* ex, int64_t partials, int64_t counters);
+void release_exec(Ctx* c, Exec* ex);
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull);
+std::string hex64(uint64_t v);
+
+}  // namespace vbe
+
+// the opaque handle of the public ABI
+struct vbe_ctx {
+  vbe::Ctx c;
+};

@@ -1,0 +1,152 @@
+"""Run recorded libvbe launches on the CPU (test infrastructure).
+
+A context created with VBE_RECORD keeps its bases in host memory and
+records each launch (kernel source, entry, grid, block, parameter words)
+instead of running it. This module compiles each generated source with
+``vbe_emu.h`` into a small shared library and executes the launches in
+order on the host, with every memory access checked against the context's
+allocations. It lets the host test suite check the code generator's index
+arithmetic and results without a GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import json
+import os
+import subprocess
+import tempfile
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+EMU_H = os.path.join(HERE, "vbe_emu.h")
+
+_GLOBALS = """
+thread_local dim3 threadIdx, blockIdx;
+dim3 blockDim, gridDim;
+std::vector<EmuRange> g_ranges;
+std::atomic<long long> g_bad{0};
+char g_bad_msg[256];
+std::barrier<>* g_block_bar = nullptr;
+std::vector<std::unique_ptr<std::barrier<>>> g_warp_bar;
+unsigned long long g_xchg[1024];
+"""
+
+_WRAP_COMMON = """
+extern "C" void emu_set_ranges(const unsigned long long* lohi, int n) {
+  g_ranges.clear();
+  for (int i = 0; i < n; ++i) g_ranges.push_back({(uintptr_t)lohi[2 * i], (uintptr_t)lohi[2 * i + 1]});
+}
+extern "C" const char* emu_msg() { return g_bad_msg; }
+static int emu_check_words(int nw) { return nw == (int)(sizeof(P) / 8) ? 0 : -1; }
+"""
+
+_WRAP_TILE = """
+extern "C" long long emu_tile(int U, const long long* w, int nw, unsigned grid, unsigned block) {
+  if (emu_check_words(nw)) return -1;
+  P p;
+  memcpy(&p, w, sizeof(P));
+  g_bad = 0;
+  emu_grid(grid, block, [&]() { if (U == 1) vbe_u1(p); else if (U == 2) vbe_u2(p); else vbe_u4(p); });
+  return g_bad.load();
+}
+"""
+
+_WRAP_PACK = """
+extern "C" long long emu_pack(int U, long long descs, long long prefix, int ninst, long long total,
+                              long long chunk, long long work, unsigned grid, unsigned block) {
+  g_bad = 0;
+  emu_grid(grid, block, [&]() {
+    if (U == 1) vbe_pack_u1((const P*)descs, (const i64*)prefix, ninst, total, chunk, (unsigned*)work);
+    else vbe_pack_u4((const P*)descs, (const i64*)prefix, ninst, total, chunk, (unsigned*)work);
+  });
+  return g_bad.load();
+}
+"""
+
+_WRAP_AXIS = """
+extern "C" long long emu_axis(const long long* w, int nw, unsigned grid, unsigned block) {
+  if (emu_check_words(nw)) return -1;
+  P p;
+  memcpy(&p, w, sizeof(P));
+  g_bad = 0;
+  emu_grid(grid, block, [&]() { vbe_axis(p); });
+  return g_bad.load();
+}
+"""
+
+
+class EmulationError(AssertionError):
+    pass
+
+
+class Emulator:
+    def __init__(self, workdir: str | None = None):
+        self.dir = workdir or os.path.join(tempfile.gettempdir(), "vbe_emu_cache")
+        os.makedirs(self.dir, exist_ok=True)
+        self.mods = {}
+        self.launches = 0
+
+    def module(self, src: str):
+        h = hashlib.sha1((src + open(EMU_H).read()).encode()).hexdigest()[:20]
+        if h in self.mods:
+            return self.mods[h]
+        so = os.path.join(self.dir, f"emu_{h}.so")
+        if not os.path.exists(so):
+            parts = [f'#include "{EMU_H}"', "#include <type_traits>", _GLOBALS, src, _WRAP_COMMON]
+            if "vbe_u1(" in src:
+                parts.append(_WRAP_TILE)
+            if "vbe_pack_u1(" in src:
+                parts.append(_WRAP_PACK)
+            if "vbe_axis(" in src:
+                parts.append(_WRAP_AXIS)
+            cpp = os.path.join(self.dir, f"emu_{h}.cpp")
+            with open(cpp, "w") as f:
+                f.write("\n".join(parts))
+            tmp = so + f".{os.getpid()}.tmp"
+            r = subprocess.run(["g++", "-std=c++20", "-O1", "-fPIC", "-shared", "-pthread", "-w", cpp, "-o", tmp],
+                               stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+            if r.returncode != 0:
+                raise EmulationError("emulation build failed:\n" + r.stdout.decode()[-4000:])
+            os.replace(tmp, so)
+        lib = ctypes.CDLL(so)
+        lib.emu_set_ranges.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
+        lib.emu_msg.restype = ctypes.c_char_p
+        if hasattr(lib, "emu_tile"):
+            lib.emu_tile.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint,
+                                     ctypes.c_uint]
+            lib.emu_tile.restype = ctypes.c_longlong
+        if hasattr(lib, "emu_axis"):
+            lib.emu_axis.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
+            lib.emu_axis.restype = ctypes.c_longlong
+        if hasattr(lib, "emu_pack"):
+            lib.emu_pack.argtypes = [ctypes.c_int] + [ctypes.c_longlong] * 2 + [ctypes.c_int] + \
+                [ctypes.c_longlong] * 3 + [ctypes.c_uint, ctypes.c_uint]
+            lib.emu_pack.restype = ctypes.c_longlong
+        self.mods[h] = lib
+        return lib
+
+    def run(self, record_json: str) -> int:
+        js = json.loads(record_json)
+        flat = []
+        for addr, nbytes in js["allocs"]:
+            flat += [addr, addr + nbytes]
+        ranges = (ctypes.c_ulonglong * max(1, len(flat)))(*flat)
+        for L in js["launches"]:
+            lib = self.module(js["sources"][L["key"]])
+            lib.emu_set_ranges(ranges, len(flat) // 2)
+            entry = L["entry"]
+            if L.get("packed"):
+                ctypes.c_uint.from_address(L["work"]).value = 0
+                bad = lib.emu_pack(int(entry.rsplit("u", 1)[1]), L["descs"], L["prefix"], L["ninst"], L["total"],
+                                   L["chunk"], L["work"], L["grid"], L["block"])
+            else:
+                w = (ctypes.c_longlong * len(L["words"]))(*L["words"])
+                if entry == "vbe_axis":
+                    bad = lib.emu_axis(w, len(L["words"]), L["grid"], L["block"])
+                else:
+                    bad = lib.emu_tile(int(entry[5:]), w, len(L["words"]), L["grid"], L["block"])
+            if bad:
+                raise EmulationError(f"{entry} (grid {L['grid']}, block {L['block']}): "
+                                     f"{'parameter block size mismatch' if bad < 0 else lib.emu_msg().decode()}")
+            self.launches += 1
+        return len(js["launches"])

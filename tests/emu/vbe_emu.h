@@ -1,0 +1,142 @@
+// CPU emulation of the CUDA features the generated kernels use, so that
+// tests can run a recorded launch on the host: every CUDA thread of a block
+// is a std::thread, blocks run one after another, __syncthreads and warp
+// shuffles are barriers, and every memory access goes through a checked
+// pointer that rejects addresses outside the allocations the library made.
+// Test infrastructure only.
+#pragma once
+#define VBE_EMU 1
+
+#include <atomic>
+#include <barrier>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <thread>
+#include <vector>
+
+struct dim3 {
+  unsigned x = 1, y = 1, z = 1;
+};
+struct uint4 {
+  unsigned x, y, z, w;
+};
+struct uint2 {
+  unsigned x, y;
+};
+
+extern thread_local dim3 threadIdx, blockIdx;
+extern dim3 blockDim, gridDim;
+
+#define __global__
+#define __device__
+#define __forceinline__ inline
+#define __launch_bounds__(x)
+#define __shared__ static
+
+struct EmuRange {
+  uintptr_t lo, hi;
+};
+extern std::vector<EmuRange> g_ranges;
+extern std::atomic<long long> g_bad;
+extern char g_bad_msg[256];
+extern std::barrier<>* g_block_bar;
+extern std::vector<std::unique_ptr<std::barrier<>>> g_warp_bar;
+extern unsigned long long g_xchg[1024];
+
+inline bool emu_ok(const volatile void* p, size_t n) {
+  uintptr_t a = (uintptr_t)p;
+  for (auto& r : g_ranges)
+    if (a >= r.lo && a + n <= r.hi) return true;
+  if (g_bad.fetch_add(1) == 0)
+    snprintf(g_bad_msg, sizeof g_bad_msg, "access of %zu bytes at %p outside every allocation", n, (const void*)a);
+  return false;
+}
+
+template <class T>
+struct CP {  // checked pointer
+  T* p;
+  T& operator[](long long i) const {
+    static thread_local typename std::remove_cv<T>::type dummy;
+    if (!emu_ok(p + i, sizeof(T))) return (T&)dummy;
+    return p[i];
+  }
+  CP operator+(long long i) const { return CP{p + i}; }
+};
+template <class T>
+inline CP<T> vbe_ptr(long long v) {
+  return CP<T>{reinterpret_cast<T*>(v)};
+}
+template <class T, int E>
+inline void vbe_vload(CP<const T> p, T (&o)[E]) {
+  if (((uintptr_t)p.p) % (sizeof(T) * E) != 0 && g_bad.fetch_add(1) == 0)
+    snprintf(g_bad_msg, sizeof g_bad_msg, "misaligned vector load at %p", (void*)p.p);
+  if (!emu_ok(p.p, sizeof(T) * E)) return;
+  for (int e = 0; e < E; ++e) o[e] = p.p[e];
+}
+template <class T, int E>
+inline void vbe_vstore(CP<T> p, const T (&o)[E]) {
+  if (((uintptr_t)p.p) % (sizeof(T) * E) != 0 && g_bad.fetch_add(1) == 0)
+    snprintf(g_bad_msg, sizeof g_bad_msg, "misaligned vector store at %p", (void*)p.p);
+  if (!emu_ok(p.p, sizeof(T) * E)) return;
+  for (int e = 0; e < E; ++e) p.p[e] = o[e];
+}
+
+inline void __syncthreads() { g_block_bar->arrive_and_wait(); }
+inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
+inline unsigned atomicAdd(CP<unsigned> p, unsigned v) {
+  if (!emu_ok(p.p, 4)) return 0;
+  return __atomic_fetch_add(p.p, v, __ATOMIC_SEQ_CST);
+}
+inline unsigned atomicAdd(unsigned* p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+
+template <class T>
+inline T __shfl_down_sync(unsigned, T v, int off) {
+  static_assert(sizeof(T) <= 8, "shuffle width");
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long bits = 0;
+  memcpy(&bits, &v, sizeof(T));
+  g_xchg[threadIdx.x] = bits;
+  g_warp_bar[w]->arrive_and_wait();
+  T r = v;
+  unsigned src = lane + (unsigned)off;
+  if (src < 32 && w * 32 + src < blockDim.x) memcpy(&r, &g_xchg[w * 32 + src], sizeof(T));
+  g_warp_bar[w]->arrive_and_wait();
+  return r;
+}
+
+inline double __longlong_as_double(long long v) {
+  double d;
+  memcpy(&d, &v, 8);
+  return d;
+}
+inline float __int_as_float(int v) {
+  float f;
+  memcpy(&f, &v, 4);
+  return f;
+}
+inline long long min(long long a, long long b) { return a < b ? a : b; }
+
+template <class F>
+void emu_grid(unsigned grid, unsigned block, F f) {
+  blockDim.x = block;
+  gridDim.x = grid;
+  for (unsigned b = 0; b < grid; ++b) {
+    std::barrier<> bar((std::ptrdiff_t)block);
+    g_block_bar = &bar;
+    g_warp_bar.clear();
+    for (unsigned w = 0; w * 32 < block; ++w)
+      g_warp_bar.emplace_back(new std::barrier<>((std::ptrdiff_t)std::min(32u, block - w * 32)));
+    std::vector<std::thread> th;
+    th.reserve(block);
+    for (unsigned t = 0; t < block; ++t)
+      th.emplace_back([&, t, b]() {
+        threadIdx.x = t;
+        blockIdx.x = b;
+        f();
+      });
+    for (auto& x : th) x.join();
+  }
+}

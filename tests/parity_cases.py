@@ -1,0 +1,339 @@
+"""Parity cases shared by the CPU-emulation tests and the GPU tests: each
+case is a seeded bytecode program plus the rule its outputs must satisfy
+against the oracle (bit-exact, ulp-bounded, or bounded by rtol * sum|x|
+for reordered sums)."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+from workloads import (Const, ProgramBuilder, blackscholes, bs_inputs, jacobi, montecarlo_pi,
+                       shallow_water)
+
+F64_REDUCE_RTOL = 1e-12
+F32_REDUCE_RTOL = 1e-5
+ULP_TRANSCENDENTAL = 4
+
+
+def special(dt, n, rng):
+    if dt == "float64" or dt == "float32":
+        x = rng.standard_normal(n) * np.exp2(rng.integers(-20, 20, n))
+        sp = [0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 5e-324 if dt == "float64" else 1e-45]
+        x[: len(sp)] = sp
+        return x.astype(dt)
+    if dt == "int64":
+        x = rng.integers(-(2**62), 2**62, n, dtype=np.int64)
+        x[:4] = [0, -1, np.iinfo(np.int64).min, np.iinfo(np.int64).max]
+        return x
+    return rng.random(n) < 0.5
+
+
+def positive(dt, n, rng):
+    return (np.exp(rng.uniform(-30, 30, n))).astype(dt)
+
+
+def _ordered(x, dt):
+    """Float bit patterns mapped onto a monotone integer line (sign and
+    magnitude -> signed integer; both zeros map to 0)."""
+    it = np.int64 if dt == "float64" else np.int32
+    i = np.asarray(x, dtype=dt).view(it).astype(np.int64)
+    mag = i & np.int64((1 << (63 if dt == "float64" else 31)) - 1)
+    return np.where(i < 0, -mag, mag)
+
+
+def ulp_diff(a, b, dt):
+    return np.abs(_ordered(a, dt) - _ordered(b, dt))
+
+
+def assert_exact(got, want, what=""):
+    got = np.asarray(got)
+    want = np.asarray(want)
+    if got.dtype.kind == "f":
+        same = (got == want) | (np.isnan(got) & np.isnan(want))
+        # signed zeros must match as well
+        same &= np.signbit(got) == np.signbit(want)
+    else:
+        same = got == want
+    if not np.all(same):
+        i = int(np.argmin(same))
+        raise AssertionError(f"{what}: {np.sum(~same)} mismatches, first at {i}: got {got[i]!r} want {want[i]!r}")
+
+
+def assert_ulp(got, want, dt, ulps, what=""):
+    both_nan = np.isnan(got) & np.isnan(want)
+    d = ulp_diff(got, want, dt)
+    d[both_nan] = 0
+    if np.any(d > ulps):
+        i = int(np.argmax(d))
+        raise AssertionError(f"{what}: {int(d[i])} ulp at {i}: got {got[i]!r} want {want[i]!r}")
+
+
+def assert_close_sum(got, want, scale, rtol, what=""):
+    err = np.abs(got.astype(np.float64) - want.astype(np.float64))
+    bound = rtol * np.maximum(scale, np.finfo(np.float64).tiny)
+    bad = ~(err <= bound) & ~(np.isnan(got) & np.isnan(want))
+    if np.any(bad):
+        i = int(np.argmax(bad))
+        raise AssertionError(f"{what}: |{got[i]} - {want[i]}| > {rtol} * {scale[i]}")
+
+
+# ------------------------------------------------------------------ cases
+
+class Case:
+    def __init__(self, name, program, check):
+        self.name = name
+        self.program = program
+        self.check = check  # check(got: dict, want: dict)
+
+    def __repr__(self):
+        return self.name
+
+
+def _exact_check(p):
+    def check(got, want):
+        for bid in p.outputs:
+            assert_exact(got[bid], want[bid], f"{p.name} base {bid}")
+    return check
+
+
+def elementwise_cases(n=1037, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    binary = ["ADD", "SUBTRACT", "MULTIPLY", "MAXIMUM", "MINIMUM"]
+    for dt in ("float64", "float32", "int64"):
+        for op in binary + (["DIVIDE"] if dt != "int64" else []):
+            b = ProgramBuilder(f"{op}_{dt}")
+            x = b.base(dt, n, special(dt, n, rng))
+            y = b.base(dt, n, special(dt, n, rng)[::-1].copy())
+            o = b.base(dt, n)
+            b.emit(op, b.whole(o), b.whole(x), b.whole(y))
+            p = b.build([o])
+            out.append(Case(p.name, p, _exact_check(p)))
+        for op in ["ABSOLUTE", "NEGATIVE"]:
+            b = ProgramBuilder(f"{op}_{dt}")
+            x = b.base(dt, n, special(dt, n, rng))
+            o = b.base(dt, n)
+            b.emit(op, b.whole(o), b.whole(x))
+            p = b.build([o])
+            out.append(Case(p.name, p, _exact_check(p)))
+        for op in ["LESS", "LESS_EQUAL", "GREATER", "GREATER_EQUAL", "EQUAL", "NOT_EQUAL"]:
+            b = ProgramBuilder(f"{op}_{dt}")
+            x = b.base(dt, n, special(dt, n, rng))
+            y = b.base(dt, n, np.where(rng.random(n) < 0.3, special(dt, n, rng), special(dt, n, rng)[::-1]))
+            o = b.base("bool", n)
+            b.emit(op, b.whole(o), b.whole(x), b.whole(y))
+            p = b.build([o])
+            out.append(Case(p.name, p, _exact_check(p)))
+    for dt in ("float64", "float32"):
+        b = ProgramBuilder(f"SQRT_{dt}")
+        x = b.base(dt, n, np.abs(special(dt, n, rng)))
+        o = b.base(dt, n)
+        b.emit("SQRT", b.whole(o), b.whole(x))
+        p = b.build([o])
+        out.append(Case(p.name, p, _exact_check(p)))
+        for op, gen in (("EXP", lambda: rng.uniform(-80, 80, n)), ("LOG", lambda: positive(dt, n, rng))):
+            b = ProgramBuilder(f"{op}_{dt}")
+            data = np.asarray(gen(), dtype=dt)
+            data[:3] = [0.0, np.inf, np.nan] if op == "EXP" else [1.0, np.inf, 0.0]
+            x = b.base(dt, n, data)
+            o = b.base(dt, n)
+            b.emit(op, b.whole(o), b.whole(x))
+            p = b.build([o])
+
+            def chk(got, want, p=p, o=o, dt=dt):
+                assert_ulp(got[o], want[o], dt, ULP_TRANSCENDENTAL, p.name)
+            out.append(Case(p.name, p, chk))
+    # SELECT, CAST, COPY/fill with constants
+    for dt in ("float64", "float32", "int64", "bool"):
+        b = ProgramBuilder(f"SELECT_{dt}")
+        c = b.base("bool", n, rng.random(n) < 0.5)
+        x = b.base(dt, n, special(dt, n, rng))
+        y = b.base(dt, n, special(dt, n, rng))
+        o = b.base(dt, n)
+        o2 = b.base(dt, n)
+        b.emit("SELECT", b.whole(o), b.whole(c), b.whole(x), b.whole(y))
+        b.emit("SELECT", b.whole(o2), b.whole(c), Const(True if dt == "bool" else 3), b.whole(y))
+        p = b.build([o, o2])
+        out.append(Case(p.name, p, _exact_check(p)))
+        for dt2 in ("float64", "float32", "int64", "bool"):
+            b = ProgramBuilder(f"CAST_{dt}_{dt2}")
+            src = special(dt, n, rng)
+            if dt in ("float64", "float32") and dt2 == "int64":
+                src = (rng.standard_normal(n) * 1e6).astype(dt)  # inside int64
+            x = b.base(dt, n, src)
+            o = b.base(dt2, n)
+            b.emit("CAST", b.whole(o), b.whole(x))
+            p = b.build([o])
+            out.append(Case(p.name, p, _exact_check(p)))
+        b = ProgramBuilder(f"FILL_{dt}")
+        o = b.base(dt, n)
+        b.emit("COPY", b.whole(o), Const(1 if dt != "bool" else True))
+        p = b.build([o])
+        out.append(Case(p.name, p, _exact_check(p)))
+    # RANDOM
+    b = ProgramBuilder("RANDOM")
+    o = b.base("float64", (7, n))
+    b.emit("RANDOM", b.whole(o), seed=12345, key=(3 << 32) | 1, step=2)
+    p = b.build([o])
+    out.append(Case(p.name, p, _exact_check(p)))
+    return out
+
+
+def view_cases(seed=1):
+    rng = np.random.default_rng(seed)
+    out = []
+    N = 67
+    data = rng.standard_normal(N * N)
+    # shifted, reversed, strided, broadcast, 3-D views into one grid
+    b = ProgramBuilder("views2d")
+    g = b.base("float64", (N, N), data)
+    o1 = b.base("float64", (N - 2, N - 2))
+    o2 = b.base("float64", (N, N))
+    o3 = b.base("float64", (30, 20))
+    o4 = b.base("float64", (5, 7, 9))
+    b.emit("ADD", b.whole(o1), b.sub2d(g, 0, N - 2, 1, N - 1), b.sub2d(g, 2, N, 1, N - 1))
+    b.emit("SUBTRACT", b.whole(o1), b.whole(o1), b.view(g, N * N - 1, (N - 2, N - 2), (-N, -1)))
+    b.emit("MULTIPLY", b.whole(o2), b.whole(g), b.view(g, 3, (N, N), (0, 1)))
+    b.emit("COPY", b.whole(o3), b.view(g, 5, (30, 20), (2 * N, 3)))
+    b.emit("ADD", b.whole(o4), b.view(g, 11, (5, 7, 9), (N * 9, 1, N)), b.view(g, 0, (5, 7, 9), (0, N, 0)))
+    p = b.build([o1, o2, o3, o4])
+    out.append(Case(p.name, p, _exact_check(p)))
+    # in-place update through identical views, then a partial overlap (staged)
+    b = ProgramBuilder("inplace_and_staged")
+    a = b.base("float64", 1000, rng.standard_normal(1000))
+    b.emit("MULTIPLY", b.whole(a), b.whole(a), Const(2.0))
+    b.emit("ADD", b.view(a, 1, (999,), (1,)), b.view(a, 0, (999,), (1,)), Const(1.0))
+    b.emit("COPY", b.whole(a), b.view(a, 999, (1000,), (-1,)))
+    p = b.build([a])
+    out.append(Case(p.name, p, _exact_check(p)))
+    # empty views
+    b = ProgramBuilder("empty")
+    a = b.base("float64", 10, np.arange(10.0))
+    o = b.base("float64", 10, np.zeros(10))
+    s = b.base("float64", 3)
+    b.emit("ADD", b.view(o, 0, (0,), (1,)), b.view(a, 0, (0,), (1,)), Const(1.0))
+    b.emit("ADD_REDUCE", b.whole(s), b.view(a, 0, (0, 3), (1, 1)), axis=0)
+    p = b.build([o, s])
+    out.append(Case(p.name, p, _exact_check(p)))
+    # misaligned one-dimensional views (no vector path) and ragged tails
+    b = ProgramBuilder("misaligned")
+    a = b.base("float32", 4099, rng.standard_normal(4099).astype(np.float32))
+    o = b.base("float32", 4099)
+    b.emit("ADD", b.view(o, 3, (4093,), (1,)), b.view(a, 1, (4093,), (1,)), b.view(a, 5, (4093,), (1,)))
+    b.emit("COPY", b.view(o, 0, (3,), (1,)), Const(0.0))
+    b.emit("COPY", b.view(o, 4096, (3,), (1,)), Const(0.0))
+    p = b.build([o])
+    out.append(Case(p.name, p, _exact_check(p)))
+    return out
+
+
+def _abs_sum(x, axis):
+    return np.add.reduce(np.abs(x.astype(np.float64)), axis=axis)
+
+
+def reduction_cases(shape=(9, 33, 70), seed=2):
+    rng = np.random.default_rng(seed)
+    out = []
+    for dt in ("float64", "float32", "int64"):
+        x = special(dt, int(np.prod(shape)), rng) if dt == "int64" else \
+            rng.standard_normal(int(np.prod(shape))).astype(dt)
+        if dt == "int64":
+            x = (x >> 20)
+        for op in ("ADD_REDUCE", "MIN_REDUCE", "MAX_REDUCE"):
+            for ax in range(3):
+                b = ProgramBuilder(f"{op}_{dt}_ax{ax}")
+                xb = b.base(dt, shape, x)
+                oshape = tuple(s for k, s in enumerate(shape) if k != ax)
+                o = b.base(dt, oshape)
+                b.emit(op, b.whole(o), b.whole(xb), axis=ax)
+                p = b.build([o])
+                if op == "ADD_REDUCE" and dt != "int64":
+                    scale = _abs_sum(x.reshape(shape), ax).reshape(-1)
+                    rtol = F64_REDUCE_RTOL if dt == "float64" else F32_REDUCE_RTOL
+
+                    def chk(got, want, o=o, scale=scale, rtol=rtol, p=p):
+                        assert_close_sum(got[o], want[o], scale, rtol, p.name)
+                else:
+                    chk = _exact_check(p)
+                out.append(Case(p.name, p, chk))
+    # fused chain with a full reduction and with an axis reduction, plus stores
+    for dt in ("float64", "float32"):
+        b = ProgramBuilder(f"chain_full_{dt}")
+        n = 50_001
+        xv = rng.standard_normal(n).astype(dt)
+        yv = rng.standard_normal(n).astype(dt)
+        x = b.base(dt, n, xv)
+        y = b.base(dt, n, yv)
+        t = b.base(dt, n)
+        s = b.base(dt, 1)
+        b.emit("MULTIPLY", b.whole(t), b.whole(x), b.whole(x))
+        b.emit("ADD", b.whole(t), b.whole(t), b.whole(y))
+        b.emit("ADD_REDUCE", b.view(s, 0, (), ()), b.whole(t), axis=0)
+        p = b.build([t, s])
+        scale = np.array([np.sum(np.abs(xv.astype(np.float64) ** 2 + yv))])
+        rtol = F64_REDUCE_RTOL if dt == "float64" else F32_REDUCE_RTOL
+
+        def chk(got, want, t=t, s=s, scale=scale, rtol=rtol, p=p):
+            assert_exact(got[t], want[t], p.name)
+            assert_close_sum(got[s], want[s], scale, rtol, p.name)
+        out.append(Case(p.name, p, chk))
+        b = ProgramBuilder(f"chain_axis_{dt}")
+        m = 300
+        xv = rng.standard_normal((m, 41)).astype(dt)
+        x = b.base(dt, (m, 41), xv)
+        t = b.base(dt, (m, 41))
+        r0 = b.base(dt, 41)
+        b.emit("ABSOLUTE", b.whole(t), b.whole(x))
+        b.emit("ADD_REDUCE", b.whole(r0), b.whole(t), axis=0)
+        p = b.build([t, r0])
+        scale = np.sum(np.abs(xv.astype(np.float64)), axis=0)
+
+        def chk2(got, want, t=t, r0=r0, scale=scale, rtol=rtol, p=p):
+            assert_exact(got[t], want[t], p.name)
+            assert_close_sum(got[r0], want[r0], scale, rtol, p.name)
+        out.append(Case(p.name, p, chk2))
+    return out
+
+
+def workload_cases(scale="small"):
+    out = []
+    n = 24 if scale == "small" else 256
+    p = jacobi(n, 3 if scale == "small" else 10)
+
+    def jchk(got, want, p=p):
+        assert_exact(got[p.meta["grid"]], want[p.meta["grid"]], "jacobi grid")
+        g0 = p.bases[p.meta["grid"]].init.reshape(n, n)
+        assert_close_sum(got[p.meta["deltas"]], want[p.meta["deltas"]],
+                         np.full(p.meta["iters"], np.sum(np.abs(g0)) * 2), F64_REDUCE_RTOL, "jacobi deltas")
+    out.append(Case(p.name, p, jchk))
+    nb = 3000 if scale == "small" else 100_000
+    for dt, rtol in (("float64", 1e-12), ("float32", 1e-5)):
+        p = blackscholes(nb, dt, seed=11)
+        inp = bs_inputs(nb, "float64", seed=11)
+        mx = np.maximum(inp["S"], inp["K"])
+
+        def bchk(got, want, p=p, mx=mx, rtol=rtol):
+            for bid in (p.meta["call"], p.meta["put"]):
+                err = np.abs(got[bid].astype(np.float64) - want[bid].astype(np.float64))
+                assert np.all(err <= rtol * mx), f"{p.name}: max err/max(S,K) {np.max(err / mx)}"
+        out.append(Case(p.name, p, bchk))
+    N = 18 if scale == "small" else 130
+    for dt in ("float64", "float32"):
+        p = shallow_water(N, 3 if scale == "small" else 10, dt)
+        out.append(Case(p.name, p, _exact_check(p)))
+    sizes = [1, 37, 1000, 4096, 333] if scale == "small" else \
+        np.floor(np.exp2(10 + 8 * np.random.default_rng(3).random(64))).astype(int).tolist()
+    p = montecarlo_pi(seed=99, sizes=sizes)
+    out.append(Case(p.name, p, _exact_check(p)))
+    return out
+
+
+def all_small_cases():
+    return elementwise_cases() + view_cases() + reduction_cases() + workload_cases("small")
+
+
+def oracle_outputs(program):
+    mem = oracle.run(program)
+    return {bid: mem[bid] for bid in program.outputs}

@@ -1,0 +1,218 @@
+"""Host-side tests of libvbe: the library loads and exports every entry
+point the header declares; the analysis and the code generator work on a
+host-only context (no GPU): fusion decisions, staging of partially
+overlapping operands, validation errors, the overlap test against NumPy,
+and NVRTC compilation of every kernel the workloads need."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1210_7774_b300 import build
+
+build.build()
+
+from paper_1210_7774_b300 import vbe as V  # noqa: E402
+from paper_1210_7774_b300.runner import Executor  # noqa: E402
+from workloads import (Const, ProgramBuilder, View, blackscholes, jacobi, montecarlo_pi,  # noqa: E402
+                       shallow_water)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HOST = V.VBE_HOST_ONLY
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "vbe.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(vbe_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_every_declared_function_is_exported():
+    names = header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(V.lib, n), n
+    assert set(names) == set(V.EXPORTED)
+
+
+def test_strerror_and_errors_table():
+    for code, name in V.ERRORS.items():
+        assert V.vbe_strerror(code)
+    assert V.vbe_strerror(-999) == "unknown error"
+
+
+def runs_of(ex, L, batch=0):
+    js = json.loads(ex.plan(L, batch))
+    return [i["run"] for i in js["items"] if "run" in i], js
+
+
+@pytest.fixture
+def fused():
+    ex = Executor(V.VBE_FUSE | V.VBE_PACK | HOST)
+    yield ex
+    ex.close()
+
+
+@pytest.fixture
+def plain():
+    ex = Executor(HOST)
+    yield ex
+    ex.close()
+
+
+def test_jacobi_iteration_fuses_into_reduction_and_copy(fused):
+    p = jacobi(16, 2)
+    L = fused.load(p, upload=False)
+    runs, _ = runs_of(fused, L)
+    assert [r["mode"] for r in runs] == ["full_reduce", "elementwise"]
+    first = runs[0]
+    assert first["ops"] == ["ADD", "ADD", "ADD", "MULTIPLY", "SUBTRACT", "ABSOLUTE"]
+    assert first["reduce"]["axes"] == [0, 1]  # row sums then their sum
+    t_id = list(p.bases)[1]  # bases: full grid, t, d, r, deltas
+    assert first["stores"] == [L.base[t_id]]  # d and r stay in registers
+    assert runs[1]["ops"] == ["COPY"]
+
+
+def test_plain_path_is_one_run_per_bytecode(plain):
+    p = blackscholes(100)
+    L = plain.load(p, upload=False)
+    runs, _ = runs_of(plain, L)
+    compute = [i for i in p.instrs if i.op not in ("SYNC", "DISCARD", "FREE")]
+    assert len(runs) == len(compute)
+    assert all(len(r["ops"]) == 1 for r in runs)
+
+
+def test_blackscholes_is_one_kernel_with_two_stores(fused):
+    p = blackscholes(1000)
+    L = fused.load(p, upload=False)
+    runs, _ = runs_of(fused, L)
+    assert len(runs) == 1
+    r = runs[0]
+    assert len(r["loads"]) == 5 and len(r["stores"]) == 2
+    assert r["vector"] is True
+
+
+def test_shallow_water_step_runs(fused):
+    p = shallow_water(12, 1)
+    L = fused.load(p, upload=False)
+    runs, _ = runs_of(fused, L)
+    # ghost columns, ghost rows, cell fluxes, x faces, y faces, update
+    assert [len(r["ops"]) for r in runs] == [6, 6, 9, 21, 21, 18]
+    # the in-place update reads and writes the same interior views
+    assert sorted(set(runs[-1]["stores"])) == sorted(L.base[k] for k in (p.meta["H"], p.meta["U"], p.meta["V"]))
+
+
+def test_montecarlo_instances_keep_everything_in_registers(fused):
+    p = montecarlo_pi(sizes=[100, 200, 300])
+    L = fused.load(p, upload=False)
+    runs, _ = runs_of(fused, L)
+    assert len(runs) == 3
+    for r in runs:
+        assert r["loads"] == [] and r["stores"] == [] and r["mode"] == "full_reduce"
+
+
+def test_partial_overlap_is_staged(fused):
+    b = ProgramBuilder("shift")
+    a = b.base("float64", 10, np.arange(10.0))
+    b.emit("ADD", b.view(a, 1, (9,), (1,)), b.view(a, 0, (9,), (1,)), Const(1.0))
+    p = b.build([a])
+    L = fused.load(p, upload=False)
+    runs, js = runs_of(fused, L)
+    assert js["staged"] == 1
+    assert runs[0]["ops"] == ["COPY"] and runs[1]["ops"] == ["ADD"]
+
+
+def test_validation_errors(fused):
+    ctx = fused.ctx
+    f = V.vbe_base_create(ctx, V.VBE_FLOAT64, 10)
+    i = V.vbe_base_create(ctx, V.VBE_INT64, 10)
+    with pytest.raises(V.VbeError) as e:
+        V.vbe_view_create(ctx, f, 5, (10,), (1,))
+    assert e.value.code == -2
+    vf = V.vbe_view_create(ctx, f, 0, (10,), (1,))
+    vi = V.vbe_view_create(ctx, i, 0, (10,), (1,))
+    vs = V.vbe_view_create(ctx, f, 0, (5,), (1,))
+    vz = V.vbe_view_create(ctx, f, 0, (5,), (0,))
+
+    def instr(op, out, *ins):
+        arr = (V.vbe_instr * 1)()
+        arr[0].op = V.OPCODES[op]
+        arr[0].const_slot = -1
+        arr[0].out = out
+        for k, x in enumerate(ins):
+            arr[0].in_[k] = x
+        return arr
+
+    cases = [(instr("ADD", vf, vf, vi), -3), (instr("DIVIDE", vi, vi, vi), -3), (instr("EXP", vi, vi), -3),
+             (instr("ADD", vf, vf, vs), -4), (instr("COPY", vz, vs), -12), (instr("ADD", vf, vf, 999), -1)]
+    for arr, code in cases:
+        with pytest.raises(V.VbeError) as e:
+            V.vbe_plan(ctx, arr, 1)
+        assert e.value.code == code
+
+
+def _np_view(buf, v):
+    return np.lib.stride_tricks.as_strided(buf[v.offset:], v.shape, tuple(8 * s for s in v.strides))
+
+
+def test_overlap_test_is_sound_and_exact_on_grids(fused):
+    """Random views of one base against np.shares_memory(max_work=None): a
+    "disjoint" answer must never be wrong; for views whose strides form a
+    divisibility chain (rows/columns/boxes of a grid) the answer is exact."""
+    ctx = fused.ctx
+    N = 24
+    base = V.vbe_base_create(ctx, V.VBE_FLOAT64, N * N)
+    buf = np.zeros(N * N)
+    rng = np.random.default_rng(0)
+    exact_checked = 0
+    for _ in range(600):
+        views = []
+        for _ in range(2):
+            kind = rng.integers(0, 3)
+            if kind == 0:  # box
+                r0, c0 = rng.integers(0, N, 2)
+                nr, nc = rng.integers(1, N - r0 + 1), rng.integers(1, N - c0 + 1)
+                views.append(View(1, int(r0 * N + c0), (int(nr), int(nc)), (N, 1)))
+            elif kind == 1:  # strided row/column
+                st = int(rng.choice([1, 2, 3, N, 2 * N]))
+                off = int(rng.integers(0, N * N))
+                n = int(rng.integers(1, max(2, (N * N - 1 - off) // st + 2)))
+                n = min(n, (N * N - 1 - off) // st + 1)
+                views.append(View(1, off, (n,), (st,)))
+            else:  # reversed box
+                r0, c0 = rng.integers(0, N, 2)
+                nr, nc = rng.integers(1, r0 + 2), rng.integers(1, c0 + 2)
+                views.append(View(1, int(r0 * N + c0), (int(nr), int(nc)), (-N, -1)))
+        a, b = views
+        ha = V.vbe_view_create(ctx, base, a.offset, a.shape, a.strides)
+        hb = V.vbe_view_create(ctx, base, b.offset, b.shape, b.strides)
+        got = V.vbe_views_may_overlap(ctx, ha, hb)
+        truth = np.shares_memory(_np_view(buf, a), _np_view(buf, b), max_work=None)
+        if truth:
+            assert got, (a, b)
+        chain = all(abs(s) in (1, N) for s in a.strides + b.strides)
+        if chain:
+            assert got == truth, (a, b)
+            exact_checked += 1
+    assert exact_checked > 200
+
+
+@pytest.mark.parametrize("flags", [V.VBE_FUSE | V.VBE_PACK, 0])
+def test_every_workload_kernel_compiles_for_sm103a(flags):
+    with Executor(flags | HOST) as ex:
+        for p in (jacobi(16, 1), blackscholes(1000), blackscholes(1000, "float32"),
+                  montecarlo_pi(sizes=[10, 20]), shallow_water(12, 1), shallow_water(12, 1, "float32")):
+            L = ex.load(p, upload=False)
+            assert V.vbe_plan_compile(ex.ctx, *L.batches[0]) >= 1
+
+
+def test_generated_source_is_plain_cuda(fused):
+    p = blackscholes(64, "float32")
+    L = fused.load(p, upload=False)
+    js = json.loads(fused.plan(L, 0, source=True))
+    src = [i["run"]["source"] for i in js["items"] if "run" in i][0]
+    assert "expf(" in src and "logf(" in src and "sqrtf(" in src
+    assert "vbe_vload" in src  # 16-byte vector path
+    assert "__fmaf" not in src and "fma(" not in src
