@@ -1,0 +1,312 @@
+"""Benchmark: fused vector-bytecode execution on one B300 (or N replicas).
+
+Default workload: Black-Scholes call+put over 16,777,216 options in float64
+(a second run in float32 is reported beside it). One step = one submitted
+batch of the whole program (about 65 elementwise bytecodes) through the C
+ABI, fused into one kernel and replayed as a CUDA graph, with the inputs
+already resident in device memory. ``value`` is the compulsory HBM traffic
+of the batch (inputs read once + outputs written once) per second; the plain
+path (one launch per bytecode) is timed on the same GPU beside it.
+``--impl reference`` times the oracle (the CPU reference interpreter) on a
+bounded sample of the same workload instead.
+
+Other workloads: ``--workload jacobi|shallow_water|montecarlo|serving``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused bytecode-batch HBM GB/s (% of peak) vs per-bytecode path; p50/p99 latency"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6400.0
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ reference arm
+
+def cpu_reference(args, rank, world):
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    from workloads import blackscholes
+    dtype = "float64"
+    n_sample = args.ref_sample
+    prog = blackscholes(n_sample, dtype)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.run(prog)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(prog)
+        times.append(time.perf_counter() - t0)
+    per_step = statistics.median(times)
+    value = prog.compulsory_bytes() / per_step / 1e9
+    cores = 1  # NumPy ufuncs run on one thread
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(1 << 24, dtype),
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n_sample} options per step (of 16,777,216), float64"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(n, dtype):
+    return {"workload": f"Black-Scholes call+put, {n} options, {dtype}", "options": n,
+            "bytes_per_option": 7 * (8 if dtype == "float64" else 4),
+            "l2": "inputs larger than L2 (no flush needed)", "path": "fused + CUDA graph + autotuned launch"}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def time_steps(fn, steps, warmup, torch, dist=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return ev0.elapsed_time(ev1) / 1e3 / steps
+
+
+def kernel_hash(ex, L):
+    import hashlib
+    js = json.loads(ex.plan(L, 0, source=True))
+    srcs = [i["run"]["source"] for i in js["items"] if "run" in i]
+    return hashlib.sha1("".join(srcs).encode()).hexdigest()[:16]
+
+
+def measured_traffic(name, khash):
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)[name]
+        return t["dram_bytes_per_launch"] if t.get("kernel_hash") == khash else None
+    except Exception:
+        return None
+
+
+def gpu_blackscholes(args, rank, world, local):
+    import torch
+    from paper_1210_7774_b300 import build
+    build.build()
+    from paper_1210_7774_b300 import vbe as V
+    from paper_1210_7774_b300.runner import Executor
+    from workloads import blackscholes, bs_inputs
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    # a dedicated stream: the library launches on it and the CUDA events
+    # that time the steps are recorded on it
+    ts = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(ts)
+    stream = ts.cuda_stream
+    assert stream != 0
+    n = args.options
+    cache = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
+    flags_fused = V.VBE_FUSE | V.VBE_GRAPHS | V.VBE_AUTOTUNE | V.VBE_PACK
+    res = {}
+    for dtype in ("float64", "float32"):
+        inp = bs_inputs(n, dtype, seed=1210_7774 + 2 + rank)
+        prog = blackscholes(n, dtype, inputs=inp)
+        cbytes = prog.compulsory_bytes()
+        out = {}
+        for name, flags in (("fused", flags_fused), ("plain", 0)):
+            ex = Executor(flags, device=local, stream=stream, cache_dir=cache)
+            L = ex.load(prog)
+            st0 = ex.stats()
+            steps = args.steps if name == "fused" else max(3, args.steps // 4)
+            sec = time_steps(lambda: ex.submit(L, 0), steps, max(3, args.warmup), torch, dist)
+            st1 = ex.stats()
+            out[name] = {"sec": sec, "GB/s": cbytes / sec / 1e9,
+                         "launches_per_step": (st1["kernel_launches"] - st0["kernel_launches"]) / (steps + max(3, args.warmup))}
+            if name == "fused":
+                out["kernel_hash"] = kernel_hash(ex, L)
+                # end to end: pinned host inputs -> device, batch, results -> pinned host
+                host_in = {bid: torch.from_numpy(b.init).pin_memory() for bid, b in prog.bases.items()
+                           if b.init is not None}
+                host_out = {bid: torch.empty(prog.bases[bid].nelem, dtype=getattr(torch, dtype)).pin_memory()
+                            for bid in prog.outputs}
+                h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+                d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+
+                def e2e_step():
+                    for bid, t in host_in.items():
+                        V.vbe_base_upload(ex.ctx, L.base[bid], t.data_ptr(), t.numel() * t.element_size())
+                    ex.submit(L, 0)
+                    for bid, t in host_out.items():
+                        V.vbe_sync(ex.ctx, L.base[bid], t.data_ptr(), t.numel() * t.element_size())
+                e2e_steps = max(2, args.steps // 4)
+                for _ in range(2):
+                    e2e_step()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(e2e_steps):
+                    e2e_step()
+                torch.cuda.synchronize()
+                e2e_sec = (time.perf_counter() - t0) / e2e_steps
+                out["e2e"] = {"value": cbytes / e2e_sec / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                              "d2h_bytes_per_step": d2h}
+            ex.close()
+        out["cbytes"] = cbytes
+        res[dtype] = out
+    return res, dist
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="vbe", choices=["vbe", "reference"])
+    ap.add_argument("--workload", default="blackscholes")
+    ap.add_argument("--options", type=int, default=1 << 24)
+    ap.add_argument("--ref-sample", type=int, default=1 << 20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        cpu_reference(args, rank, world)
+        return
+    if args.workload != "blackscholes":
+        from paper_1210_7774_b300 import workload_bench
+        workload_bench.main(args)
+        return
+    clocks = Clocks(local)
+    clocks.start()
+    res, dist = gpu_blackscholes(args, rank, world, local)
+    ck = clocks.stop()
+    # max over ranks of the per-step time
+    sec = res["float64"]["fused"]["sec"]
+    if dist:
+        import torch
+        t = torch.tensor([sec])
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t[0])
+    if rank != 0:
+        return
+    hbm, src = peaks()
+    f64 = res["float64"]
+    value = world * f64["cbytes"] / sec / 1e9
+    achieved = f64["cbytes"] / sec / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        from workloads import blackscholes
+        prog = blackscholes(args.ref_sample, "float64")
+        t0 = time.perf_counter()
+        oracle.run(prog)
+        dt = time.perf_counter() - t0
+        cpu = {"value": prog.compulsory_bytes() / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.ref_sample} options of the same workload, float64, one pass ({dt:.1f} s)"}
+    f32 = res["float32"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.options, "float64"),
+        "hbm_fraction": achieved / hbm,
+        "plain": {"value": f64["plain"]["GB/s"], "ms_per_step": f64["plain"]["sec"] * 1e3,
+                  "launches_per_step": f64["plain"]["launches_per_step"]},
+        "speedup_vs_plain": f64["plain"]["sec"] / sec,
+        "float32": {"value": f32["fused"]["GB/s"], "hbm_fraction": f32["fused"]["GB/s"] / hbm,
+                    "ms_per_step": f32["fused"]["sec"] * 1e3, "plain_value": f32["plain"]["GB/s"],
+                    "speedup_vs_plain": f32["plain"]["sec"] / f32["fused"]["sec"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": src, "traffic": measured_traffic("blackscholes_f64", f64["kernel_hash"]),
+                     "kernel_hash": f64["kernel_hash"]},
+        "e2e": f64["e2e"],
+        "gpu_launches": int(round(f64["fused"]["launches_per_step"] * args.steps)),
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -51,9 +51,10 @@ def assert_exact(got, want, what=""):
     got = np.asarray(got)
     want = np.asarray(want)
     if got.dtype.kind == "f":
-        same = (got == want) | (np.isnan(got) & np.isnan(want))
-        # signed zeros must match as well
-        same &= np.signbit(got) == np.signbit(want)
+        # equal values with equal signs (so signed zeros must match), or both
+        # NaN (the sign and payload of a NaN carry no meaning and are not
+        # compared: GPU arithmetic returns its canonical NaN)
+        same = ((got == want) & (np.signbit(got) == np.signbit(want))) | (np.isnan(got) & np.isnan(want))
     else:
         same = got == want
     if not np.all(same):
@@ -306,7 +307,7 @@ def workload_cases(scale="small"):
         assert_exact(got[p.meta["grid"]], want[p.meta["grid"]], "jacobi grid")
         g0 = p.bases[p.meta["grid"]].init.reshape(n, n)
         assert_close_sum(got[p.meta["deltas"]], want[p.meta["deltas"]],
-                         np.full(p.meta["iters"], np.sum(np.abs(g0)) * 2), F64_REDUCE_RTOL, "jacobi deltas")
+                         np.full(want[p.meta["deltas"]].size, np.sum(np.abs(g0)) * 2), F64_REDUCE_RTOL, "jacobi deltas")
     out.append(Case(p.name, p, jchk))
     nb = 3000 if scale == "small" else 100_000
     for dt, rtol in (("float64", 1e-12), ("float32", 1e-5)):

@@ -1,0 +1,175 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, element
+by element, on seeded inputs; fused, plain (one launch per bytecode) and
+graph-replayed execution; and the full-size configurations checked on
+samples or properties that hold at any size."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1210_7774_b300 import build
+
+build.build()
+
+from paper_1210_7774_b300 import vbe as V  # noqa: E402
+from paper_1210_7774_b300.runner import Executor  # noqa: E402
+
+import oracle  # noqa: E402
+from parity_cases import (F64_REDUCE_RTOL, all_small_cases, assert_close_sum, assert_exact,  # noqa: E402
+                          oracle_outputs, workload_cases)
+from workloads import (blackscholes, bs_inputs, jacobi, mc_sizes, montecarlo_pi, shallow_water,  # noqa: E402
+                       sw_inputs)
+
+pytestmark = pytest.mark.gpu
+CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
+
+FUSED = V.VBE_FUSE | V.VBE_PACK | V.VBE_AUTOTUNE
+MODES = {"fused": FUSED, "plain": 0, "fused_graphs": FUSED | V.VBE_GRAPHS}
+
+
+def run_gpu(program, flags, repeat_batches=1):
+    with Executor(flags, cache_dir=CACHE) as ex:
+        L = ex.load(program)
+        for _ in range(repeat_batches):
+            ex.run(L)
+        out = {bid: ex.read(L, bid) for bid in program.outputs}
+        out["_stats"] = ex.stats()
+        return out
+
+
+SMALL = all_small_cases()
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("case", SMALL, ids=[c.name for c in SMALL])
+def test_small_parity(case, mode):
+    got = run_gpu(case.program, MODES[mode])
+    case.check(got, oracle_outputs(case.program))
+
+
+MEDIUM = workload_cases("medium")
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("case", MEDIUM, ids=[c.name for c in MEDIUM])
+def test_medium_workload_parity(case, mode):
+    got = run_gpu(case.program, MODES[mode])
+    case.check(got, oracle_outputs(case.program))
+    if mode == "fused_graphs" and case.name.startswith(("jacobi", "shallow")):
+        assert got["_stats"]["graph_launches"] > 0  # repeated iterations replay a graph
+
+
+def test_jacobi_config_full_size_graphs_and_plain_agree():
+    """Config: 256x256 float64, 10 iterations, fused + graph replay; the grid
+    is bit-exact with the oracle and with the plain path."""
+    p = jacobi(256, 10)
+    want = oracle_outputs(p)
+    for flags in (FUSED | V.VBE_GRAPHS, 0):
+        got = run_gpu(p, flags)
+        assert_exact(got[p.meta["grid"]], want[p.meta["grid"]], "grid")
+        g0 = p.bases[p.meta["grid"]].init
+        assert_close_sum(got[p.meta["deltas"]], want[p.meta["deltas"]], np.full(1, 2 * np.abs(g0).sum()),
+                         F64_REDUCE_RTOL, "deltas")
+
+
+@pytest.mark.parametrize("dtype,rtol", [("float64", 1e-12), ("float32", 1e-5)])
+def test_blackscholes_full_size_sampled(dtype, rtol):
+    """16M options, in the launch configuration the benchmark times; 20,000
+    sampled options recomputed by the oracle one program at a time."""
+    n = 1 << 24
+    inp = bs_inputs(n, dtype)
+    p = blackscholes(n, dtype, inputs=inp)
+    got = run_gpu(p, FUSED | V.VBE_GRAPHS)
+    idx = np.sort(np.random.default_rng(7).choice(n, 20_000, replace=False))
+    idx = np.concatenate([[0, 1, n - 2, n - 1], idx])
+    sub = blackscholes(len(idx), dtype, inputs={k: v[idx] for k, v in inp.items()})
+    want = oracle_outputs(sub)
+    mx = np.maximum(inp["S"][idx], inp["K"][idx]).astype(np.float64)
+    for full_id, sub_id in ((p.meta["call"], sub.meta["call"]), (p.meta["put"], sub.meta["put"])):
+        err = np.abs(got[full_id][idx].astype(np.float64) - want[sub_id].astype(np.float64))
+        assert np.all(err <= rtol * mx), np.max(err / mx)
+
+
+def test_shallow_water_full_size_one_step_exact_and_mass():
+    """4096x4096 float64: one step bit-exact with the oracle (the scheme uses
+    only + - * /, so IEEE arithmetic fixes every bit); five steps conserve
+    mass to rounding and keep the droplet's mirror symmetry bitwise."""
+    N = 4096
+    p = shallow_water(N, 1)
+    want = oracle_outputs(p)
+    got = run_gpu(p, FUSED | V.VBE_GRAPHS)
+    for q in ("H", "U", "V"):
+        assert_exact(got[p.meta[q]], want[p.meta[q]], q)
+    inp = sw_inputs(N, centred=True)
+    p5 = shallow_water(N, 5, inputs=inp)
+    got = run_gpu(p5, FUSED | V.VBE_GRAPHS)
+    H = got[p5.meta["H"]].reshape(N, N)[1:-1, 1:-1]
+    H0 = inp["H"][1:-1, 1:-1]
+    assert abs(H.sum(dtype=np.float64) - H0.sum(dtype=np.float64)) <= 1e-11 * H0.sum()
+    assert np.array_equal(H, H[::-1, :]) or np.max(np.abs(H - H[::-1, :])) <= 1e-13
+
+
+def test_montecarlo_full_config_sampled_instances_exact():
+    """All 256 instances (2^10..2^24 samples) in one packed launch; the
+    smallest 24 instances recomputed exactly by the oracle; every estimate
+    within 6 sigma of pi/4."""
+    sizes = mc_sizes(256)
+    p = montecarlo_pi(sizes=sizes)
+    got = run_gpu(p, FUSED)
+    counts = got[p.meta["count"]]
+    pick = np.argsort(sizes)[:24]
+    sub = montecarlo_pi(sizes=sizes[pick], keys=pick)
+    want = oracle_outputs(sub)[sub.meta["count"]]
+    assert counts[pick].tolist() == want.tolist()
+    q = np.pi / 4
+    sig = np.sqrt(q * (1 - q) / sizes)
+    assert np.all(np.abs(counts / sizes - q) < 6 * sig)
+    pp = montecarlo_pi(sizes=sizes[:32])
+    plain = run_gpu(pp, 0)
+    assert plain[pp.meta["count"]].tolist() == counts[:32].tolist()
+
+
+def test_errors_on_device():
+    with Executor(FUSED, cache_dir=CACHE) as ex:
+        ctx = ex.ctx
+        a = V.vbe_base_create(ctx, V.VBE_FLOAT64, 16)
+        o = V.vbe_base_create(ctx, V.VBE_FLOAT64, 16)
+        va = V.vbe_view_create(ctx, a, 0, (16,), (1,))
+        vo = V.vbe_view_create(ctx, o, 0, (16,), (1,))
+        arr = (V.vbe_instr * 1)()
+        arr[0].op = V.OPCODES["SQRT"]
+        arr[0].const_slot = -1
+        arr[0].out = vo
+        arr[0].in_[0] = va
+        with pytest.raises(V.VbeError) as e:  # a was never written
+            V.vbe_submit(ctx, arr, 1)
+        assert e.value.code == -10
+        host = np.arange(16.0)
+        V.vbe_base_upload(ctx, a, host.ctypes.data, host.nbytes)
+        t = V.vbe_submit(ctx, arr, 1)
+        V.vbe_wait(ctx, t, 10_000_000_000)
+        out = np.empty(16)
+        V.vbe_sync(ctx, o, out.ctypes.data, out.nbytes)
+        assert np.array_equal(out, np.sqrt(host))
+
+
+def test_registered_device_memory():
+    torch = pytest.importorskip("torch")
+    x = torch.arange(1000, dtype=torch.float64, device="cuda")
+    y = torch.empty(1000, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    with Executor(FUSED, cache_dir=CACHE, stream=torch.cuda.current_stream().cuda_stream) as ex:
+        ctx = ex.ctx
+        bx = V.vbe_base_register(ctx, V.VBE_FLOAT64, 1000, x.data_ptr())
+        by = V.vbe_base_register(ctx, V.VBE_FLOAT64, 1000, y.data_ptr())
+        vx = V.vbe_view_create(ctx, bx, 0, (1000,), (1,))
+        vy = V.vbe_view_create(ctx, by, 0, (1000,), (1,))
+        arr = (V.vbe_instr * 1)()
+        arr[0].op = V.OPCODES["MULTIPLY"]
+        arr[0].const_slot = 1
+        arr[0].konst.f64 = 3.0
+        arr[0].out = vy
+        arr[0].in_[0] = vx
+        V.vbe_submit(ctx, arr, 1)
+        torch.cuda.current_stream().synchronize()
+        assert torch.equal(y, x * 3.0)

@@ -34,7 +34,7 @@ def _jacobi_brute(g, iters):
 
 def test_jacobi_matches_loops_bitwise():
     n, iters = 8, 4
-    p = jacobi(n, iters, seed=11)
+    p = jacobi(n, iters, seed=11, history=True)
     mem = oracle.run(p)
     grid0 = jacobi_inputs(n, seed=11)
     want, deltas = _jacobi_brute(grid0.tolist(), iters)
@@ -47,7 +47,7 @@ def test_jacobi_matches_loops_bitwise():
 def test_jacobi_linear_data_is_a_fixed_point():
     # a + b i + c j is discrete-harmonic; small integers keep it exact
     n = 12
-    p = jacobi(n, 3, init="linear", linear=(5, 3, 7))
+    p = jacobi(n, 3, init="linear", linear=(5, 3, 7), history=True)
     mem = oracle.run(p)
     assert np.array_equal(mem[p.meta["grid"]], jacobi_inputs(n, init="linear", linear=(5, 3, 7)).ravel())
     assert mem[p.meta["deltas"]].tolist() == [0.0, 0.0, 0.0]
@@ -55,7 +55,7 @@ def test_jacobi_linear_data_is_a_fixed_point():
 
 def test_jacobi_converges_to_boundary_and_keeps_maximum_principle():
     n = 10
-    p = jacobi(n, 400, seed=3)
+    p = jacobi(n, 400, seed=3, history=True)
     mem = oracle.run(p)
     g = mem[p.meta["grid"]]
     g0 = jacobi_inputs(n, seed=3)

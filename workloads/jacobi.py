@@ -42,8 +42,10 @@ def jacobi_inputs(n: int, dtype: str = "float64", seed: int = SEED + 1,
 
 
 def jacobi(n: int = 256, iters: int = 10, dtype: str = "float64",
-           seed: int = SEED + 1, init: str = "random", linear=(1, 2, 3)):
-    """The Jacobi program. Outputs: the grid and the per-iteration deltas.
+           seed: int = SEED + 1, init: str = "random", linear=(1, 2, 3), history: bool = False):
+    """The Jacobi program. Outputs: the grid and ``deltas``: the scalar delta
+    of the last iteration (every iteration overwrites it, so all iterations
+    are the same batch), or with ``history`` the delta of each iteration.
     ``meta['batches']`` lists one instruction range per iteration."""
     b = ProgramBuilder(f"jacobi{n}_{dtype}_{iters}it")
     grid = jacobi_inputs(n, dtype, seed, init, linear)
@@ -57,7 +59,7 @@ def jacobi(n: int = 256, iters: int = 10, dtype: str = "float64",
     t = b.base(dtype, (m, m))
     d = b.base(dtype, (m, m))
     r = b.base(dtype, (m,))
-    deltas = b.base(dtype, (iters,))
+    deltas = b.base(dtype, (iters if history else 1,))
     tv, dv, rv = b.whole(t), b.whole(d), b.whole(r)
     batches = []
     for k in range(iters):
@@ -69,7 +71,7 @@ def jacobi(n: int = 256, iters: int = 10, dtype: str = "float64",
         b.emit("SUBTRACT", dv, center, tv)
         b.emit("ABSOLUTE", dv, dv)
         b.emit("ADD_REDUCE", rv, dv, axis=1)
-        b.emit("ADD_REDUCE", b.view(deltas, k, (), ()), rv, axis=0)
+        b.emit("ADD_REDUCE", b.view(deltas, k if history else 0, (), ()), rv, axis=0)
         b.emit("COPY", center, tv)
         b.discard(t, d, r)
         batches.append((start, len(b.p.instrs)))

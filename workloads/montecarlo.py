@@ -33,21 +33,26 @@ def mc_sizes(n_inst: int = 256, seed: int = SEED + 4, lo: int = 10, hi: int = 24
     return np.floor(np.exp2(lo + (hi - lo) * u)).astype(np.int64)
 
 
-def montecarlo_pi(n_inst: int = 256, seed: int = SEED + 4, sizes=None, draw_seed: int | None = None):
-    """The MC-pi program. Output: ``count`` (int64, one per instance)."""
+def montecarlo_pi(n_inst: int = 256, seed: int = SEED + 4, sizes=None, draw_seed: int | None = None,
+                  keys=None):
+    """The MC-pi program. Output: ``count`` (int64, one per instance).
+    ``keys`` gives the instance numbers used in the counters (default
+    0..n-1), so that a few instances of a large configuration can be
+    rebuilt on their own."""
     sizes = mc_sizes(n_inst, seed) if sizes is None else np.asarray(sizes, dtype=np.int64)
     n_inst = len(sizes)
+    keys = list(range(n_inst)) if keys is None else [int(k) for k in keys]
     draw_seed = seed if draw_seed is None else draw_seed
     b = ProgramBuilder(f"mcpi{n_inst}")
     count = b.base("int64", n_inst)
-    for i, n in enumerate(sizes.tolist()):
+    for i, (n, inst) in enumerate(zip(sizes.tolist(), keys)):
         x = b.base("float64", n)
         y = b.base("float64", n)
         c = b.base("bool", n)
         ci = b.base("int64", n)
         xv, yv, cv, civ = b.whole(x), b.whole(y), b.whole(c), b.whole(ci)
-        b.emit("RANDOM", xv, seed=draw_seed, key=(i << 32) | 0, step=2)
-        b.emit("RANDOM", yv, seed=draw_seed, key=(i << 32) | 1, step=2)
+        b.emit("RANDOM", xv, seed=draw_seed, key=(inst << 32) | 0, step=2)
+        b.emit("RANDOM", yv, seed=draw_seed, key=(inst << 32) | 1, step=2)
         b.emit("MULTIPLY", xv, xv, xv)
         b.emit("MULTIPLY", yv, yv, yv)
         b.emit("ADD", xv, xv, yv)
