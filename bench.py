@@ -192,12 +192,14 @@ def gpu_blackscholes(args, rank, world, local):
     cache = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
     flags_fused = V.VBE_FUSE | V.VBE_GRAPHS | V.VBE_AUTOTUNE | V.VBE_PACK
     res = {}
-    for dtype in ("float64", "float32"):
+    for dtype in args.dtypes.split(","):
         inp = bs_inputs(n, dtype, seed=1210_7774 + 2 + rank)
         prog = blackscholes(n, dtype, inputs=inp)
         cbytes = prog.compulsory_bytes()
         out = {}
         for name, flags in (("fused", flags_fused), ("plain", 0)):
+            if name not in args.paths.split(","):
+                continue
             ex = Executor(flags, device=local, stream=stream, cache_dir=cache)
             L = ex.load(prog)
             st0 = ex.stats()
@@ -239,6 +241,136 @@ def gpu_blackscholes(args, rank, world, local):
     return res, dist
 
 
+# ------------------------------------------------------ the other workloads
+
+def other_workload(args, local):
+    """Jacobi, shallow water, Monte-Carlo pi and the serving loop: one JSON
+    line each with fused / plain timings (these are reported beside the
+    headline, not as it)."""
+    import torch
+    from paper_1210_7774_b300 import build
+    build.build()
+    from paper_1210_7774_b300 import vbe as V
+    from paper_1210_7774_b300.runner import Executor
+
+    torch.cuda.set_device(local)
+    ts = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(ts)
+    stream = ts.cuda_stream
+    cache = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
+    hbm, _ = peaks()
+    F = V.VBE_FUSE | V.VBE_AUTOTUNE | V.VBE_PACK
+    modes = {"fused_graphs": F | V.VBE_GRAPHS, "fused": F, "plain": 0, "plain_graphs": V.VBE_GRAPHS}
+    out = {"workload": args.workload}
+
+    def timed_batches(program, flags, reps):
+        ex = Executor(flags, device=local, stream=stream, cache_dir=cache)
+        L = ex.load(program)
+        nb = len(L.batches)
+
+        def step():
+            for k in range(nb):
+                ex.submit(L, k)
+        sec = time_steps(step, reps, 2, torch)
+        st = ex.stats()
+        ex.close()
+        return sec, st
+
+    if args.workload == "jacobi":
+        from workloads import jacobi
+        p = jacobi(256, 10)
+        cbytes = 256 * 256 * 8 + 254 * 254 * 8  # read the grid, write the interior, per iteration
+        for name, flags in modes.items():
+            sec, st = timed_batches(p, flags, 20)
+            out[name] = {"us_per_iteration": sec / 10 * 1e6, "GB/s": cbytes * 10 / sec / 1e9}
+        out["note"] = "256x256 float64, 10 iterations; the grid (0.5 MB) is L2-resident, so this is launch-bound"
+    elif args.workload == "shallow_water":
+        from workloads import shallow_water
+        for dtype in ("float64", "float32"):
+            p = shallow_water(4096, 50, dtype)
+            isz = 8 if dtype == "float64" else 4
+            cbytes = 6 * isz * 4096 * 4096 * 50  # H, U, V read once and written once per step
+            res = {}
+            for name in ("fused_graphs", "plain_graphs"):
+                sec, st = timed_batches(p, modes[name], 2)
+                res[name] = {"ms_per_step": sec / 50 * 1e3, "GB/s": cbytes / sec / 1e9,
+                             "hbm_fraction": cbytes / sec / 1e9 / hbm}
+            res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_step"] / res["fused_graphs"]["ms_per_step"]
+            out[dtype] = res
+    elif args.workload == "montecarlo":
+        from workloads import mc_sizes, montecarlo_pi
+        p = montecarlo_pi(sizes=mc_sizes(256))
+        samples = p.meta["samples"]
+        for name, flags in (("packed", F), ("unpacked", V.VBE_FUSE | V.VBE_AUTOTUNE), ("plain", 0)):
+            sec, st = timed_batches(p, flags, 3 if name != "plain" else 1)
+            out[name] = {"ms_per_step": sec * 1e3, "samples_per_s": samples / sec}
+        out["samples"] = samples
+    elif args.workload == "serving":
+        out.update(serving_bench(args, V, local))
+    print(json.dumps(out), flush=True)
+
+
+def serving_bench(args, V, local):
+    """64 clients, Poisson arrivals at 0.7 of the measured capacity, the
+    request mix of the serving workload; p50/p99 latency and throughput,
+    fused versus plain."""
+    import threading
+
+    from paper_1210_7774_b300.runner import Request
+    from workloads.serving import poisson_arrivals, request_mix, request_program
+
+    n_req = args.requests
+    mix = request_mix(n_req)
+    cache = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
+    res = {}
+    for name, flags in (("fused", V.VBE_FUSE | V.VBE_PACK), ("plain", 0)):
+        ctx = V.vbe_init(local, flags, 0, None, cache)
+        srv = V.vbe_server_create(ctx, 16, 60 << 30, flags)
+        # capacity: a closed loop over the first requests
+        warm = [Request(request_program(k, p)) for k, p in mix[:64]]
+        t0 = time.perf_counter()
+        ids = [V.vbe_server_submit(srv, r.req) for r in warm]
+        for i in ids:
+            V.vbe_server_wait(srv, i, -1)
+        t0 = time.perf_counter()
+        ids = [V.vbe_server_submit(srv, r.req) for r in warm]
+        for i in ids:
+            V.vbe_server_wait(srv, i, -1)
+        cap = len(warm) / (time.perf_counter() - t0)
+        rate = 0.7 * cap if name == "fused" else res["fused"]["arrival_rate"]
+        arrivals = poisson_arrivals(n_req, rate)
+        reqs = [None] * n_req
+        lat = [None] * n_req
+        nclients = 64
+        start = time.perf_counter() + 0.2
+
+        def client(c):
+            for i in range(c, n_req, nclients):
+                if reqs[i] is None:
+                    reqs[i] = Request(request_program(*mix[i]))
+                delay = start + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                rid = V.vbe_server_submit(srv, reqs[i].req)
+                r = V.vbe_server_wait(srv, rid, -1)
+                lat[i] = (r.t_done_ns - r.t_arrive_ns) / 1e6
+                reqs[i] = None
+
+        th = [threading.Thread(target=client, args=(c,)) for c in range(nclients)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        wall = time.perf_counter() - start
+        V.vbe_server_destroy(srv)
+        V.vbe_finalize(ctx)
+        lat = np.array(lat)
+        res[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "throughput_req_s": n_req / wall, "capacity_req_s": cap, "arrival_rate": rate}
+    res["requests"] = n_req
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,19 +381,25 @@ def main():
     ap.add_argument("--options", type=int, default=1 << 24)
     ap.add_argument("--ref-sample", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtypes", default="float64,float32", help="profiling: restrict the dtypes run")
+    ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
+    ap.add_argument("--paths", default="fused,plain", help="profiling: restrict the paths run")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         cpu_reference(args, rank, world)
         return
     if args.workload != "blackscholes":
-        from paper_1210_7774_b300 import workload_bench
-        workload_bench.main(args)
+        other_workload(args, local)
         return
     clocks = Clocks(local)
     clocks.start()
     res, dist = gpu_blackscholes(args, rank, world, local)
     ck = clocks.stop()
+    if args.dtypes != "float64,float32" or args.paths != "fused,plain":
+        if rank == 0:  # a restricted profiling run prints only its timings
+            print(json.dumps({k: {p: v[p]["sec"] for p in ("fused", "plain") if p in v} for k, v in res.items()}))
+        return
     # max over ranks of the per-step time
     sec = res["float64"]["fused"]["sec"]
     if dist:

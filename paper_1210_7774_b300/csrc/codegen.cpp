@@ -567,7 +567,7 @@ struct Gen {
   // --------------------------------------------------------- tile kernels
   void emit_tile_kernel(int U) {
     const int nd = c.spec.nd;
-    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_u" << U << "(const P p) {\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_u" << U << "(const P p) {\n";
     emit_pointers("  ");
     emit_acc_init("  ");
     // inner strides
@@ -713,7 +713,7 @@ struct Gen {
 
   // ---------------------------------------------------- packed 1-D kernel
   void emit_packed_kernel(int U) {
-    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_pack_u" << U
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_pack_u" << U
       << "(const P* __restrict__ descs, const i64* __restrict__ prefix, int ninst, i64 total, i64 chunk, unsigned* work) {\n"
       << "  __shared__ i64 s_c;\n"
       << "  for (;;) {\n"
@@ -765,7 +765,7 @@ struct Gen {
   void emit_axis_kernel() {
     const int ndk = c.spec.ndk, ndr = c.spec.ndr;
     bool block = c.spec.mode == Mode::AXIS_BLOCK;
-    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_axis(const P p) {\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_axis(const P p) {\n";
     emit_pointers("  ");
     o << "  const auto rp = vbe_ptr<" << rt() << ">(" << W(L.red_ptr) << ");\n"
       << "  const i64 nout = " << W(L.nout) << ", nred = " << W(L.nred) << ";\n";
@@ -842,12 +842,18 @@ std::string generate_source(const Run& r, const Canon& c, std::string* entry_pre
     for (int U : {1, 2, 4}) g.emit_tile_kernel(U);
     if (c.spec.nd == 1)
       for (int U : {1, 4}) g.emit_packed_kernel(U);
-    if (entry_prefix) *entry_prefix = "vbe_u";
   } else {
     g.emit_axis_kernel();
-    if (entry_prefix) *entry_prefix = "vbe_axis";
   }
-  return g.o.str();
+  // kernel names carry the run's form, its operation count and a hash of
+  // the source, so profiles tell the kernels apart
+  std::string src = g.o.str();
+  static const char* mode_tag[] = {"e", "r", "at", "ab"};
+  std::string tag = std::string(mode_tag[(int)c.spec.mode]) + std::to_string(r.steps.size()) + "_" +
+                    hex64(fnv1a(src.data(), src.size())).substr(8);
+  for (size_t pos; (pos = src.find("@TAG@")) != std::string::npos;) src.replace(pos, 5, tag);
+  if (entry_prefix) *entry_prefix = "vbe_" + tag;
+  return src;
 }
 
 }  // namespace vbe

@@ -248,8 +248,6 @@ void release_exec(Ctx* c, Exec* ex) {
 
 // --------------------------------------------------------------- launches
 
-namespace {
-
 struct Launch {
   cudaKernel_t fn = nullptr;
   std::string key, entry;          // module and kernel name (recorded launches)
@@ -264,6 +262,8 @@ struct Launch {
   void* d_prefix = nullptr;
   int64_t d_bytes = 0;
 };
+
+namespace {
 
 int occupancy(cudaKernel_t fn, int block) {
   int n = 0;
@@ -389,6 +389,7 @@ struct Prepared {
   std::string src;
   std::shared_ptr<Kernel> kern;
   std::string key;
+  std::string prefix;  // kernel name prefix
 };
 
 std::string tune_key(const std::string& src, const Canon& cn) {
@@ -408,7 +409,7 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
   const Canon& cn = P.canon;
   LaunchArgs a;
   if (cn.spec.mode == Mode::ELEM || cn.spec.mode == Mode::FULL) {
-    L.entry = "vbe_u" + std::to_string(tc.U);
+    L.entry = P.prefix + "_u" + std::to_string(tc.U);
     L.key = P.key;
     L.fn = kernel_fn(P.kern.get(), L.entry);
     L.block = tc.block;
@@ -421,7 +422,7 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
     fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, (uintptr_t)ex->scratch.partials, (uintptr_t)ex->scratch.counters,
                tc.block, tc.U, &a);
   } else {
-    L.entry = "vbe_axis";
+    L.entry = P.prefix + "_axis";
     L.key = P.key;
     L.fn = kernel_fn(P.kern.get(), L.entry);
     int64_t nout = 1, nred = 1;
@@ -616,15 +617,24 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   for (auto& r : rp)
     if (r.op == VBE_OP_FREE) has_free = true;
   bool graphs = allow_graph && (c->cfg.flags & VBE_GRAPHS) && !has_free && !c->record;
-  uint64_t key = graphs ? batch_key(prog, n) : 0;
+  // a batch without FREE that comes again unchanged (same instructions,
+  // views and base addresses) skips analysis and code generation: its
+  // launches are replayed from a graph (VBE_GRAPHS) or one by one
+  bool cacheable = allow_graph && !has_free && !c->record;  // never for one-shot server requests
+  uint64_t key = cacheable ? (batch_key(prog, n) ^ (uint64_t)(uintptr_t)ex) : 0;
   CachedBatch* cb = nullptr;
-  if (graphs) {
+  if (cacheable) {
     cb = &c->batches[key];
     cb->key = key;
-    if (cb->exec && cb->fingerprint == fingerprint(c, rp)) {
+    auto fp = fingerprint(c, rp);
+    if (graphs && cb->exec && cb->fingerprint == fp) {
       cuda_check(cudaGraphLaunch(cb->exec, ex->stream), "cudaGraphLaunch");
       c->stats.graph_launches++;
       c->stats.kernel_launches += cb->launches;
+      return;
+    }
+    if (!graphs && !cb->eager.empty() && cb->eager_fingerprint == fp) {
+      for (auto& L : cb->eager) issue(c, ex, *L, false);
       return;
     }
   }
@@ -674,6 +684,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   }
 
   std::vector<Launch> recorded;
+  std::vector<std::shared_ptr<Launch>> issued;
   std::vector<HostAction> deferred;
   auto flush_deferred = [&]() {
     for (auto& a : deferred) do_action(c, ex, a);
@@ -702,7 +713,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
     P.run = &r;
     RunPtrs ptr = run_ptrs(c, r);
     P.canon = canonicalize(r, true, ptr.lp, ptr.sp, ptr.rp);
-    P.src = generate_source(r, P.canon, nullptr);
+    P.src = generate_source(r, P.canon, &P.prefix);
     P.key = src_key(P.src);
     P.kern = get_kernel(c, P.src);
     bool tile = P.canon.spec.mode == Mode::ELEM || P.canon.spec.mode == Mode::FULL;
@@ -738,7 +749,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       Launch L;
       L.packed = true;
       int U = 4;
-      L.entry = "vbe_pack_u" + std::to_string(U);
+      L.entry = P.prefix + "_pack_u" + std::to_string(U);
       L.key = P.key;
       L.fn = kernel_fn(P.kern.get(), L.entry);
       L.block = 256;
@@ -771,6 +782,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
         recorded.push_back(std::move(L));
       } else {
         issue(c, ex, L, false);
+        if (cacheable) issued.push_back(std::make_shared<Launch>(L));
       }
       // host actions skipped over while packing run after the pack
       for (size_t k = i + 1; k < j; ++k)
@@ -781,13 +793,21 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
     }
     TuneChoice tc = choose(c, ex, P, ptr, !capture);
     Launch L = build_single(c, ex, P, tc, ptr);
-    if (capture) recorded.push_back(std::move(L));
-    else issue(c, ex, L, false);
+    if (capture) {
+      recorded.push_back(std::move(L));
+    } else {
+      issue(c, ex, L, false);
+      if (cacheable) issued.push_back(std::make_shared<Launch>(L));
+    }
     ++i;
     if (!capture) flush_deferred();
   }
   if (!capture) {
     flush_deferred();
+    if (cacheable) {
+      cb->eager = std::move(issued);
+      cb->eager_fingerprint = fingerprint(c, rp);
+    }
     return;
   }
   // capture the recorded launches into a graph and replay it

@@ -212,9 +212,15 @@ struct Exec {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
+struct Launch;  // a recorded kernel launch (runtime.cpp)
+
 struct CachedBatch {
   uint64_t key = 0;
   int seen = 0;
+  // launches of the batch's last eager execution, replayed directly when
+  // the same batch comes again with the same base addresses
+  std::vector<std::shared_ptr<Launch>> eager;
+  std::vector<std::pair<int64_t, uintptr_t>> eager_fingerprint;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   std::vector<std::pair<int64_t, uintptr_t>> fingerprint;

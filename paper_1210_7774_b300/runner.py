@@ -147,6 +147,69 @@ class Executor:
         L.view.clear()
 
 
+class Request:
+    """A program packed as a ``vbe_request`` for the serving loop. The
+    ctypes arrays and the result buffers live as long as this object."""
+
+    def __init__(self, program: Program, results=None):
+        self.program = program
+        ids = list(program.bases)
+        index = {bid: i for i, bid in enumerate(ids)}
+        self.results = {}
+        self.bases = (V.vbe_req_base * max(1, len(ids)))()
+        self._keep = []
+        want = program.outputs if results is None else results
+        for i, bid in enumerate(ids):
+            b = program.bases[bid]
+            rb = self.bases[i]
+            rb.dtype = V.DTYPE_CODE[b.dtype]
+            rb.nelem = b.nelem
+            if b.init is not None:
+                arr = np.ascontiguousarray(b.init)
+                self._keep.append(arr)
+                rb.init = arr.ctypes.data
+            if bid in want:
+                out = np.empty(b.nelem, dtype=NP_DTYPE[b.dtype])
+                self.results[bid] = out
+                rb.result = out.ctypes.data
+        views = {}
+        for ins in program.instrs:
+            for v in (ins.out, *ins.ins):
+                if isinstance(v, View) and v not in views:
+                    views[v] = len(views) + 1
+        self.views = (V.vbe_req_view * max(1, len(views)))()
+        for v, k in views.items():
+            rv = self.views[k - 1]
+            rv.base = index[v.base]
+            rv.ndim = v.ndim
+            rv.offset = v.offset
+            for d in range(v.ndim):
+                rv.shape[d] = v.shape[d]
+                rv.strides[d] = v.strides[d]
+        dtypes = {bid: b.dtype for bid, b in program.bases.items()}
+        n = len(program.instrs)
+        self.instrs = (V.vbe_instr * max(1, n))()
+        for i, ins in enumerate(program.instrs):
+            e = self.instrs[i]
+            e.op = V.OPCODES[ins.op]
+            e.const_slot = -1
+            e.out = views[ins.out] if ins.out is not None else 0
+            for k, x in enumerate(ins.ins):
+                if isinstance(x, Const):
+                    e.const_slot = k
+                    if _const_dtype(ins, k, dtypes) in ("float32", "float64"):
+                        e.konst.f64 = float(x.value)
+                    else:
+                        e.konst.i64 = int(x.value)
+                else:
+                    e.in_[k] = views[x]
+            e.axis = ins.axis
+            e.seed = ins.seed & ((1 << 64) - 1)
+            e.key = ins.key & ((1 << 64) - 1)
+            e.step = ins.step
+        self.req = V.vbe_request(self.bases, len(ids), len(views), self.views, self.instrs, n)
+
+
 def run_program(program: Program, flags: int = V.VBE_FUSE | V.VBE_GRAPHS | V.VBE_AUTOTUNE | V.VBE_PACK,
                 outputs=None, device: int = 0) -> dict:
     """Execute ``program`` on the GPU and return ``{base id: flat array}``

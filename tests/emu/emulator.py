@@ -14,6 +14,7 @@ import ctypes
 import hashlib
 import json
 import os
+import re
 import subprocess
 import tempfile
 
@@ -46,7 +47,7 @@ extern "C" long long emu_tile(int U, const long long* w, int nw, unsigned grid, 
   P p;
   memcpy(&p, w, sizeof(P));
   g_bad = 0;
-  emu_grid(grid, block, [&]() { if (U == 1) vbe_u1(p); else if (U == 2) vbe_u2(p); else vbe_u4(p); });
+  emu_grid(grid, block, [&]() { if (U == 1) @P@_u1(p); else if (U == 2) @P@_u2(p); else @P@_u4(p); });
   return g_bad.load();
 }
 """
@@ -56,8 +57,8 @@ extern "C" long long emu_pack(int U, long long descs, long long prefix, int nins
                               long long chunk, long long work, unsigned grid, unsigned block) {
   g_bad = 0;
   emu_grid(grid, block, [&]() {
-    if (U == 1) vbe_pack_u1((const P*)descs, (const i64*)prefix, ninst, total, chunk, (unsigned*)work);
-    else vbe_pack_u4((const P*)descs, (const i64*)prefix, ninst, total, chunk, (unsigned*)work);
+    if (U == 1) @P@_pack_u1((const P*)descs, (const i64*)prefix, ninst, total, chunk, (unsigned*)work);
+    else @P@_pack_u4((const P*)descs, (const i64*)prefix, ninst, total, chunk, (unsigned*)work);
   });
   return g_bad.load();
 }
@@ -69,7 +70,7 @@ extern "C" long long emu_axis(const long long* w, int nw, unsigned grid, unsigne
   P p;
   memcpy(&p, w, sizeof(P));
   g_bad = 0;
-  emu_grid(grid, block, [&]() { vbe_axis(p); });
+  emu_grid(grid, block, [&]() { @P@_axis(p); });
   return g_bad.load();
 }
 """
@@ -86,28 +87,57 @@ class Emulator:
         self.mods = {}
         self.launches = 0
 
+    def _key(self, src: str) -> str:
+        return hashlib.sha1((src + self._emu_h).encode()).hexdigest()[:20]
+
+    @property
+    def _emu_h(self) -> str:
+        if not hasattr(self, "_emu_text"):
+            self._emu_text = open(EMU_H).read()
+        return self._emu_text
+
+    def prebuild(self, sources) -> None:
+        """Compile many sources at once (in parallel processes)."""
+        from concurrent.futures import ThreadPoolExecutor
+        todo = {self._key(s): s for s in sources}
+        todo = [s for h, s in todo.items() if not os.path.exists(os.path.join(self.dir, f"emu_{h}.so"))]
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as pool:
+            list(pool.map(self.build, todo))
+
     def module(self, src: str):
-        h = hashlib.sha1((src + open(EMU_H).read()).encode()).hexdigest()[:20]
+        h = self._key(src)
         if h in self.mods:
             return self.mods[h]
+        so = self.build(src)
+        return self._load(h, so)
+
+    def build(self, src: str) -> str:
+        h = self._key(src)
         so = os.path.join(self.dir, f"emu_{h}.so")
         if not os.path.exists(so):
             parts = [f'#include "{EMU_H}"', "#include <type_traits>", _GLOBALS, src, _WRAP_COMMON]
-            if "vbe_u1(" in src:
-                parts.append(_WRAP_TILE)
-            if "vbe_pack_u1(" in src:
-                parts.append(_WRAP_PACK)
-            if "vbe_axis(" in src:
-                parts.append(_WRAP_AXIS)
+            names = re.findall(r"__global__ void __launch_bounds__\(\d+\) (\w+)\(", src)
+            prefix = names[0].rsplit("_", 1)[0] if names else "vbe"
+            if prefix.endswith("_pack"):
+                prefix = prefix[:-5]
+            if prefix + "_u1" in names:
+                parts.append(_WRAP_TILE.replace("@P@", prefix))
+            if prefix + "_pack_u1" in names:
+                parts.append(_WRAP_PACK.replace("@P@", prefix))
+            if prefix + "_axis" in names:
+                parts.append(_WRAP_AXIS.replace("@P@", prefix))
             cpp = os.path.join(self.dir, f"emu_{h}.cpp")
             with open(cpp, "w") as f:
                 f.write("\n".join(parts))
             tmp = so + f".{os.getpid()}.tmp"
-            r = subprocess.run(["g++", "-std=c++20", "-O1", "-fPIC", "-shared", "-pthread", "-w", cpp, "-o", tmp],
+            r = subprocess.run(["g++", "-std=c++20", "-O0", "-fPIC", "-shared", "-pthread", "-w", cpp, "-o", tmp],
                                stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
             if r.returncode != 0:
                 raise EmulationError("emulation build failed:\n" + r.stdout.decode()[-4000:])
             os.replace(tmp, so)
+        return so
+
+    def _load(self, h: str, so: str):
         lib = ctypes.CDLL(so)
         lib.emu_set_ranges.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
         lib.emu_msg.restype = ctypes.c_char_p
@@ -141,10 +171,10 @@ class Emulator:
                                    L["chunk"], L["work"], L["grid"], L["block"])
             else:
                 w = (ctypes.c_longlong * len(L["words"]))(*L["words"])
-                if entry == "vbe_axis":
+                if entry.endswith("_axis"):
                     bad = lib.emu_axis(w, len(L["words"]), L["grid"], L["block"])
                 else:
-                    bad = lib.emu_tile(int(entry[5:]), w, len(L["words"]), L["grid"], L["block"])
+                    bad = lib.emu_tile(int(entry.rsplit("_u", 1)[1]), w, len(L["words"]), L["grid"], L["block"])
             if bad:
                 raise EmulationError(f"{entry} (grid {L['grid']}, block {L['block']}): "
                                      f"{'parameter block size mismatch' if bad < 0 else lib.emu_msg().decode()}")

@@ -4,6 +4,7 @@ launch shapes and parameter blocks as on the GPU) and the emulator runs
 them with every memory access bounds-checked. Results must match the
 oracle under the same rules as the GPU parity tests. This checks the index
 arithmetic of every kernel form on the host before it runs on a device."""
+import json
 import os
 
 import pytest
@@ -30,17 +31,35 @@ MODES = {
 SHAPES = [(64, 1, 2), (32, 4, 3), (128, 2, 1)]
 
 
-def emulate(program, flags, shape):
+def emulate(program, flags, shape, run=True):
     block, U, sms = shape
     os.environ["VBE_RECORD_BLOCK"] = str(block)
     os.environ["VBE_RECORD_U"] = str(U)
     os.environ["VBE_RECORD_SMS"] = str(sms)
+    sources = []
     with Executor(flags) as ex:
         L = ex.load(program)
         for k in range(len(L.batches)):
             ex.submit(L, k)
-            EMU.run(V.vbe_debug_take_launches(ex.ctx))
+            rec = V.vbe_debug_take_launches(ex.ctx)
+            if run:
+                EMU.run(rec)
+            else:
+                sources += list(json.loads(rec)["sources"].values())
+        if not run:
+            return sources
         return {bid: ex.read(L, bid) for bid in program.outputs}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _prebuild_kernels():
+    """Record every case once (launch records do not depend on data) and
+    compile all distinct kernel sources in parallel before the tests run."""
+    srcs = []
+    for case in CASES:
+        for mode, flags in MODES.items():
+            srcs += emulate(case.program, flags, SHAPES[hash(case.name) % len(SHAPES)], run=False)
+    EMU.prebuild(srcs)
 
 
 @pytest.mark.parametrize("mode", list(MODES))

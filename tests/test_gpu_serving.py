@@ -1,0 +1,107 @@
+"""Serving loop on the GPU: concurrent clients, continuous batching under a
+memory cap, and each request's result identical alone and in the mix."""
+import os
+import threading
+
+import numpy as np
+import pytest
+
+from paper_1210_7774_b300 import build
+
+build.build()
+
+from paper_1210_7774_b300 import vbe as V  # noqa: E402
+from paper_1210_7774_b300.runner import Request  # noqa: E402
+
+import oracle  # noqa: E402
+from parity_cases import assert_exact  # noqa: E402
+from workloads.serving import blackscholes_request, jacobi_request, request_mix, request_program  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
+FLAGS = V.VBE_FUSE | V.VBE_PACK
+
+
+def small_mix(n):
+    """The request mix with sizes scaled down so the test stays short."""
+    out = []
+    for kind, prm in request_mix(n, seed=5):
+        prm = dict(prm)
+        if kind == "jacobi":
+            prm["n"] = 32 + (prm["n"] // 16)
+            prm["iters"] = min(prm["iters"], 6)
+        else:
+            prm["n"] = max(1, prm["n"] // 64)
+        out.append((kind, prm))
+    return out
+
+
+def serve(programs, slots=4, cap=8 << 30, threads=8):
+    ctx = V.vbe_init(0, FLAGS, 0, None, CACHE)
+    srv = V.vbe_server_create(ctx, slots, cap, FLAGS)
+    reqs = [Request(p) for p in programs]
+    results = [None] * len(reqs)
+
+    def client(k):
+        for i in range(k, len(reqs), threads):
+            rid = V.vbe_server_submit(srv, reqs[i].req)
+            results[i] = V.vbe_server_wait(srv, rid, 120_000_000_000)
+
+    th = [threading.Thread(target=client, args=(k,)) for k in range(threads)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    V.vbe_server_destroy(srv)
+    V.vbe_finalize(ctx)
+    return reqs, results
+
+
+def test_requests_match_oracle_and_solo_results():
+    mix = small_mix(40)
+    programs = [request_program(k, p) for k, p in mix]
+    reqs, res = serve(programs)
+    assert all(r.status == 0 for r in res)
+    assert all(r.t_arrive_ns <= r.t_admit_ns <= r.t_done_ns for r in res)
+    # each result equals the same request run alone (bitwise: kernels and
+    # launch shapes depend only on the request, never on co-tenants)
+    solo_reqs, _ = serve(programs[:12], slots=1, threads=1)
+    for a, b in zip(reqs[:12], solo_reqs):
+        for bid in a.results:
+            assert_exact(a.results[bid], b.results[bid], a.program.name)
+    # and the oracle agrees (float tolerance for the transcendental pricing)
+    for r in reqs[:10]:
+        want = oracle.run(r.program)
+        for bid, got in r.results.items():
+            if r.program.meta["kind"] == "jacobi" and bid == r.program.outputs[0]:
+                assert_exact(got, want[bid], r.program.name)
+            elif r.program.meta["kind"] == "blackscholes":
+                tol = 1e-12 if got.dtype == np.float64 else 1e-5
+                assert np.max(np.abs(got.astype(np.float64) - want[bid].astype(np.float64))) <= tol * 100.0
+
+
+def test_admission_respects_memory_cap_and_rejects_oversize():
+    programs = [jacobi_request(64, 2, "float64", s) for s in range(6)]
+    foot = sum(b.nelem * 8 for b in programs[0].bases.values())
+    # a cap that fits one request at a time: all complete, one by one
+    reqs, res = serve(programs, slots=4, cap=foot + 1024, threads=3)
+    assert all(r.status == 0 for r in res)
+    spans = sorted((r.t_admit_ns, r.t_done_ns) for r in res)
+    for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
+        assert a1 >= d0 - 1e6  # admitted only after the previous one finished
+    ctx = V.vbe_init(0, FLAGS, 0, None, CACHE)
+    srv = V.vbe_server_create(ctx, 2, foot // 2, FLAGS)
+    big = Request(programs[0])
+    with pytest.raises(V.VbeError) as e:
+        V.vbe_server_submit(srv, big.req)
+    assert e.value.code == -6
+    V.vbe_server_destroy(srv)
+    V.vbe_finalize(ctx)
+
+
+def test_blackscholes_request_random_inputs_are_in_range():
+    p = blackscholes_request(5000, "float64", 3)
+    reqs, res = serve([p], slots=1, threads=1)
+    call = reqs[0].results[p.outputs[0]]
+    put = reqs[0].results[p.outputs[1]]
+    assert np.all(call >= -1e-9) and np.all(put >= -1e-9) and np.all(call <= 100.0)
