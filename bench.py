@@ -160,13 +160,35 @@ def kernel_hash(ex, L):
     return hashlib.sha1("".join(srcs).encode()).hexdigest()[:16]
 
 
-def measured_traffic(name, khash):
+def measured_counters(name, khash):
+    """ncu counters recorded for this kernel (profiles/traffic.json), or None
+    when the kernel has changed since they were taken."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)[name]
-        return t["dram_bytes_per_launch"] if t.get("kernel_hash") == khash else None
+        return t if t.get("kernel_hash") == khash else None
     except Exception:
         return None
+
+
+# B300: 148 SMs; the FP64 pipe retires 2 lanes per clock per SM (1/64 of the
+# FP32 rate; 1.97/clk/SM measured by ncu on the Black-Scholes kernel)
+FP64_LANES_PER_SM_CLK = 2
+SMS = 148
+
+
+def roofline_f64(achieved_gbs, hbm, src, counters, n, sec, clk_mhz):
+    hbm_part = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                "peak_source": src}
+    if not counters or "fp64_inst_per_unit" not in counters:
+        hbm_part["traffic"] = counters["dram_bytes_per_launch"] if counters else None
+        return hbm_part
+    peak = SMS * FP64_LANES_PER_SM_CLK * clk_mhz * 1e6 / 1e9
+    ach = counters["fp64_inst_per_unit"] * n / sec / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G FP64-inst/s", "frac": ach / peak,
+            "peak_source": f"derived: {SMS} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes/clk x {clk_mhz:.0f} MHz",
+            "work": f"{counters['fp64_inst_per_unit']:.0f} FP64 instructions per option (ncu, this kernel)",
+            "traffic": counters["dram_bytes_per_launch"], "hbm": hbm_part}
 
 
 def gpu_blackscholes(args, rank, world, local):
@@ -435,9 +457,9 @@ def main():
         "float32": {"value": f32["fused"]["GB/s"], "hbm_fraction": f32["fused"]["GB/s"] / hbm,
                     "ms_per_step": f32["fused"]["sec"] * 1e3, "plain_value": f32["plain"]["GB/s"],
                     "speedup_vs_plain": f32["plain"]["sec"] / f32["fused"]["sec"]},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "peak_source": src, "traffic": measured_traffic("blackscholes_f64", f64["kernel_hash"]),
-                     "kernel_hash": f64["kernel_hash"]},
+        "roofline": dict(roofline_f64(achieved, hbm, src, measured_counters("blackscholes_f64", f64["kernel_hash"]),
+                                      args.options, sec, ck.get("sm_mhz") or 2032.0),
+                         kernel_hash=f64["kernel_hash"]),
         "e2e": f64["e2e"],
         "gpu_launches": int(round(f64["fused"]["launches_per_step"] * args.steps)),
         "clocks": ck,

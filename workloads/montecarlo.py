@@ -59,7 +59,9 @@ def montecarlo_pi(n_inst: int = 256, seed: int = SEED + 4, sizes=None, draw_seed
         b.emit("LESS_EQUAL", cv, xv, Const(1.0))
         b.emit("CAST", civ, cv)
         b.emit("ADD_REDUCE", b.view(count, i, (), ()), civ, axis=0)
-        b.free(x, y, c, ci)
+        # the temporaries' values are dead; the handles stay valid so the
+        # same batch can be submitted again
+        b.discard(x, y, c, ci)
     b.sync(count)
     p = b.build([count])
     p.meta.update(sizes=sizes, count=count, samples=int(sizes.sum()), seed=draw_seed)
