@@ -228,6 +228,20 @@ int vbe_get_stats(vbe_ctx* ctx, vbe_stats* out);
 const char* vbe_strerror(int code);
 const char* vbe_last_error(vbe_ctx* ctx);
 
+/* Sum of n float64 values x[0..n) into *out (both device pointers), on
+ * `stream` (a cudaStream_t, or NULL), allocating nothing. The paper has no
+ * counterpart: this is for callers that must not let a library allocate
+ * device memory (code captured into a CUDA graph by its caller, inference
+ * plugin enqueue functions, real-time loops). The reduction's scratch (one
+ * partial per 16,384 elements and a completion counter) is a fixed 512 KiB
+ * array inside the library, held by every GPU that loads it until exit, so
+ * n is limited to 2^30 (VBE_ERR_INVALID beyond, or for null pointers). The
+ * first call on a device looks up the array's device address: make it
+ * before any stream capture. Calls share the array: calls that overlap on
+ * the GPU race; serialise them. Summation order depends only on n.
+ * VBE_ERR_CUDA if a CUDA call fails. No context is needed. */
+int vbe_reduce_add_f64_noalloc(const double* x, int64_t n, double* out, void* stream);
+
 /* ------------------------------------------------------------ serving */
 /* A request is a self-contained program executed by the server loop:
  * bases (with optional host input and result buffers), views over them

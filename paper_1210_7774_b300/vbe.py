@@ -112,6 +112,7 @@ _SIGS = {
     "vbe_server_submit": [_P, POINTER(vbe_request), POINTER(c_int64)],
     "vbe_server_wait": [_P, c_int64, c_int64, POINTER(vbe_request_result)],
     "vbe_server_destroy": [_P],
+    "vbe_reduce_add_f64_noalloc": [c_void_p, c_int64, c_void_p, c_void_p],
 }
 EXPORTED = tuple(_SIGS)
 for _name, _args in _SIGS.items():
@@ -263,3 +264,9 @@ def vbe_server_wait(srv, req_id: int, timeout_ns: int = -1) -> vbe_request_resul
 
 def vbe_server_destroy(srv) -> None:
     _check(lib.vbe_server_destroy(srv))
+
+
+def vbe_reduce_add_f64_noalloc(x_ptr: int, n: int, out_ptr: int, stream: int | None = None) -> None:
+    code = lib.vbe_reduce_add_f64_noalloc(x_ptr, n, out_ptr, stream or None)
+    if code < 0:
+        raise VbeError(code, "vbe_reduce_add_f64_noalloc")
