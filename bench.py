@@ -185,10 +185,17 @@ def roofline_f64(achieved_gbs, hbm, src, counters, n, sec, clk_mhz):
         return hbm_part
     peak = SMS * FP64_LANES_PER_SM_CLK * clk_mhz * 1e6 / 1e9
     ach = counters["fp64_inst_per_unit"] * n / sec / 1e9
-    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G FP64-inst/s", "frac": ach / peak,
-            "peak_source": f"derived: {SMS} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes/clk x {clk_mhz:.0f} MHz",
-            "work": f"{counters['fp64_inst_per_unit']:.0f} FP64 instructions per option (ncu, this kernel)",
-            "traffic": counters["dram_bytes_per_launch"], "hbm": hbm_part}
+    out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G FP64-inst/s", "frac": ach / peak,
+           "peak_source": f"derived: {SMS} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes/clk x {clk_mhz:.0f} MHz",
+           "work": f"{counters['fp64_inst_per_unit']:.1f} FP64 instructions per option (ncu, this kernel)",
+           "traffic": counters["dram_bytes_per_launch"], "hbm": hbm_part}
+    if "inst_per_unit" in counters:
+        # all instructions against the issue rate (4 schedulers x 32 lanes per SM)
+        ipeak = SMS * 128 * clk_mhz * 1e6 / 1e12
+        iach = counters["inst_per_unit"] * n / sec / 1e12
+        out["issue"] = {"achieved": iach, "peak": ipeak, "unit": "T thread-inst/s", "frac": iach / ipeak,
+                        "work": f"{counters['inst_per_unit']:.0f} instructions per option"}
+    return out
 
 
 def gpu_blackscholes(args, rank, world, local):

@@ -133,6 +133,9 @@ enum {
   VBE_AUTOTUNE = 1u << 2,  /* time launch shapes per kernel signature and keep the fastest  */
   VBE_PACK = 1u << 3,      /* pack consecutive independent same-signature runs in one launch */
   VBE_HOST_ONLY = 1u << 4, /* no device: analysis, planning and code generation only        */
+  VBE_NATIVE_F64 = 1u << 6,/* float64 divide/sqrt/exp/log on the FP64 pipe; by default they run
+                              as integer arithmetic (correctly rounded divide and sqrt, exp/log
+                              within 1 ulp), because B300's FP64 pipe is 1/64 of its FP32 rate */
   VBE_RECORD = 1u << 5     /* host-only context whose bases live in host memory and whose
                               launches are recorded (vbe_debug_take_launches) instead of run,
                               so tests can execute the generated kernels on a CPU; implies

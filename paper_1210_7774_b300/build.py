@@ -30,11 +30,26 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+        glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+def embed_device_sources() -> None:
+    """Write _embed_sf64.inc: the device-side soft float64 code (tables and
+    functions) as one C++ raw string, which the code generator prepends to
+    kernels that need it."""
+    text = open(os.path.join(CSRC, "sf64_tables.h")).read() + "\n" + open(os.path.join(CSRC, "sf64.cuh")).read()
+    assert ")VBESF64" not in text
+    out = os.path.join(CSRC, "_embed_sf64.inc")
+    body = 'R"VBESF64(' + text + ')VBESF64"\n'
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    embed_device_sources()
     if not force and not _stale():
         return LIB
     nvcc = os.path.join(CUDA, "bin", "nvcc")

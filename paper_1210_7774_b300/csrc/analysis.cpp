@@ -161,6 +161,7 @@ struct Builder {
 
   void start(const ViewDesc& shape_view) {
     cur = Run();
+    cur.soft_f64 = (c->cfg.flags & VBE_NATIVE_F64) == 0;
     cur.shape.assign(shape_view.shape, shape_view.shape + shape_view.ndim);
     load_views.clear();
     written.clear();

@@ -381,8 +381,37 @@ template <class T, int E> __device__ __forceinline__ void vbe_vstore(T* p, const
   for (int e = 0; e < E; ++e) u.t[e] = o[e];
   *reinterpret_cast<V*>(p) = u.v;
 }
+__device__ __forceinline__ unsigned long long vbe_umulhi(unsigned long long a, unsigned long long b) {
+  return __umul64hi(a, b);
+}
+__device__ __forceinline__ long long vbe_smulhi(long long a, long long b) { return __mul64hi(a, b); }
+__device__ __forceinline__ int vbe_clz64(unsigned long long x) { return __clzll((long long)x); }
+__device__ __forceinline__ float vbe_rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float vbe_rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 #endif
 )CUDA";
+
+// float64 divide/sqrt/exp/log on the integer pipes (sf64_tables.h + sf64.cuh)
+const char* kSf64 =
+#include "_embed_sf64.inc"
+    ;
+
+bool uses_soft_f64(const Run& r) {
+  if (!r.soft_f64) return false;
+  for (auto& s : r.steps)
+    if (s.dt_in == VBE_FLOAT64 &&
+        (s.op == VBE_OP_DIVIDE || s.op == VBE_OP_SQRT || s.op == VBE_OP_EXP || s.op == VBE_OP_LOG))
+      return true;
+  return false;
+}
 
 struct Gen {
   const Run& r;
@@ -417,12 +446,20 @@ struct Gen {
       case VBE_OP_ADD: return i64t ? "vbe_iadd(" + a + "," + b + ")" : "(" + a + " + " + b + ")";
       case VBE_OP_SUBTRACT: return i64t ? "vbe_isub(" + a + "," + b + ")" : "(" + a + " - " + b + ")";
       case VBE_OP_MULTIPLY: return i64t ? "vbe_imul(" + a + "," + b + ")" : "(" + a + " * " + b + ")";
-      case VBE_OP_DIVIDE: return "(" + a + " / " + b + ")";
+      case VBE_OP_DIVIDE:
+        if (r.soft_f64 && s.dt_in == VBE_FLOAT64) return "vbe_ddiv(" + a + ", " + b + ")";
+        return "(" + a + " / " + b + ")";
       case VBE_OP_MAXIMUM: return "vbe_max(" + a + "," + b + ")";
       case VBE_OP_MINIMUM: return "vbe_min(" + a + "," + b + ")";
-      case VBE_OP_SQRT: return std::string(f32 ? "sqrtf(" : "sqrt(") + a + ")";
-      case VBE_OP_EXP: return std::string(f32 ? "expf(" : "exp(") + a + ")";
-      case VBE_OP_LOG: return std::string(f32 ? "logf(" : "log(") + a + ")";
+      case VBE_OP_SQRT:
+        if (r.soft_f64 && !f32) return "vbe_dsqrt(" + a + ")";
+        return std::string(f32 ? "sqrtf(" : "sqrt(") + a + ")";
+      case VBE_OP_EXP:
+        if (r.soft_f64 && !f32) return "vbe_dexp(" + a + ")";
+        return std::string(f32 ? "expf(" : "exp(") + a + ")";
+      case VBE_OP_LOG:
+        if (r.soft_f64 && !f32) return "vbe_dlog(" + a + ")";
+        return std::string(f32 ? "logf(" : "log(") + a + ")";
       case VBE_OP_ABSOLUTE:
         return i64t ? "vbe_iabs(" + a + ")" : std::string(f32 ? "fabsf(" : "fabs(") + a + ")";
       case VBE_OP_NEGATIVE: return i64t ? "vbe_ineg(" + a + ")" : "(-" + a + ")";
@@ -836,6 +873,7 @@ std::string generate_source(const Run& r, const Canon& c, std::string* entry_pre
   g.o << "// generated by libvbe: " << r.steps.size() << " operations, " << r.loads.size() << " loads, "
       << r.stores.size() << " stores\n";
   g.o << kPrelude;
+  if (uses_soft_f64(r)) g.o << kSf64 << "\n";
   g.emit_elem();
   g.emit_block_reduce();
   if (tile_mode(c.spec.mode)) {

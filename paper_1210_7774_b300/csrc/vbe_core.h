@@ -123,6 +123,7 @@ struct Run {
   std::vector<int> instrs;    // batch indices
   int nrandom = 0;
   std::vector<Operand> consts;  // constant operands, passed as parameter words
+  bool soft_f64 = false;        // float64 divide/sqrt/exp/log on the integer pipes (sf64.cuh)
   int64_t elements() const;
 };
 

@@ -33,6 +33,7 @@ extern dim3 blockDim, gridDim;
 #define __global__
 #define __device__
 #define __forceinline__ inline
+#define SF_CALL __attribute__((noinline))
 #define __launch_bounds__(x)
 #define __shared__ static
 
@@ -118,6 +119,28 @@ inline float __int_as_float(int v) {
   return f;
 }
 inline long long min(long long a, long long b) { return a < b ? a : b; }
+inline long long __double_as_longlong(double d) {
+  long long v;
+  memcpy(&v, &d, 8);
+  return v;
+}
+inline unsigned __float_as_uint(float f) {
+  unsigned v;
+  memcpy(&v, &f, 4);
+  return v;
+}
+inline float __uint_as_float(unsigned v) {
+  float f;
+  memcpy(&f, &v, 4);
+  return f;
+}
+inline unsigned long long vbe_umulhi(unsigned long long a, unsigned long long b) {
+  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+}
+inline long long vbe_smulhi(long long a, long long b) { return (long long)(((__int128)a * b) >> 64); }
+inline int vbe_clz64(unsigned long long x) { return x ? __builtin_clzll(x) : 64; }
+inline float vbe_rcp_approx(float x) { return 1.0f / x; }
+inline float vbe_rsqrt_approx(float x) { return 1.0f / std::sqrt(x); }
 
 template <class F>
 void emu_grid(unsigned grid, unsigned block, F f) {
