@@ -25,6 +25,7 @@
 // Every reduction order depends only on the launch shape, never on timing,
 // so a result is reproducible for a given signature and size.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <sstream>
 
@@ -407,10 +408,42 @@ const char* kSf64 =
 bool uses_soft_f64(const Run& r) {
   if (!r.soft_f64) return false;
   for (auto& s : r.steps)
-    if (s.dt_in == VBE_FLOAT64 &&
-        (s.op == VBE_OP_DIVIDE || s.op == VBE_OP_SQRT || s.op == VBE_OP_EXP || s.op == VBE_OP_LOG))
-      return true;
+    if (s.dt_in == VBE_FLOAT64 || s.op == VBE_OP_RANDOM) return true;
   return false;
+}
+
+bool is_simple_f64(const Step& s) {
+  if (s.dt_in != VBE_FLOAT64) return false;
+  switch (s.op) {
+    case VBE_OP_ADD: case VBE_OP_SUBTRACT: case VBE_OP_MULTIPLY: case VBE_OP_LESS: case VBE_OP_LESS_EQUAL:
+    case VBE_OP_GREATER: case VBE_OP_GREATER_EQUAL: case VBE_OP_EQUAL: case VBE_OP_NOT_EQUAL:
+      return true;
+  }
+  return false;
+}
+
+// Which float64 add/subtract/multiply/compare steps run on the integer
+// pipes. Measured on B300 (Black-Scholes, shallow water, Monte-Carlo, all in
+// float64), emulating any of them was slower than the FP64 pipe: an
+// emulated add or multiply costs about as many SM cycles on the ALU and IMAD
+// pipes as the native one does on the FP64 pipe, and its longer dependency
+// chain hides latency worse. So by default only divide, square root, exp,
+// log, the RANDOM conversion and sign operations are emulated; the
+// environment variable VBE_F64_SIMPLE=mul|all moves multiplies and
+// compares, or every simple step, to the integer pipes for experiments.
+// Either choice gives the same (correctly rounded) results.
+std::vector<char> balance_f64(const Run& r) {
+  std::vector<char> soft(r.steps.size(), 0);
+  if (!r.soft_f64) return soft;
+  static const char* pol = getenv("VBE_F64_SIMPLE");
+  const std::string policy = pol ? pol : "none";
+  for (size_t i = 0; i < r.steps.size(); ++i) {
+    const Step& s = r.steps[i];
+    if (!is_simple_f64(s)) continue;
+    if (policy == "all") soft[i] = 1;
+    if (policy == "mul" && s.op != VBE_OP_ADD && s.op != VBE_OP_SUBTRACT) soft[i] = 1;
+  }
+  return soft;
 }
 
 struct Gen {
@@ -421,7 +454,9 @@ struct Gen {
   const char* rt() const { return ctype(r.red_dtype); }
   bool kahan() const { return r.has_red && r.red_op == VBE_OP_ADD_REDUCE && r.red_dtype == VBE_FLOAT32; }
 
-  Gen(const Run& r_, const Canon& c_) : r(r_), c(c_), L(layout_of(r_, c_)) {}
+  std::vector<char> soft;  // per step: float64 add/subtract/multiply/compare emulated
+
+  Gen(const Run& r_, const Canon& c_) : r(r_), c(c_), L(layout_of(r_, c_)), soft(balance_f64(r_)) {}
 
   std::string opnd(const Operand& a) {
     if (a.kind == 0) return "l" + std::to_string(a.idx);
@@ -442,6 +477,22 @@ struct Gen {
                 d = s.nin > 2 ? opnd(s.a[2]) : "";
     bool i64t = s.dt_in == VBE_INT64;
     bool f32 = s.dt_in == VBE_FLOAT32;
+    const bool sf = r.soft_f64 && s.dt_in == VBE_FLOAT64;  // float64 on the integer pipes available
+    if (sf && soft[&s - &r.steps[0]]) {
+      switch (s.op) {
+        case VBE_OP_ADD: return "vbe_dadd(" + a + ", " + b + ")";
+        case VBE_OP_SUBTRACT: return "vbe_dsub(" + a + ", " + b + ")";
+        case VBE_OP_MULTIPLY: return "vbe_dmul(" + a + ", " + b + ")";
+        case VBE_OP_LESS: return "vbe_dlt(" + a + ", " + b + ")";
+        case VBE_OP_LESS_EQUAL: return "vbe_dle(" + a + ", " + b + ")";
+        case VBE_OP_GREATER: return "vbe_dlt(" + b + ", " + a + ")";
+        case VBE_OP_GREATER_EQUAL: return "vbe_dle(" + b + ", " + a + ")";
+        case VBE_OP_EQUAL: return "vbe_deq(" + a + ", " + b + ")";
+        case VBE_OP_NOT_EQUAL: return "(!vbe_deq(" + a + ", " + b + "))";
+      }
+    }
+    if (sf && s.op == VBE_OP_NEGATIVE) return "vbe_dneg(" + a + ")";
+    if (sf && s.op == VBE_OP_ABSOLUTE) return "vbe_dabs(" + a + ")";
     switch (s.op) {
       case VBE_OP_ADD: return i64t ? "vbe_iadd(" + a + "," + b + ")" : "(" + a + " + " + b + ")";
       case VBE_OP_SUBTRACT: return i64t ? "vbe_isub(" + a + "," + b + ")" : "(" + a + " - " + b + ")";
@@ -476,8 +527,8 @@ struct Gen {
       case VBE_OP_COPY: return a;
       case VBE_OP_RANDOM: {
         int w = L.rnd[s.random_idx];
-        return "vbe_u01((u64)p.w[" + std::to_string(w) + "], (u64)p.w[" + std::to_string(w + 1) +
-               "], (u64)p.w[" + std::to_string(w + 2) + "], (u64)m)";
+        return std::string(r.soft_f64 ? "vbe_u01s" : "vbe_u01") + "((u64)p.w[" + std::to_string(w) +
+               "], (u64)p.w[" + std::to_string(w + 1) + "], (u64)p.w[" + std::to_string(w + 2) + "], (u64)m)";
       }
     }
     fail(VBE_ERR_INVALID, "codegen: unsupported opcode");
@@ -873,7 +924,13 @@ std::string generate_source(const Run& r, const Canon& c, std::string* entry_pre
   g.o << "// generated by libvbe: " << r.steps.size() << " operations, " << r.loads.size() << " loads, "
       << r.stores.size() << " stores\n";
   g.o << kPrelude;
-  if (uses_soft_f64(r)) g.o << kSf64 << "\n";
+  if (uses_soft_f64(r))
+    g.o << kSf64 << "\n"
+        << "__device__ __forceinline__ double vbe_u01s(u64 seed, u64 key, u64 step, u64 m) {\n"
+        << "  u64 z = seed + (key + step * m + 1ull) * 0x9E3779B97F4A7C15ull;\n"
+        << "  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;\n"
+        << "  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;\n"
+        << "  return vbe_u53_to_unit((z ^ (z >> 31)) >> 11);\n}\n";
   g.emit_elem();
   g.emit_block_reduce();
   if (tile_mode(c.spec.mode)) {

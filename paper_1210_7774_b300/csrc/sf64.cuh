@@ -144,6 +144,116 @@ __device__ SF_CALL double vbe_dsqrt(double a) {
   return __longlong_as_double((sf_i64)(((sf_u64)er << 52) | (q & SF_M52)));
 }
 
+// --------------------------------------------- multiply, add, compare
+
+// a * b, correctly rounded (round to nearest, ties to even)
+__device__ __forceinline__ double vbe_dmul(double a, double b) {
+  const sf_u64 ua = (sf_u64)__double_as_longlong(a), ub = (sf_u64)__double_as_longlong(b);
+  const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
+  int e = ea + eb - 1023;
+  if (ea == 0 || ea == 0x7ff || eb == 0 || eb == 0x7ff || e < 1 || e > 2045) return a * b;
+  const sf_u64 A = ((ua & SF_M52) | SF_H52) << 11, mb = (ub & SF_M52) | SF_H52;
+  const sf_u64 hi = vbe_umulhi(A, mb), lo = A * mb;  // P = ma mb: hi = P >> 53, lo = P << 11
+  sf_u64 q, round, sticky;
+  if (hi >> 52) {  // P in [2^105, 2^106)
+    q = hi;
+    round = lo >> 63;
+    sticky = (lo << 1) != 0;
+    e += 1;
+  } else {
+    q = (hi << 1) | (lo >> 63);
+    round = (lo >> 62) & 1;
+    sticky = (lo << 2) != 0;
+  }
+  q += round & (sticky | (q & 1));
+  if (q == (SF_H52 << 1)) {
+    q >>= 1;
+    e += 1;
+  }
+  if (e > 2046) return a * b;
+  return __longlong_as_double((sf_i64)(((ua ^ ub) & SF_SIGN) | ((sf_u64)e << 52) | (q & SF_M52)));
+}
+
+// a + b, correctly rounded (round to nearest, ties to even)
+__device__ __forceinline__ double vbe_dadd(double a, double b) {
+  sf_u64 ua = (sf_u64)__double_as_longlong(a), ub = (sf_u64)__double_as_longlong(b);
+  int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
+  if (ea == 0 || ea == 0x7ff || eb == 0 || eb == 0x7ff) return a + b;
+  if ((ua & ~SF_SIGN) < (ub & ~SF_SIGN)) {  // |a| >= |b| from here on
+    const sf_u64 t = ua;
+    ua = ub;
+    ub = t;
+    const int te = ea;
+    ea = eb;
+    eb = te;
+  }
+  const int d = ea - eb;
+  const sf_u64 ma = ((ua & SF_M52) | SF_H52) << 10;  // leading bit at 62, 10 guard bits
+  const sf_u64 mb = ((ub & SF_M52) | SF_H52) << 10;
+  const sf_u64 mbs = d >= 64 ? 0 : (mb >> d);
+  const sf_u64 st = d >= 64 ? 1 : (d > 0 && (mb << (64 - d)) != 0);  // bits of b shifted out
+  int e = ea;
+  sf_u64 m;
+  if (((ua ^ ub) & SF_SIGN) == 0) {
+    m = ma + mbs;
+    if (m >> 63) {
+      m = (m >> 1) | (m & 1);
+      e += 1;
+    }
+    m |= st;
+  } else {
+    m = ma - mbs - st;  // floor of the exact difference
+    if (m == 0) return 0.0;
+    const int lz = vbe_clz64(m) - 1;
+    m = (m << lz) | st;
+    e -= lz;
+  }
+  // keep bits 62..10; bits 9..0 decide the rounding (sticky in bit 0)
+  sf_u64 q = m >> 10;
+  const sf_u64 rest = m & 0x3ff;
+  if (rest > 0x200 || (rest == 0x200 && (q & 1))) q += 1;
+  if (q == (SF_H52 << 1)) {
+    q >>= 1;
+    e += 1;
+  }
+  if (e < 1 || e > 2046) return a + b;
+  return __longlong_as_double((sf_i64)((ua & SF_SIGN) | ((sf_u64)e << 52) | (q & SF_M52)));
+}
+
+__device__ __forceinline__ double vbe_dsub(double a, double b) {
+  return vbe_dadd(a, __longlong_as_double(__double_as_longlong(b) ^ (sf_i64)SF_SIGN));
+}
+
+// IEEE ordering on bit patterns: NaN compares false (NOT_EQUAL true), -0 == +0
+__device__ __forceinline__ sf_i64 sf_key(sf_u64 u) {
+  return (u & SF_SIGN) ? -(sf_i64)(u & ~SF_SIGN) : (sf_i64)u;
+}
+__device__ __forceinline__ bool sf_isnan(sf_u64 u) { return (u & ~SF_SIGN) > 0x7ff0000000000000ull; }
+__device__ __forceinline__ bool vbe_dlt(double a, double b) {
+  const sf_u64 ua = (sf_u64)__double_as_longlong(a), ub = (sf_u64)__double_as_longlong(b);
+  return !sf_isnan(ua) && !sf_isnan(ub) && sf_key(ua) < sf_key(ub);
+}
+__device__ __forceinline__ bool vbe_dle(double a, double b) {
+  const sf_u64 ua = (sf_u64)__double_as_longlong(a), ub = (sf_u64)__double_as_longlong(b);
+  return !sf_isnan(ua) && !sf_isnan(ub) && sf_key(ua) <= sf_key(ub);
+}
+__device__ __forceinline__ bool vbe_deq(double a, double b) {
+  const sf_u64 ua = (sf_u64)__double_as_longlong(a), ub = (sf_u64)__double_as_longlong(b);
+  return !sf_isnan(ua) && !sf_isnan(ub) && sf_key(ua) == sf_key(ub);
+}
+__device__ __forceinline__ double vbe_dneg(double a) {
+  return __longlong_as_double(__double_as_longlong(a) ^ (sf_i64)SF_SIGN);
+}
+__device__ __forceinline__ double vbe_dabs(double a) {
+  return __longlong_as_double(__double_as_longlong(a) & (sf_i64)~SF_SIGN);
+}
+// v 2^-53 for an integer 0 <= v < 2^53 (exact)
+__device__ __forceinline__ double vbe_u53_to_unit(sf_u64 v) {
+  if (v == 0) return 0.0;
+  const int lz = vbe_clz64(v);  // >= 11
+  return __longlong_as_double((sf_i64)(((sf_u64)(1033 - lz) << 52) | ((v << (lz - 11)) & SF_M52)));
+}
+
 // ---------------------------------------------------- 128-bit helpers
 
 struct sf_i128 {  // two's complement, value = hi * 2^64 + lo

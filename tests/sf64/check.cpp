@@ -45,6 +45,30 @@ int main(int argc, char** argv) {
       a = std::fabs(a);
       got = vbe_dsqrt(a);
       want = std::sqrt(a);
+    } else if (!strcmp(op, "mul") || !strcmp(op, "add") || !strcmp(op, "sub")) {
+      a = mode == 0 ? rnd_double(g, -1030, 1030) : rnd_double(g, -60, 60);
+      b = mode == 1 ? rnd_double(g, -1030, 1030) : rnd_double(g, -60, 60);
+      if (mode == 2) b = a * (1.0 + (double)((int)(g() % 64) - 32) * 0x1p-52);   // near-cancellation
+      if (mode == 3) b = -a;                                                       // exact zero
+      if (mode == 4) b = std::ldexp(b, -(int)(g() % 70));                         // wide exponent gaps
+      if (mode == 5) { a = (double)(int64_t)(g() % 2000001) - 1000000; b = (double)(int64_t)(g() % 2001) - 1000; }
+      if (mode == 6) { a = 0x1p1023 * (1 + (g() % 100) * 0x1p-52); b = a; }       // overflow edge
+      if (!strcmp(op, "mul")) { got = vbe_dmul(a, b); want = a * b; }
+      else if (!strcmp(op, "add")) { got = vbe_dadd(a, b); want = a + b; }
+      else { got = vbe_dsub(a, b); want = a - b; }
+      if (got == 0 && want == 0 && std::signbit(got) != std::signbit(want)) { got = 1; want = 2; }
+    } else if (!strcmp(op, "cmp")) {
+      const double sp[] = {0.0, -0.0, INFINITY, -INFINITY, NAN, 1.0, -1.0, 0x1p-1074};
+      a = mode < 2 ? sp[g() % 8] : rnd_double(g, -5, 5);
+      b = mode < 3 ? sp[g() % 8] : (mode == 4 ? a : rnd_double(g, -5, 5));
+      int gv = vbe_dlt(a, b) + 2 * vbe_dle(a, b) + 4 * vbe_deq(a, b) + 8 * vbe_dlt(b, a);
+      int wv = (a < b) + 2 * (a <= b) + 4 * (a == b) + 8 * (b < a);
+      got = gv; want = wv;
+    } else if (!strcmp(op, "u53")) {
+      unsigned long long v = g() >> (11 + (g() % 40));
+      if (mode == 0) v = 0;
+      got = vbe_u53_to_unit(v); want = (double)v * 0x1p-53;
+      a = (double)v; b = 0;
     } else if (!strcmp(op, "exp")) {
       a = mode < 4 ? std::ldexp((double)(g() >> 11) * 0x1p-53 * 2 - 1, 10) : rnd_double(g, -45, 9);
       if (mode == 5) a = -std::fabs(a);

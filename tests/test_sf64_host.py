@@ -1,6 +1,8 @@
 """The integer-pipe float64 routines (csrc/sf64.cuh) compiled for the host
 and checked against the host's IEEE arithmetic: division and square root
-must be bit-identical (correctly rounded), exp and log within 1 ulp of a
+(and multiply, add, subtract, the comparisons and the integer-to-unit
+conversion of RANDOM) must be bit-identical (correctly rounded), exp and
+log within 1 ulp of a
 long-double reference, over millions of operands including near-1 ratios,
 exact quotients, perfect squares and the whole exponent range (operands
 outside the fast path take the native operation). The single-precision
@@ -23,7 +25,9 @@ def checker(tmp_path_factory):
     return exe
 
 
-@pytest.mark.parametrize("op,n", [("div", 2_000_000), ("sqrt", 2_000_000), ("exp", 1_000_000), ("log", 1_000_000)])
+@pytest.mark.parametrize("op,n", [("div", 2_000_000), ("sqrt", 2_000_000), ("exp", 1_000_000), ("log", 1_000_000),
+                                  ("mul", 2_000_000), ("add", 2_000_000), ("sub", 2_000_000), ("cmp", 500_000),
+                                  ("u53", 500_000)])
 def test_sf64_against_host_ieee(checker, op, n):
     for seed in (1, 2):
         r = subprocess.run([checker, op, str(n), str(seed)], stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
