@@ -78,6 +78,7 @@ int vbe_init(const vbe_config* cfg, vbe_ctx** out) {
     c.sm_count = 2;
     if (const char* e = getenv("VBE_RECORD_SMS")) c.sm_count = atoi(e);
   }
+  if (const char* e = getenv("VBE_STAGING")) c.force_bulk = atoi(e);
   c.device = cfg->device;
   if (cfg->cache_dir) {
     // the context keeps its own copy of the path
@@ -99,6 +100,7 @@ int vbe_init(const vbe_config* cfg, vbe_ctx** out) {
     uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool
     cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
+  if (!c.host_only || c.record) vbe::init_error_word(&c);
   *out = h.release();
   API_END
 }
@@ -109,6 +111,7 @@ int vbe_finalize(vbe_ctx* ctx) {
   Ctx& c = ctx->c;
   if (c.record) {
     vbe::release_exec(&c, &c.exec);
+    vbe::release_error_word(&c);
     for (auto& kv : c.host_allocs) free((void*)kv.first);
     c.host_allocs.clear();
   }
@@ -124,6 +127,7 @@ int vbe_finalize(vbe_ctx* ctx) {
     for (auto& kv : c.tickets) cudaEventDestroy(kv.second);
     cudaStreamSynchronize(c.exec.stream);
     vbe::release_exec(&c, &c.exec);
+    vbe::release_error_word(&c);
     for (auto& kv : c.kernels)
       if (kv.second->lib) cudaLibraryUnload(kv.second->lib);
     if (c.own_stream) cudaStreamDestroy(c.exec.stream);
@@ -269,6 +273,7 @@ int vbe_wait(vbe_ctx* ctx, vbe_ticket ticket, int64_t timeout_ns) {
   }
   cudaEventDestroy(it->second);
   c.tickets.erase(it);
+  vbe::check_error_word(&c);
   API_END
 }
 
@@ -283,6 +288,7 @@ int vbe_sync(vbe_ctx* ctx, vbe_base base, void* host_dst, int64_t nbytes) {
   if (nbytes > 0 && !it->second.dptr) vbe::fail(VBE_ERR_UNINIT, "base was never written");
   if (c.record) {
     if (nbytes > 0) memcpy(host_dst, it->second.dptr, (size_t)nbytes);
+    vbe::check_error_word(&c);
     return VBE_OK;
   }
   if (nbytes > 0) {
@@ -291,6 +297,7 @@ int vbe_sync(vbe_ctx* ctx, vbe_base base, void* host_dst, int64_t nbytes) {
                     "sync copy");
   }
   vbe::cuda_check(cudaStreamSynchronize(c.exec.stream), "sync");
+  vbe::check_error_word(&c);
   API_END
 }
 

@@ -45,6 +45,7 @@ struct Layout {
   int idx_st = -1;
   std::vector<int> rnd;
   int consts = -1;
+  int bulk_ch = -1, err = -1;  // tile kernels: bulk-copy chunk (elements), error word
 };
 
 bool tile_mode(Mode m) { return m == Mode::ELEM || m == Mode::FULL; }
@@ -95,6 +96,10 @@ Layout layout_of(const Run& r, const Canon& c) {
   }
   L.consts = w;
   w += (int)r.consts.size();
+  if (tile_mode(c.spec.mode)) {
+    L.bulk_ch = w++;
+    L.err = w++;
+  }
   L.nwords = std::max(w, 1);
   return L;
 }
@@ -276,7 +281,7 @@ int words_count(const Run& r, const Canon& c) { return layout_of(r, c).nwords; }
 
 void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load_ptrs,
                 const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr, uintptr_t partials,
-                uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out) {
+                uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out, int64_t chunk, uintptr_t err) {
   (void)block;
   (void)U;
   Layout L = layout_of(r, c);
@@ -326,6 +331,10 @@ void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load
       bits = (int64_t)b32;
     }
     w[L.consts + k] = bits;
+  }
+  if (L.bulk_ch >= 0) {
+    w[L.bulk_ch] = chunk;
+    w[L.err] = (int64_t)err;
   }
   int ri = 0;
   for (auto& s : r.steps) {
@@ -382,6 +391,31 @@ template <class T, int E> __device__ __forceinline__ void vbe_vstore(T* p, const
   for (int e = 0; e < E; ++e) u.t[e] = o[e];
   *reinterpret_cast<V*>(p) = u.v;
 }
+// bulk asynchronous copies (TMA engine) into shared memory, completed on an
+// mbarrier; waits are bounded and report failure instead of hanging
+__device__ __forceinline__ unsigned vbe_saddr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void vbe_mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(vbe_saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void vbe_fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void vbe_fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void vbe_mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vbe_saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void vbe_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(vbe_saddr(dst)), "l"(src), "r"(bytes), "r"(vbe_saddr(bar)) : "memory");
+}
+__device__ __forceinline__ bool vbe_mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 24); ++it) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(vbe_saddr(bar)), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+#define VBE_DYN_SMEM extern __shared__ __align__(128) unsigned char vbe_smem[]
 __device__ __forceinline__ unsigned long long vbe_umulhi(unsigned long long a, unsigned long long b) {
   return __umul64hi(a, b);
 }
@@ -740,6 +774,125 @@ struct Gen {
     o << "}\n";
   }
 
+  int bulk_slots() const {
+    int k = 0;
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      if (c.spec.load_cls[s] == 1) ++k;
+    return k;
+  }
+
+  // One-dimensional vector run with its unit-stride inputs staged through
+  // shared memory by bulk asynchronous copies: chunks of CH elements, two
+  // stages per CTA, thread 0 issues the copies of the next chunk while the
+  // block computes on the current one; the tail (n mod CH) and broadcast
+  // inputs use plain loads.
+  void emit_bulk_kernel() {
+    const int E = c.spec.E;
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_bulk(const P p) {\n"
+      << "  VBE_DYN_SMEM;\n";
+    emit_pointers("  ");
+    emit_acc_init("  ");
+    o << "  const i64 n = " << W(L.inner) << ", CH = " << W(L.bulk_ch) << ";\n"
+      << "  const i64 nfull = n / CH;\n"
+      << "  const i64 bd = blockDim.x;\n";
+    // stage layout: per stage the unit-stride slots' chunks, back to back
+    std::string stage_bytes = "(";
+    std::vector<std::string> off;
+    std::string acc = "0";
+    for (size_t s = 0; s < r.loads.size(); ++s) {
+      if (c.spec.load_cls[s] != 1) {
+        off.push_back("");
+        continue;
+      }
+      off.push_back(acc);
+      acc += " + CH * " + std::to_string(itemsize(r.loads[s].dtype));
+    }
+    stage_bytes += acc + ")";
+    o << "  const i64 SB = " << stage_bytes << ";\n"
+      << "  unsigned long long* bars = (unsigned long long*)(vbe_smem + 2 * SB);\n"
+      << "  __shared__ int s_ok;\n";
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      if (c.spec.load_cls[s] == 0) o << "  const " << T(r.loads[s].dtype) << " z" << s << " = lp" << s << "[0];\n";
+    o << "  if (threadIdx.x == 0) { vbe_mbar_init(&bars[0], 1); vbe_mbar_init(&bars[1], 1); vbe_fence_mbar_init(); }\n"
+      << "  __syncthreads();\n";
+    auto issue = [&](const std::string& pfx, const std::string& chunk, const std::string& stage) {
+      o << pfx << "{ const i64 ic = " << chunk << "; const int is = " << stage << ";\n"
+        << pfx << "  vbe_mbar_expect_tx(&bars[is], (unsigned)SB);\n";
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        if (c.spec.load_cls[s] == 1)
+          o << pfx << "  vbe_bulk_g2s(vbe_smem + is * SB + " << off[s] << ", &lp" << s << "[ic * CH], (unsigned)(CH * "
+            << itemsize(r.loads[s].dtype) << "), &bars[is]);\n";
+      o << pfx << "}\n";
+    };
+    o << "  unsigned inflight = 0;\n"
+      << "  if (threadIdx.x == 0) {\n";
+    o << "    if ((i64)blockIdx.x < nfull) {";
+    issue("      ", "(i64)blockIdx.x", "0");
+    o << "      inflight |= 1; }\n";
+    o << "    if ((i64)blockIdx.x + gridDim.x < nfull) {";
+    issue("      ", "(i64)blockIdx.x + gridDim.x", "1");
+    o << "      inflight |= 2; }\n  }\n";
+    o << "  bool failed = false;\n"
+      << "  int k = 0;\n"
+      << "  for (i64 cc = blockIdx.x; cc < nfull; cc += gridDim.x, ++k) {\n"
+      << "    const int st = k & 1;\n"
+      << "    if (threadIdx.x == 0) { s_ok = vbe_mbar_wait(&bars[st], (unsigned)((k >> 1) & 1)); if (s_ok) inflight &= ~(1u << st); }\n"
+      << "    __syncthreads();\n"
+      << "    if (!s_ok) { failed = true; break; }\n"
+      << "    for (i64 vi = threadIdx.x; vi < CH / " << E << "; vi += bd) {\n";
+    for (size_t s = 0; s < r.loads.size(); ++s)
+      if (c.spec.load_cls[s] == 1)
+        o << "      " << T(r.loads[s].dtype) << " a" << s << "[" << E << "];\n"
+          << "      vbe_vload((const " << T(r.loads[s].dtype) << "*)(vbe_smem + st * SB + " << off[s] << ") + vi * " << E
+          << ", a" << s << ");\n";
+    for (size_t s = 0; s < r.stores.size(); ++s) o << "      " << T(r.stores[s].dtype) << " b" << s << "[" << E << "];\n";
+    o << "#pragma unroll\n      for (int e = 0; e < " << E << "; ++e) {\n";
+    {
+      std::vector<std::string> lv, sv;
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        lv.push_back(c.spec.load_cls[s] == 1 ? "a" + std::to_string(s) + "[e]" : "z" + std::to_string(s));
+      for (size_t s = 0; s < r.stores.size(); ++s) sv.push_back("b" + std::to_string(s) + "[e]");
+      o << "        " << call("cc * CH + vi * " + std::to_string(E) + " + e", lv, sv) << "\n";
+    }
+    o << "      }\n";
+    for (size_t s = 0; s < r.stores.size(); ++s)
+      o << "      vbe_vstore(sp" << s << " + cc * CH + vi * " << E << ", b" << s << ");\n";
+    o << "    }\n"
+      << "    __syncthreads();\n"
+      << "    if (threadIdx.x == 0 && cc + 2 * (i64)gridDim.x < nfull) {\n"
+      << "      vbe_fence_proxy_async();\n";
+    issue("      ", "cc + 2 * (i64)gridDim.x", "st");
+    o << "      inflight |= 1u << st;\n    }\n  }\n";
+    // on a failed wait: report (the error word is mapped host memory),
+    // drain the copies still in flight (bounded) and skip the rest; a full
+    // reduction still takes part in the grid's final combine so that its
+    // completion counter stays consistent
+    o << "  if (failed) {\n"
+      << "    if (threadIdx.x == 0) {\n"
+      << "      vbe_ptr<volatile unsigned>(" << W(L.err) << ")[0] = 1u;\n"
+      << "      for (int st = 0; st < 2; ++st)\n"
+      << "        if (inflight & (1u << st)) vbe_mbar_wait(&bars[st], (unsigned)(((k + ((st - k) & 1)) >> 1) & 1));\n"
+      << "    }\n"
+      << "  } else\n";
+    // tail with plain loads
+    o << "  for (i64 e = nfull * CH + (i64)blockIdx.x * bd + threadIdx.x; e < n; e += (i64)gridDim.x * bd) {\n";
+    {
+      std::vector<std::string> lv, sv;
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        lv.push_back(c.spec.load_cls[s] == 1 ? "lp" + std::to_string(s) + "[e]" : "z" + std::to_string(s));
+      for (size_t s = 0; s < r.stores.size(); ++s) {
+        o << "    " << T(r.stores[s].dtype) << " b" << s << ";\n";
+        sv.push_back("b" + std::to_string(s));
+      }
+      o << "    " << call("e", lv, sv) << "\n";
+      for (size_t s = 0; s < r.stores.size(); ++s) o << "    sp" << s << "[e] = b" << s << ";\n";
+    }
+    o << "  }\n";
+    if (c.spec.mode == Mode::FULL)
+      emit_full_epilogue("  ", W(L.partials), "blockIdx.x", W(L.counter), "gridDim.x", W(L.red_ptr));
+    o << "}\n";
+  }
+
   void emit_vec_body(int U) {
     const int E = c.spec.E;
     o << "  const i64 n = " << W(L.inner) << ";\n"
@@ -935,6 +1088,7 @@ std::string generate_source(const Run& r, const Canon& c, std::string* entry_pre
   g.emit_block_reduce();
   if (tile_mode(c.spec.mode)) {
     for (int U : {1, 2, 4}) g.emit_tile_kernel(U);
+    if (c.spec.vec && g.bulk_slots() > 0) g.emit_bulk_kernel();
     if (c.spec.nd == 1)
       for (int U : {1, 4}) g.emit_packed_kernel(U);
   } else {

@@ -172,6 +172,43 @@ static void host_free(Ctx* c, void* p) {
   free(p);
 }
 
+// The error word: staged kernels whose bounded waits ran out set it. It
+// lives in mapped host memory, so the host reads it after a synchronisation
+// without a copy.
+void init_error_word(Ctx* c) {
+  if (c->record) {
+    c->err_word = c->err_word_dev = (unsigned*)host_alloc(c, 64);
+    return;
+  }
+  void* p = nullptr;
+  cuda_check(cudaHostAlloc(&p, 64, cudaHostAllocMapped | cudaHostAllocPortable), "cudaHostAlloc(error word)");
+  memset(p, 0, 64);
+  void* d = nullptr;
+  cuda_check(cudaHostGetDevicePointer(&d, p, 0), "cudaHostGetDevicePointer(error word)");
+  c->err_word = (unsigned*)p;
+  c->err_word_dev = (unsigned*)d;
+}
+
+void release_error_word(Ctx* c) {
+  if (!c->err_word) return;
+  if (c->record) host_free(c, c->err_word);
+  else cudaFreeHost(c->err_word);
+  c->err_word = c->err_word_dev = nullptr;
+}
+
+bool take_error_word(Ctx* c) {
+  if (!c->err_word) return false;
+  volatile unsigned* w = c->err_word;
+  if (*w == 0) return false;
+  *w = 0;
+  return true;
+}
+
+void check_error_word(Ctx* c) {
+  if (take_error_word(c))
+    fail(VBE_ERR_TIMEOUT, "a staged kernel's bulk-copy wait ran out; the results of its batch are invalid");
+}
+
 void* dev_alloc(Ctx* c, Exec* ex, int64_t bytes) {
   if (bytes <= 0) bytes = 16;
   if (c->record) {
@@ -252,6 +289,7 @@ struct Launch {
   cudaKernel_t fn = nullptr;
   std::string key, entry;          // module and kernel name (recorded launches)
   unsigned grid = 1, block = 256;
+  unsigned smem = 0;               // dynamic shared memory bytes (staged kernels)
   std::vector<int64_t> words;      // by-value parameter block (single runs)
   bool packed = false;
   std::vector<int64_t> descs;      // packed: words of every instance
@@ -265,10 +303,10 @@ struct Launch {
 
 namespace {
 
-int occupancy(cudaKernel_t fn, int block) {
+int occupancy(cudaKernel_t fn, int block, size_t smem = 0) {
   int n = 0;
   if (fn == (cudaKernel_t)(uintptr_t)1) return 2;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)fn, block, 0) != cudaSuccess || n <= 0) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)fn, block, smem) != cudaSuccess || n <= 0) {
     cudaGetLastError();
     n = std::max(1, 2048 / block);
   }
@@ -289,7 +327,8 @@ std::string words_json(const std::vector<int64_t>& w) {
 
 void record_launch(Ctx* c, Exec* ex, Launch& L) {
   std::string j = "{\"key\":\"" + L.key + "\",\"entry\":\"" + L.entry + "\",\"grid\":" +
-                  std::to_string(L.grid) + ",\"block\":" + std::to_string(L.block);
+                  std::to_string(L.grid) + ",\"block\":" + std::to_string(L.block) + ",\"smem\":" +
+                  std::to_string(L.smem);
   if (L.packed) {
     int64_t db = (int64_t)(L.descs.size() * 8), pb = (int64_t)(L.prefix.size() * 8);
     char* d = (char*)dev_alloc(c, ex, db + pb);  // kept until the context ends
@@ -338,7 +377,7 @@ void issue(Ctx* c, Exec* ex, Launch& L, bool capturing) {
     }
   } else {
     void* args[] = {(void*)L.words.data()};
-    cuda_check(cudaLaunchKernel((const void*)L.fn, dim3(L.grid), dim3(L.block), args, 0, s), "launch");
+    cuda_check(cudaLaunchKernel((const void*)L.fn, dim3(L.grid), dim3(L.block), args, L.smem, s), "launch");
   }
   if (!capturing) c->stats.kernel_launches++;
 }
@@ -370,6 +409,31 @@ void allocate_outputs(Ctx* c, Exec* ex, const Run& r) {
     BaseRec& br = c->bases[s.base];
     if (!br.dptr) fail(VBE_ERR_UNINIT, "a run reads base " + std::to_string(s.base) + " which was never written");
   }
+}
+
+// bytes of shared memory one element of a staged run occupies in one stage
+int64_t bulk_bytes_per_elem(const Run& r, const Canon& cn) {
+  int64_t b = 0;
+  for (size_t s = 0; s < r.loads.size(); ++s)
+    if (cn.spec.load_cls[s] == 1) b += itemsize(r.loads[s].dtype);
+  return b;
+}
+
+constexpr int64_t kBulkSmemMax = 200 * 1024;
+
+// a staged launch needs the vector form, at least one unit-stride input,
+// room for two stages and 16-byte aligned sources for the bulk copies
+bool bulk_ok(const Run& r, const Canon& cn, const RunPtrs& ptr, int64_t CH) {
+  if (!cn.spec.vec || CH <= 0 || CH % 16 != 0) return false;
+  if (cn.spec.mode != Mode::ELEM && cn.spec.mode != Mode::FULL) return false;
+  int64_t bpe = bulk_bytes_per_elem(r, cn);
+  if (bpe == 0 || 2 * CH * bpe + 64 > kBulkSmemMax || cn.dims[0] < CH) return false;
+  for (size_t s = 0; s < r.loads.size(); ++s) {
+    if (cn.spec.load_cls[s] != 1) continue;
+    uintptr_t a = ptr.lp[s] + (uintptr_t)(r.loads[s].offset * itemsize(r.loads[s].dtype));
+    if (a % 16) return false;
+  }
+  return true;
 }
 
 int64_t tiles_of(const Canon& cn, int block, int U) {
@@ -408,7 +472,26 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
   const Run& r = *P.run;
   const Canon& cn = P.canon;
   LaunchArgs a;
-  if (cn.spec.mode == Mode::ELEM || cn.spec.mode == Mode::FULL) {
+  if (tc.bulk_chunk > 0 && bulk_ok(r, cn, ptr, tc.bulk_chunk)) {
+    // inputs staged through shared memory: two stages of CH elements per unit-stride input
+    const int64_t CH = tc.bulk_chunk;
+    L.entry = P.prefix + "_bulk";
+    L.key = P.key;
+    L.fn = kernel_fn(P.kern.get(), L.entry);
+    L.block = tc.block;
+    L.smem = (unsigned)(2 * CH * bulk_bytes_per_elem(r, cn) + 64);
+    if (!c->record)
+      cuda_check(cudaKernelSetAttributeForDevice(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem,
+                                                 c->device),
+                 "dynamic shared memory attribute");
+    int64_t chunks = std::max<int64_t>(1, cn.dims[0] / CH);
+    int64_t cap = (int64_t)occupancy(L.fn, tc.block, L.smem) * c->sm_count;
+    int64_t g = std::min(chunks, cap);
+    if (cn.spec.mode == Mode::FULL) g = std::min<int64_t>(g, ex->scratch.n_partials);
+    L.grid = (unsigned)std::max<int64_t>(1, g);
+    fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, (uintptr_t)ex->scratch.partials, (uintptr_t)ex->scratch.counters,
+               tc.block, 1, &a, CH, (uintptr_t)c->err_word_dev);
+  } else if (cn.spec.mode == Mode::ELEM || cn.spec.mode == Mode::FULL) {
     L.entry = P.prefix + "_u" + std::to_string(tc.U);
     L.key = P.key;
     L.fn = kernel_fn(P.kern.get(), L.entry);
@@ -420,7 +503,7 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
     if (cn.spec.mode == Mode::FULL) g = std::min<int64_t>(g, ex->scratch.n_partials);
     L.grid = (unsigned)std::max<int64_t>(1, g);
     fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, (uintptr_t)ex->scratch.partials, (uintptr_t)ex->scratch.counters,
-               tc.block, tc.U, &a);
+               tc.block, tc.U, &a, 0, (uintptr_t)c->err_word_dev);
   } else {
     L.entry = P.prefix + "_axis";
     L.key = P.key;
@@ -479,11 +562,23 @@ TuneChoice autotune(Ctx* c, Exec* ex, Prepared& P, const RunPtrs& real) {
     cudaEventCreate(&ex->ev0);
     cudaEventCreate(&ex->ev1);
   }
-  for (int block : {128, 256, 512}) {
+  std::vector<TuneChoice> cands;
+  for (int block : {128, 256, 512})
     for (int U : {1, 2, 4}) {
       TuneChoice tc;
       tc.block = block;
       tc.U = U;
+      cands.push_back(tc);
+    }
+  for (int block : {256, 512})
+    for (int ch : {1024, 2048, 4096}) {
+      TuneChoice tc;
+      tc.block = block;
+      tc.bulk_chunk = ch;
+      if (bulk_ok(r, P.canon, real, ch)) cands.push_back(tc);
+    }
+  for (const TuneChoice& tc : cands) {
+    {
       Launch L = build_single(c, ex, P, tc, ptr);
       issue(c, ex, L, false);  // warm
       c->stats.kernel_launches--;
@@ -513,6 +608,13 @@ TuneChoice choose(Ctx* c, Exec* ex, Prepared& P, const RunPtrs& ptr, bool may_tu
     TuneChoice tc;
     tc.block = c->rec_block;
     tc.U = c->rec_U;
+    tc.bulk_chunk = c->force_bulk;
+    return tc;
+  }
+  if (c->force_bulk > 0 && bulk_ok(*P.run, P.canon, ptr, c->force_bulk)) {
+    TuneChoice tc;
+    tc.block = 512;
+    tc.bulk_chunk = c->force_bulk;
     return tc;
   }
   std::string tk = tune_key(P.src, P.canon);

@@ -194,6 +194,7 @@ void loop(vbe_server* s) {
       cudaError_t e = cudaEventQuery(r->ev);
       if (e == cudaErrorNotReady) continue;
       if (e != cudaSuccess) r->res.status = VBE_ERR_CUDA;
+      else if (vbe::take_error_word(&s->ctx->c)) r->res.status = VBE_ERR_TIMEOUT;
       finish_request(s, r);
       r->res.t_done_ns = now_ns();
       r->done = true;

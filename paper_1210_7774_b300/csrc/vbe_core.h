@@ -176,7 +176,8 @@ struct LaunchArgs {
 };
 void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load_ptrs,
                 const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr, uintptr_t partials,
-                uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out);
+                uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out, int64_t chunk = 0,
+                uintptr_t err = 0);
 int words_count(const Run& r, const Canon& c);
 
 // ----------------------------------------------------------------- context
@@ -198,6 +199,7 @@ struct Kernel {
 struct TuneChoice {
   int block = 256;
   int U = 2;
+  int bulk_chunk = 0;  // > 0: stage unit-stride inputs through shared memory in chunks of this many elements
   int grid_mult = 0;  // 0: enough CTAs for the work (capped by residency)
 };
 
@@ -257,6 +259,10 @@ struct Ctx {
   std::map<uintptr_t, size_t> host_allocs;
   std::vector<std::string> rec_launches;
   std::unordered_map<std::string, std::string> rec_sources;
+  int force_bulk = 0;  // VBE_STAGING: stage every eligible run in chunks of this many elements
+  // set by staged kernels whose bounded waits ran out (mapped host memory)
+  unsigned* err_word = nullptr;
+  unsigned* err_word_dev = nullptr;
 };
 
 // analysis
@@ -272,6 +278,10 @@ void* dev_alloc(Ctx* c, Exec* ex, int64_t bytes);
 void dev_free(Ctx* c, Exec* ex, void* p, int64_t bytes);
 void ensure_scratch(Ctx* c, Exec* ex, int64_t partials, int64_t counters);
 void release_exec(Ctx* c, Exec* ex);
+void init_error_word(Ctx* c);
+void release_error_word(Ctx* c);
+bool take_error_word(Ctx* c);  // true (and cleared) when a staged kernel reported a failed wait
+void check_error_word(Ctx* c);  // fails with VBE_ERR_TIMEOUT when take_error_word is true
 uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull);
 std::string hex64(uint64_t v);
 

@@ -64,6 +64,17 @@ extern "C" long long emu_pack(int U, long long descs, long long prefix, int nins
 }
 """
 
+_WRAP_BULK = """
+extern "C" long long emu_bulk(const long long* w, int nw, unsigned grid, unsigned block) {
+  if (emu_check_words(nw)) return -1;
+  P p;
+  memcpy(&p, w, sizeof(P));
+  g_bad = 0;
+  emu_grid(grid, block, [&]() { @P@_bulk(p); });
+  return g_bad.load();
+}
+"""
+
 _WRAP_AXIS = """
 extern "C" long long emu_axis(const long long* w, int nw, unsigned grid, unsigned block) {
   if (emu_check_words(nw)) return -1;
@@ -126,6 +137,8 @@ class Emulator:
                 parts.append(_WRAP_PACK.replace("@P@", prefix))
             if prefix + "_axis" in names:
                 parts.append(_WRAP_AXIS.replace("@P@", prefix))
+            if prefix + "_bulk" in names:
+                parts.append(_WRAP_BULK.replace("@P@", prefix))
             cpp = os.path.join(self.dir, f"emu_{h}.cpp")
             with open(cpp, "w") as f:
                 f.write("\n".join(parts))
@@ -145,6 +158,9 @@ class Emulator:
             lib.emu_tile.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint,
                                      ctypes.c_uint]
             lib.emu_tile.restype = ctypes.c_longlong
+        if hasattr(lib, "emu_bulk"):
+            lib.emu_bulk.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
+            lib.emu_bulk.restype = ctypes.c_longlong
         if hasattr(lib, "emu_axis"):
             lib.emu_axis.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
             lib.emu_axis.restype = ctypes.c_longlong
@@ -171,7 +187,9 @@ class Emulator:
                                    L["chunk"], L["work"], L["grid"], L["block"])
             else:
                 w = (ctypes.c_longlong * len(L["words"]))(*L["words"])
-                if entry.endswith("_axis"):
+                if entry.endswith("_bulk"):
+                    bad = lib.emu_bulk(w, len(L["words"]), L["grid"], L["block"])
+                elif entry.endswith("_axis"):
                     bad = lib.emu_axis(w, len(L["words"]), L["grid"], L["block"])
                 else:
                     bad = lib.emu_tile(int(entry.rsplit("_u", 1)[1]), w, len(L["words"]), L["grid"], L["block"])

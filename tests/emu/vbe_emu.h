@@ -85,6 +85,24 @@ inline void vbe_vstore(CP<T> p, const T (&o)[E]) {
   for (int e = 0; e < E; ++e) p.p[e] = o[e];
 }
 
+template <class T, int E>
+inline void vbe_vload(const T* p, T (&o)[E]) {  // shared-memory source (unchecked)
+  for (int e = 0; e < E; ++e) o[e] = p[e];
+}
+// bulk copies complete at once on the host; the barriers have nothing to wait for
+#define VBE_DYN_SMEM static unsigned char vbe_smem[262144] __attribute__((aligned(128)))
+inline void vbe_mbar_init(unsigned long long*, unsigned) {}
+inline void vbe_fence_mbar_init() {}
+inline void vbe_fence_proxy_async() {}
+inline void vbe_mbar_expect_tx(unsigned long long*, unsigned) {}
+inline bool vbe_mbar_wait(unsigned long long*, unsigned) { return true; }
+inline void vbe_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long*) {
+  if ((((uintptr_t)dst) | ((uintptr_t)src) | bytes) % 16 != 0 && g_bad.fetch_add(1) == 0)
+    snprintf(g_bad_msg, sizeof g_bad_msg, "bulk copy not 16-byte aligned: %p <- %p, %u bytes", dst, src, bytes);
+  if (!emu_ok(src, bytes)) return;
+  memcpy(dst, src, bytes);
+}
+
 inline void __syncthreads() { g_block_bar->arrive_and_wait(); }
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 inline unsigned atomicAdd(CP<unsigned> p, unsigned v) {

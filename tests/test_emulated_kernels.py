@@ -25,19 +25,27 @@ EMU = Emulator()
 MODES = {
     "fused": V.VBE_FUSE | V.VBE_PACK | V.VBE_RECORD,
     "plain": V.VBE_RECORD,
+    # fused, with every eligible one-dimensional run staged through shared
+    # memory by bulk copies in chunks of 64 elements (several chunks per
+    # block, and a tail, at these sizes)
+    "staged": V.VBE_FUSE | V.VBE_PACK | V.VBE_RECORD,
 }
+STAGING = {"staged": 64}
 # launch shapes: (block, U, SMs) -- several, so that multi-block and ragged
 # tiles are exercised
 SHAPES = [(64, 1, 2), (32, 4, 3), (128, 2, 1)]
 
 
-def emulate(program, flags, shape, run=True):
+def emulate(program, flags, shape, run=True, staging=0):
     block, U, sms = shape
+    os.environ["VBE_STAGING"] = str(staging)  # read when the context is created
     os.environ["VBE_RECORD_BLOCK"] = str(block)
     os.environ["VBE_RECORD_U"] = str(U)
     os.environ["VBE_RECORD_SMS"] = str(sms)
     sources = []
-    with Executor(flags) as ex:
+    ex = Executor(flags)
+    os.environ.pop("VBE_STAGING")
+    with ex:
         L = ex.load(program)
         for k in range(len(L.batches)):
             ex.submit(L, k)
@@ -58,7 +66,8 @@ def _prebuild_kernels():
     srcs = []
     for case in CASES:
         for mode, flags in MODES.items():
-            srcs += emulate(case.program, flags, SHAPES[hash(case.name) % len(SHAPES)], run=False)
+            srcs += emulate(case.program, flags, SHAPES[hash(case.name) % len(SHAPES)], run=False,
+                            staging=STAGING.get(mode, 0))
     EMU.prebuild(srcs)
 
 
@@ -67,7 +76,7 @@ def _prebuild_kernels():
 def test_emulated_parity(case, mode):
     want = oracle_outputs(case.program)
     shape = SHAPES[hash(case.name) % len(SHAPES)]
-    got = emulate(case.program, MODES[mode], shape)
+    got = emulate(case.program, MODES[mode], shape, staging=STAGING.get(mode, 0))
     case.check(got, want)
 
 

@@ -24,11 +24,29 @@ pytestmark = pytest.mark.gpu
 CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
 
 FUSED = V.VBE_FUSE | V.VBE_PACK | V.VBE_AUTOTUNE
-MODES = {"fused": FUSED, "plain": 0, "fused_graphs": FUSED | V.VBE_GRAPHS}
+MODES = {"fused": FUSED, "plain": 0, "fused_graphs": FUSED | V.VBE_GRAPHS,
+         # every eligible one-dimensional run staged through shared memory by
+         # bulk copies, in chunks of 256 elements
+         "fused_staged": FUSED | V.VBE_GRAPHS}
+STAGING = {"fused_staged": 256}
 
 
-def run_gpu(program, flags, repeat_batches=1):
-    with Executor(flags, cache_dir=CACHE) as ex:
+def make_executor(flags, staging=0, **kw):
+    """An executor; staging > 0 forces staged runs (the variable is read
+    when the context is created, and restored right after)."""
+    old = os.environ.pop("VBE_STAGING", None)
+    if staging:
+        os.environ["VBE_STAGING"] = str(staging)
+    try:
+        return Executor(flags, cache_dir=CACHE, **kw)
+    finally:
+        os.environ.pop("VBE_STAGING", None)
+        if old is not None:
+            os.environ["VBE_STAGING"] = old
+
+
+def run_gpu(program, flags, repeat_batches=1, staging=0):
+    with make_executor(flags, staging) as ex:
         L = ex.load(program)
         for _ in range(repeat_batches):
             ex.run(L)
@@ -43,7 +61,7 @@ SMALL = all_small_cases()
 @pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("case", SMALL, ids=[c.name for c in SMALL])
 def test_small_parity(case, mode):
-    got = run_gpu(case.program, MODES[mode])
+    got = run_gpu(case.program, MODES[mode], staging=STAGING.get(mode, 0))
     case.check(got, oracle_outputs(case.program))
 
 
@@ -53,7 +71,7 @@ MEDIUM = workload_cases("medium")
 @pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("case", MEDIUM, ids=[c.name for c in MEDIUM])
 def test_medium_workload_parity(case, mode):
-    got = run_gpu(case.program, MODES[mode])
+    got = run_gpu(case.program, MODES[mode], staging=STAGING.get(mode, 0))
     case.check(got, oracle_outputs(case.program))
     if mode == "fused_graphs" and case.name.startswith(("jacobi", "shallow")):
         assert got["_stats"]["graph_launches"] > 0  # repeated iterations replay a graph
@@ -72,14 +90,16 @@ def test_jacobi_config_full_size_graphs_and_plain_agree():
                          F64_REDUCE_RTOL, "deltas")
 
 
+@pytest.mark.parametrize("staging", [0, 2048])
 @pytest.mark.parametrize("dtype,rtol", [("float64", 1e-12), ("float32", 1e-5)])
-def test_blackscholes_full_size_sampled(dtype, rtol):
-    """16M options, in the launch configuration the benchmark times; 20,000
-    sampled options recomputed by the oracle one program at a time."""
+def test_blackscholes_full_size_sampled(dtype, rtol, staging):
+    """16M options, in the launch configuration the benchmark times (and
+    with the inputs staged through shared memory in 2048-element chunks);
+    20,000 sampled options recomputed by the oracle one program at a time."""
     n = 1 << 24
     inp = bs_inputs(n, dtype)
     p = blackscholes(n, dtype, inputs=inp)
-    got = run_gpu(p, FUSED | V.VBE_GRAPHS)
+    got = run_gpu(p, FUSED | V.VBE_GRAPHS, staging=staging)
     idx = np.sort(np.random.default_rng(7).choice(n, 20_000, replace=False))
     idx = np.concatenate([[0, 1, n - 2, n - 1], idx])
     sub = blackscholes(len(idx), dtype, inputs={k: v[idx] for k, v in inp.items()})
