@@ -320,7 +320,8 @@ def other_workload(args, local):
             isz = 8 if dtype == "float64" else 4
             cbytes = 6 * isz * 4096 * 4096 * 50  # H, U, V read once and written once per step
             res = {}
-            for name in ("fused_graphs", "plain_graphs"):
+            modes["fused_graphs_untiled"] = F | V.VBE_GRAPHS | V.VBE_NO_TILE_FUSION
+            for name in ("fused_graphs", "fused_graphs_untiled", "plain_graphs"):
                 sec, st = timed_batches(p, modes[name], 2)
                 res[name] = {"ms_per_step": sec / 50 * 1e3, "GB/s": cbytes / sec / 1e9,
                              "hbm_fraction": cbytes / sec / 1e9 / hbm}

@@ -136,6 +136,13 @@ enum {
   VBE_NATIVE_F64 = 1u << 6,/* float64 divide/sqrt/exp/log on the FP64 pipe; by default they run
                               as integer arithmetic (correctly rounded divide and sqrt, exp/log
                               within 1 ulp), because B300's FP64 pipe is 1/64 of its FP32 rate */
+  VBE_NO_TILE_FUSION = 1u << 7, /* with VBE_FUSE: keep two-dimensional runs that exchange
+                              temporaries at small shifts as separate kernels (by default they
+                              become one tile-fused kernel: temporaries in shared memory with
+                              recomputed halos; a base the group both reads around and updates
+                              gets a second buffer that replaces it after the launch, so
+                              vbe_base_device_ptr of a library-owned base is valid only until
+                              the next submit) */
   VBE_RECORD = 1u << 5     /* host-only context whose bases live in host memory and whose
                               launches are recorded (vbe_debug_take_launches) instead of run,
                               so tests can execute the generated kernels on a CPU; implies

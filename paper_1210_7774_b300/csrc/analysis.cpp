@@ -52,6 +52,8 @@ bool reads_base(const RInstr& r, int64_t base) {
   return false;
 }
 
+}  // namespace
+
 // true when base's contents written so far may still be read after
 // instruction idx (by a later instruction, a SYNC, or after the batch)
 bool live_after(const std::vector<RInstr>& prog, int64_t base, size_t idx) {
@@ -66,6 +68,8 @@ bool live_after(const std::vector<RInstr>& prog, int64_t base, size_t idx) {
   }
   return true;
 }
+
+namespace {
 
 struct Builder {
   Ctx* c;
@@ -408,6 +412,7 @@ Plan make_plan(Ctx* c, std::vector<RInstr>& prog, bool fuse, bool pack) {
   Builder b(c, prog, fuse);
   b.plan.staging = pre.staging;
   b.run_all();
+  if (fuse && !(c->cfg.flags & VBE_NO_TILE_FUSION)) form_groups(c, prog, &b.plan);
   return std::move(b.plan);
 }
 
@@ -444,6 +449,37 @@ std::string plan_json(Ctx* c, const std::vector<RInstr>& prog, const Plan& p, bo
     if (it.kind == 1) {
       static const char* names[] = {"FREE", "DISCARD", "SYNC"};
       os << "{\"action\":\"" << names[it.act.kind] << "\",\"base\":" << it.act.base << "}";
+      continue;
+    }
+    if (it.kind == 2) {
+      const Group& g = *it.group;
+      os << "{\"group\":{\"runs\":[";
+      for (size_t k = 0; k < g.runs.size(); ++k) {
+        const Run& r = g.runs[k];
+        os << (k ? "," : "") << "{\"shape\":[" << r.shape[0] << "," << r.shape[1] << "],\"instrs\":[";
+        for (size_t q = 0; q < r.instrs.size(); ++q) os << (q ? "," : "") << r.instrs[q];
+        os << "],\"box\":[" << g.box[k][0] << "," << g.box[k][1] << "," << g.box[k][2] << "," << g.box[k][3]
+           << "],\"loads\":[";
+        for (size_t q = 0; q < r.loads.size(); ++q) {
+          const GroupLoad& ld = g.lds[k][q];
+          os << (q ? "," : "") << "{\"base\":" << r.loads[q].base << ",\"from\":" << ld.prod;
+          if (ld.prod >= 0) os << ",\"shift\":[" << ld.dr << "," << ld.dc << "]";
+          os << "}";
+        }
+        os << "],\"stores\":[";
+        for (size_t q = 0; q < r.stores.size(); ++q)
+          os << (q ? "," : "") << "{\"base\":" << r.stores[q].base << ",\"shared\":"
+             << (g.consumed[k][q] ? "true" : "false") << "}";
+        os << "]}";
+      }
+      os << "],\"renamed\":[";
+      for (size_t q = 0; q < g.renamed.size(); ++q) os << (q ? "," : "") << g.renamed[q];
+      os << "]";
+      if (want_source) {
+        os << ",\"source\":";
+        json_str(os, generate_group_source(g, nullptr, nullptr));
+      }
+      os << "}}";
       continue;
     }
     const Run& r = it.run;

@@ -117,13 +117,12 @@ int vbe_finalize(vbe_ctx* ctx) {
   }
   if (!c.host_only) {
     cudaStreamSynchronize(c.exec.stream);
-    for (auto& kv : c.bases)
+    for (auto& kv : c.bases) {
       if (kv.second.dptr && !kv.second.external) cudaFreeAsync(kv.second.dptr, c.exec.stream);
-    for (auto& kv : c.batches) {
-      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-      if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
-      for (void* p : kv.second.keep) cudaFree(p);
+      if (kv.second.shadow) cudaFreeAsync(kv.second.shadow, c.exec.stream);
     }
+    for (auto& kv : c.batches)
+      for (auto& v : kv.second.v) vbe::release_variant(v);
     for (auto& kv : c.tickets) cudaEventDestroy(kv.second);
     cudaStreamSynchronize(c.exec.stream);
     vbe::release_exec(&c, &c.exec);
@@ -317,6 +316,7 @@ int vbe_free(vbe_ctx* ctx, vbe_base base) {
   auto it = c.bases.find(base);
   if (it == c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
   if (it->second.dptr && !it->second.external) vbe::dev_free(&c, &c.exec, it->second.dptr, it->second.bytes());
+  if (it->second.shadow) vbe::dev_free(&c, &c.exec, it->second.shadow, it->second.bytes());
   for (auto v = c.views.begin(); v != c.views.end();) {
     if (v->second.base == base) v = c.views.erase(v);
     else ++v;
@@ -358,6 +358,11 @@ int vbe_plan_compile(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, int64_t* nk
   int64_t k = 0;
   std::vector<std::string> srcs;
   for (auto& it : p.items) {
+    if (it.kind == 2) {
+      srcs.push_back(vbe::generate_group_source(*it.group, nullptr, nullptr));
+      ++k;
+      continue;
+    }
     if (it.kind != 0) continue;
     std::vector<uintptr_t> lp(it.run.loads.size(), 0), sp(it.run.stores.size(), 0);
     vbe::Canon cn = vbe::canonicalize(it.run, true, lp, sp, 0);

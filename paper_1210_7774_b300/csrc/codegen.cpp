@@ -279,6 +279,20 @@ Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& l
 
 int words_count(const Run& r, const Canon& c) { return layout_of(r, c).nwords; }
 
+// a constant operand as the parameter word the generated code decodes
+static int64_t const_bits(const Operand& o) {
+  int64_t bits = o.i;
+  if (o.dtype == VBE_FLOAT64) {
+    memcpy(&bits, &o.f, 8);
+  } else if (o.dtype == VBE_FLOAT32) {
+    float g = (float)o.f;
+    uint32_t b32;
+    memcpy(&b32, &g, 4);
+    bits = (int64_t)b32;
+  }
+  return bits;
+}
+
 void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load_ptrs,
                 const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr, uintptr_t partials,
                 uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out, int64_t chunk, uintptr_t err) {
@@ -319,19 +333,7 @@ void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load
   }
   if (L.idx_st >= 0)
     for (size_t k = 0; k < c.idx_st.size(); ++k) w[L.idx_st + k] = c.idx_st[k];
-  for (size_t k = 0; k < r.consts.size(); ++k) {
-    const Operand& o = r.consts[k];
-    int64_t bits = o.i;
-    if (o.dtype == VBE_FLOAT64) {
-      memcpy(&bits, &o.f, 8);
-    } else if (o.dtype == VBE_FLOAT32) {
-      float g = (float)o.f;
-      uint32_t b32;
-      memcpy(&b32, &g, 4);
-      bits = (int64_t)b32;
-    }
-    w[L.consts + k] = bits;
-  }
+  for (size_t k = 0; k < r.consts.size(); ++k) w[L.consts + k] = const_bits(r.consts[k]);
   if (L.bulk_ch >= 0) {
     w[L.bulk_ch] = chunk;
     w[L.err] = (int64_t)err;
@@ -595,9 +597,11 @@ struct Gen {
   }
 
   // the per-element function: loaded values in, values to store out
+  std::string elem_name = "vbe_elem";
+  bool emit_struct = true;
   void emit_elem() {
-    o << "struct P { i64 w[" << L.nwords << "]; };\n";
-    o << "__device__ __forceinline__ void vbe_elem(const P& p, i64 m";
+    if (emit_struct) o << "struct P { i64 w[" << L.nwords << "]; };\n";
+    o << "__device__ __forceinline__ void " << elem_name << "(const P& p, i64 m";
     for (size_t s = 0; s < r.loads.size(); ++s) o << ", const " << ctype(r.loads[s].dtype) << " l" << s;
     for (size_t s = 0; s < r.stores.size(); ++s) o << ", " << ctype(r.stores[s].dtype) << "& o" << s;
     if (r.has_red) {
@@ -1103,6 +1107,286 @@ std::string generate_source(const Run& r, const Canon& c, std::string* entry_pre
   for (size_t pos; (pos = src.find("@TAG@")) != std::string::npos;) src.replace(pos, 5, tag);
   if (entry_prefix) *entry_prefix = "vbe_" + tag;
   return src;
+}
+
+// ------------------------------------------------------ tile-fused groups
+
+namespace {
+
+struct GroupLayout {
+  int nwords = 0;
+  std::vector<int> dims;                 // per run: rows, cols
+  std::vector<std::vector<int>> lw, sw;  // per run, per slot: pointer, row stride, column stride (-1: shared)
+  std::vector<int> consts, rnd;          // per run: first constant word, first RANDOM word
+  std::vector<int> ren;                  // per renamed base: source, destination, offset, pitch, rows, cols, count
+};
+
+GroupLayout group_layout(const Group& g) {
+  GroupLayout L;
+  const int m = (int)g.runs.size();
+  int w = 4;  // anchor rows, anchor cols, tiles per row, tiles
+  for (int k = 0; k < m; ++k) {
+    L.dims.push_back(w);
+    w += 2;
+  }
+  L.lw.resize(m);
+  L.sw.resize(m);
+  for (int k = 0; k < m; ++k) {
+    for (size_t s = 0; s < g.runs[k].loads.size(); ++s) {
+      if (g.lds[k][s].prod >= 0) {
+        L.lw[k].push_back(-1);
+        continue;
+      }
+      L.lw[k].push_back(w);
+      w += 3;
+    }
+    for (size_t s = 0; s < g.runs[k].stores.size(); ++s) {
+      if (k != m - 1) {
+        L.sw[k].push_back(-1);
+        continue;
+      }
+      L.sw[k].push_back(w);
+      w += 3;
+    }
+  }
+  for (int k = 0; k < m; ++k) {
+    L.consts.push_back(w);
+    w += (int)g.runs[k].consts.size();
+    L.rnd.push_back(w);
+    w += 3 * g.runs[k].nrandom;
+  }
+  for (size_t r = 0; r < g.renamed.size(); ++r) {
+    L.ren.push_back(w);
+    w += 7;
+  }
+  L.nwords = w;
+  return L;
+}
+
+// box of run k around a th x tw tile: rows, columns
+int box_rows(const Group& g, int k, int th) { return th + g.box[k][1] - g.box[k][0]; }
+int box_cols(const Group& g, int k, int tw) { return tw + g.box[k][3] - g.box[k][2]; }
+
+// shared-memory offsets of the consumed stores for one tile shape
+std::vector<std::vector<int64_t>> group_smem(const Group& g, int th, int tw, int64_t* total) {
+  std::vector<std::vector<int64_t>> off(g.runs.size());
+  int64_t acc = 0;
+  for (size_t k = 0; k < g.runs.size(); ++k)
+    for (size_t s = 0; s < g.runs[k].stores.size(); ++s) {
+      if (!g.consumed[k][s]) {
+        off[k].push_back(-1);
+        continue;
+      }
+      off[k].push_back(acc);
+      int64_t pts = (int64_t)box_rows(g, (int)k, th) * box_cols(g, (int)k, tw);
+      acc += (pts * itemsize(g.runs[k].stores[s].dtype) + 15) / 16 * 16;
+    }
+  *total = acc;
+  return off;
+}
+
+constexpr int64_t kGroupSmemLimit = 200 * 1024;
+
+std::vector<TileShape> group_shapes(const Group& g) {
+  std::vector<TileShape> out;
+  for (auto t : std::vector<std::array<int, 3>>{{8, 16, 128}, {16, 32, 256}, {32, 32, 256}, {16, 64, 256},
+                                                {32, 64, 256}}) {
+    TileShape ts;
+    ts.th = t[0];
+    ts.tw = t[1];
+    ts.block = t[2];
+    group_smem(g, ts.th, ts.tw, &ts.smem);
+    if (ts.smem <= kGroupSmemLimit) out.push_back(ts);
+  }
+  return out;
+}
+
+}  // namespace
+
+std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes_out) {
+  const int m = (int)g.runs.size();
+  const int anchor = m - 1;
+  GroupLayout GL = group_layout(g);
+  std::ostringstream o;
+  int nsteps = 0;
+  bool soft = false;
+  for (auto& r : g.runs) {
+    nsteps += (int)r.steps.size();
+    soft = soft || uses_soft_f64(r);
+  }
+  o << "// generated by libvbe: tile-fused group of " << m << " runs, " << nsteps << " operations\n";
+  o << kPrelude;
+  if (soft)
+    o << kSf64 << "\n"
+      << "__device__ __forceinline__ double vbe_u01s(u64 seed, u64 key, u64 step, u64 m) {\n"
+      << "  u64 z = seed + (key + step * m + 1ull) * 0x9E3779B97F4A7C15ull;\n"
+      << "  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;\n"
+      << "  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;\n"
+      << "  return vbe_u53_to_unit((z ^ (z >> 31)) >> 11);\n}\n";
+  o << "struct P { i64 w[" << GL.nwords << "]; };\n";
+  // one element function per run, reading its constants at the group's words
+  std::vector<Canon> canons(m);
+  for (int k = 0; k < m; ++k) {
+    const Run& r = g.runs[k];
+    Canon& cn = canons[k];
+    cn.spec.mode = Mode::ELEM;
+    cn.spec.nd = 2;
+    cn.spec.load_cls.assign(r.loads.size(), 2);
+    cn.spec.store_cls.assign(r.stores.size(), 2);
+    Gen gen(r, cn);
+    gen.L.consts = GL.consts[k];
+    for (int q = 0; q < r.nrandom; ++q) gen.L.rnd[q] = GL.rnd[k] + 3 * q;
+    gen.elem_name = "vbe_elem" + std::to_string(k);
+    gen.emit_struct = false;
+    gen.emit_elem();
+    o << gen.o.str();
+  }
+  auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
+  std::vector<TileShape> shapes = group_shapes(g);
+  for (const TileShape& ts : shapes) {
+    int64_t total = 0;
+    auto soff = group_smem(g, ts.th, ts.tw, &total);
+    o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@_sg" << ts.th << "x" << ts.tw
+      << "(const P p) {\n"
+      << "  VBE_DYN_SMEM;\n"
+      << "  if ((i64)blockIdx.x < p.w[3]) {\n"
+      << "    const i64 ti = (i64)blockIdx.x / p.w[2], tj = (i64)blockIdx.x - ti * p.w[2];\n"
+      << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n";
+    for (int k = 0; k < m; ++k) {
+      const Run& r = g.runs[k];
+      const int BH = box_rows(g, k, ts.th), BW = box_cols(g, k, ts.tw);
+      o << "    {  // run " << k << ": " << r.steps.size() << " operations over a " << BH << " x " << BW << " box\n"
+        << "      const i64 rows = " << W(GL.dims[k]) << ", cols = " << W(GL.dims[k] + 1) << ";\n";
+      std::vector<std::string> lv, sv;
+      for (size_t s = 0; s < r.loads.size(); ++s) {
+        const std::string T = ctype(r.loads[s].dtype), n = std::to_string(s);
+        const GroupLoad& ld = g.lds[k][s];
+        if (ld.prod < 0) {
+          int w = GL.lw[k][s];
+          o << "      const auto lp" << n << " = vbe_ptr<const " << T << ">(" << W(w) << ");\n"
+            << "      const i64 la" << n << " = " << W(w + 1) << ", lb" << n << " = " << W(w + 2) << ";\n";
+          lv.push_back("lp" + n + "[i * la" + n + " + j * lb" + n + "]");
+        } else {
+          const int pk = ld.prod;
+          const int roff = g.box[k][0] + ld.dr - g.box[pk][0], coff = g.box[k][2] + ld.dc - g.box[pk][2];
+          const int PBW = box_cols(g, pk, ts.tw);
+          o << "      const " << T << "* sl" << n << " = (const " << T << "*)(vbe_smem + " << soff[pk][ld.prod_store]
+            << ");\n";
+          lv.push_back("sl" + n + "[(li + " + std::to_string(roff) + ") * " + std::to_string(PBW) + " + (lj + " +
+                       std::to_string(coff) + ")]");
+        }
+      }
+      for (size_t s = 0; s < r.stores.size(); ++s) {
+        const std::string T = ctype(r.stores[s].dtype), n = std::to_string(s);
+        if (g.consumed[k][s])
+          o << "      " << T << "* ss" << n << " = (" << T << "*)(vbe_smem + " << soff[k][s] << ");\n";
+        if (k == anchor) {
+          int w = GL.sw[k][s];
+          o << "      const auto sp" << n << " = vbe_ptr<" << T << ">(" << W(w) << ");\n"
+            << "      const i64 sa" << n << " = " << W(w + 1) << ", sb" << n << " = " << W(w + 2) << ";\n";
+        }
+        sv.push_back("b" + n);
+      }
+      o << "      for (int q = threadIdx.x; q < " << BH * BW << "; q += blockDim.x) {\n"
+        << "        const int li = q / " << BW << ", lj = q - li * " << BW << ";\n"
+        << "        const i64 i = i0 + (" << g.box[k][0] << " + li), j = j0 + (" << g.box[k][2] << " + lj);\n"
+        << "        if (i < 0 || i >= rows || j < 0 || j >= cols) continue;\n";
+      for (size_t s = 0; s < r.stores.size(); ++s) o << "        " << ctype(r.stores[s].dtype) << " b" << s << ";\n";
+      o << "        vbe_elem" << k << "(p, i * cols + j";
+      for (auto& x : lv) o << ", " << x;
+      for (auto& x : sv) o << ", " << x;
+      o << ");\n";
+      for (size_t s = 0; s < r.stores.size(); ++s) {
+        if (g.consumed[k][s]) o << "        ss" << s << "[q] = b" << s << ";\n";
+        if (k == anchor) o << "        sp" << s << "[i * sa" << s << " + j * sb" << s << "] = b" << s << ";\n";
+      }
+      o << "      }\n";
+      if (k != anchor) o << "      __syncthreads();\n";
+      o << "    }\n";
+    }
+    o << "  }\n";
+    // elements of renamed bases the anchor does not write: copied to the new buffer
+    for (size_t rr = 0; rr < g.renamed.size(); ++rr) {
+      const std::string T = ctype(g.runs[anchor].stores[g.renamed_slot[rr]].dtype);
+      const int w = GL.ren[rr];
+      o << "  {\n"
+        << "    const auto src = vbe_ptr<const " << T << ">(" << W(w) << ");\n"
+        << "    const auto dst = vbe_ptr<" << T << ">(" << W(w + 1) << ");\n"
+        << "    const i64 off = " << W(w + 2) << ", P = " << W(w + 3) << ", S0 = " << W(w + 4) << ", S1 = " << W(w + 5)
+        << ", nc = " << W(w + 6) << ";\n"
+        << "    const i64 gap = P - S1, ng = (S0 - 1) * gap;\n"
+        << "    for (i64 q = (i64)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (i64)gridDim.x * blockDim.x) {\n"
+        << "      i64 e;\n"
+        << "      if (q < off) e = q;\n"
+        << "      else if (q - off < ng) { const i64 u = q - off, rw = u / gap; e = off + rw * P + S1 + (u - rw * gap); }\n"
+        << "      else e = off + (S0 - 1) * P + S1 + (q - off - ng);\n"
+        << "      dst[e] = src[e];\n"
+        << "    }\n"
+        << "  }\n";
+    }
+    o << "}\n";
+  }
+  std::string src = o.str();
+  std::string tag = "g" + std::to_string(m) + "_" + hex64(fnv1a(src.data(), src.size())).substr(8);
+  for (size_t pos; (pos = src.find("@TAG@")) != std::string::npos;) src.replace(pos, 5, tag);
+  if (entry_prefix) *entry_prefix = "vbe_" + tag;
+  if (shapes_out) *shapes_out = shapes;
+  return src;
+}
+
+void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std::vector<uintptr_t>>& load_ptrs,
+                      const std::vector<std::vector<uintptr_t>>& store_ptrs,
+                      const std::vector<std::pair<uintptr_t, uintptr_t>>& renamed_ptrs, LaunchArgs* out) {
+  const int m = (int)g.runs.size();
+  const int anchor = m - 1;
+  GroupLayout GL = group_layout(g);
+  std::vector<int64_t>& w = out->w;
+  w.assign(GL.nwords, 0);
+  const int64_t R = g.rows(anchor), C = g.cols(anchor);
+  const int64_t tpr = (C + ts.tw - 1) / ts.tw;
+  w[0] = R;
+  w[1] = C;
+  w[2] = tpr;
+  w[3] = ((R + ts.th - 1) / ts.th) * tpr;
+  for (int k = 0; k < m; ++k) {
+    const Run& r = g.runs[k];
+    w[GL.dims[k]] = r.shape[0];
+    w[GL.dims[k] + 1] = r.shape[1];
+    for (size_t s = 0; s < r.loads.size(); ++s) {
+      int q = GL.lw[k][s];
+      if (q < 0) continue;
+      w[q] = (int64_t)(load_ptrs[k][s] + (uintptr_t)(r.loads[s].offset * itemsize(r.loads[s].dtype)));
+      w[q + 1] = r.loads[s].st[0];
+      w[q + 2] = r.loads[s].st[1];
+    }
+    for (size_t s = 0; s < r.stores.size(); ++s) {
+      int q = GL.sw[k][s];
+      if (q < 0) continue;
+      w[q] = (int64_t)(store_ptrs[k][s] + (uintptr_t)(r.stores[s].offset * itemsize(r.stores[s].dtype)));
+      w[q + 1] = r.stores[s].st[0];
+      w[q + 2] = r.stores[s].st[1];
+    }
+    for (size_t q = 0; q < r.consts.size(); ++q) w[GL.consts[k] + q] = const_bits(r.consts[q]);
+    int ri = 0;
+    for (auto& st : r.steps) {
+      if (st.op != VBE_OP_RANDOM) continue;
+      w[GL.rnd[k] + 3 * ri] = (int64_t)st.seed;
+      w[GL.rnd[k] + 3 * ri + 1] = (int64_t)st.key;
+      w[GL.rnd[k] + 3 * ri + 2] = st.rstep;
+      ++ri;
+    }
+  }
+  for (size_t rr = 0; rr < g.renamed.size(); ++rr) {
+    const Slot& st = g.runs[anchor].stores[g.renamed_slot[rr]];
+    const int q = GL.ren[rr];
+    w[q] = (int64_t)renamed_ptrs[rr].first;
+    w[q + 1] = (int64_t)renamed_ptrs[rr].second;
+    w[q + 2] = st.offset;
+    w[q + 3] = st.st[0];
+    w[q + 4] = R;
+    w[q + 5] = C;
+    w[q + 6] = g.renamed_nelem[rr] - R * C;
+  }
 }
 
 }  // namespace vbe

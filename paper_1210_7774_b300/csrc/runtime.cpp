@@ -253,19 +253,23 @@ void ensure_scratch(Ctx* c, Exec* ex, int64_t partials, int64_t counters) {
   if (s.partials) cudaFree(s.partials);
   if (s.counters) cudaFree(s.counters);
   // cached graphs may reference the old buffers
-  for (auto& kv : c->batches) {
-    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
-    for (void* p : kv.second.keep) cudaFree(p);
-    kv.second.exec = nullptr;
-    kv.second.graph = nullptr;
-    kv.second.keep.clear();
-  }
+  for (auto& kv : c->batches)
+    for (auto& v : kv.second.v) release_variant(v);
   s.n_partials = std::max<int64_t>(partials, 1 << 20);
   s.n_counters = std::max<int64_t>(counters, 1 << 16);
   cuda_check(cudaMalloc(&s.partials, (size_t)s.n_partials * 8), "cudaMalloc(partials)");
   cuda_check(cudaMalloc((void**)&s.counters, (size_t)s.n_counters * 4), "cudaMalloc(counters)");
   cuda_check(cudaMemset(s.counters, 0, (size_t)s.n_counters * 4), "cudaMemset(counters)");
+}
+
+void release_variant(CachedVariant& v) {
+  if (v.exec) cudaGraphExecDestroy(v.exec);
+  if (v.graph) cudaGraphDestroy(v.graph);
+  for (void* p : v.keep) cudaFree(p);
+  v.exec = nullptr;
+  v.graph = nullptr;
+  v.keep.clear();
+  v.launches = 0;
 }
 
 void release_exec(Ctx* c, Exec* ex) {
@@ -671,6 +675,169 @@ bool independent(const Run& a, const Run& b, Ctx* c) {
   return true;
 }
 
+// ------------------------------------------------------ tile-fused groups
+
+struct GroupPrepared {
+  Group* g = nullptr;
+  std::string src, prefix, key;
+  std::shared_ptr<Kernel> kern;
+  std::vector<TileShape> shapes;
+};
+
+struct GroupPtrs {
+  std::vector<std::vector<uintptr_t>> lp, sp;
+  std::vector<std::pair<uintptr_t, uintptr_t>> ren;  // (current buffer, second buffer)
+};
+
+// memory the group reads must exist; the anchor's targets are allocated,
+// renamed bases get their second buffer
+void allocate_group(Ctx* c, Exec* ex, const Group& g) {
+  const int anchor = (int)g.runs.size() - 1;
+  for (size_t k = 0; k < g.runs.size(); ++k)
+    for (size_t s = 0; s < g.runs[k].loads.size(); ++s) {
+      if (g.lds[k][s].prod >= 0) continue;
+      BaseRec& br = c->bases[g.runs[k].loads[s].base];
+      if (!br.dptr)
+        fail(VBE_ERR_UNINIT, "a run reads base " + std::to_string(g.runs[k].loads[s].base) + " which was never written");
+    }
+  for (auto& st : g.runs[anchor].stores) {
+    BaseRec& br = c->bases[st.base];
+    if (!br.dptr) br.dptr = dev_alloc(c, ex, br.bytes());
+    br.written = true;
+  }
+  for (int64_t b : g.renamed) {
+    BaseRec& br = c->bases[b];
+    if (!br.shadow) br.shadow = dev_alloc(c, ex, br.bytes());
+  }
+}
+
+GroupPtrs group_ptrs(Ctx* c, const Group& g) {
+  GroupPtrs p;
+  const int m = (int)g.runs.size(), anchor = m - 1;
+  p.lp.resize(m);
+  p.sp.resize(m);
+  for (int k = 0; k < m; ++k) {
+    for (size_t s = 0; s < g.runs[k].loads.size(); ++s)
+      p.lp[k].push_back(g.lds[k][s].prod >= 0 ? 0 : base_ptr(c, g.runs[k].loads[s].base));
+    for (size_t s = 0; s < g.runs[k].stores.size(); ++s) {
+      uintptr_t a = 0;
+      if (k == anchor) {
+        int64_t b = g.runs[k].stores[s].base;
+        a = base_ptr(c, b);
+        for (size_t r = 0; r < g.renamed.size(); ++r)
+          if (g.renamed[r] == b) a = (uintptr_t)c->bases[b].shadow;
+      }
+      p.sp[k].push_back(a);
+    }
+  }
+  for (int64_t b : g.renamed) p.ren.push_back({base_ptr(c, b), (uintptr_t)c->bases[b].shadow});
+  return p;
+}
+
+Launch build_group(Ctx* c, GroupPrepared& G, const TileShape& ts, const GroupPtrs& ptr) {
+  Launch L;
+  L.entry = G.prefix + "_sg" + std::to_string(ts.th) + "x" + std::to_string(ts.tw);
+  L.key = G.key;
+  L.fn = kernel_fn(G.kern.get(), L.entry);
+  L.block = (unsigned)ts.block;
+  L.smem = (unsigned)ts.smem;
+  if (!c->record)
+    cuda_check(cudaKernelSetAttributeForDevice(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem,
+                                               c->device),
+               "dynamic shared memory attribute");
+  LaunchArgs a;
+  fill_group_words(*G.g, ts, ptr.lp, ptr.sp, ptr.ren, &a);
+  L.grid = (unsigned)std::max<int64_t>(1, a.w[3]);
+  L.words = std::move(a.w);
+  return L;
+}
+
+std::string group_tune_key(const GroupPrepared& G) {
+  const Group& g = *G.g;
+  int64_t n = std::max<int64_t>(1, g.rows((int)g.runs.size() - 1) * g.cols((int)g.runs.size() - 1));
+  int lg = 0;
+  while (n > 1) {
+    n >>= 1;
+    ++lg;
+  }
+  return src_key(G.src) + ":" + std::to_string(lg);
+}
+
+// the tile shape: fixed in record mode (VBE_RECORD_TILE=THxTW), else timed
+// per signature and size class with the anchor's in-place targets
+// redirected to scratch buffers
+TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real, bool may_tune) {
+  if (G.shapes.empty()) fail(VBE_ERR_INVALID, "tile-fused group without a tile shape");
+  if (c->record) {
+    const char* e = getenv("VBE_RECORD_TILE");
+    if (e)
+      for (auto& ts : G.shapes)
+        if (std::to_string(ts.th) + "x" + std::to_string(ts.tw) == e) return ts;
+    return G.shapes[0];
+  }
+  std::string tk = group_tune_key(G);
+  auto it = c->tune.find(tk);
+  if (it != c->tune.end())
+    for (auto& ts : G.shapes)
+      if (ts.th == it->second.block && ts.tw == it->second.U) return ts;
+  TileShape def = G.shapes[0];
+  for (auto& ts : G.shapes)
+    if (ts.th * ts.tw <= 1024 && ts.th * ts.tw >= def.th * def.tw) def = ts;
+  const Group& g = *G.g;
+  const int anchor = (int)g.runs.size() - 1;
+  if (!(may_tune && (c->cfg.flags & VBE_AUTOTUNE) && g.rows(anchor) * g.cols(anchor) >= (1 << 16))) return def;
+  GroupPtrs ptr = real;
+  std::vector<std::pair<void*, int64_t>> bufs;
+  const Run& ra = g.runs[anchor];
+  for (size_t s = 0; s < ra.stores.size(); ++s) {
+    bool renamed = false;
+    for (int64_t b : g.renamed)
+      if (b == ra.stores[s].base) renamed = true;
+    if (renamed) continue;  // writes the second buffer only
+    const Slot& st = ra.stores[s];
+    int64_t lo = st.offset, hi = st.offset;
+    for (int k = 0; k < 2; ++k) {
+      int64_t e = (ra.shape[k] - 1) * st.st[k];
+      if (e < 0) lo += e; else hi += e;
+    }
+    int64_t bytes = (hi - lo + 1) * itemsize(st.dtype);
+    void* b = dev_alloc(c, ex, bytes);
+    bufs.push_back({b, bytes});
+    ptr.sp[anchor][s] = (uintptr_t)b - (uintptr_t)(lo * itemsize(st.dtype));
+  }
+  if (!ex->ev0) {
+    cudaEventCreate(&ex->ev0);
+    cudaEventCreate(&ex->ev1);
+  }
+  TileShape best = def;
+  float best_ms = 1e30f;
+  for (const TileShape& ts : G.shapes) {
+    Launch L = build_group(c, G, ts, ptr);
+    issue(c, ex, L, false);  // warm
+    c->stats.kernel_launches--;
+    cuda_check(cudaEventRecord(ex->ev0, ex->stream), "event");
+    for (int rep = 0; rep < 3; ++rep) {
+      issue(c, ex, L, false);
+      c->stats.kernel_launches--;
+    }
+    cuda_check(cudaEventRecord(ex->ev1, ex->stream), "event");
+    cuda_check(cudaEventSynchronize(ex->ev1), "event sync");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ex->ev0, ex->ev1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = ts;
+    }
+  }
+  for (auto& b : bufs) dev_free(c, ex, b.first, b.second);
+  c->stats.autotunes++;
+  TuneChoice tc;
+  tc.block = best.th;
+  tc.U = best.tw;
+  c->tune[tk] = tc;
+  return best;
+}
+
 uint64_t batch_key(const vbe_instr* prog, int64_t n) {
   uint64_t h = fnv1a(&n, sizeof n);
   return fnv1a(prog, (size_t)n * sizeof(vbe_instr), h);
@@ -689,6 +856,7 @@ std::vector<std::pair<int64_t, uintptr_t>> fingerprint(Ctx* c, const std::vector
   for (auto b : ids) {
     auto it = c->bases.find(b);
     f.push_back({b, it == c->bases.end() ? 0 : (uintptr_t)it->second.dptr});
+    if (it != c->bases.end() && it->second.shadow) f.push_back({-b, (uintptr_t)it->second.shadow});
   }
   return f;
 }
@@ -698,6 +866,7 @@ void do_action(Ctx* c, Exec* ex, const HostAction& a) {
   if (it == c->bases.end()) return;
   if (a.kind == 0) {  // FREE
     if (it->second.dptr && !it->second.external) dev_free(c, ex, it->second.dptr, it->second.bytes());
+    if (it->second.shadow) dev_free(c, ex, it->second.shadow, it->second.bytes());
     for (auto v = c->views.begin(); v != c->views.end();) {
       if (v->second.base == a.base) v = c->views.erase(v);
       else ++v;
@@ -711,6 +880,8 @@ void do_action(Ctx* c, Exec* ex, const HostAction& a) {
 // Execute one batch on ex's stream. Eager the first time a batch is seen;
 // with VBE_GRAPHS, a batch seen again (same instructions, same views, same
 // base addresses, no FREE) is captured into a CUDA graph and later replayed.
+// A batch whose tile-fused groups rename bases alternates between two
+// address sets; each has its own cached launches.
 void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_graph) {
   if (c->host_only && !c->record) fail(VBE_ERR_NO_DEVICE, "host-only context");
   std::vector<RInstr> rp = resolve_batch(c, prog, n);
@@ -724,20 +895,36 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   // launches are replayed from a graph (VBE_GRAPHS) or one by one
   bool cacheable = allow_graph && !has_free && !c->record;  // never for one-shot server requests
   uint64_t key = cacheable ? (batch_key(prog, n) ^ (uint64_t)(uintptr_t)ex) : 0;
+  static uint64_t use_clock = 0;
   CachedBatch* cb = nullptr;
+  CachedVariant* var = nullptr;
+  auto apply_after = [&](const CachedVariant& v) {
+    for (auto& a : v.after) {
+      BaseRec& br = c->bases[a.first];
+      br.dptr = a.second.first;
+      br.shadow = a.second.second;
+    }
+  };
   if (cacheable) {
     cb = &c->batches[key];
     cb->key = key;
     auto fp = fingerprint(c, rp);
-    if (graphs && cb->exec && cb->fingerprint == fp) {
-      cuda_check(cudaGraphLaunch(cb->exec, ex->stream), "cudaGraphLaunch");
-      c->stats.graph_launches++;
-      c->stats.kernel_launches += cb->launches;
-      return;
-    }
-    if (!graphs && !cb->eager.empty() && cb->eager_fingerprint == fp) {
-      for (auto& L : cb->eager) issue(c, ex, *L, false);
-      return;
+    for (auto& v : cb->v)
+      if (v.fingerprint == fp) var = &v;
+    if (var) {
+      var->last_use = ++use_clock;
+      if (graphs && var->exec) {
+        cuda_check(cudaGraphLaunch(var->exec, ex->stream), "cudaGraphLaunch");
+        c->stats.graph_launches++;
+        c->stats.kernel_launches += var->launches;
+        apply_after(*var);
+        return;
+      }
+      if (!graphs && var->has_eager) {
+        for (auto& L : var->eager) issue(c, ex, *L, false);
+        apply_after(*var);
+        return;
+      }
     }
   }
   bool fuse = (c->cfg.flags & VBE_FUSE) != 0;
@@ -745,13 +932,16 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   std::vector<RInstr> staged = rp;
   Plan plan = make_plan(c, staged, fuse, pack);
   ensure_scratch(c, ex, 1 << 20, 1 << 16);
-  bool capture = graphs && cb->seen >= 1;
-  if (graphs) cb->seen++;
+  bool capture = graphs && var && var->seen >= 1;
 
   // compile the batch's kernels in parallel on first sight
   {
     std::vector<std::string> srcs;
     for (auto& it : plan.items) {
+      if (it.kind == 2) {
+        srcs.push_back(generate_group_source(*it.group, nullptr, nullptr));
+        continue;
+      }
       if (it.kind != 0) continue;
       RunPtrs pp;
       for (auto& s : it.run.loads) pp.lp.push_back((uintptr_t)c->bases[s.base].dptr);
@@ -767,6 +957,16 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
     for (auto& kv : c->bases)
       if (kv.second.dptr) avail.insert(kv.first);
     for (auto& it : plan.items) {
+      if (it.kind == 2) {
+        const Group& g = *it.group;
+        for (size_t k = 0; k < g.runs.size(); ++k)
+          for (size_t s = 0; s < g.runs[k].loads.size(); ++s)
+            if (g.lds[k][s].prod < 0 && !avail.count(g.runs[k].loads[s].base))
+              fail(VBE_ERR_UNINIT, "the batch reads base " + std::to_string(g.runs[k].loads[s].base) +
+                                       " before anything wrote it");
+        for (auto& s : g.runs.back().stores) avail.insert(s.base);
+        continue;
+      }
       if (it.kind != 0) continue;
       for (auto& s : it.run.loads)
         if (!avail.count(s.base))
@@ -775,9 +975,16 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       if (it.run.has_red) avail.insert(it.run.red_out.base);
     }
   }
-  // capture needs every store target allocated already
+  // capture needs every store target (and second buffer) allocated already
   if (capture) {
     for (auto& it : plan.items) {
+      if (it.kind == 2) {
+        for (auto& s : it.group->runs.back().stores)
+          if (!c->bases[s.base].dptr) capture = false;
+        for (int64_t b : it.group->renamed)
+          if (!c->bases[b].shadow) capture = false;
+        continue;
+      }
       if (it.kind != 0) continue;
       for (auto& s : it.run.stores)
         if (!c->bases[s.base].dptr) capture = false;
@@ -788,6 +995,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   std::vector<Launch> recorded;
   std::vector<std::shared_ptr<Launch>> issued;
   std::vector<HostAction> deferred;
+  std::map<int64_t, int> swaps;  // renamed bases: times swapped in this batch
   auto flush_deferred = [&]() {
     for (auto& a : deferred) do_action(c, ex, a);
     deferred.clear();
@@ -803,6 +1011,32 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       deferred.push_back(it.act);
       ++i;
       if (it.act.kind == 2) flush_deferred();
+      continue;
+    }
+    if (it.kind == 2) {
+      Group& g = *it.group;
+      allocate_group(c, ex, g);
+      GroupPrepared G;
+      G.g = &g;
+      G.src = generate_group_source(g, &G.prefix, &G.shapes);
+      G.key = src_key(G.src);
+      G.kern = get_kernel(c, G.src);
+      GroupPtrs ptr = group_ptrs(c, g);
+      TileShape ts = choose_group(c, ex, G, ptr, !capture);
+      Launch L = build_group(c, G, ts, ptr);
+      if (capture) {
+        recorded.push_back(std::move(L));
+      } else {
+        issue(c, ex, L, false);
+        if (cacheable) issued.push_back(std::make_shared<Launch>(L));
+      }
+      for (int64_t b : g.renamed) {
+        BaseRec& br = c->bases[b];
+        std::swap(br.dptr, br.shadow);
+        swaps[b]++;
+      }
+      ++i;
+      if (!capture) flush_deferred();
       continue;
     }
     Run& r = it.run;
@@ -826,6 +1060,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       std::vector<size_t> skipped;
       while (j < plan.items.size()) {
         PlanItem& nx = plan.items[j];
+        if (nx.kind == 2) break;
         if (nx.kind == 1) {
           if (nx.act.kind == 2) break;  // SYNC
           ++j;
@@ -904,11 +1139,48 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
     ++i;
     if (!capture) flush_deferred();
   }
+  if (!capture) flush_deferred();
+
+  // the address set these launches are valid for: the end state with this
+  // batch's renames undone
+  std::vector<std::pair<int64_t, std::pair<void*, void*>>> after;
+  std::vector<std::pair<int64_t, uintptr_t>> valid_fp;
+  if (cacheable) {
+    for (auto& kv : swaps) {
+      BaseRec& br = c->bases[kv.first];
+      after.push_back({kv.first, {br.dptr, br.shadow}});
+      if (kv.second % 2) std::swap(br.dptr, br.shadow);
+    }
+    valid_fp = fingerprint(c, rp);
+    for (auto& a : after) {
+      BaseRec& br = c->bases[a.first];
+      br.dptr = a.second.first;
+      br.shadow = a.second.second;
+    }
+    var = nullptr;
+    for (auto& v : cb->v)
+      if (v.fingerprint == valid_fp) var = &v;
+    if (!var) {
+      if (cb->v.size() >= 2) {
+        // replace the least recently used address set
+        auto lru = std::min_element(cb->v.begin(), cb->v.end(), [](const CachedVariant& a, const CachedVariant& b) {
+          return a.last_use < b.last_use;
+        });
+        release_variant(*lru);
+        cb->v.erase(lru);
+      }
+      cb->v.emplace_back();
+      var = &cb->v.back();
+      var->fingerprint = valid_fp;
+    }
+    var->after = after;
+    var->last_use = ++use_clock;
+    if (graphs) var->seen++;
+  }
   if (!capture) {
-    flush_deferred();
     if (cacheable) {
-      cb->eager = std::move(issued);
-      cb->eager_fingerprint = fingerprint(c, rp);
+      var->eager = std::move(issued);
+      var->has_eager = true;
     }
     return;
   }
@@ -942,18 +1214,15 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   cuda_check(cudaStreamEndCapture(cap, &graph), "cudaStreamEndCapture");
   cudaGraphExec_t gexec;
   cuda_check(cudaGraphInstantiate(&gexec, graph, 0), "cudaGraphInstantiate");
-  if (cb->exec) cudaGraphExecDestroy(cb->exec);
-  if (cb->graph) cudaGraphDestroy(cb->graph);
-  for (void* p : cb->keep) cudaFree(p);
-  cb->exec = gexec;
-  cb->graph = graph;
-  cb->keep = keep;
-  cb->launches = (int64_t)recorded.size();
-  cb->fingerprint = fingerprint(c, rp);
+  release_variant(*var);
+  var->exec = gexec;
+  var->graph = graph;
+  var->keep = keep;
+  var->launches = (int64_t)recorded.size();
   c->stats.graph_captures++;
   cuda_check(cudaGraphLaunch(gexec, ex->stream), "cudaGraphLaunch");
   c->stats.graph_launches++;
-  c->stats.kernel_launches += cb->launches;
+  c->stats.kernel_launches += var->launches;
 }
 
 }  // namespace vbe

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <atomic>
 #include <condition_variable>
 #include <cstdint>
@@ -133,11 +134,37 @@ struct HostAction {
   int64_t base = 0;
 };
 
+// Tile fusion: consecutive two-dimensional runs that communicate through
+// temporaries read at small shifts become one kernel. Each block owns a
+// TH x TW tile of the last run (the anchor); every earlier run is computed
+// over the tile grown by the halo its consumers need, into shared memory.
+struct GroupLoad {
+  int prod = -1;        // producing run in the group (-1: read from memory)
+  int prod_store = -1;  // the producer's store slot
+  int dr = 0, dc = 0;   // producer point = loader point + (dr, dc)
+};
+
+struct Group {
+  std::vector<Run> runs;                     // program order; the last is the anchor
+  std::vector<std::array<int, 4>> box;       // per run: row lo/hi, col lo/hi margins around the tile
+  std::vector<std::vector<GroupLoad>> lds;   // per run, per load slot
+  std::vector<std::vector<char>> consumed;   // per run, per store slot: kept in shared memory
+  // bases the anchor stores that other views of the group read: the anchor
+  // writes them into a second buffer that replaces the base after the
+  // launch (elements the anchor does not write are copied across)
+  std::vector<int64_t> renamed;
+  std::vector<int> renamed_slot;             // the anchor's store slot of each renamed base
+  std::vector<int64_t> renamed_nelem;        // element count of each renamed base
+  int64_t rows(int k) const { return runs[k].shape[0]; }
+  int64_t cols(int k) const { return runs[k].shape[1]; }
+};
+
 struct PlanItem {
-  int kind = 0;  // 0 run, 1 host action
+  int kind = 0;  // 0 run, 1 host action, 2 tile-fused group
   Run run;
   HostAction act;
   int pack_with_next = 0;  // >0: this run starts a pack of that many runs
+  std::shared_ptr<Group> group;
 };
 
 struct Plan {
@@ -180,11 +207,22 @@ void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load
                 uintptr_t err = 0);
 int words_count(const Run& r, const Canon& c);
 
+// tile-fused groups: source with one kernel per tile shape, and its words
+struct TileShape {
+  int th = 0, tw = 0, block = 0;
+  int64_t smem = 0;  // dynamic shared memory bytes
+};
+std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes);
+void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std::vector<uintptr_t>>& load_ptrs,
+                      const std::vector<std::vector<uintptr_t>>& store_ptrs,
+                      const std::vector<std::pair<uintptr_t, uintptr_t>>& renamed_ptrs, LaunchArgs* out);
+
 // ----------------------------------------------------------------- context
 struct BaseRec {
   int dtype = 0;
   int64_t nelem = 0;
   void* dptr = nullptr;
+  void* shadow = nullptr;  // second buffer of a base renamed by tile-fused groups
   bool external = false;
   bool written = false;
   bool internal = false;  // created by the library (staging)
@@ -217,19 +255,28 @@ struct Exec {
 
 struct Launch;  // a recorded kernel launch (runtime.cpp)
 
-struct CachedBatch {
-  uint64_t key = 0;
+// one way a batch ran: the launches are valid for the base addresses in
+// the fingerprint (and leave the renamed bases as in `after`)
+struct CachedVariant {
+  std::vector<std::pair<int64_t, uintptr_t>> fingerprint;  // (base, address), (-base, second buffer)
   int seen = 0;
-  // launches of the batch's last eager execution, replayed directly when
-  // the same batch comes again with the same base addresses
-  std::vector<std::shared_ptr<Launch>> eager;
-  std::vector<std::pair<int64_t, uintptr_t>> eager_fingerprint;
+  bool has_eager = false;
+  std::vector<std::shared_ptr<Launch>> eager;  // replayed one by one (no VBE_GRAPHS)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
-  std::vector<std::pair<int64_t, uintptr_t>> fingerprint;
   std::vector<void*> keep;  // device buffers the graph references
   int64_t launches = 0;
+  std::vector<std::pair<int64_t, std::pair<void*, void*>>> after;  // renamed base -> (buffer, second buffer)
+  uint64_t last_use = 0;
 };
+
+struct CachedBatch {
+  uint64_t key = 0;
+  // a batch whose groups rename bases alternates between two address sets
+  std::vector<CachedVariant> v;
+};
+
+void release_variant(CachedVariant& v);
 
 struct Ctx {
   vbe_config cfg{};
@@ -266,6 +313,8 @@ struct Ctx {
 };
 
 // analysis
+bool live_after(const std::vector<RInstr>& prog, int64_t base, size_t idx);
+void form_groups(Ctx* c, const std::vector<RInstr>& prog, Plan* plan);  // tile fusion (groups.cpp)
 std::vector<RInstr> resolve_batch(Ctx* c, const vbe_instr* prog, int64_t n);
 Plan make_plan(Ctx* c, std::vector<RInstr>& prog, bool fuse, bool pack);
 std::string plan_json(Ctx* c, const std::vector<RInstr>& prog, const Plan& p, bool want_source);

@@ -27,6 +27,7 @@ OPCODES = {name: i + 1 for i, name in enumerate([
 
 # config flags
 VBE_FUSE, VBE_GRAPHS, VBE_AUTOTUNE, VBE_PACK, VBE_HOST_ONLY, VBE_RECORD = 1, 2, 4, 8, 16, 32
+VBE_NATIVE_F64, VBE_NO_TILE_FUSION = 64, 128
 VBE_MAX_NDIM = 8
 
 ERRORS = {0: "VBE_OK", -1: "VBE_ERR_INVALID", -2: "VBE_ERR_OUT_OF_BOUNDS", -3: "VBE_ERR_DTYPE",

@@ -75,6 +75,17 @@ extern "C" long long emu_bulk(const long long* w, int nw, unsigned grid, unsigne
 }
 """
 
+_WRAP_ENTRY = """
+extern "C" long long emu_@E@(const long long* w, int nw, unsigned grid, unsigned block) {
+  if (emu_check_words(nw)) return -1;
+  P p;
+  memcpy(&p, w, sizeof(P));
+  g_bad = 0;
+  emu_grid(grid, block, [&]() { @E@(p); });
+  return g_bad.load();
+}
+"""
+
 _WRAP_AXIS = """
 extern "C" long long emu_axis(const long long* w, int nw, unsigned grid, unsigned block) {
   if (emu_check_words(nw)) return -1;
@@ -139,6 +150,9 @@ class Emulator:
                 parts.append(_WRAP_AXIS.replace("@P@", prefix))
             if prefix + "_bulk" in names:
                 parts.append(_WRAP_BULK.replace("@P@", prefix))
+            for name in names:  # tile-fused groups: one kernel per tile shape
+                if re.search(r"_sg\d+x\d+$", name):
+                    parts.append(_WRAP_ENTRY.replace("@E@", name))
             cpp = os.path.join(self.dir, f"emu_{h}.cpp")
             with open(cpp, "w") as f:
                 f.write("\n".join(parts))
@@ -187,7 +201,12 @@ class Emulator:
                                    L["chunk"], L["work"], L["grid"], L["block"])
             else:
                 w = (ctypes.c_longlong * len(L["words"]))(*L["words"])
-                if entry.endswith("_bulk"):
+                if re.search(r"_sg\d+x\d+$", entry):
+                    fn = getattr(lib, "emu_" + entry)
+                    fn.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
+                    fn.restype = ctypes.c_longlong
+                    bad = fn(w, len(L["words"]), L["grid"], L["block"])
+                elif entry.endswith("_bulk"):
                     bad = lib.emu_bulk(w, len(L["words"]), L["grid"], L["block"])
                 elif entry.endswith("_axis"):
                     bad = lib.emu_axis(w, len(L["words"]), L["grid"], L["block"])

@@ -227,6 +227,45 @@ def view_cases(seed=1):
     b.emit("COPY", b.view(o, 4096, (3,), (1,)), Const(0.0))
     p = b.build([o])
     out.append(Case(p.name, p, _exact_check(p)))
+    out += tile_group_cases(seed + 10)
+    return out
+
+
+def tile_group_cases(seed=11, N=37, M=45):
+    """Chains of two-dimensional runs handing temporaries to each other at
+    small shifts (tile-fused into one kernel): an in-place anchor that each
+    point reads only through its own view (no renaming), with RANDOM and
+    constants in the producer; and a three-run chain with shifts in both
+    dimensions writing a separate base. Sizes are ragged for every tile."""
+    rng = np.random.default_rng(seed)
+    out = []
+    b = ProgramBuilder("tile_group_inplace")
+    a = b.base("float64", (N, M), rng.standard_normal(N * M))
+    c = b.base("float64", (N, M), rng.standard_normal(N * M))
+    t = b.base("float64", (N, M - 1))
+    r = b.base("float64", (N, M - 1))
+    b.emit("SUBTRACT", b.whole(t), b.sub2d(a, 0, N, 1, M), b.sub2d(a, 0, N, 0, M - 1))
+    b.emit("RANDOM", b.whole(r), seed=5, key=3)
+    b.emit("MULTIPLY", b.whole(t), b.whole(t), b.whole(r))
+    b.emit("MULTIPLY", b.whole(t), b.whole(t), Const(0.5))
+    cc = b.sub2d(c, 0, N, 1, M - 1)
+    b.emit("ADD", cc, cc, b.sub2d(t, 0, N, 1, M - 1))
+    b.emit("SUBTRACT", cc, cc, b.sub2d(t, 0, N, 0, M - 2))
+    b.discard(t, r)
+    p = b.build([c])
+    out.append(Case(p.name, p, _exact_check(p)))
+    b = ProgramBuilder("tile_group_chain3_float32")
+    a = b.base("float32", (N, M), rng.standard_normal(N * M).astype(np.float32))
+    o = b.base("float32", (N, M), np.zeros(N * M, np.float32))
+    t1 = b.base("float32", (N - 1, M))
+    t2 = b.base("float32", (N - 1, M - 1))
+    b.emit("ADD", b.whole(t1), b.sub2d(a, 0, N - 1, 0, M), b.sub2d(a, 1, N, 0, M))
+    b.emit("MULTIPLY", b.whole(t2), b.sub2d(t1, 0, N - 1, 0, M - 1), b.sub2d(t1, 0, N - 1, 1, M))
+    b.emit("SUBTRACT", b.sub2d(o, 0, N - 2, 0, M - 2), b.sub2d(t2, 1, N - 1, 1, M - 1),
+           b.sub2d(t2, 0, N - 2, 0, M - 2))
+    b.free(t1, t2)
+    p = b.build([o])
+    out.append(Case(p.name, p, _exact_check(p)))
     return out
 
 

@@ -18,6 +18,7 @@ from paper_1210_7774_b300 import vbe as V  # noqa: E402
 from paper_1210_7774_b300.runner import Executor  # noqa: E402
 from workloads import (Const, ProgramBuilder, View, blackscholes, jacobi, montecarlo_pi,  # noqa: E402
                        shallow_water)
+from parity_cases import tile_group_cases  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HOST = V.VBE_HOST_ONLY
@@ -94,14 +95,61 @@ def test_blackscholes_is_one_kernel_with_two_stores(fused):
     assert r["vector"] is True
 
 
-def test_shallow_water_step_runs(fused):
+def test_shallow_water_step_runs():
     p = shallow_water(12, 1)
+    with Executor(V.VBE_FUSE | V.VBE_PACK | V.VBE_NO_TILE_FUSION | HOST) as ex:
+        L = ex.load(p, upload=False)
+        runs, _ = runs_of(ex, L)
+        # ghost columns, ghost rows, cell fluxes, x faces, y faces, update
+        assert [len(r["ops"]) for r in runs] == [6, 6, 9, 21, 21, 18]
+        # the in-place update reads and writes the same interior views
+        assert sorted(set(runs[-1]["stores"])) == sorted(L.base[k] for k in (p.meta["H"], p.meta["U"], p.meta["V"]))
+
+
+def test_shallow_water_step_is_one_tile_fused_group(fused):
+    """Cell fluxes, both half steps and the update become one kernel: the
+    fluxes and face values stay in shared memory (halo margins 2, 1, 1
+    around the update's tile), only H, U, V are written, and they are
+    renamed because the earlier runs read them around every point."""
+    N = 12
+    p = shallow_water(N, 1)
     L = fused.load(p, upload=False)
-    runs, _ = runs_of(fused, L)
-    # ghost columns, ghost rows, cell fluxes, x faces, y faces, update
-    assert [len(r["ops"]) for r in runs] == [6, 6, 9, 21, 21, 18]
-    # the in-place update reads and writes the same interior views
-    assert sorted(set(runs[-1]["stores"])) == sorted(L.base[k] for k in (p.meta["H"], p.meta["U"], p.meta["V"]))
+    js = json.loads(fused.plan(L, 0))
+    kinds = ["group" if "group" in i else ("run" if "run" in i else "action") for i in js["items"]]
+    assert kinds[:3] == ["run", "run", "group"] and set(kinds[3:]) == {"action"}
+    g = js["items"][2]["group"]
+    n = N - 2
+    assert [r["shape"] for r in g["runs"]] == [[N, N], [n + 1, n], [n, n + 1], [n, n]]
+    assert [r["box"] for r in g["runs"]] == [[0, 2, 0, 2], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 0, 0]]
+    hv = sorted(L.base[k] for k in (p.meta["H"], p.meta["U"], p.meta["V"]))
+    assert sorted(g["renamed"]) == hv
+    assert all(s["shared"] for r in g["runs"][:-1] for s in r["stores"])
+    assert sorted(s["base"] for s in g["runs"][-1]["stores"]) == hv
+    # every value read from shared memory comes from an earlier run at a shift of at most one
+    for k, r in enumerate(g["runs"]):
+        for ld in r["loads"]:
+            if ld["from"] >= 0:
+                assert ld["from"] < k and all(0 <= d <= 1 for d in ld["shift"])
+
+
+def test_tile_fusion_needs_dead_temporaries(fused):
+    """A temporary that is still live after the chain (no DISCARD) must reach
+    memory, so its producer stays a separate kernel."""
+    def chain(discard):
+        b = ProgramBuilder("live_temp")
+        a = b.base("float64", (20, 20), np.zeros(400))
+        t = b.base("float64", (19, 20))
+        o = b.base("float64", (18, 20))
+        b.emit("ADD", b.whole(t), b.sub2d(a, 0, 19, 0, 20), b.sub2d(a, 1, 20, 0, 20))
+        b.emit("SUBTRACT", b.whole(o), b.sub2d(t, 1, 19, 0, 20), b.sub2d(t, 0, 18, 0, 20))
+        if discard:
+            b.discard(t)
+        return b.build([o] if discard else [o, t])
+
+    for discard, groups in ((False, 0), (True, 1)):
+        L = fused.load(chain(discard), upload=False)
+        js = json.loads(fused.plan(L, 0))
+        assert sum("group" in i for i in js["items"]) == groups
 
 
 def test_montecarlo_instances_keep_everything_in_registers(fused):
@@ -203,7 +251,8 @@ def test_overlap_test_is_sound_and_exact_on_grids(fused):
 def test_every_workload_kernel_compiles_for_sm103a(flags):
     with Executor(flags | HOST) as ex:
         for p in (jacobi(16, 1), blackscholes(1000), blackscholes(1000, "float32"),
-                  montecarlo_pi(sizes=[10, 20]), shallow_water(12, 1), shallow_water(12, 1, "float32")):
+                  montecarlo_pi(sizes=[10, 20]), shallow_water(12, 1), shallow_water(12, 1, "float32"),
+                  *[c.program for c in tile_group_cases()]):
             L = ex.load(p, upload=False)
             assert V.vbe_plan_compile(ex.ctx, *L.batches[0]) >= 1
 

@@ -17,7 +17,8 @@ from paper_1210_7774_b300 import vbe as V  # noqa: E402
 from paper_1210_7774_b300.runner import Executor  # noqa: E402
 
 from emu.emulator import Emulator  # noqa: E402
-from parity_cases import all_small_cases, oracle_outputs  # noqa: E402
+from parity_cases import Case, _exact_check, all_small_cases, oracle_outputs, tile_group_cases  # noqa: E402
+from workloads import shallow_water  # noqa: E402
 
 CASES = all_small_cases()
 EMU = Emulator()
@@ -87,3 +88,21 @@ def test_emulated_shapes_on_stencil_and_packing(shape):
             want = oracle_outputs(case.program)
             got = emulate(case.program, MODES["fused"], shape)
             case.check(got, want)
+
+
+@pytest.mark.parametrize("tile", ["8x16", "16x32", "32x32"])
+def test_emulated_tile_groups(tile):
+    """Tile-fused groups at several tile shapes (ragged edge tiles, halos
+    across tile borders): shallow water (state renamed every step, ghost
+    ring copied across) and the synthetic chains."""
+    cases = tile_group_cases()
+    for dt in ("float64", "float32"):
+        p = shallow_water(40, 2, dt)
+        cases.append(Case(p.name, p, _exact_check(p)))
+    os.environ["VBE_RECORD_TILE"] = tile
+    try:
+        for case in cases:
+            got = emulate(case.program, MODES["fused"], (64, 1, 2))
+            case.check(got, oracle_outputs(case.program))
+    finally:
+        os.environ.pop("VBE_RECORD_TILE")
