@@ -315,17 +315,20 @@ def other_workload(args, local):
         out["note"] = "256x256 float64, 10 iterations; the grid (0.5 MB) is L2-resident, so this is launch-bound"
     elif args.workload == "shallow_water":
         from workloads import shallow_water
-        for dtype in ("float64", "float32"):
+        for dtype in [d for d in ("float64", "float32") if d in args.dtypes.split(",")]:
             p = shallow_water(4096, 50, dtype)
             isz = 8 if dtype == "float64" else 4
             cbytes = 6 * isz * 4096 * 4096 * 50  # H, U, V read once and written once per step
             res = {}
             modes["fused_graphs_untiled"] = F | V.VBE_GRAPHS | V.VBE_NO_TILE_FUSION
-            for name in ("fused_graphs", "fused_graphs_untiled", "plain_graphs"):
+            names = [m for m in ("fused_graphs", "fused_graphs_untiled", "plain_graphs")
+                     if args.paths == "fused,plain" or m in args.paths.split(",")]
+            for name in names:
                 sec, st = timed_batches(p, modes[name], 2)
                 res[name] = {"ms_per_step": sec / 50 * 1e3, "GB/s": cbytes / sec / 1e9,
                              "hbm_fraction": cbytes / sec / 1e9 / hbm}
-            res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_step"] / res["fused_graphs"]["ms_per_step"]
+            if "plain_graphs" in res and "fused_graphs" in res:
+                res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_step"] / res["fused_graphs"]["ms_per_step"]
             out[dtype] = res
     elif args.workload == "montecarlo":
         from workloads import mc_sizes, montecarlo_pi

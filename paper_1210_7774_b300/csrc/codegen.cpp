@@ -361,6 +361,16 @@ __device__ __forceinline__ i64 vbe_imul(i64 a, i64 b) { return (i64)((u64)a * (u
 __device__ __forceinline__ i64 vbe_ineg(i64 a) { return (i64)(0ull - (u64)a); }
 __device__ __forceinline__ i64 vbe_iabs(i64 a) { return a < 0 ? vbe_ineg(a) : a; }
 template <class T> __device__ __forceinline__ T vbe_max(T a, T b) { return (a > b || a != a) ? a : b; }
+// IEEE division with zero numerators kept off the hardware sequence's slow
+// path (tile-fused stencil kernels: state fields such as the momenta of a
+// fluid at rest are mostly zeros). For a == 0 the quotient is a * (1 / b'),
+// b' = b * 2^64 (so that 1 / b' cannot overflow for a subnormal b): the
+// signed zero, or NaN for b = 0 or NaN, exactly as a / b.
+template <class T> __device__ __forceinline__ T vbe_zdiv(T a, T b) {
+  const bool z = a == (T)0;
+  const T q = (z ? (T)1 : a) / (z ? b * (T)18446744073709551616.0 : b);
+  return z ? a * q : q;
+}
 template <class T> __device__ __forceinline__ T vbe_min(T a, T b) { return (a < b || a != a) ? a : b; }
 // RANDOM: splitmix64 finaliser of seed + (key + step*m + 1) * golden gamma,
 // top 53 bits scaled to [0, 1)
@@ -535,7 +545,7 @@ struct Gen {
       case VBE_OP_MULTIPLY: return i64t ? "vbe_imul(" + a + "," + b + ")" : "(" + a + " * " + b + ")";
       case VBE_OP_DIVIDE:
         if (r.soft_f64 && s.dt_in == VBE_FLOAT64) return "vbe_ddiv(" + a + ", " + b + ")";
-        return "(" + a + " / " + b + ")";
+        return guard_div ? "vbe_zdiv(" + a + ", " + b + ")" : "(" + a + " / " + b + ")";
       case VBE_OP_MAXIMUM: return "vbe_max(" + a + "," + b + ")";
       case VBE_OP_MINIMUM: return "vbe_min(" + a + "," + b + ")";
       case VBE_OP_SQRT:
@@ -599,6 +609,7 @@ struct Gen {
   // the per-element function: loaded values in, values to store out
   std::string elem_name = "vbe_elem";
   bool emit_struct = true;
+  bool guard_div = false;  // zero-numerator guard on native divisions
   void emit_elem() {
     if (emit_struct) o << "struct P { i64 w[" << L.nwords << "]; };\n";
     o << "__device__ __forceinline__ void " << elem_name << "(const P& p, i64 m";
@@ -1237,6 +1248,7 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     gen.L.consts = GL.consts[k];
     for (int q = 0; q < r.nrandom; ++q) gen.L.rnd[q] = GL.rnd[k] + 3 * q;
     gen.elem_name = "vbe_elem" + std::to_string(k);
+    gen.guard_div = true;
     gen.emit_struct = false;
     gen.emit_elem();
     o << gen.o.str();
@@ -1256,51 +1268,94 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
       const Run& r = g.runs[k];
       const int BH = box_rows(g, k, ts.th), BW = box_cols(g, k, ts.tw);
       o << "    {  // run " << k << ": " << r.steps.size() << " operations over a " << BH << " x " << BW << " box\n"
-        << "      const i64 rows = " << W(GL.dims[k]) << ", cols = " << W(GL.dims[k] + 1) << ";\n";
-      std::vector<std::string> lv, sv;
+        << "      const i64 rows = " << W(GL.dims[k]) << ", cols = " << W(GL.dims[k] + 1) << ";\n"
+        << "      const i64 r0 = i0 + (" << g.box[k][0] << "), c0 = j0 + (" << g.box[k][2] << ");\n"
+        << "      const bool inside = r0 >= 0 && c0 >= 0 && r0 + " << BH << " <= rows && c0 + " << BW
+        << " <= cols;\n";
+      // memory slots: pointer to the box origin and 32-bit offsets inside the
+      // box (strides are limited to 2^24 when the group is formed); slots
+      // with equal strides share one offset per point
+      std::vector<std::vector<int64_t>> pats;
+      auto pattern = [&](const Slot& sl) {
+        for (size_t q = 0; q < pats.size(); ++q)
+          if (pats[q] == sl.st) return (int)q;
+        pats.push_back(sl.st);
+        return (int)pats.size() - 1;
+      };
+      std::vector<std::pair<int, int>> pat_word;  // (pattern, stride word of a slot using it)
+      auto mem_slot = [&](const char* pfx, const std::string& n, const std::string& T, int w, const Slot& sl) {
+        int q = pattern(sl);
+        if ((int)pat_word.size() <= q) pat_word.push_back({q, w});
+        o << "      const auto " << pfx << "p" << n << " = vbe_ptr<" << T << ">(" << W(w) << ") + (r0 * " << W(w + 1)
+          << " + c0 * " << W(w + 2) << ");\n";
+        return std::string(pfx) + "p" + n + "[ix" + std::to_string(q) + "]";
+      };
+      std::vector<std::string> lv, sv, sm;
       for (size_t s = 0; s < r.loads.size(); ++s) {
         const std::string T = ctype(r.loads[s].dtype), n = std::to_string(s);
         const GroupLoad& ld = g.lds[k][s];
         if (ld.prod < 0) {
-          int w = GL.lw[k][s];
-          o << "      const auto lp" << n << " = vbe_ptr<const " << T << ">(" << W(w) << ");\n"
-            << "      const i64 la" << n << " = " << W(w + 1) << ", lb" << n << " = " << W(w + 2) << ";\n";
-          lv.push_back("lp" + n + "[i * la" + n + " + j * lb" + n + "]");
+          lv.push_back(mem_slot("l", n, "const " + T, GL.lw[k][s], r.loads[s]));
         } else {
           const int pk = ld.prod;
           const int roff = g.box[k][0] + ld.dr - g.box[pk][0], coff = g.box[k][2] + ld.dc - g.box[pk][2];
           const int PBW = box_cols(g, pk, ts.tw);
           o << "      const " << T << "* sl" << n << " = (const " << T << "*)(vbe_smem + " << soff[pk][ld.prod_store]
-            << ");\n";
-          lv.push_back("sl" + n + "[(li + " + std::to_string(roff) + ") * " + std::to_string(PBW) + " + (lj + " +
-                       std::to_string(coff) + ")]");
+            << ") + " << (roff * PBW + coff) << ";\n";
+          lv.push_back("sl" + n + "[li * " + std::to_string(PBW) + " + lj]");
         }
       }
       for (size_t s = 0; s < r.stores.size(); ++s) {
         const std::string T = ctype(r.stores[s].dtype), n = std::to_string(s);
         if (g.consumed[k][s])
           o << "      " << T << "* ss" << n << " = (" << T << "*)(vbe_smem + " << soff[k][s] << ");\n";
-        if (k == anchor) {
-          int w = GL.sw[k][s];
-          o << "      const auto sp" << n << " = vbe_ptr<" << T << ">(" << W(w) << ");\n"
-            << "      const i64 sa" << n << " = " << W(w + 1) << ", sb" << n << " = " << W(w + 2) << ";\n";
-        }
+        sm.push_back(k == anchor ? mem_slot("s", n, T, GL.sw[k][s], r.stores[s]) : "");
         sv.push_back("b" + n);
       }
-      o << "      for (int q = threadIdx.x; q < " << BH * BW << "; q += blockDim.x) {\n"
-        << "        const int li = q / " << BW << ", lj = q - li * " << BW << ";\n"
-        << "        const i64 i = i0 + (" << g.box[k][0] << " + li), j = j0 + (" << g.box[k][2] << " + lj);\n"
-        << "        if (i < 0 || i >= rows || j < 0 || j >= cols) continue;\n";
-      for (size_t s = 0; s < r.stores.size(); ++s) o << "        " << ctype(r.stores[s].dtype) << " b" << s << ";\n";
-      o << "        vbe_elem" << k << "(p, i * cols + j";
-      for (auto& x : lv) o << ", " << x;
-      for (auto& x : sv) o << ", " << x;
-      o << ");\n";
-      for (size_t s = 0; s < r.stores.size(); ++s) {
-        if (g.consumed[k][s]) o << "        ss" << s << "[q] = b" << s << ";\n";
-        if (k == anchor) o << "        sp" << s << "[i * sa" << s << " + j * sb" << s << "] = b" << s << ";\n";
+      for (auto& pw : pat_word) {
+        const std::string q = std::to_string(pw.first);
+        o << "      const int pa" << q << " = (int)" << W(pw.second + 1);
+        if (pats[pw.first][1] != 1) o << ", pb" << q << " = (int)" << W(pw.second + 2);
+        o << ";\n";
       }
-      o << "      }\n";
+      // points of the box in row-major order, blockDim at a time; the row and
+      // column advance by constants. Tiles whose box lies inside the run's
+      // shape take a loop without bounds tests.
+      const int DI = ts.block / BW, DJ = ts.block % BW;
+      auto body = [&](const std::string& ind) {
+        for (auto& pw : pat_word) {
+          const std::string q = std::to_string(pw.first);
+          o << ind << "const int ix" << q << " = li * pa" << q << " + "
+            << (pats[pw.first][1] == 1 ? std::string("lj") : "lj * pb" + q) << ";\n";
+        }
+        for (size_t s = 0; s < r.stores.size(); ++s) o << ind << ctype(r.stores[s].dtype) << " b" << s << ";\n";
+        o << ind << "vbe_elem" << k << "(p, (r0 + li) * cols + (c0 + lj)";
+        for (auto& x : lv) o << ", " << x;
+        for (auto& x : sv) o << ", " << x;
+        o << ");\n";
+        for (size_t s = 0; s < r.stores.size(); ++s) {
+          if (g.consumed[k][s]) o << ind << "ss" << s << "[q] = b" << s << ";\n";
+          if (k == anchor) o << ind << sm[s] << " = b" << s << ";\n";
+        }
+      };
+      auto advance = [&](const std::string& ind) {
+        o << ind << "li += " << DI << "; lj += " << DJ << ";\n"
+          << ind << "if (lj >= " << BW << ") { lj -= " << BW << "; ++li; }\n";
+      };
+      o << "      int li = threadIdx.x / " << BW << ", lj = threadIdx.x - li * " << BW << ";\n"
+        << "      if (inside) {\n"
+        << "        for (int q = threadIdx.x; q < " << BH * BW << "; q += " << ts.block << ") {\n";
+      body("          ");
+      advance("          ");
+      o << "        }\n"
+        << "      } else {\n"
+        << "        for (int q = threadIdx.x; q < " << BH * BW << "; q += " << ts.block << ") {\n"
+        << "          if (r0 + li >= 0 && r0 + li < rows && c0 + lj >= 0 && c0 + lj < cols) {\n";
+      body("            ");
+      o << "          }\n";
+      advance("          ");
+      o << "        }\n"
+        << "      }\n";
       if (k != anchor) o << "      __syncthreads();\n";
       o << "    }\n";
     }

@@ -46,6 +46,7 @@ constexpr int kMaxMargin = 16;      // largest halo of a run around the tile
 constexpr int kMaxGroupRuns = 8;
 constexpr int kMaxGroupSteps = 600;
 constexpr int64_t kGroupSmemMax = 200 * 1024;  // shared memory of the smallest tile shape (8 x 16)
+constexpr int64_t kMaxStride = 1 << 24;          // element strides of the group's views
 
 int64_t last_instr(const Run& r) {
   int64_t m = -1;
@@ -83,10 +84,10 @@ std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const 
   for (size_t i : items) {
     const Run& r = plan.items[i].run;
     if (r.has_red || r.shape.size() != 2 || r.shape[0] <= 0 || r.shape[1] <= 0) return nullptr;
-    for (auto& s : r.loads)
-      if (s.st.size() != 2) return nullptr;
-    for (auto& s : r.stores)
-      if (s.st.size() != 2) return nullptr;
+    // two strides per view, small enough for 32-bit offsets inside a tile
+    for (auto* v : {&r.loads, &r.stores})
+      for (auto& s : *v)
+        if (s.st.size() != 2 || std::llabs(s.st[0]) > kMaxStride || std::llabs(s.st[1]) > kMaxStride) return nullptr;
     steps += (int)r.steps.size();
     g->runs.push_back(r);
   }

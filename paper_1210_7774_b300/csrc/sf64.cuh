@@ -46,8 +46,11 @@ typedef long long sf_i64;
 __device__ SF_CALL double vbe_ddiv(double a, double b) {
   const sf_u64 ua = (sf_u64)__double_as_longlong(a), ub = (sf_u64)__double_as_longlong(b);
   const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
-  if (ea == 0 || ea == 0x7ff || eb == 0 || eb == 0x7ff) return a / b;
   const sf_u64 sign = (ua ^ ub) & SF_SIGN;
+  // a zero numerator over a normal or infinite divisor: a signed zero
+  // (frequent in practice, e.g. momenta of a fluid at rest)
+  if ((ua << 1) == 0 && eb != 0 && ((ub << 12) == 0 || eb != 0x7ff)) return __longlong_as_double((sf_i64)sign);
+  if (ea == 0 || ea == 0x7ff || eb == 0 || eb == 0x7ff) return a / b;
   const sf_u64 ma = (ua & SF_M52) | SF_H52, mb = (ub & SF_M52) | SF_H52;
   if ((ub & SF_M52) == 0) {  // b = +-2^k: the quotient is exact
     const int er = ea - eb + 1023;

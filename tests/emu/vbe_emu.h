@@ -142,6 +142,11 @@ inline long long __double_as_longlong(double d) {
   memcpy(&v, &d, 8);
   return v;
 }
+inline int __float_as_int(float f) {
+  int v;
+  memcpy(&v, &f, 4);
+  return v;
+}
 inline unsigned __float_as_uint(float f) {
   unsigned v;
   memcpy(&v, &f, 4);

@@ -266,6 +266,29 @@ def tile_group_cases(seed=11, N=37, M=45):
     b.free(t1, t2)
     p = b.build([o])
     out.append(Case(p.name, p, _exact_check(p)))
+    # divisions with zero numerators and special divisors (zero, subnormal,
+    # huge, infinite, NaN) inside a tile-fused group
+    for dt in ("float32", "float64"):
+        info = np.finfo(dt)
+        sp = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, info.tiny / 8, -info.tiny / 1024, info.max / 2, 1.5,
+                       -3.0], dt)
+        num = rng.standard_normal(N * M).astype(dt)
+        num[rng.random(N * M) < 0.6] = 0.0
+        num[rng.random(N * M) < 0.1] = -0.0
+        den = rng.standard_normal(N * M).astype(dt)
+        pick = rng.random(N * M) < 0.3
+        den[pick] = sp[rng.integers(0, len(sp), pick.sum())]
+        b = ProgramBuilder(f"tile_group_div_{dt}")
+        a = b.base(dt, (N, M), num)
+        d = b.base(dt, (N, M), den)
+        o = b.base(dt, (N, M), np.zeros(N * M, dt))
+        t = b.base(dt, (N, M - 1))
+        b.emit("DIVIDE", b.whole(t), b.sub2d(a, 0, N, 1, M), b.sub2d(d, 0, N, 0, M - 1))
+        b.emit("DIVIDE", b.sub2d(o, 0, N, 0, M - 2), b.sub2d(t, 0, N, 1, M - 1), b.sub2d(d, 0, N, 2, M))
+        b.emit("ADD", b.sub2d(o, 0, N, 0, M - 2), b.sub2d(o, 0, N, 0, M - 2), b.sub2d(t, 0, N, 0, M - 2))
+        b.discard(t)
+        p = b.build([o])
+        out.append(Case(p.name, p, _exact_check(p)))
     return out
 
 

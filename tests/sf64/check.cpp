@@ -36,8 +36,15 @@ int main(int argc, char** argv) {
       if (mode == 2) b = __longlong_as_double(__double_as_longlong(b) & ~0xFFFFFll);  // short mantissas
       if (mode == 3) a = b * (1.0 + (double)(g() % 1000) * 0x1p-52);                    // near-1 quotients
       if (mode == 4) { a = (double)(g() % 100000 + 1); b = (double)(g() % 1000 + 1); }   // exact quotients
+      if (mode == 5) a = (g() & 1) ? -0.0 : 0.0;                                         // zero numerators
+      if (mode == 6) {                                                                   // special operands
+        const double sp[] = {0.0, -0.0, INFINITY, -INFINITY, NAN, 1.0, -1.0, 0x1p-1074, -0x1p-1060};
+        a = (g() & 1) ? sp[g() % 9] : a;
+        b = sp[g() % 9];
+      }
       got = vbe_ddiv(a, b);
       want = a / b;
+      if (got == 0 && want == 0 && std::signbit(got) != std::signbit(want)) { got = 1; want = 2; }
     } else if (!strcmp(op, "sqrt")) {
       a = mode == 0 ? rnd_double(g, -1022, 1023) : std::fabs(rnd_double(g, -80, 80));
       if (mode == 1) { double r = (double)(g() % 94906265); a = r * r; }                  // perfect squares
