@@ -467,7 +467,12 @@ def main():
         "speedup_vs_plain": f64["plain"]["sec"] / sec,
         "float32": {"value": f32["fused"]["GB/s"], "hbm_fraction": f32["fused"]["GB/s"] / hbm,
                     "ms_per_step": f32["fused"]["sec"] * 1e3, "plain_value": f32["plain"]["GB/s"],
-                    "speedup_vs_plain": f32["plain"]["sec"] / f32["fused"]["sec"]},
+                    "speedup_vs_plain": f32["plain"]["sec"] / f32["fused"]["sec"],
+                    "roofline": {"bound": "hbm", "achieved": f32["fused"]["GB/s"], "peak": hbm, "unit": "GB/s",
+                                 "frac": f32["fused"]["GB/s"] / hbm, "peak_source": src,
+                                 "traffic": (measured_counters("blackscholes_f32", f32["kernel_hash"]) or {}).get(
+                                     "dram_bytes_per_launch"),
+                                 "kernel_hash": f32["kernel_hash"]}},
         "roofline": dict(roofline_f64(achieved, hbm, src, measured_counters("blackscholes_f64", f64["kernel_hash"]),
                                       args.options, sec, ck.get("sm_mhz") or 2032.0),
                          kernel_hash=f64["kernel_hash"]),

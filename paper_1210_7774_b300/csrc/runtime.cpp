@@ -838,6 +838,88 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
   return best;
 }
 
+// Whether the group runs faster as its separate kernels (temporaries through
+// memory, no halo recomputation). Timed once per signature and size class
+// with VBE_AUTOTUNE: the group kernel writes only second buffers and
+// scratch; the separate kernels write the group's temporaries (dead after
+// it) and scratch in place of the anchor's targets, so nothing live changes.
+bool group_split(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const GroupPtrs& real, bool may_tune) {
+  if (c->record) return getenv("VBE_RECORD_SPLIT") != nullptr;
+  const std::string sk = group_tune_key(G) + ":split";
+  auto it = c->tune.find(sk);
+  if (it != c->tune.end()) return it->second.block == 1;
+  Group& g = *G.g;
+  const int anchor = (int)g.runs.size() - 1;
+  if (!(may_tune && (c->cfg.flags & VBE_AUTOTUNE) && g.rows(anchor) * g.cols(anchor) >= (1 << 16))) return false;
+  std::vector<std::pair<void*, int64_t>> bufs;
+  auto scratch_for = [&](const Slot& st, const std::vector<int64_t>& shape) {
+    int64_t lo = st.offset, hi = st.offset;
+    for (int k = 0; k < 2; ++k) {
+      int64_t e = (shape[k] - 1) * st.st[k];
+      if (e < 0) lo += e; else hi += e;
+    }
+    int64_t bytes = (hi - lo + 1) * itemsize(st.dtype);
+    void* b = dev_alloc(c, ex, bytes);
+    bufs.push_back({b, bytes});
+    return (uintptr_t)b - (uintptr_t)(lo * itemsize(st.dtype));
+  };
+  // the group kernel, non-renamed anchor targets redirected
+  GroupPtrs gp = real;
+  const Run& ra = g.runs[anchor];
+  for (size_t s = 0; s < ra.stores.size(); ++s) {
+    bool renamed = false;
+    for (int64_t b : g.renamed)
+      if (b == ra.stores[s].base) renamed = true;
+    if (!renamed) gp.sp[anchor][s] = scratch_for(ra.stores[s], ra.shape);
+  }
+  std::vector<Launch> grp{build_group(c, G, ts, gp)};
+  // the separate kernels
+  std::vector<Launch> sep;
+  std::vector<Prepared> preps(g.runs.size());
+  for (int k = 0; k <= anchor; ++k) {
+    Run& r = g.runs[k];
+    if (k < anchor) allocate_outputs(c, ex, r);
+    Prepared& P = preps[k];
+    P.run = &r;
+    RunPtrs rp = run_ptrs(c, r);
+    if (k == anchor)
+      for (size_t s = 0; s < r.stores.size(); ++s) rp.sp[s] = scratch_for(r.stores[s], r.shape);
+    P.canon = canonicalize(r, true, rp.lp, rp.sp, rp.rp);
+    P.src = generate_source(r, P.canon, &P.prefix);
+    P.key = src_key(P.src);
+    P.kern = get_kernel(c, P.src);
+    TuneChoice tc = choose(c, ex, P, rp, true);
+    sep.push_back(build_single(c, ex, P, tc, rp));
+  }
+  if (!ex->ev0) {
+    cudaEventCreate(&ex->ev0);
+    cudaEventCreate(&ex->ev1);
+  }
+  auto time_of = [&](std::vector<Launch>& Ls) {
+    for (auto& L : Ls) {
+      issue(c, ex, L, false);
+      c->stats.kernel_launches--;
+    }
+    cuda_check(cudaEventRecord(ex->ev0, ex->stream), "event");
+    for (int rep = 0; rep < 3; ++rep)
+      for (auto& L : Ls) {
+        issue(c, ex, L, false);
+        c->stats.kernel_launches--;
+      }
+    cuda_check(cudaEventRecord(ex->ev1, ex->stream), "event");
+    cuda_check(cudaEventSynchronize(ex->ev1), "event sync");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ex->ev0, ex->ev1);
+    return ms;
+  };
+  const float t_group = time_of(grp), t_sep = time_of(sep);
+  for (auto& b : bufs) dev_free(c, ex, b.first, b.second);
+  TuneChoice tc;
+  tc.block = t_sep < t_group ? 1 : 0;
+  c->tune[sk] = tc;
+  return tc.block == 1;
+}
+
 uint64_t batch_key(const vbe_instr* prog, int64_t n) {
   uint64_t h = fnv1a(&n, sizeof n);
   return fnv1a(prog, (size_t)n * sizeof(vbe_instr), h);
@@ -1023,6 +1105,32 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       G.kern = get_kernel(c, G.src);
       GroupPtrs ptr = group_ptrs(c, g);
       TileShape ts = choose_group(c, ex, G, ptr, !capture);
+      if (group_split(c, ex, G, ts, ptr, !capture)) {
+        // measured faster as separate kernels (e.g. when the halo
+        // recomputation costs more arithmetic than the temporaries' traffic)
+        for (Run& r : g.runs) {
+          if (!r.has_red && r.elements() == 0) continue;
+          allocate_outputs(c, ex, r);
+          Prepared P;
+          P.run = &r;
+          RunPtrs rp = run_ptrs(c, r);
+          P.canon = canonicalize(r, true, rp.lp, rp.sp, rp.rp);
+          P.src = generate_source(r, P.canon, &P.prefix);
+          P.key = src_key(P.src);
+          P.kern = get_kernel(c, P.src);
+          TuneChoice tc = choose(c, ex, P, rp, !capture);
+          Launch L = build_single(c, ex, P, tc, rp);
+          if (capture) {
+            recorded.push_back(std::move(L));
+          } else {
+            issue(c, ex, L, false);
+            if (cacheable) issued.push_back(std::make_shared<Launch>(L));
+          }
+        }
+        ++i;
+        if (!capture) flush_deferred();
+        continue;
+      }
       Launch L = build_group(c, G, ts, ptr);
       if (capture) {
         recorded.push_back(std::move(L));

@@ -90,19 +90,22 @@ def test_emulated_shapes_on_stencil_and_packing(shape):
             case.check(got, want)
 
 
-@pytest.mark.parametrize("tile", ["8x16", "16x32", "32x32"])
+@pytest.mark.parametrize("tile", ["8x16", "16x32", "32x32", "split"])
 def test_emulated_tile_groups(tile):
     """Tile-fused groups at several tile shapes (ragged edge tiles, halos
     across tile borders): shallow water (state renamed every step, ghost
-    ring copied across) and the synthetic chains."""
+    ring copied across) and the synthetic chains; and the same groups run
+    as their separate kernels (the choice the tuner makes when that is
+    faster)."""
     cases = tile_group_cases()
     for dt in ("float64", "float32"):
         p = shallow_water(40, 2, dt)
         cases.append(Case(p.name, p, _exact_check(p)))
-    os.environ["VBE_RECORD_TILE"] = tile
+    var = "VBE_RECORD_SPLIT" if tile == "split" else "VBE_RECORD_TILE"
+    os.environ[var] = tile
     try:
         for case in cases:
             got = emulate(case.program, MODES["fused"], (64, 1, 2))
             case.check(got, oracle_outputs(case.program))
     finally:
-        os.environ.pop("VBE_RECORD_TILE")
+        os.environ.pop(var)
