@@ -504,11 +504,17 @@ struct Gen {
 
   Gen(const Run& r_, const Canon& c_) : r(r_), c(c_), L(layout_of(r_, c_)), soft(balance_f64(r_)) {}
 
+  bool const_params = false;  // constants arrive as arguments of the element function
   std::string opnd(const Operand& a) {
     if (a.kind == 0) return "l" + std::to_string(a.idx);
     if (a.kind == 2) return "v" + std::to_string(a.idx);
-    // constants are parameter words (so kernels that differ only in their
-    // constants share one compiled module)
+    if (const_params) return "kc" + std::to_string(a.idx);
+    return const_expr(a);
+  }
+
+  // constants are parameter words (so kernels that differ only in their
+  // constants share one compiled module)
+  std::string const_expr(const Operand& a) {
     std::string w = "p.w[" + std::to_string(L.consts + a.idx) + "]";
     switch (a.dtype) {
       case VBE_FLOAT64: return "__longlong_as_double(" + w + ")";
@@ -619,6 +625,8 @@ struct Gen {
       o << ", " << rt() << "& acc";
       if (kahan()) o << ", float& kc";
     }
+    if (const_params)
+      for (size_t k = 0; k < r.consts.size(); ++k) o << ", const " << ctype(r.consts[k].dtype) << " kc" << k;
     o << ") {\n  (void)m; (void)p;\n";
     for (auto& s : r.steps) o << "  const " << ctype(s.dt_out) << " v" << s.value << " = " << expr(s) << ";\n";
     for (size_t s = 0; s < r.stores.size(); ++s) o << "  o" << s << " = v" << r.store_value[s] << ";\n";
@@ -1237,6 +1245,7 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
   o << "struct P { i64 w[" << GL.nwords << "]; };\n";
   // one element function per run, reading its constants at the group's words
   std::vector<Canon> canons(m);
+  std::vector<std::vector<std::string>> cdecl(m);  // per run: the constants, decoded once per block
   for (int k = 0; k < m; ++k) {
     const Run& r = g.runs[k];
     Canon& cn = canons[k];
@@ -1249,6 +1258,8 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     for (int q = 0; q < r.nrandom; ++q) gen.L.rnd[q] = GL.rnd[k] + 3 * q;
     gen.elem_name = "vbe_elem" + std::to_string(k);
     gen.guard_div = true;
+    gen.const_params = true;
+    for (auto& cst : r.consts) cdecl[k].push_back(std::string(ctype(cst.dtype)) + " = " + gen.const_expr(cst));
     gen.emit_struct = false;
     gen.emit_elem();
     o << gen.o.str();
@@ -1318,10 +1329,16 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
         if (pats[pw.first][1] != 1) o << ", pb" << q << " = (int)" << W(pw.second + 2);
         o << ";\n";
       }
-      // points of the box in row-major order, blockDim at a time; the row and
-      // column advance by constants. Tiles whose box lies inside the run's
-      // shape take a loop without bounds tests.
-      const int DI = ts.block / BW, DJ = ts.block % BW;
+      for (size_t q = 0; q < cdecl[k].size(); ++q) {
+        const std::string& d = cdecl[k][q];
+        const size_t eq = d.find(" = ");
+        o << "      const " << d.substr(0, eq) << " kc" << q << d.substr(eq) << ";\n";
+      }
+      // points of the box in row-major order, blockDim at a time, unrolled
+      // (a compile-time trip count lets loads of several points overlap).
+      // Tiles whose box lies inside the run's shape skip the bounds tests.
+      const int NK = (BH * BW + ts.block - 1) / ts.block;
+      const bool partial = NK * ts.block > BH * BW;
       auto body = [&](const std::string& ind) {
         for (auto& pw : pat_word) {
           const std::string q = std::to_string(pw.first);
@@ -1332,30 +1349,38 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
         o << ind << "vbe_elem" << k << "(p, (r0 + li) * cols + (c0 + lj)";
         for (auto& x : lv) o << ", " << x;
         for (auto& x : sv) o << ", " << x;
+        for (size_t q = 0; q < r.consts.size(); ++q) o << ", kc" << q;
         o << ");\n";
         for (size_t s = 0; s < r.stores.size(); ++s) {
           if (g.consumed[k][s]) o << ind << "ss" << s << "[q] = b" << s << ";\n";
           if (k == anchor) o << ind << sm[s] << " = b" << s << ";\n";
         }
       };
-      auto advance = [&](const std::string& ind) {
-        o << ind << "li += " << DI << "; lj += " << DJ << ";\n"
-          << ind << "if (lj >= " << BW << ") { lj -= " << BW << "; ++li; }\n";
+      auto loop = [&](bool checked) {
+        o << "#pragma unroll\n"
+          << "        for (int kq = 0; kq < " << NK << "; ++kq) {\n"
+          << "          const int q = threadIdx.x + kq * " << ts.block << ";\n"
+          << "          const int li = q / " << BW << ", lj = q - li * " << BW << ";\n";
+        std::string cond;
+        if (partial) cond = "q < " + std::to_string(BH * BW);
+        if (checked) {
+          if (!cond.empty()) cond += " && ";
+          cond += "r0 + li >= 0 && r0 + li < rows && c0 + lj >= 0 && c0 + lj < cols";
+        }
+        if (cond.empty()) {
+          body("          ");
+        } else {
+          o << "          if (" << cond << ") {\n";
+          body("            ");
+          o << "          }\n";
+        }
+        o << "        }\n";
       };
-      o << "      int li = threadIdx.x / " << BW << ", lj = threadIdx.x - li * " << BW << ";\n"
-        << "      if (inside) {\n"
-        << "        for (int q = threadIdx.x; q < " << BH * BW << "; q += " << ts.block << ") {\n";
-      body("          ");
-      advance("          ");
-      o << "        }\n"
-        << "      } else {\n"
-        << "        for (int q = threadIdx.x; q < " << BH * BW << "; q += " << ts.block << ") {\n"
-        << "          if (r0 + li >= 0 && r0 + li < rows && c0 + lj >= 0 && c0 + lj < cols) {\n";
-      body("            ");
-      o << "          }\n";
-      advance("          ");
-      o << "        }\n"
-        << "      }\n";
+      o << "      if (inside) {\n";
+      loop(false);
+      o << "      } else {\n";
+      loop(true);
+      o << "      }\n";
       if (k != anchor) o << "      __syncthreads();\n";
       o << "    }\n";
     }
