@@ -191,7 +191,11 @@ int vbe_view_destroy(vbe_ctx* ctx, vbe_view view);
  * The batch is validated first; on any error nothing is enqueued. */
 int vbe_submit(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, vbe_ticket* ticket);
 /* Wait for a ticket. timeout_ns < 0 waits forever; VBE_ERR_TIMEOUT when the
- * limit passes (the work continues). */
+ * limit passes (the work continues). A ticket may be waited on any number
+ * of times. Tickets share a ring of 1024 events: waiting on a ticket more
+ * than 1024 submits old also waits for the later submit that reused its
+ * event (later work on the same stream), never for less. VBE_ERR_INVALID for
+ * a ticket this context never issued. */
 int vbe_wait(vbe_ctx* ctx, vbe_ticket ticket, int64_t timeout_ns);
 /* Read access (section "Vector Engine Manager", sync): wait for all work
  * enqueued so far, then copy nbytes of the base into host_dst. */

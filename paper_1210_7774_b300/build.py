@@ -37,12 +37,15 @@ def _stale() -> bool:
 
 def embed_device_sources() -> None:
     """Write _embed_sf64.inc: the device-side soft float64 code (tables and
-    functions) as one C++ raw string, which the code generator prepends to
-    kernels that need it."""
-    text = open(os.path.join(CSRC, "sf64_tables.h")).read() + "\n" + open(os.path.join(CSRC, "sf64.cuh")).read()
-    assert ")VBESF64" not in text
+    functions) as two C++ raw strings, which the runtime hands to NVRTC as
+    the headers "sf64_tables.h" and "sf64.cuh" of the kernels that need them."""
+    parts = []
+    for var, name in (("kSf64Tables", "sf64_tables.h"), ("kSf64Code", "sf64.cuh")):
+        text = open(os.path.join(CSRC, name)).read()
+        assert ")VBESF64" not in text
+        parts.append(f'static const char* const {var} = R"VBESF64({text})VBESF64";\n')
     out = os.path.join(CSRC, "_embed_sf64.inc")
-    body = 'R"VBESF64(' + text + ')VBESF64"\n'
+    body = "".join(parts)
     if not os.path.exists(out) or open(out).read() != body:
         with open(out, "w") as f:
             f.write(body)

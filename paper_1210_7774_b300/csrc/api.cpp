@@ -123,7 +123,8 @@ int vbe_finalize(vbe_ctx* ctx) {
     }
     for (auto& kv : c.batches)
       for (auto& v : kv.second.v) vbe::release_variant(v);
-    for (auto& kv : c.tickets) cudaEventDestroy(kv.second);
+    for (auto ev : c.ticket_ring)
+      if (ev) cudaEventDestroy(ev);
     cudaStreamSynchronize(c.exec.stream);
     vbe::release_exec(&c, &c.exec);
     vbe::release_error_word(&c);
@@ -230,6 +231,7 @@ int vbe_view_destroy(vbe_ctx* ctx, vbe_view view) {
   API_BEGIN
   if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
   if (!ctx->c.views.erase(view)) vbe::fail(VBE_ERR_INVALID, "unknown view");
+  ctx->c.epoch++;
   API_END
 }
 
@@ -240,11 +242,11 @@ int vbe_submit(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, vbe_ticket* ticke
   vbe::exec_batch(&c, &c.exec, prog, n, true);
   if (ticket && c.record) *ticket = 0;
   if (ticket && !c.record) {
-    cudaEvent_t ev;
-    vbe::cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
-    vbe::cuda_check(cudaEventRecord(ev, c.exec.stream), "event record");
+    if (c.ticket_ring.empty()) c.ticket_ring.assign(Ctx::kTicketRing, nullptr);
     int64_t t = c.next_ticket++;
-    c.tickets[t] = ev;
+    cudaEvent_t& ev = c.ticket_ring[t % Ctx::kTicketRing];
+    if (!ev) vbe::cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    vbe::cuda_check(cudaEventRecord(ev, c.exec.stream), "event record");
     *ticket = t;
   }
   API_END
@@ -255,14 +257,14 @@ int vbe_wait(vbe_ctx* ctx, vbe_ticket ticket, int64_t timeout_ns) {
   if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
   Ctx& c = ctx->c;
   if (c.record && ticket == 0) return VBE_OK;
-  auto it = c.tickets.find(ticket);
-  if (it == c.tickets.end()) vbe::fail(VBE_ERR_INVALID, "unknown ticket");
+  if (ticket <= 0 || ticket >= c.next_ticket || c.ticket_ring.empty()) vbe::fail(VBE_ERR_INVALID, "unknown ticket");
+  cudaEvent_t ev = c.ticket_ring[ticket % Ctx::kTicketRing];
   if (timeout_ns < 0) {
-    vbe::cuda_check(cudaEventSynchronize(it->second), "wait");
+    vbe::cuda_check(cudaEventSynchronize(ev), "wait");
   } else {
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
-      cudaError_t e = cudaEventQuery(it->second);
+      cudaError_t e = cudaEventQuery(ev);
       if (e == cudaSuccess) break;
       if (e != cudaErrorNotReady) vbe::cuda_check(e, "wait");
       auto el = std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
@@ -270,8 +272,6 @@ int vbe_wait(vbe_ctx* ctx, vbe_ticket ticket, int64_t timeout_ns) {
       std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
   }
-  cudaEventDestroy(it->second);
-  c.tickets.erase(it);
   vbe::check_error_word(&c);
   API_END
 }
@@ -322,6 +322,7 @@ int vbe_free(vbe_ctx* ctx, vbe_base base) {
     else ++v;
   }
   c.bases.erase(it);
+  c.epoch++;
   API_END
 }
 

@@ -447,9 +447,19 @@ __device__ __forceinline__ float vbe_rsqrt_approx(float x) {
 )CUDA";
 
 // float64 divide/sqrt/exp/log on the integer pipes (sf64_tables.h + sf64.cuh)
-const char* kSf64 =
 #include "_embed_sf64.inc"
-    ;
+
+// the soft float64 library reaches generated kernels as NVRTC headers; the
+// include line carries a hash of their text so that compiled-kernel caches
+// keyed by the source see every change of the library
+std::string sf64_include() {
+  static const std::string line = [] {
+    uint64_t h = fnv1a(kSf64Tables, strlen(kSf64Tables));
+    h = fnv1a(kSf64Code, strlen(kSf64Code), h);
+    return "#include \"sf64.cuh\"  // " + hex64(h) + "\n";
+  }();
+  return line;
+}
 
 bool uses_soft_f64(const Run& r) {
   if (!r.soft_f64) return false;
@@ -1095,13 +1105,65 @@ struct Gen {
 
 }  // namespace
 
+// Everything the generated text depends on (not sizes, strides, addresses
+// or constant values, which are parameter words), as a compact key.
+static std::string signature(const Run& r, const Canon& c) {
+  std::string k;
+  auto put = [&](int64_t v) { k.append((const char*)&v, sizeof v); };
+  put((int64_t)r.steps.size());
+  for (auto& s : r.steps) {
+    put(s.op); put(s.dt_out); put(s.dt_in); put(s.nin); put(s.value); put(s.random_idx);
+    for (int a = 0; a < s.nin; ++a) { put(s.a[a].kind); put(s.a[a].idx); put(s.a[a].dtype); }
+  }
+  put((int64_t)r.value_dtype.size());
+  for (int d : r.value_dtype) put(d);
+  put((int64_t)r.loads.size());
+  for (auto& l : r.loads) put(l.dtype);
+  put((int64_t)r.stores.size());
+  for (size_t q = 0; q < r.stores.size(); ++q) { put(r.stores[q].dtype); put(r.store_value[q]); }
+  put(r.has_red); put(r.red_op); put(r.red_dtype); put(r.red_value); put(r.nrandom); put(r.soft_f64);
+  put((int64_t)r.consts.size());
+  for (auto& o : r.consts) put(o.dtype);
+  const Spec& p = c.spec;
+  put((int)p.mode); put(p.nd); put(p.ndk); put(p.ndr); put(p.vec); put(p.E); put(p.red_cls); put(p.packed);
+  for (int v : p.load_cls) put(v);
+  put(-1);
+  for (int v : p.store_cls) put(v);
+  return k;
+}
+
+static std::string generate_source_uncached(const Run& r, const Canon& c, std::string* entry_prefix);
+
+// Generated sources are memoised by signature: a serving loop or a long
+// batch plans many runs of a few signatures.
 std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix) {
+  static std::mutex mu;
+  static std::unordered_map<std::string, std::pair<std::string, std::string>> memo;
+  const std::string key = signature(r, c);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) {
+      if (entry_prefix) *entry_prefix = it->second.second;
+      return it->second.first;
+    }
+  }
+  std::string prefix;
+  std::string src = generate_source_uncached(r, c, &prefix);
+  std::lock_guard<std::mutex> lk(mu);
+  if (memo.size() > 4096) memo.clear();
+  memo[key] = {src, prefix};
+  if (entry_prefix) *entry_prefix = prefix;
+  return src;
+}
+
+static std::string generate_source_uncached(const Run& r, const Canon& c, std::string* entry_prefix) {
   Gen g(r, c);
   g.o << "// generated by libvbe: " << r.steps.size() << " operations, " << r.loads.size() << " loads, "
       << r.stores.size() << " stores\n";
   g.o << kPrelude;
   if (uses_soft_f64(r))
-    g.o << kSf64 << "\n"
+    g.o << sf64_include()
         << "__device__ __forceinline__ double vbe_u01s(u64 seed, u64 key, u64 step, u64 m) {\n"
         << "  u64 z = seed + (key + step * m + 1ull) * 0x9E3779B97F4A7C15ull;\n"
         << "  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;\n"
@@ -1236,7 +1298,7 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
   o << "// generated by libvbe: tile-fused group of " << m << " runs, " << nsteps << " operations\n";
   o << kPrelude;
   if (soft)
-    o << kSf64 << "\n"
+    o << sf64_include()
       << "__device__ __forceinline__ double vbe_u01s(u64 seed, u64 key, u64 step, u64 m) {\n"
       << "  u64 z = seed + (key + step * m + 1ull) * 0x9E3779B97F4A7C15ull;\n"
       << "  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;\n"
@@ -1467,6 +1529,10 @@ void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std
     w[q + 5] = C;
     w[q + 6] = g.renamed_nelem[rr] - R * C;
   }
+}
+
+std::vector<std::pair<const char*, const char*>> nvrtc_headers() {
+  return {{"sf64_tables.h", kSf64Tables}, {"sf64.cuh", kSf64Code}};
 }
 
 }  // namespace vbe

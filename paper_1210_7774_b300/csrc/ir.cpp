@@ -347,6 +347,29 @@ std::vector<RInstr> resolve_batch(Ctx* c, const vbe_instr* prog, int64_t n) {
   return out;
 }
 
+// 64-bit words at a time: each word is multiplied in, the state rotated
+// and multiplied, then a splitmix64-style finaliser (keys for caches of
+// generated sources and batches; not a cryptographic hash)
+uint64_t hash64(const void* data, size_t n, uint64_t seed) {
+  const unsigned char* p = (const unsigned char*)data;
+  uint64_t h = seed ^ ((uint64_t)n * 0x9E3779B97F4A7C15ull);
+  size_t i = 0;
+  for (; i + 8 <= n; i += 8) {
+    uint64_t w;
+    memcpy(&w, p + i, 8);
+    h ^= w * 0xBF58476D1CE4E5B9ull;
+    h = ((h << 31) | (h >> 33)) * 0x94D049BB133111EBull;
+  }
+  uint64_t t = 0;
+  for (size_t k = 0; i + k < n; ++k) t |= (uint64_t)p[i + k] << (8 * k);
+  h ^= t * 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 30;
+  h *= 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 27;
+  h *= 0x94D049BB133111EBull;
+  return h ^ (h >> 31);
+}
+
 uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
   const unsigned char* p = (const unsigned char*)data;
   for (size_t i = 0; i < n; ++i) {

@@ -22,7 +22,14 @@ namespace vbe {
 
 static std::vector<char> nvrtc_compile(const std::string& src, std::string* log) {
   nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "vbe_run.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+  static const auto headers = nvrtc_headers();
+  std::vector<const char*> htext, hname;
+  for (auto& h : headers) {
+    hname.push_back(h.first);
+    htext.push_back(h.second);
+  }
+  if (nvrtcCreateProgram(&prog, src.c_str(), "vbe_run.cu", (int)headers.size(), htext.data(), hname.data()) !=
+      NVRTC_SUCCESS)
     fail(VBE_ERR_COMPILE, "nvrtcCreateProgram failed");
   // IEEE arithmetic: no contraction into FMA, no flush to zero, correctly
   // rounded division and square root
@@ -47,7 +54,7 @@ static std::vector<char> nvrtc_compile(const std::string& src, std::string* log)
 }
 
 static std::string src_key(const std::string& src) {
-  return hex64(fnv1a(src.data(), src.size())) + hex64(fnv1a(src.data(), src.size(), 7ull));
+  return hex64(hash64(src.data(), src.size(), 1)) + hex64(hash64(src.data(), src.size(), 0x5bd1e995ull));
 }
 
 std::vector<char> compile_cached(Ctx* c, const std::string& src, bool* compiled) {
@@ -921,8 +928,7 @@ bool group_split(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const 
 }
 
 uint64_t batch_key(const vbe_instr* prog, int64_t n) {
-  uint64_t h = fnv1a(&n, sizeof n);
-  return fnv1a(prog, (size_t)n * sizeof(vbe_instr), h);
+  return hash64(prog, (size_t)n * sizeof(vbe_instr), (uint64_t)n);
 }
 
 std::vector<std::pair<int64_t, uintptr_t>> fingerprint(Ctx* c, const std::vector<RInstr>& rp) {
@@ -954,6 +960,7 @@ void do_action(Ctx* c, Exec* ex, const HostAction& a) {
       else ++v;
     }
     c->bases.erase(it);
+    c->epoch++;
   }
 }
 
@@ -966,17 +973,26 @@ void do_action(Ctx* c, Exec* ex, const HostAction& a) {
 // address sets; each has its own cached launches.
 void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_graph) {
   if (c->host_only && !c->record) fail(VBE_ERR_NO_DEVICE, "host-only context");
-  std::vector<RInstr> rp = resolve_batch(c, prog, n);
   c->stats.batches++;
+  // a batch without FREE that comes again unchanged (same instructions,
+  // views and base addresses) skips validation, analysis and code
+  // generation: its launches are replayed from a graph (VBE_GRAPHS) or one
+  // by one. Never for one-shot server requests.
+  const bool may_cache = allow_graph && !c->record;
+  uint64_t key = may_cache ? (batch_key(prog, n) ^ (uint64_t)(uintptr_t)ex) : 0;
+  CachedBatch* known = nullptr;
+  if (may_cache) {
+    auto kb = c->batches.find(key);
+    if (kb != c->batches.end() && kb->second.rp_epoch == c->epoch) known = &kb->second;
+  }
+  std::vector<RInstr> rp_local;
+  if (!known) rp_local = resolve_batch(c, prog, n);
+  const std::vector<RInstr>& rp = known ? known->rp : rp_local;
   bool has_free = false;
   for (auto& r : rp)
     if (r.op == VBE_OP_FREE) has_free = true;
   bool graphs = allow_graph && (c->cfg.flags & VBE_GRAPHS) && !has_free && !c->record;
-  // a batch without FREE that comes again unchanged (same instructions,
-  // views and base addresses) skips analysis and code generation: its
-  // launches are replayed from a graph (VBE_GRAPHS) or one by one
-  bool cacheable = allow_graph && !has_free && !c->record;  // never for one-shot server requests
-  uint64_t key = cacheable ? (batch_key(prog, n) ^ (uint64_t)(uintptr_t)ex) : 0;
+  bool cacheable = may_cache && !has_free;
   static uint64_t use_clock = 0;
   CachedBatch* cb = nullptr;
   CachedVariant* var = nullptr;
@@ -990,6 +1006,10 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   if (cacheable) {
     cb = &c->batches[key];
     cb->key = key;
+    if (!known) {
+      cb->rp = rp_local;
+      cb->rp_epoch = c->epoch;
+    }
     auto fp = fingerprint(c, rp);
     for (auto& v : cb->v)
       if (v.fingerprint == fp) var = &v;

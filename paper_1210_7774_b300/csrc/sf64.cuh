@@ -28,6 +28,8 @@
 #ifndef VBE_SF64_CUH
 #define VBE_SF64_CUH
 
+#include "sf64_tables.h"
+
 // the four entry points are real calls: inlined, a kernel that uses them
 // several times grows large and compiles slowly
 #ifndef SF_CALL

@@ -196,6 +196,7 @@ struct Canon {  // a run in the form the generated kernel consumes
 Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& load_ptrs,
                    const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr);
 std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix);
+std::vector<std::pair<const char*, const char*>> nvrtc_headers();  // (include name, text)
 
 // words of the kernel parameter block, in the order the generated code reads them
 struct LaunchArgs {
@@ -272,6 +273,10 @@ struct CachedVariant {
 
 struct CachedBatch {
   uint64_t key = 0;
+  // the batch's validated instructions, reused while no view or base has
+  // been removed from the context since (epoch unchanged)
+  std::vector<RInstr> rp;
+  uint64_t rp_epoch = ~0ull;
   // a batch whose groups rename bases alternates between two address sets
   std::vector<CachedVariant> v;
 };
@@ -290,13 +295,17 @@ struct Ctx {
   std::unordered_map<int64_t, BaseRec> bases;
   std::unordered_map<int64_t, ViewDesc> views;
   int64_t next_handle = 1;
+  uint64_t epoch = 0;  // advanced whenever a view or base is removed
   std::string last_error;
   // caches
   std::unordered_map<std::string, std::shared_ptr<Kernel>> kernels;  // by source hash
   std::unordered_map<std::string, TuneChoice> tune;                  // by source hash
   std::unordered_map<uint64_t, CachedBatch> batches;
-  // tickets
-  std::unordered_map<int64_t, cudaEvent_t> tickets;
+  // tickets: ticket t is recorded in ring slot t mod kTicketRing; a slot
+  // reused by a later submit holds a later point of the same stream, so
+  // waiting on it also covers the older ticket
+  static constexpr int64_t kTicketRing = 1024;
+  std::vector<cudaEvent_t> ticket_ring;
   int64_t next_ticket = 1;
   vbe_stats stats{};
   cudaMemPool_t pool = nullptr;
@@ -332,6 +341,7 @@ void release_error_word(Ctx* c);
 bool take_error_word(Ctx* c);  // true (and cleared) when a staged kernel reported a failed wait
 void check_error_word(Ctx* c);  // fails with VBE_ERR_TIMEOUT when take_error_word is true
 uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull);
+uint64_t hash64(const void* data, size_t n, uint64_t seed);
 std::string hex64(uint64_t v);
 
 }  // namespace vbe

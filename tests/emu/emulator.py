@@ -20,6 +20,8 @@ import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 EMU_H = os.path.join(HERE, "vbe_emu.h")
+# the soft float64 headers that generated kernels include
+CSRC = os.path.join(os.path.dirname(os.path.dirname(HERE)), "paper_1210_7774_b300", "csrc")
 
 _GLOBALS = """
 thread_local dim3 threadIdx, blockIdx;
@@ -110,7 +112,7 @@ class Emulator:
         self.launches = 0
 
     def _key(self, src: str) -> str:
-        return hashlib.sha1((src + self._emu_h).encode()).hexdigest()[:20]
+        return hashlib.sha1((src + self._emu_h).encode()).hexdigest()[:20]  # the source names the headers' hash
 
     @property
     def _emu_h(self) -> str:
@@ -157,7 +159,8 @@ class Emulator:
             with open(cpp, "w") as f:
                 f.write("\n".join(parts))
             tmp = so + f".{os.getpid()}.tmp"
-            r = subprocess.run(["g++", "-std=c++20", "-O0", "-fPIC", "-shared", "-pthread", "-w", cpp, "-o", tmp],
+            r = subprocess.run(["g++", "-std=c++20", "-O0", "-fPIC", "-shared", "-pthread", "-w", "-I", CSRC, cpp,
+                                "-o", tmp],
                                stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
             if r.returncode != 0:
                 raise EmulationError("emulation build failed:\n" + r.stdout.decode()[-4000:])
