@@ -624,6 +624,7 @@ struct Gen {
 
   // the per-element function: loaded values in, values to store out
   std::string elem_name = "vbe_elem";
+  std::string block_reduce_name = "vbe_block_reduce";
   bool emit_struct = true;
   bool guard_div = false;  // zero-numerator guard on native divisions
   void emit_elem() {
@@ -653,7 +654,7 @@ struct Gen {
 
   void emit_block_reduce() {
     if (!r.has_red) return;
-    o << "__device__ __forceinline__ " << rt() << " vbe_block_reduce(" << rt() << " v) {\n"
+    o << "__device__ __forceinline__ " << rt() << " " << block_reduce_name << "(" << rt() << " v) {\n"
       << "  __shared__ " << rt() << " sh[32];\n"
       << "  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;\n"
       << "  for (int off = 16; off > 0; off >>= 1) { " << rt() << " t = __shfl_down_sync(0xffffffffu, v, off); v = "
@@ -697,7 +698,7 @@ struct Gen {
   void emit_full_epilogue(const std::string& pfx, const std::string& part, const std::string& slot,
                           const std::string& count, const std::string& nparts, const std::string& out) {
     o << pfx << "{\n"
-      << pfx << "  " << rt() << " bsum = vbe_block_reduce(" << acc_final() << ");\n"
+      << pfx << "  " << rt() << " bsum = " << block_reduce_name << "(" << acc_final() << ");\n"
       << pfx << "  __shared__ int s_last;\n"
       << pfx << "  if (threadIdx.x == 0) {\n"
       << pfx << "    vbe_ptr<" << rt() << ">(" << part << ")[" << slot << "] = bsum;\n"
@@ -712,7 +713,7 @@ struct Gen {
       << pfx << "    const auto pp = vbe_ptr<const volatile " << rt() << ">(" << part << ");\n"
       << pfx << "    for (i64 i = threadIdx.x; i < (i64)(" << nparts << "); i += blockDim.x) { " << rt()
       << " x = pp[i]; v = " << comb("v", "x") << "; }\n"
-      << pfx << "    v = vbe_block_reduce(v);\n"
+      << pfx << "    v = " << block_reduce_name << "(v);\n"
       << pfx << "    if (threadIdx.x == 0) { vbe_ptr<" << rt() << ">(" << out << ")[0] = v; vbe_ptr<unsigned>(" << count
       << ")[0] = 0u; }\n"
       << pfx << "  }\n"
@@ -1200,6 +1201,7 @@ struct GroupLayout {
   std::vector<std::vector<int>> lw, sw;  // per run, per slot: pointer, row stride, column stride (-1: shared)
   std::vector<int> consts, rnd;          // per run: first constant word, first RANDOM word
   std::vector<int> ren;                  // per renamed base: source, destination, offset, pitch, rows, cols, count
+  std::vector<int> red;                  // per run: reduction output, partials, counter (-1: no reduction)
 };
 
 GroupLayout group_layout(const Group& g) {
@@ -1239,6 +1241,10 @@ GroupLayout group_layout(const Group& g) {
   for (size_t r = 0; r < g.renamed.size(); ++r) {
     L.ren.push_back(w);
     w += 7;
+  }
+  for (int k = 0; k < m; ++k) {
+    L.red.push_back(g.runs[k].has_red ? w : -1);
+    if (g.runs[k].has_red) w += 3;
   }
   L.nwords = w;
   return L;
@@ -1308,14 +1314,16 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
   // one element function per run, reading its constants at the group's words
   std::vector<Canon> canons(m);
   std::vector<std::vector<std::string>> cdecl(m);  // per run: the constants, decoded once per block
+  std::vector<std::unique_ptr<Gen>> gens(m);
   for (int k = 0; k < m; ++k) {
     const Run& r = g.runs[k];
     Canon& cn = canons[k];
-    cn.spec.mode = Mode::ELEM;
+    cn.spec.mode = r.has_red ? Mode::FULL : Mode::ELEM;
     cn.spec.nd = 2;
     cn.spec.load_cls.assign(r.loads.size(), 2);
     cn.spec.store_cls.assign(r.stores.size(), 2);
-    Gen gen(r, cn);
+    gens[k].reset(new Gen(r, cn));
+    Gen& gen = *gens[k];
     gen.L.consts = GL.consts[k];
     for (int q = 0; q < r.nrandom; ++q) gen.L.rnd[q] = GL.rnd[k] + 3 * q;
     gen.elem_name = "vbe_elem" + std::to_string(k);
@@ -1323,8 +1331,11 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     gen.const_params = true;
     for (auto& cst : r.consts) cdecl[k].push_back(std::string(ctype(cst.dtype)) + " = " + gen.const_expr(cst));
     gen.emit_struct = false;
+    gen.block_reduce_name = "vbe_block_reduce" + std::to_string(k);
     gen.emit_elem();
+    gen.emit_block_reduce();
     o << gen.o.str();
+    gen.o.str("");
   }
   auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
   std::vector<TileShape> shapes = group_shapes(g);
@@ -1411,6 +1422,7 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
         o << ind << "vbe_elem" << k << "(p, (r0 + li) * cols + (c0 + lj)";
         for (auto& x : lv) o << ", " << x;
         for (auto& x : sv) o << ", " << x;
+        if (r.has_red) o << (gens[k]->kahan() ? ", acc, kc" : ", acc");
         for (size_t q = 0; q < r.consts.size(); ++q) o << ", kc" << q;
         o << ");\n";
         for (size_t s = 0; s < r.stores.size(); ++s) {
@@ -1438,11 +1450,24 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
         }
         o << "        }\n";
       };
+      if (r.has_red) {
+        gens[k]->o.str("");
+        gens[k]->emit_acc_init("      ");
+        o << gens[k]->o.str();
+      }
       o << "      if (inside) {\n";
       loop(false);
       o << "      } else {\n";
       loop(true);
       o << "      }\n";
+      if (r.has_red) {
+        // each point of this run belongs to exactly one tile (no halo), so
+        // block partials summed in block order give the whole reduction
+        const int w = GL.red[k];
+        gens[k]->o.str("");
+        gens[k]->emit_full_epilogue("      ", W(w + 1), "blockIdx.x", W(w + 2), "gridDim.x", W(w));
+        o << gens[k]->o.str();
+      }
       if (k != anchor) o << "      __syncthreads();\n";
       o << "    }\n";
     }
@@ -1478,7 +1503,8 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
 
 void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std::vector<uintptr_t>>& load_ptrs,
                       const std::vector<std::vector<uintptr_t>>& store_ptrs,
-                      const std::vector<std::pair<uintptr_t, uintptr_t>>& renamed_ptrs, LaunchArgs* out) {
+                      const std::vector<std::pair<uintptr_t, uintptr_t>>& renamed_ptrs,
+                      const std::vector<uintptr_t>& red_ptrs, uintptr_t partials, uintptr_t counters, LaunchArgs* out) {
   const int m = (int)g.runs.size();
   const int anchor = m - 1;
   GroupLayout GL = group_layout(g);
@@ -1528,6 +1554,16 @@ void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std
     w[q + 4] = R;
     w[q + 5] = C;
     w[q + 6] = g.renamed_nelem[rr] - R * C;
+  }
+  // reductions: one partial per block, a region and a completion counter per reducing run
+  int nq = 0;
+  for (int k = 0; k < m; ++k) {
+    if (GL.red[k] < 0) continue;
+    const Run& r = g.runs[k];
+    w[GL.red[k]] = (int64_t)(red_ptrs[k] + (uintptr_t)(r.red_out.offset * itemsize(r.red_dtype)));
+    w[GL.red[k] + 1] = (int64_t)(partials + (uintptr_t)(nq * w[3] * 8));
+    w[GL.red[k] + 2] = (int64_t)(counters + (uintptr_t)(nq * 4));
+    ++nq;
   }
 }
 

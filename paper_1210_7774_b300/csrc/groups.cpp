@@ -83,7 +83,10 @@ std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const 
   int steps = 0;
   for (size_t i : items) {
     const Run& r = plan.items[i].run;
-    if (r.has_red || r.shape.size() != 2 || r.shape[0] <= 0 || r.shape[1] <= 0) return nullptr;
+    if (r.shape.size() != 2 || r.shape[0] <= 0 || r.shape[1] <= 0) return nullptr;
+    // a reduction over the whole run (both dims) can stay: each of its
+    // points must then belong to exactly one tile (checked with the margins)
+    if (r.has_red && r.red_axes != std::vector<int>{0, 1}) return nullptr;
     // two strides per view, small enough for 32-bit offsets inside a tile
     for (auto* v : {&r.loads, &r.stores})
       for (auto& s : *v)
@@ -145,6 +148,19 @@ std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const 
     for (int v : {lo_r, hi_r, lo_c, hi_c})
       if (std::abs(v) > kMaxMargin) return nullptr;
     g->box[k] = {lo_r, hi_r, lo_c, hi_c};
+  }
+  for (int k = 0; k < m; ++k) {
+    const Run& r = g->runs[k];
+    if (!r.has_red) continue;
+    if (g->box[k] != std::array<int, 4>{0, 0, 0, 0}) return nullptr;
+    // nothing in the group may touch the reduction's output
+    for (auto& rr : g->runs) {
+      for (auto& l : rr.loads)
+        if (l.base == r.red_out.base) return nullptr;
+      for (auto& st : rr.stores)
+        if (st.base == r.red_out.base) return nullptr;
+      if (&rr != &r && rr.has_red && rr.red_out.base == r.red_out.base) return nullptr;
+    }
   }
   // renaming of bases the anchor updates while the group reads them around
   const Run& ra = g->runs[anchor];

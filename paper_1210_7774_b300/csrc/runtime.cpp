@@ -694,6 +694,7 @@ struct GroupPrepared {
 struct GroupPtrs {
   std::vector<std::vector<uintptr_t>> lp, sp;
   std::vector<std::pair<uintptr_t, uintptr_t>> ren;  // (current buffer, second buffer)
+  std::vector<uintptr_t> red;                        // per run: reduction output (0: none)
 };
 
 // memory the group reads must exist; the anchor's targets are allocated,
@@ -715,6 +716,12 @@ void allocate_group(Ctx* c, Exec* ex, const Group& g) {
   for (int64_t b : g.renamed) {
     BaseRec& br = c->bases[b];
     if (!br.shadow) br.shadow = dev_alloc(c, ex, br.bytes());
+  }
+  for (auto& r : g.runs) {
+    if (!r.has_red) continue;
+    BaseRec& br = c->bases[r.red_out.base];
+    if (!br.dptr) br.dptr = dev_alloc(c, ex, br.bytes());
+    br.written = true;
   }
 }
 
@@ -738,10 +745,11 @@ GroupPtrs group_ptrs(Ctx* c, const Group& g) {
     }
   }
   for (int64_t b : g.renamed) p.ren.push_back({base_ptr(c, b), (uintptr_t)c->bases[b].shadow});
+  for (auto& r : g.runs) p.red.push_back(r.has_red ? base_ptr(c, r.red_out.base) : 0);
   return p;
 }
 
-Launch build_group(Ctx* c, GroupPrepared& G, const TileShape& ts, const GroupPtrs& ptr) {
+Launch build_group(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const GroupPtrs& ptr) {
   Launch L;
   L.entry = G.prefix + "_sg" + std::to_string(ts.th) + "x" + std::to_string(ts.tw);
   L.key = G.key;
@@ -753,7 +761,13 @@ Launch build_group(Ctx* c, GroupPrepared& G, const TileShape& ts, const GroupPtr
                                                c->device),
                "dynamic shared memory attribute");
   LaunchArgs a;
-  fill_group_words(*G.g, ts, ptr.lp, ptr.sp, ptr.ren, &a);
+  int nred = 0;
+  for (auto& r : G.g->runs) nred += r.has_red ? 1 : 0;
+  const Run& ra = G.g->runs.back();
+  const int64_t ntiles = ((ra.shape[0] + ts.th - 1) / ts.th) * ((ra.shape[1] + ts.tw - 1) / ts.tw);
+  if (nred * ntiles > ex->scratch.n_partials) fail(VBE_ERR_INVALID, "tile-fused group needs more reduction partials");
+  fill_group_words(*G.g, ts, ptr.lp, ptr.sp, ptr.ren, ptr.red, (uintptr_t)ex->scratch.partials,
+                   (uintptr_t)ex->scratch.counters, &a);
   L.grid = (unsigned)std::max<int64_t>(1, a.w[3]);
   L.words = std::move(a.w);
   return L;
@@ -819,7 +833,7 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
   TileShape best = def;
   float best_ms = 1e30f;
   for (const TileShape& ts : G.shapes) {
-    Launch L = build_group(c, G, ts, ptr);
+    Launch L = build_group(c, ex, G, ts, ptr);
     issue(c, ex, L, false);  // warm
     c->stats.kernel_launches--;
     cuda_check(cudaEventRecord(ex->ev0, ex->stream), "event");
@@ -879,7 +893,7 @@ bool group_split(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const 
       if (b == ra.stores[s].base) renamed = true;
     if (!renamed) gp.sp[anchor][s] = scratch_for(ra.stores[s], ra.shape);
   }
-  std::vector<Launch> grp{build_group(c, G, ts, gp)};
+  std::vector<Launch> grp{build_group(c, ex, G, ts, gp)};
   // the separate kernels
   std::vector<Launch> sep;
   std::vector<Prepared> preps(g.runs.size());
@@ -1033,7 +1047,19 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   bool pack = (c->cfg.flags & VBE_PACK) != 0;
   std::vector<RInstr> staged = rp;
   Plan plan = make_plan(c, staged, fuse, pack);
-  ensure_scratch(c, ex, 1 << 20, 1 << 16);
+  {
+    // reduction partials of tile-fused groups: one per tile of the smallest
+    // tile shape (8 x 16) per reducing run, reserved before anything is issued
+    int64_t need = 1 << 20;
+    for (auto& it : plan.items) {
+      if (it.kind != 2) continue;
+      int64_t nred = 0;
+      for (auto& r : it.group->runs) nred += r.has_red ? 1 : 0;
+      const Run& ra = it.group->runs.back();
+      need = std::max<int64_t>(need, nred * ((ra.shape[0] + 7) / 8) * ((ra.shape[1] + 15) / 16));
+    }
+    ensure_scratch(c, ex, need, 1 << 16);
+  }
   bool capture = graphs && var && var->seen >= 1;
 
   // compile the batch's kernels in parallel on first sight
@@ -1151,7 +1177,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
         if (!capture) flush_deferred();
         continue;
       }
-      Launch L = build_group(c, G, ts, ptr);
+      Launch L = build_group(c, ex, G, ts, ptr);
       if (capture) {
         recorded.push_back(std::move(L));
       } else {

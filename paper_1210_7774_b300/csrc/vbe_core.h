@@ -216,7 +216,8 @@ struct TileShape {
 std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes);
 void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std::vector<uintptr_t>>& load_ptrs,
                       const std::vector<std::vector<uintptr_t>>& store_ptrs,
-                      const std::vector<std::pair<uintptr_t, uintptr_t>>& renamed_ptrs, LaunchArgs* out);
+                      const std::vector<std::pair<uintptr_t, uintptr_t>>& renamed_ptrs,
+                      const std::vector<uintptr_t>& red_ptrs, uintptr_t partials, uintptr_t counters, LaunchArgs* out);
 
 // ----------------------------------------------------------------- context
 struct BaseRec {

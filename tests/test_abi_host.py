@@ -63,8 +63,23 @@ def plain():
     ex.close()
 
 
-def test_jacobi_iteration_fuses_into_reduction_and_copy(fused):
+def test_jacobi_iteration_is_one_tile_fused_kernel(fused):
+    """The stencil run (with its merged reduction) and the copy back become
+    one kernel: t stays in shared memory, the grid is renamed (the stencil
+    reads it around every point), each point reduced exactly once."""
     p = jacobi(16, 2)
+    L = fused.load(p, upload=False)
+    js = json.loads(fused.plan(L, 0))
+    groups = [i["group"] for i in js["items"] if "group" in i]
+    assert len(groups) == 1 and not [i for i in js["items"] if "run" in i]
+    g = groups[0]
+    assert [r["box"] for r in g["runs"]] == [[0, 0, 0, 0], [0, 0, 0, 0]]
+    assert g["renamed"] == [L.base[p.meta["grid"]]]
+
+
+def test_jacobi_iteration_fuses_into_reduction_and_copy():
+    p = jacobi(16, 2)
+    fused = Executor(V.VBE_FUSE | V.VBE_PACK | V.VBE_NO_TILE_FUSION | HOST)
     L = fused.load(p, upload=False)
     runs, _ = runs_of(fused, L)
     assert [r["mode"] for r in runs] == ["full_reduce", "elementwise"]
@@ -74,6 +89,7 @@ def test_jacobi_iteration_fuses_into_reduction_and_copy(fused):
     t_id = list(p.bases)[1]  # bases: full grid, t, d, r, deltas
     assert first["stores"] == [L.base[t_id]]  # d and r stay in registers
     assert runs[1]["ops"] == ["COPY"]
+    fused.close()
 
 
 def test_plain_path_is_one_run_per_bytecode(plain):

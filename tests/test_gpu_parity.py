@@ -90,6 +90,19 @@ def test_jacobi_config_full_size_graphs_and_plain_agree():
                          F64_REDUCE_RTOL, "deltas")
 
 
+def test_jacobi_paper_size_tile_fused():
+    """The paper's Jacobi size (7168^2 float64, 4 iterations), each iteration
+    one tile-fused kernel with the grid renamed: grid bit-exact with the
+    oracle, deltas within the reduction tolerance."""
+    p = jacobi(7168, 4)
+    want = oracle_outputs(p)
+    got = run_gpu(p, FUSED | V.VBE_GRAPHS)
+    assert_exact(got[p.meta["grid"]], want[p.meta["grid"]], "grid")
+    g0 = p.bases[p.meta["grid"]].init
+    assert_close_sum(got[p.meta["deltas"]], want[p.meta["deltas"]], np.full(1, 2 * np.abs(g0).sum()),
+                     F64_REDUCE_RTOL, "deltas")
+
+
 @pytest.mark.parametrize("staging", [0, 2048])
 @pytest.mark.parametrize("dtype,rtol", [("float64", 1e-12), ("float32", 1e-5)])
 def test_blackscholes_full_size_sampled(dtype, rtol, staging):
