@@ -10,7 +10,7 @@ path (one launch per bytecode) is timed on the same GPU beside it.
 ``--impl reference`` times the oracle (the CPU reference interpreter) on a
 bounded sample of the same workload instead.
 
-Other workloads: ``--workload jacobi|shallow_water|montecarlo|serving``.
+Other workloads: ``--workload jacobi|shallow_water|stencil|montecarlo|serving``.
 """
 from __future__ import annotations
 
@@ -342,6 +342,22 @@ def other_workload(args, local):
             if "plain_graphs" in res and "fused_graphs" in res:
                 res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_step"] / res["fused_graphs"]["ms_per_step"]
             out[dtype] = res
+    elif args.workload == "stencil":
+        from workloads import gray_scott
+        R, C, steps = 10240, 1024, 10
+        for dtype in [d for d in ("float64", "float32") if d in args.dtypes.split(",")]:
+            p = gray_scott(R, C, steps, dtype)
+            isz = 8 if dtype == "float64" else 4
+            cbytes = (2 * R * C + 2 * (R - 2) * (C - 2)) * isz * steps  # U, V read once, interiors written once
+            res = {}
+            modes["fused_graphs_untiled"] = F | V.VBE_GRAPHS | V.VBE_NO_TILE_FUSION
+            for name in ("fused_graphs", "fused_graphs_untiled", "plain_graphs"):
+                sec, st = timed_batches(p, modes[name], 3)
+                res[name] = {"ms_per_step": sec / steps * 1e3, "GB/s": cbytes / sec / 1e9,
+                             "hbm_fraction": cbytes / sec / 1e9 / hbm}
+            res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_step"] / res["fused_graphs"]["ms_per_step"]
+            out[dtype] = res
+        out["note"] = "Gray-Scott reaction-diffusion, 10240x1024, 10 steps (the paper's synthetic-stencil size)"
     elif args.workload == "montecarlo":
         from workloads import mc_sizes, montecarlo_pi
         p = montecarlo_pi(sizes=mc_sizes(256))

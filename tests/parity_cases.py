@@ -9,7 +9,7 @@ import math
 import numpy as np
 
 import oracle
-from workloads import (Const, ProgramBuilder, blackscholes, bs_inputs, jacobi, montecarlo_pi,
+from workloads import (Const, ProgramBuilder, blackscholes, bs_inputs, gray_scott, jacobi, montecarlo_pi,
                        shallow_water)
 
 F64_REDUCE_RTOL = 1e-12
@@ -385,6 +385,10 @@ def workload_cases(scale="small"):
     N = 18 if scale == "small" else 130
     for dt in ("float64", "float32"):
         p = shallow_water(N, 3 if scale == "small" else 10, dt)
+        out.append(Case(p.name, p, _exact_check(p)))
+    R, C = (20, 24) if scale == "small" else (130, 70)
+    for dt in ("float64", "float32"):
+        p = gray_scott(R, C, 3 if scale == "small" else 10, dt)
         out.append(Case(p.name, p, _exact_check(p)))
     sizes = [1, 37, 1000, 4096, 333] if scale == "small" else \
         np.floor(np.exp2(10 + 8 * np.random.default_rng(3).random(64))).astype(int).tolist()

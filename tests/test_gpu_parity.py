@@ -17,8 +17,8 @@ from paper_1210_7774_b300.runner import Executor  # noqa: E402
 import oracle  # noqa: E402
 from parity_cases import (F64_REDUCE_RTOL, all_small_cases, assert_close_sum, assert_exact,  # noqa: E402
                           oracle_outputs, workload_cases)
-from workloads import (blackscholes, bs_inputs, jacobi, mc_sizes, montecarlo_pi, shallow_water,  # noqa: E402
-                       sw_inputs)
+from workloads import (blackscholes, bs_inputs, gray_scott, jacobi, mc_sizes, montecarlo_pi,  # noqa: E402
+                       shallow_water, sw_inputs)
 
 pytestmark = pytest.mark.gpu
 CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
@@ -88,6 +88,18 @@ def test_jacobi_config_full_size_graphs_and_plain_agree():
         g0 = p.bases[p.meta["grid"]].init
         assert_close_sum(got[p.meta["deltas"]], want[p.meta["deltas"]], np.full(1, 2 * np.abs(g0).sum()),
                          F64_REDUCE_RTOL, "deltas")
+
+
+def test_synthetic_stencil_full_size():
+    """10240 x 1024 Gray-Scott fields, float64 and float32: two steps
+    bit-exact with the oracle (only + - * in a fixed order), tile-fused
+    with both fields renamed."""
+    for dt in ("float64", "float32"):
+        p = gray_scott(10240, 1024, 2, dt)
+        want = oracle_outputs(p)
+        got = run_gpu(p, FUSED | V.VBE_GRAPHS)
+        for q in ("U", "V"):
+            assert_exact(got[p.meta[q]], want[p.meta[q]], q + " " + dt)
 
 
 def test_jacobi_paper_size_tile_fused():

@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import (Const, ProgramBuilder, blackscholes, bs_inputs, jacobi, jacobi_inputs,
-                       montecarlo_pi, shallow_water, sw_inputs)
+from workloads import (Const, ProgramBuilder, blackscholes, bs_inputs, gray_scott, jacobi, jacobi_inputs,
+                       montecarlo_pi, shallow_water, stencil_inputs, sw_inputs)
 from workloads.blackscholes import AS_B, AS_P, _cnd
 
 # ---------------------------------------------------------------- Jacobi
@@ -260,3 +260,62 @@ def test_montecarlo_estimate_is_statistically_sound():
     sigma = math.sqrt(q * (1 - q) / n)
     for c in mem[p.meta["count"]].tolist():
         assert abs(c / n - q) < 5 * sigma
+
+
+# ------------------------------------------------------ synthetic stencil
+
+def _gray_scott_loops(U, V, steps, Du, Dv, f, k):
+    """Explicit Euler steps of the Gray-Scott equations, one cell at a time
+    in plain Python floats (the ring stays fixed), with the five-point
+    Laplacian summed up, down, left, right, then minus 4 times the centre."""
+    U = [list(map(float, r)) for r in U]
+    V = [list(map(float, r)) for r in V]
+    R, C = len(U), len(U[0])
+    for _ in range(steps):
+        nU = [r[:] for r in U]
+        nV = [r[:] for r in V]
+        for i in range(1, R - 1):
+            for j in range(1, C - 1):
+                u, v = U[i][j], V[i][j]
+                lu = U[i - 1][j] + U[i + 1][j] + U[i][j - 1] + U[i][j + 1] - u * 4.0
+                lv = V[i - 1][j] + V[i + 1][j] + V[i][j - 1] + V[i][j + 1] - v * 4.0
+                uvv = u * v * v
+                nU[i][j] = lu * Du - uvv + (1.0 - u) * f + u
+                nV[i][j] = lv * Dv + uvv - v * (f + k) + v
+        U, V = nU, nV
+    return np.array(U), np.array(V)
+
+
+def test_stencil_matches_cell_loops_bitwise():
+    inp = stencil_inputs(11, 13, patches=3, seed=4)
+    p = gray_scott(11, 13, 3, inputs=inp)
+    mem = oracle.run(p)
+    U, V = _gray_scott_loops(inp["U"], inp["V"], 3, p.meta["Du"], p.meta["Dv"], p.meta["F"], p.meta["k"])
+    assert np.array_equal(mem[p.meta["U"]].reshape(11, 13), U)
+    assert np.array_equal(mem[p.meta["V"]].reshape(11, 13), V)
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_stencil_rest_state_is_bitwise_steady(dtype):
+    """U = 1, V = 0 is a fixed point: every Laplacian is exactly 0 and the
+    reaction terms vanish."""
+    inp = stencil_inputs(12, 14, dtype, kind="rest")
+    p = gray_scott(12, 14, 4, dtype, inputs=inp)
+    mem = oracle.run(p)
+    assert np.array_equal(mem[p.meta["U"]], inp["U"].ravel())
+    assert np.array_equal(mem[p.meta["V"]], inp["V"].ravel())
+
+
+def test_stencil_keeps_row_mirror_symmetry_bitwise():
+    """A state symmetric under i -> R-1-i stays so bitwise (up and down
+    enter the Laplacian through one commutative addition)."""
+    R, C = 14, 10
+    rng = np.random.default_rng(3)
+    half = rng.random((R // 2, C))
+    V = np.concatenate([half, half[::-1]]) * 0.25
+    U = 1.0 - V
+    p = gray_scott(R, C, 5, inputs={"U": U, "V": V})
+    mem = oracle.run(p)
+    for q in ("U", "V"):
+        a = mem[p.meta[q]].reshape(R, C)
+        assert np.array_equal(a, a[::-1])

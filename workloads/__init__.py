@@ -10,7 +10,8 @@ from .jacobi import jacobi, jacobi_inputs
 from .blackscholes import blackscholes, bs_inputs
 from .shallow_water import shallow_water, sw_inputs
 from .montecarlo import montecarlo_pi, mc_sizes
+from .stencil import gray_scott, stencil_inputs
 
 __all__ = ["DTYPES", "ITEMSIZE", "NP_DTYPE", "Base", "Const", "Instr", "Program", "ProgramBuilder",
            "View", "c_strides", "jacobi", "jacobi_inputs", "blackscholes", "bs_inputs",
-           "shallow_water", "sw_inputs", "montecarlo_pi", "mc_sizes"]
+           "shallow_water", "sw_inputs", "montecarlo_pi", "mc_sizes", "gray_scott", "stencil_inputs"]
