@@ -100,7 +100,12 @@ enum {
                              device memory here (a fusion barrier)        */
   VBE_OP_DISCARD = 26,    /* [0] out's base contents are dead until written
                              again; the handle stays valid                */
-  VBE_OP_FREE = 27        /* [0] out's base is released after the batch   */
+  VBE_OP_FREE = 27,       /* [0] out's base is released after the batch   */
+  VBE_OP_ARGMIN_REDUCE = 28, /* [1] int64 out = index along `axis` of the first
+                             minimum (a NaN counts as the minimum: index of
+                             the first NaN); empty axis is an error       */
+  VBE_OP_ARGMAX_REDUCE = 29, /* [1] likewise for the first maximum          */
+  VBE_OP_USER_BASE = 64   /* opcodes from here on are user-defined (vbe_op_register) */
 };
 #define VBE_MAX_NDIM 8
 
@@ -241,6 +246,26 @@ int vbe_get_stats(vbe_ctx* ctx, vbe_stats* out);
 
 const char* vbe_strerror(int code);
 const char* vbe_last_error(vbe_ctx* ctx);
+
+/* Register a user-defined elementwise operation (section "Interface": the
+ * engine's API includes registration of a user-defined operation). `body`
+ * is the body of a CUDA device function of nin (1..3) arguments named a, b,
+ * c, all of `dtype` (VBE_FLOAT32, VBE_FLOAT64 or VBE_INT64), returning that
+ * dtype, e.g. "return a * a + b;". It is compiled into every fused kernel
+ * that uses the operation, so it fuses with the bytecodes around it; the
+ * code generator compiles with IEEE arithmetic (no FMA contraction), so a
+ * body of + - * / sqrt is evaluated exactly as written. `name` is an
+ * identifier of at most 48 characters. *opcode receives the operation's
+ * opcode (>= VBE_OP_USER_BASE) for vbe_instr.op; registering the same
+ * (name, body, nin, dtype) again returns the same opcode, in any context.
+ * Opcodes are process-wide; at most 1024 operations. Errors:
+ * VBE_ERR_INVALID (name, arity, dtype, a name registered with another
+ * definition, table full), VBE_ERR_COMPILE (the body does not compile; the
+ * message holds the compiler log). Instructions using the opcode follow
+ * the arithmetic rules: inputs and output of the registered dtype, one
+ * input may be a constant. */
+int vbe_op_register(vbe_ctx* ctx, const char* name, const char* body, int32_t nin, int32_t dtype,
+                    int32_t* opcode);
 
 /* Sum of n float64 values x[0..n) into *out (both device pointers), on
  * `stream` (a cudaStream_t, or NULL), allocating nothing. The paper has no

@@ -71,6 +71,7 @@ class Memory:
     def __init__(self, program: Program):
         self.dtype = {}
         self.buf = {}
+        self.user_ops = getattr(program, "user_ops", {})
         for bid, b in program.bases.items():
             dt = NP_DTYPE[b.dtype]
             self.dtype[bid] = dt
@@ -243,6 +244,18 @@ def execute(mem: Memory, ins_) -> None:
             if idt != odt or odt.name not in NUMERIC:
                 raise OracleError(f"{op} dtype")
             o[...] = (np.absolute if op == "ABSOLUTE" else np.negative)(args[0])
+        elif op.startswith("USER:"):
+            # section "Interface": a registered user-defined operation,
+            # run through its NumPy definition
+            u = mem.user_ops.get(op[5:])
+            if u is None:
+                raise OracleError(f"unknown user operation {op}")
+            if len(args) != u.nin or any(a.dtype != np.dtype(u.dtype) for a in args) or odt != np.dtype(u.dtype):
+                raise OracleError(f"{op}: operands must be {u.nin} x {u.dtype}")
+            r = np.asarray(u.fn(*args))
+            if r.dtype != odt:
+                raise OracleError(f"{op}: the NumPy definition returned {r.dtype}, not {odt}")
+            o[...] = r
         else:
             raise OracleError(f"unknown opcode {op}")
 

@@ -4,6 +4,8 @@
 #include <cstring>
 #include <thread>
 
+#include <cctype>
+
 #include "vbe_core.h"
 
 using vbe::Ctx;
@@ -374,6 +376,30 @@ int vbe_plan_compile(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, int64_t* nk
   else vbe::precompile(&c, srcs);
   for (auto& st : p.staging) c.bases.erase(st.first);
   if (nkernels) *nkernels = k;
+  API_END
+}
+
+int vbe_op_register(vbe_ctx* ctx, const char* name, const char* body, int32_t nin, int32_t dtype,
+                    int32_t* opcode) {
+  API_BEGIN
+  if (!ctx || !name || !body || !opcode) vbe::fail(VBE_ERR_INVALID, "null argument");
+  Ctx& c = ctx->c;
+  if (nin < 1 || nin > 3 || (dtype != VBE_FLOAT32 && dtype != VBE_FLOAT64 && dtype != VBE_INT64))
+    vbe::fail(VBE_ERR_INVALID, "a user operation takes 1 to 3 inputs of float32, float64 or int64");
+  // the body must compile for the target before the opcode exists
+  const std::string T = vbe::ctype(dtype), nm = name;
+  std::string src = "typedef long long i64;\n__device__ __forceinline__ " + T + " vbe_user_" + nm + "(" + T + " a";
+  if (nin > 1) src += ", " + T + " b";
+  if (nin > 2) src += ", " + T + " c";
+  src += ") {\n" + std::string(body) + "\n}\nextern \"C\" __global__ void vbe_user_probe(" + T + "* o, const " + T +
+         "* x) { o[0] = vbe_user_" + nm + "(x[0]";
+  if (nin > 1) src += ", x[1]";
+  if (nin > 2) src += ", x[2]";
+  src += "); }\n";
+  for (char ch : nm)
+    if (!(isalnum((unsigned char)ch) || ch == '_')) vbe::fail(VBE_ERR_INVALID, "operation name must be an identifier");
+  vbe::compile_cached(&c, src, nullptr);
+  *opcode = vbe::register_user_op(nm, body, nin, dtype);
   API_END
 }
 

@@ -461,6 +461,25 @@ std::string sf64_include() {
   return line;
 }
 
+// definitions of the user operations a run uses (section "Interface":
+// registered user-defined operations), ahead of its element function
+std::string user_op_defs(const std::vector<const Run*>& runs) {
+  std::vector<int> seen;
+  std::string out;
+  for (const Run* r : runs)
+    for (auto& s : r->steps) {
+      const UserOp* u = user_op(s.op);
+      if (!u || std::find(seen.begin(), seen.end(), s.op) != seen.end()) continue;
+      seen.push_back(s.op);
+      const std::string T = ctype(u->dtype);
+      out += "__device__ __forceinline__ " + T + " vbe_user_" + u->name + "(" + T + " a";
+      if (u->nin > 1) out += ", " + T + " b";
+      if (u->nin > 2) out += ", " + T + " c";
+      out += ") {\n" + u->body + "\n}\n";
+    }
+  return out;
+}
+
 bool uses_soft_f64(const Run& r) {
   if (!r.soft_f64) return false;
   for (auto& s : r.steps)
@@ -552,6 +571,12 @@ struct Gen {
         case VBE_OP_EQUAL: return "vbe_deq(" + a + ", " + b + ")";
         case VBE_OP_NOT_EQUAL: return "(!vbe_deq(" + a + ", " + b + "))";
       }
+    }
+    if (const UserOp* u = user_op(s.op)) {
+      std::string call = "vbe_user_" + u->name + "(" + a;
+      if (s.nin > 1) call += ", " + b;
+      if (s.nin > 2) call += ", " + d;
+      return call + ")";
     }
     if (sf && s.op == VBE_OP_NEGATIVE) return "vbe_dneg(" + a + ")";
     if (sf && s.op == VBE_OP_ABSOLUTE) return "vbe_dabs(" + a + ")";
@@ -1170,6 +1195,7 @@ static std::string generate_source_uncached(const Run& r, const Canon& c, std::s
         << "  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;\n"
         << "  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;\n"
         << "  return vbe_u53_to_unit((z ^ (z >> 31)) >> 11);\n}\n";
+  g.o << user_op_defs({&r});
   g.emit_elem();
   g.emit_block_reduce();
   if (tile_mode(c.spec.mode)) {
@@ -1311,6 +1337,11 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
       << "  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;\n"
       << "  return vbe_u53_to_unit((z ^ (z >> 31)) >> 11);\n}\n";
   o << "struct P { i64 w[" << GL.nwords << "]; };\n";
+  {
+    std::vector<const Run*> rs;
+    for (auto& r : g.runs) rs.push_back(&r);
+    o << user_op_defs(rs);
+  }
   // one element function per run, reading its constants at the group's words
   std::vector<Canon> canons(m);
   std::vector<std::vector<std::string>> cdecl(m);  // per run: the constants, decoded once per block

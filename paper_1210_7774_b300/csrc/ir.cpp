@@ -6,6 +6,9 @@
 // operands, operands are multidimensional arrays). Views follow section
 // "Numerical Python" (array-base / array-view).
 #include <algorithm>
+#include <cctype>
+#include <deque>
+#include <mutex>
 #include <cstring>
 #include <numeric>
 #include <set>
@@ -70,9 +73,50 @@ OpKind op_kind(int op) {
     case VBE_OP_COPY: return K_COPY;
     case VBE_OP_RANDOM: return K_RANDOM;
     case VBE_OP_ADD_REDUCE: case VBE_OP_MIN_REDUCE: case VBE_OP_MAX_REDUCE: return K_REDUCE;
+    case VBE_OP_ARGMIN_REDUCE: case VBE_OP_ARGMAX_REDUCE: return K_REDUCE;
     case VBE_OP_SYNC: case VBE_OP_DISCARD: case VBE_OP_FREE: return K_CONTROL;
   }
+  if (user_op(op)) return K_USER;
   fail(VBE_ERR_INVALID, "unknown opcode " + std::to_string(op));
+}
+
+// ------------------------------------------------ user-defined operations
+
+namespace {
+std::mutex g_user_mu;
+std::deque<UserOp> g_user_ops;  // stable addresses
+constexpr int kMaxUserOps = 1024;
+}  // namespace
+
+const UserOp* user_op(int op) {
+  if (op < VBE_OP_USER_BASE) return nullptr;
+  std::lock_guard<std::mutex> lk(g_user_mu);
+  const size_t i = (size_t)(op - VBE_OP_USER_BASE);
+  return i < g_user_ops.size() ? &g_user_ops[i] : nullptr;
+}
+
+int register_user_op(const std::string& name, const std::string& body, int nin, int dtype) {
+  bool ok = !name.empty() && name.size() <= 48 && (isalpha((unsigned char)name[0]) || name[0] == '_');
+  for (char ch : name) ok = ok && (isalnum((unsigned char)ch) || ch == '_');
+  if (!ok) fail(VBE_ERR_INVALID, "operation name must be an identifier of at most 48 characters");
+  if (nin < 1 || nin > 3) fail(VBE_ERR_INVALID, "a user operation takes 1 to 3 inputs");
+  if (dtype != VBE_FLOAT32 && dtype != VBE_FLOAT64 && dtype != VBE_INT64)
+    fail(VBE_ERR_INVALID, "a user operation works on float32, float64 or int64");
+  std::lock_guard<std::mutex> lk(g_user_mu);
+  for (size_t i = 0; i < g_user_ops.size(); ++i) {
+    const UserOp& u = g_user_ops[i];
+    if (u.name != name) continue;
+    if (u.body == body && u.nin == nin && u.dtype == dtype) return VBE_OP_USER_BASE + (int)i;
+    fail(VBE_ERR_INVALID, "operation " + name + " is registered with another definition");
+  }
+  if ((int)g_user_ops.size() >= kMaxUserOps) fail(VBE_ERR_INVALID, "user operation table is full");
+  UserOp u;
+  u.name = name;
+  u.body = body;
+  u.nin = nin;
+  u.dtype = dtype;
+  g_user_ops.push_back(u);
+  return VBE_OP_USER_BASE + (int)g_user_ops.size() - 1;
 }
 
 int op_arity(int op) {
@@ -81,6 +125,7 @@ int op_arity(int op) {
     case K_FUNARY: case K_SUNARY: case K_CAST: case K_COPY: case K_REDUCE: return 1;
     case K_SELECT: return 3;
     case K_RANDOM: case K_CONTROL: return 0;
+    case K_USER: return user_op(op)->nin;
   }
   return 0;
 }
@@ -90,8 +135,9 @@ const char* op_name(int op) {
                                 "SQRT", "EXP", "LOG", "ABSOLUTE", "NEGATIVE", "LESS", "LESS_EQUAL",
                                 "GREATER", "GREATER_EQUAL", "EQUAL", "NOT_EQUAL", "SELECT", "CAST",
                                 "COPY", "RANDOM", "ADD_REDUCE", "MIN_REDUCE", "MAX_REDUCE", "SYNC",
-                                "DISCARD", "FREE"};
-  if (op < 1 || op > VBE_OP_FREE) return "?";
+                                "DISCARD", "FREE", "ARGMIN_REDUCE", "ARGMAX_REDUCE"};
+  if (const UserOp* u = user_op(op)) return u->name.c_str();
+  if (op < 1 || op > VBE_OP_ARGMAX_REDUCE) return "?";
   return names[op];
 }
 
@@ -320,8 +366,20 @@ std::vector<RInstr> resolve_batch(Ctx* c, const vbe_instr* prog, int64_t n) {
         if (r.dt_out != VBE_FLOAT64) err(VBE_ERR_DTYPE, "RANDOM writes float64");
         break;
       case K_REDUCE:
-        if (d0 != r.dt_out || d0 == VBE_BOOL) err(VBE_ERR_DTYPE, "reduction keeps a numeric dtype");
+        if (s.op == VBE_OP_ARGMIN_REDUCE || s.op == VBE_OP_ARGMAX_REDUCE) {
+          if (d0 == VBE_BOOL) err(VBE_ERR_DTYPE, "argmin/argmax needs a numeric input");
+          if (r.dt_out != VBE_INT64) err(VBE_ERR_DTYPE, "argmin/argmax writes int64");
+        } else if (d0 != r.dt_out || d0 == VBE_BOOL) {
+          err(VBE_ERR_DTYPE, "reduction keeps a numeric dtype");
+        }
         break;
+      case K_USER: {
+        const UserOp* u = user_op(s.op);
+        for (int k = 0; k < ar; ++k)
+          if (r.dt_in[k] != u->dtype) err(VBE_ERR_DTYPE, std::string("inputs of ") + u->name + " must be " + dtype_name(u->dtype));
+        if (r.dt_out != u->dtype) err(VBE_ERR_DTYPE, std::string("output of ") + u->name + " must be " + dtype_name(u->dtype));
+        break;
+      }
       default:
         break;
     }

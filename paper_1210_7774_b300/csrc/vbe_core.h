@@ -56,10 +56,18 @@ bool may_overlap(const ViewDesc& a, const ViewDesc& b);
 
 // ------------------------------------------------------------ instructions
 enum OpKind { K_ARITH, K_DIV, K_FUNARY, K_SUNARY, K_CMP, K_SELECT, K_CAST, K_COPY, K_RANDOM,
-              K_REDUCE, K_CONTROL };
+              K_REDUCE, K_CONTROL, K_USER };
 OpKind op_kind(int op);
 int op_arity(int op);
 const char* op_name(int op);
+
+// user-defined elementwise operations (process-wide table, vbe_op_register)
+struct UserOp {
+  std::string name, body;
+  int nin = 0, dtype = 0;
+};
+const UserOp* user_op(int op);  // nullptr when op is not a registered user opcode
+int register_user_op(const std::string& name, const std::string& body, int nin, int dtype);
 
 struct RInstr {  // a validated, resolved instruction
   int op = 0;

@@ -20,6 +20,15 @@ from . import vbe as V
 _SELECT = "SELECT"
 
 
+def opcode_of(ctx, program: Program, op: str) -> int:
+    """The opcode of a mnemonic; ``"USER:<name>"`` registers the program's
+    user-defined operation of that name with the library."""
+    if op.startswith("USER:"):
+        u = program.user_ops[op[5:]]
+        return V.vbe_op_register(ctx, u.name, u.body, u.nin, V.DTYPE_CODE[u.dtype])
+    return V.OPCODES[op]
+
+
 def _const_dtype(instr, k: int, dtypes: dict) -> str:
     if instr.op == _SELECT:
         return "bool" if k == 0 else dtypes[instr.out.base]
@@ -93,9 +102,12 @@ class Executor:
     def encode(self, L: Loaded, instrs) -> tuple:
         dtypes = {bid: b.dtype for bid, b in L.program.bases.items()}
         arr = (V.vbe_instr * max(1, len(instrs)))()
+        codes = {}
         for i, ins in enumerate(instrs):
             e = arr[i]
-            e.op = V.OPCODES[ins.op]
+            if ins.op not in codes:
+                codes[ins.op] = opcode_of(self.ctx, L.program, ins.op)
+            e.op = codes[ins.op]
             e.const_slot = -1
             e.out = self.view_handle(L, ins.out) if ins.out is not None else 0
             for k, x in enumerate(ins.ins):

@@ -23,7 +23,9 @@ DTYPE_CODE = {"bool": VBE_BOOL, "int64": VBE_INT64, "float32": VBE_FLOAT32, "flo
 OPCODES = {name: i + 1 for i, name in enumerate([
     "ADD", "SUBTRACT", "MULTIPLY", "DIVIDE", "MAXIMUM", "MINIMUM", "SQRT", "EXP", "LOG", "ABSOLUTE",
     "NEGATIVE", "LESS", "LESS_EQUAL", "GREATER", "GREATER_EQUAL", "EQUAL", "NOT_EQUAL", "SELECT", "CAST",
-    "COPY", "RANDOM", "ADD_REDUCE", "MIN_REDUCE", "MAX_REDUCE", "SYNC", "DISCARD", "FREE"])}
+    "COPY", "RANDOM", "ADD_REDUCE", "MIN_REDUCE", "MAX_REDUCE", "SYNC", "DISCARD", "FREE", "ARGMIN_REDUCE",
+    "ARGMAX_REDUCE"])}
+VBE_OP_USER_BASE = 64
 
 # config flags
 VBE_FUSE, VBE_GRAPHS, VBE_AUTOTUNE, VBE_PACK, VBE_HOST_ONLY, VBE_RECORD = 1, 2, 4, 8, 16, 32
@@ -113,6 +115,7 @@ _SIGS = {
     "vbe_server_submit": [_P, POINTER(vbe_request), POINTER(c_int64)],
     "vbe_server_wait": [_P, c_int64, c_int64, POINTER(vbe_request_result)],
     "vbe_server_destroy": [_P],
+    "vbe_op_register": [_P, ctypes.c_char_p, ctypes.c_char_p, c_int32, c_int32, POINTER(c_int32)],
     "vbe_reduce_add_f64_noalloc": [c_void_p, c_int64, c_void_p, c_void_p],
 }
 EXPORTED = tuple(_SIGS)
@@ -218,6 +221,12 @@ def vbe_plan_compile(ctx, prog, n: int) -> int:
     k = c_int64()
     _check(lib.vbe_plan_compile(ctx, prog, n, byref(k)), ctx)
     return k.value
+
+
+def vbe_op_register(ctx, name: str, body: str, nin: int, dtype: int) -> int:
+    code = c_int32()
+    _check(lib.vbe_op_register(ctx, name.encode(), body.encode(), nin, dtype, byref(code)), ctx)
+    return code.value
 
 
 def vbe_views_may_overlap(ctx, a: int, b: int) -> bool:

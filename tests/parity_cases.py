@@ -228,6 +228,34 @@ def view_cases(seed=1):
     p = b.build([o])
     out.append(Case(p.name, p, _exact_check(p)))
     out += tile_group_cases(seed + 10)
+    out += user_op_cases(seed + 20)
+    return out
+
+
+def user_op_cases(seed=21, n=1537):
+    """User-defined operations (section "Interface"), fused with ordinary
+    bytecodes: one to three inputs, float64 / float32 / int64, a constant
+    operand, and use inside a stencil chain."""
+    rng = np.random.default_rng(seed)
+    out = []
+    b = ProgramBuilder("user_ops_mixed")
+    x = b.base("float64", n, rng.standard_normal(n))
+    y = b.base("float64", n, rng.standard_normal(n))
+    z = b.base("float64", n, rng.random(n) + 0.5)
+    xf = b.base("float32", n, rng.standard_normal(n).astype(np.float32))
+    xi = b.base("int64", n, rng.integers(-1000, 1000, n))
+    o1, o2, o3 = b.base("float64", n), b.base("float32", n), b.base("int64", n)
+    fma3 = b.user_op("axpy_div", "return (a * b + c) / c;", 3, "float64", lambda a, bb, c: (a * bb + c) / c)
+    sq = b.user_op("sq_plus_one", "return a * a + 1.0f;", 1, "float32",
+                   lambda a: a * a + np.float32(1.0))
+    tri = b.user_op("tri", "return a * (a - 1) / 2 + b;", 2, "int64", lambda a, bb: a * (a - 1) // 2 + bb)
+    b.emit(fma3, b.whole(o1), b.whole(x), b.whole(y), b.whole(z))
+    b.emit("MULTIPLY", b.whole(o1), b.whole(o1), Const(0.5))
+    b.emit(sq, b.whole(o2), b.whole(xf))
+    b.emit("ADD", b.whole(o2), b.whole(o2), Const(2.0))
+    b.emit(tri, b.whole(o3), b.whole(xi), Const(7))
+    p = b.build([o1, o2, o3])
+    out.append(Case(p.name, p, _exact_check(p)))
     return out
 
 

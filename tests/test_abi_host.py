@@ -281,3 +281,42 @@ def test_generated_source_is_plain_cuda(fused):
     assert "expf(" in src and "logf(" in src and "sqrtf(" in src
     assert "vbe_vload" in src  # 16-byte vector path
     assert "__fmaf" not in src and "fma(" not in src
+
+
+def test_user_operation_registration(fused):
+    """Section "Interface": registration of a user-defined operation. The
+    body is compiled at registration; the same definition gets the same
+    opcode (in any context); the operation fuses with ordinary bytecodes."""
+    ctx = fused.ctx
+    a = V.vbe_op_register(ctx, "hyp_test", "return a * a + b * b;", 2, V.VBE_FLOAT64)
+    assert a >= V.VBE_OP_USER_BASE
+    assert V.vbe_op_register(ctx, "hyp_test", "return a * a + b * b;", 2, V.VBE_FLOAT64) == a
+    with Executor(V.VBE_HOST_ONLY) as other:
+        assert V.vbe_op_register(other.ctx, "hyp_test", "return a * a + b * b;", 2, V.VBE_FLOAT64) == a
+    bad = [("hyp_test", "return a;", 2, V.VBE_FLOAT64, -1),      # another definition under the name
+           ("9bad", "return a;", 1, V.VBE_FLOAT64, -1),           # not an identifier
+           ("ok_name", "return a;", 0, V.VBE_FLOAT64, -1),        # arity
+           ("ok_name", "return a;", 1, V.VBE_BOOL, -1),           # dtype
+           ("broken", "return a +;", 1, V.VBE_FLOAT32, -7)]       # does not compile
+    for name, body, nin, dt, code in bad:
+        with pytest.raises(V.VbeError) as e:
+            V.vbe_op_register(ctx, name, body, nin, dt)
+        assert e.value.code == code, (name, e.value)
+    from parity_cases import user_op_cases
+    case = user_op_cases()[0]
+    L = fused.load(case.program, upload=False)
+    runs, _ = runs_of(fused, L)
+    # three independent chains of one shape: user op + ordinary op each, one kernel
+    assert len(runs) == 1 and {"axpy_div", "sq_plus_one", "tri", "MULTIPLY", "ADD"} <= set(runs[0]["ops"])
+    # dtype rules apply to user operations
+    b = V.vbe_base_create(ctx, V.VBE_FLOAT32, 8)
+    vb = V.vbe_view_create(ctx, b, 0, (8,), (1,))
+    arr = (V.vbe_instr * 1)()
+    arr[0].op = a
+    arr[0].const_slot = -1
+    arr[0].out = vb
+    arr[0].in_[0] = vb
+    arr[0].in_[1] = vb
+    with pytest.raises(V.VbeError) as e:
+        V.vbe_plan(ctx, arr, 1, False)
+    assert e.value.code == -3

@@ -380,3 +380,25 @@ def test_random_is_sequential_stream_interleaved():
     # a 2-D output numbers its elements in row-major order
     z = run1("RANDOM", "float64", (4, 5), [], seed=seed, key=0, step=1)
     assert z.reshape(-1).tolist() == [(seq[m] >> 11) * 2.0**-53 for m in range(20)]
+
+
+def test_user_operation_dispatch():
+    """A user-defined operation runs its NumPy definition on the views, with
+    the arithmetic rules' dtype checks: compared with a per-element loop."""
+    from workloads import ProgramBuilder
+    rng = np.random.default_rng(9)
+    b = ProgramBuilder("user")
+    x = b.base("float64", (6, 5), rng.standard_normal(30))
+    y = b.base("float64", (6, 5), rng.standard_normal(30))
+    o = b.base("float64", (6, 5))
+    op = b.user_op("hyp", "return a * a + b * b;", 2, "float64", lambda a, c: a * a + c * c)
+    b.emit(op, b.whole(o), b.view(x, 29, (6, 5), (-5, -1)), b.whole(y))
+    p = b.build([o])
+    got = oracle.run(p)[o]
+    xs, ys = p.bases[x].init, p.bases[y].init
+    want = [xs[29 - k] * xs[29 - k] + ys[k] * ys[k] for k in range(30)]
+    assert got.tolist() == want
+    bad = b.base("float32", (6, 5), np.zeros(30, np.float32))
+    b.emit(op, b.whole(o), b.whole(bad), b.whole(y))
+    with pytest.raises(oracle.OracleError):
+        oracle.run(b.build([o]))

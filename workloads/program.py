@@ -86,6 +86,20 @@ class Base:
     shape: tuple = ()  # logical shape used by ``whole()``; product == nelem
 
 
+@dataclass(frozen=True)
+class UserOp:
+    """A user-defined elementwise operation: ``body`` is the CUDA device
+    function body the executor compiles (arguments ``a``, ``b``, ``c``);
+    ``fn`` is the same operation written for NumPy arrays of ``dtype``,
+    which the oracle runs. The two are written independently."""
+
+    name: str
+    body: str
+    nin: int
+    dtype: str
+    fn: object = None
+
+
 @dataclass
 class Program:
     name: str
@@ -93,6 +107,8 @@ class Program:
     instrs: list = field(default_factory=list)
     outputs: list = field(default_factory=list)  # base ids holding the result
     meta: dict = field(default_factory=dict)
+    # user-defined operations used as ``"USER:<name>"``: name -> UserOp
+    user_ops: dict = field(default_factory=dict)
 
     def compulsory_bytes(self) -> int:
         """Live-in bytes read plus live-out bytes written, each once: the
@@ -158,6 +174,11 @@ class ProgramBuilder:
     def emit(self, op: str, out: Optional[View], *ins: Operand, axis: int = 0,
              seed: int = 0, key: int = 0, step: int = 1) -> None:
         self.p.instrs.append(Instr(op, out, tuple(ins), axis, seed, key, step))
+
+    def user_op(self, name: str, body: str, nin: int, dtype: str, fn) -> str:
+        """Declare a user-defined operation; returns its mnemonic for emit()."""
+        self.p.user_ops[name] = UserOp(name, body, nin, dtype, fn)
+        return "USER:" + name
 
     def discard(self, *bids: int) -> None:
         for bid in bids:
