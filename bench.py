@@ -10,7 +10,7 @@ path (one launch per bytecode) is timed on the same GPU beside it.
 ``--impl reference`` times the oracle (the CPU reference interpreter) on a
 bounded sample of the same workload instead.
 
-Other workloads: ``--workload jacobi|shallow_water|stencil|montecarlo|serving``.
+Other workloads: ``--workload jacobi|shallow_water|stencil|knn|montecarlo|serving``.
 """
 from __future__ import annotations
 
@@ -358,6 +358,20 @@ def other_workload(args, local):
             res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_step"] / res["fused_graphs"]["ms_per_step"]
             out[dtype] = res
         out["note"] = "Gray-Scott reaction-diffusion, 10240x1024, 10 steps (the paper's synthetic-stencil size)"
+    elif args.workload == "knn":
+        from workloads import knn
+        N, M, D, k = 10_000, 1_000, 16, 4
+        for dtype in [d for d in ("float64", "float32") if d in args.dtypes.split(",")]:
+            p = knn(N, M, D, k, dtype)
+            res = {}
+            for name in ("fused_graphs", "plain_graphs"):
+                sec, st = timed_batches(p, modes[name], 5)
+                res[name] = {"ms_per_job": sec * 1e3, "queries_per_s": M / sec,
+                             "distance_terms_per_s": M * N * D / sec}
+            res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_job"] / res["fused_graphs"]["ms_per_job"]
+            out[dtype] = res
+        out["note"] = ("naive kNN, 10,000 points x 1,000 queries (16-D, k = 4): broadcast differences, "
+                       "axis sums, then k rounds of MIN/ARGMIN reductions and masking")
     elif args.workload == "montecarlo":
         from workloads import mc_sizes, montecarlo_pi
         p = montecarlo_pi(sizes=mc_sizes(256))

@@ -46,7 +46,7 @@ FLOAT_BINARY = {"DIVIDE"}
 FLOAT_UNARY = {"SQRT", "EXP", "LOG"}
 SIGNED_UNARY = {"ABSOLUTE", "NEGATIVE"}
 COMPARE = {"LESS", "LESS_EQUAL", "GREATER", "GREATER_EQUAL", "EQUAL", "NOT_EQUAL"}
-REDUCE = {"ADD_REDUCE", "MIN_REDUCE", "MAX_REDUCE"}
+REDUCE = {"ADD_REDUCE", "MIN_REDUCE", "MAX_REDUCE", "ARGMIN_REDUCE", "ARGMAX_REDUCE"}
 CONTROL = {"SYNC", "DISCARD", "FREE"}
 
 NUMERIC = {"int64", "float32", "float64"}
@@ -173,6 +173,19 @@ def execute(mem: Memory, ins_) -> None:
             ax = ins_.axis
             if not (0 <= ax < a.ndim):
                 raise OracleError("reduction axis out of range")
+            if op in ("ARGMIN_REDUCE", "ARGMAX_REDUCE"):
+                # NumPy's argmin/argmax: the first occurrence of the minimum
+                # (maximum); a NaN counts as the minimum (maximum), so the
+                # first NaN wins
+                if odt != np.int64 or a.dtype.kind not in "if":
+                    raise OracleError("argmin/argmax reads a number and writes int64")
+                if tuple(np.delete(np.array(a.shape, dtype=np.int64), ax)) != tuple(out.shape):
+                    raise OracleError("reduction output shape")
+                if a.shape[ax] == 0:
+                    raise OracleError("argmin/argmax over an empty axis")
+                f = np.argmin if op == "ARGMIN_REDUCE" else np.argmax
+                o[...] = f(a, axis=ax).astype(np.int64)
+                return
             if a.dtype != odt or odt.kind not in "if":
                 raise OracleError("reduction dtype")
             if tuple(np.delete(np.array(a.shape, dtype=np.int64), ax)) != tuple(out.shape):

@@ -265,6 +265,7 @@ struct Builder {
 
   bool can_merge_reduction(const RInstr& r, size_t idx) {
     if (!cur.has_red || r.op != cur.red_op) return false;
+    if (r.op == VBE_OP_ARGMIN_REDUCE || r.op == VBE_OP_ARGMAX_REDUCE) return false;  // indices do not compose
     if (!r.in[0].identical(red_view)) return false;
     if (live_after(prog, red_view.base, idx)) return false;
     // the merged output must not touch anything else in the run

@@ -153,7 +153,9 @@ Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& l
     if ((int)s.st.size() != D) fail(VBE_ERR_INVALID, "internal: store slot rank differs from the run's");
   if (r.has_red && (int)r.red_out.st.size() != D - (int)r.red_axes.size())
     fail(VBE_ERR_INVALID, "internal: reduction output rank");
-  bool full = r.has_red && (int)r.red_axes.size() == D;
+  // ARGMIN/ARGMAX keep the axis path (an index along the reduced axis)
+  bool full = r.has_red && (int)r.red_axes.size() == D && r.red_op != VBE_OP_ARGMIN_REDUCE &&
+              r.red_op != VBE_OP_ARGMAX_REDUCE;
   if (!r.has_red || full) {
     c.spec.mode = r.has_red ? Mode::FULL : Mode::ELEM;
     std::vector<int64_t> dims = r.shape;
@@ -372,6 +374,16 @@ template <class T> __device__ __forceinline__ T vbe_zdiv(T a, T b) {
   return z ? a * q : q;
 }
 template <class T> __device__ __forceinline__ T vbe_min(T a, T b) { return (a < b || a != a) ? a : b; }
+// ARGMIN/ARGMAX: keep (x, j) over (v, i) when x is better, a NaN counting
+// as better than any number and equal values going to the lower index (the
+// first occurrence); associative and commutative, so every combining order
+// gives the same pair
+template <class T> __device__ __forceinline__ void vbe_arg_upd(T& v, i64& i, T x, i64 j, bool maxi) {
+  const bool xn = x != x, vn = v != v;
+  const bool better = maxi ? (x > v) : (x < v);
+  const bool take = (xn || vn) ? (xn && (!vn || j < i)) : (better || (x == v && j < i));
+  if (take) { v = x; i = j; }
+}
 // RANDOM: splitmix64 finaliser of seed + (key + step*m + 1) * golden gamma,
 // top 53 bits scaled to [0, 1)
 __device__ __forceinline__ double vbe_u01(u64 seed, u64 key, u64 step, u64 m) {
@@ -528,6 +540,10 @@ struct Gen {
   std::ostringstream o;
   const char* rt() const { return ctype(r.red_dtype); }
   bool kahan() const { return r.has_red && r.red_op == VBE_OP_ADD_REDUCE && r.red_dtype == VBE_FLOAT32; }
+  bool arg() const { return r.has_red && (r.red_op == VBE_OP_ARGMIN_REDUCE || r.red_op == VBE_OP_ARGMAX_REDUCE); }
+  bool argmax() const { return r.has_red && r.red_op == VBE_OP_ARGMAX_REDUCE; }
+  // type of the values an ARGMIN/ARGMAX compares
+  std::string vt() const { return ctype(r.value_dtype[r.red_value]); }
 
   std::vector<char> soft;  // per step: float64 add/subtract/multiply/compare emulated
 
@@ -622,8 +638,8 @@ struct Gen {
   }
 
   std::string red_id() {
-    int dt = r.red_dtype;
-    switch (r.red_op) {
+    int dt = arg() ? r.value_dtype[r.red_value] : r.red_dtype;
+    switch (arg() ? (argmax() ? VBE_OP_MAX_REDUCE : VBE_OP_MIN_REDUCE) : r.red_op) {
       case VBE_OP_ADD_REDUCE: return dt == VBE_INT64 ? "((i64)0)" : (dt == VBE_FLOAT32 ? "0.0f" : "0.0");
       case VBE_OP_MIN_REDUCE:
         return dt == VBE_INT64 ? "((i64)0x7fffffffffffffffll)"
@@ -657,7 +673,9 @@ struct Gen {
     o << "__device__ __forceinline__ void " << elem_name << "(const P& p, i64 m";
     for (size_t s = 0; s < r.loads.size(); ++s) o << ", const " << ctype(r.loads[s].dtype) << " l" << s;
     for (size_t s = 0; s < r.stores.size(); ++s) o << ", " << ctype(r.stores[s].dtype) << "& o" << s;
-    if (r.has_red) {
+    if (arg()) {
+      o << ", " << vt() << "& acc, i64& acci, const i64 ai";
+    } else if (r.has_red) {
       o << ", " << rt() << "& acc";
       if (kahan()) o << ", float& kc";
     }
@@ -668,7 +686,9 @@ struct Gen {
     for (size_t s = 0; s < r.stores.size(); ++s) o << "  o" << s << " = v" << r.store_value[s] << ";\n";
     if (r.has_red) {
       std::string x = "v" + std::to_string(r.red_value);
-      if (kahan()) {
+      if (arg()) {
+        o << "  vbe_arg_upd(acc, acci, " << x << ", ai, " << (argmax() ? "true" : "false") << ");\n";
+      } else if (kahan()) {
         o << "  { const float y = " << x << " - kc; const float t = acc + y; kc = (t - acc) - y; acc = t; }\n";
       } else {
         o << "  acc = " << comb("acc", x) << ";\n";
@@ -679,6 +699,25 @@ struct Gen {
 
   void emit_block_reduce() {
     if (!r.has_red) return;
+    if (arg()) {
+      // (value, index) pairs: warp shuffles of both, then one warp over the
+      // warps' pairs; returns the index of the block's best pair
+      const std::string V = vt(), mx = argmax() ? "true" : "false";
+      o << "__device__ __forceinline__ i64 " << block_reduce_name << "(" << V << " v, i64 i) {\n"
+        << "  __shared__ " << V << " shv[32];\n  __shared__ i64 shi[32];\n"
+        << "  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;\n"
+        << "  for (int off = 16; off > 0; off >>= 1) { const " << V
+        << " tv = __shfl_down_sync(0xffffffffu, v, off); const i64 ti = __shfl_down_sync(0xffffffffu, i, off);"
+        << " vbe_arg_upd(v, i, tv, ti, " << mx << "); }\n"
+        << "  if (lane == 0) { shv[wid] = v; shi[wid] = i; }\n  __syncthreads();\n"
+        << "  if (wid == 0) {\n    v = lane < nw ? shv[lane] : " << red_id() << ";\n"
+        << "    i = lane < nw ? shi[lane] : (i64)0x7fffffffffffffffll;\n"
+        << "    for (int off = 16; off > 0; off >>= 1) { const " << V
+        << " tv = __shfl_down_sync(0xffffffffu, v, off); const i64 ti = __shfl_down_sync(0xffffffffu, i, off);"
+        << " vbe_arg_upd(v, i, tv, ti, " << mx << "); }\n  }\n"
+        << "  __syncthreads();\n  return i;\n}\n";
+      return;
+    }
     o << "__device__ __forceinline__ " << rt() << " " << block_reduce_name << "(" << rt() << " v) {\n"
       << "  __shared__ " << rt() << " sh[32];\n"
       << "  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;\n"
@@ -699,7 +738,8 @@ struct Gen {
     std::string s = "vbe_elem(p, " + m;
     for (auto& x : lv) s += ", " + x;
     for (auto& x : sv) s += ", " + x;
-    if (r.has_red) s += kahan() ? ", acc, kc" : ", acc";
+    if (arg()) s += ", acc, acci, ri";
+    else if (r.has_red) s += kahan() ? ", acc, kc" : ", acc";
     return s + ");";
   }
 
@@ -713,6 +753,10 @@ struct Gen {
 
   void emit_acc_init(const std::string& pfx) {
     if (!r.has_red) return;
+    if (arg()) {
+      o << pfx << vt() << " acc = " << red_id() << ";\n" << pfx << "i64 acci = (i64)0x7fffffffffffffffll;\n";
+      return;
+    }
     o << pfx << rt() << " acc = " << red_id() << ";\n";
     if (kahan()) o << pfx << "float kc = 0.0f;\n";
   }
@@ -1120,7 +1164,11 @@ struct Gen {
     for (size_t s = 0; s < r.stores.size(); ++s)
       o << "      sp" << s << "[sk" << s << " + sr" << s << "] = b" << s << ";\n";
     o << "    }\n";
-    if (block) {
+    if (arg() && block) {
+      o << "    { const i64 v = " << block_reduce_name << "(acc, acci); if (threadIdx.x == 0) rp[rk] = v; }\n";
+    } else if (arg()) {
+      o << "    rp[rk] = acci;\n";
+    } else if (block) {
       o << "    { " << rt() << " v = vbe_block_reduce(" << acc_final() << "); if (threadIdx.x == 0) rp[rk] = v; }\n";
     } else {
       o << "    rp[rk] = " << acc_final() << ";\n";

@@ -9,7 +9,7 @@ import math
 import numpy as np
 
 import oracle
-from workloads import (Const, ProgramBuilder, blackscholes, bs_inputs, gray_scott, jacobi, montecarlo_pi,
+from workloads import (Const, ProgramBuilder, blackscholes, bs_inputs, gray_scott, jacobi, knn, montecarlo_pi,
                        shallow_water)
 
 F64_REDUCE_RTOL = 1e-12
@@ -349,6 +349,29 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
                 else:
                     chk = _exact_check(p)
                 out.append(Case(p.name, p, chk))
+    # ARGMIN / ARGMAX: ties (values drawn from a few levels), NaNs and
+    # infinities, every axis, a 1-D input (whole-array index) and a long axis
+    lv = np.array([0.0, -0.0, 1.0, -1.0, 2.5, np.inf, -np.inf, np.nan])
+    for dt in ("float64", "float32", "int64"):
+        x = rng.integers(-3, 4, int(np.prod(shape))).astype(dt)
+        if dt != "int64":
+            sp = rng.random(x.size) < 0.05
+            x[sp] = lv[rng.integers(0, len(lv), int(sp.sum()))].astype(dt)
+        for op in ("ARGMIN_REDUCE", "ARGMAX_REDUCE"):
+            for ax in range(3):
+                b = ProgramBuilder(f"{op}_{dt}_ax{ax}")
+                xb = b.base(dt, shape, x)
+                o = b.base("int64", tuple(s for k, s in enumerate(shape) if k != ax))
+                b.emit(op, b.whole(o), b.whole(xb), axis=ax)
+                p = b.build([o])
+                out.append(Case(p.name, p, _exact_check(p)))
+            b = ProgramBuilder(f"{op}_{dt}_1d")
+            n1 = 100_003
+            xb = b.base(dt, n1, rng.integers(-50, 50, n1).astype(dt))
+            o = b.base("int64", 1)
+            b.emit(op, b.view(o, 0, (), ()), b.whole(xb), axis=0)
+            p = b.build([o])
+            out.append(Case(p.name, p, _exact_check(p)))
     # fused chain with a full reduction and with an axis reduction, plus stores
     for dt in ("float64", "float32"):
         b = ProgramBuilder(f"chain_full_{dt}")
@@ -388,6 +411,40 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
     return out
 
 
+def knn_check(p, rows=None):
+    """kNN results: distances within the reduction tolerance (the squared
+    distances are sums of D squares, summed in another order than the
+    oracle's); an index may differ from the oracle's only at a near tie,
+    i.e. where both points' distances (float64, from the inputs) agree
+    within that tolerance; every row's indices are distinct. ``rows``: the
+    query rows the oracle computed (a sample of a larger run)."""
+    rtol = F64_REDUCE_RTOL if p.meta["dtype"] == "float64" else F32_REDUCE_RTOL
+    X = p.bases[p.meta["X"]].init.reshape(p.meta["N"], p.meta["D"]).astype(np.float64)
+    Q = p.bases[p.meta["Q"]].init.reshape(p.meta["M"], p.meta["D"]).astype(np.float64)
+    k = p.meta["k"]
+
+    def check(got, want):
+        """``want``: the oracle's outputs for all rows, or (with ``rows``)
+        for a program over the sampled queries only, keyed like ``got``."""
+        gd = got[p.meta["dist"]].reshape(-1, k)
+        gi = got[p.meta["idx"]].reshape(-1, k)
+        sel = np.arange(gd.shape[0]) if rows is None else np.asarray(rows)
+        wd = want[p.meta["dist"]].reshape(-1, k)
+        wi = want[p.meta["idx"]].reshape(-1, k)
+        gd, gi = gd[sel], gi[sel]
+        assert_close_sum(gd.reshape(-1), wd.reshape(-1).astype(gd.dtype), np.abs(wd.reshape(-1)).astype(np.float64) + 1e-300,
+                         rtol, p.name + " dist")
+        for r in range(len(sel)):
+            assert len(set(gi[r].tolist())) == k, (p.name, r)
+            for j in range(k):
+                if gi[r, j] != wi[r, j]:
+                    q = Q[sel[r]]
+                    da = np.sum((q - X[gi[r, j]]) ** 2)
+                    db = np.sum((q - X[wi[r, j]]) ** 2)
+                    assert abs(da - db) <= 4 * rtol * max(da, db), (p.name, r, j, gi[r, j], wi[r, j], da, db)
+    return check
+
+
 def workload_cases(scale="small"):
     out = []
     n = 24 if scale == "small" else 256
@@ -414,6 +471,9 @@ def workload_cases(scale="small"):
     for dt in ("float64", "float32"):
         p = shallow_water(N, 3 if scale == "small" else 10, dt)
         out.append(Case(p.name, p, _exact_check(p)))
+    for dt in ("float64", "float32"):
+        p = knn(211, 37, 5, 3, dt) if scale == "small" else knn(2000, 300, 16, 4, dt)
+        out.append(Case(p.name, p, knn_check(p)))
     R, C = (20, 24) if scale == "small" else (130, 70)
     for dt in ("float64", "float32"):
         p = gray_scott(R, C, 3 if scale == "small" else 10, dt)

@@ -17,8 +17,8 @@ from paper_1210_7774_b300.runner import Executor  # noqa: E402
 import oracle  # noqa: E402
 from parity_cases import (F64_REDUCE_RTOL, all_small_cases, assert_close_sum, assert_exact,  # noqa: E402
                           oracle_outputs, workload_cases)
-from workloads import (blackscholes, bs_inputs, gray_scott, jacobi, mc_sizes, montecarlo_pi,  # noqa: E402
-                       shallow_water, sw_inputs)
+from workloads import (blackscholes, bs_inputs, gray_scott, jacobi, knn, knn_inputs, mc_sizes,  # noqa: E402
+                       montecarlo_pi, shallow_water, sw_inputs)
 
 pytestmark = pytest.mark.gpu
 CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
@@ -100,6 +100,21 @@ def test_synthetic_stencil_full_size():
         got = run_gpu(p, FUSED | V.VBE_GRAPHS)
         for q in ("U", "V"):
             assert_exact(got[p.meta[q]], want[p.meta[q]], q + " " + dt)
+
+
+def test_knn_paper_size_sampled():
+    """10,000 points, 1,000 queries (16-D, k = 4), float64 and float32: 64
+    sampled queries recomputed by the oracle as a program of their own."""
+    from parity_cases import knn_check
+    for dt in ("float64", "float32"):
+        inp = knn_inputs(10_000, 1_000, 16, dt)
+        p = knn(10_000, 1_000, 16, 4, dt, inputs=inp)
+        got = run_gpu(p, FUSED | V.VBE_GRAPHS)
+        rows = np.sort(np.random.default_rng(5).choice(1_000, 64, replace=False))
+        sub = knn(10_000, 64, 16, 4, dt, inputs={"X": inp["X"], "Q": inp["Q"][rows]})
+        w = oracle_outputs(sub)
+        want = {p.meta["dist"]: w[sub.meta["dist"]], p.meta["idx"]: w[sub.meta["idx"]]}
+        knn_check(p, rows)(got, want)
 
 
 def test_jacobi_paper_size_tile_fused():

@@ -402,3 +402,38 @@ def test_user_operation_dispatch():
     b.emit(op, b.whole(o), b.whole(bad), b.whole(y))
     with pytest.raises(oracle.OracleError):
         oracle.run(b.build([o]))
+
+
+def _arg_loop(row, maxi):
+    """Index of the first best element of a list, a NaN being best."""
+    best = None
+    for j, x in enumerate(row):
+        if best is None:
+            best = j
+            continue
+        v = row[best]
+        if math.isnan(v):
+            continue
+        if math.isnan(x) or (x > v if maxi else x < v):
+            best = j
+    return best
+
+
+@pytest.mark.parametrize("op", ["ARGMIN_REDUCE", "ARGMAX_REDUCE"])
+def test_argmin_argmax_first_occurrence_and_nan(op):
+    """Brute force over rows with ties, NaNs and infinities, along each axis
+    of a 2-D view and of a reversed view."""
+    from workloads import ProgramBuilder
+    rng = np.random.default_rng(4)
+    vals = np.array([0.0, -0.0, 1.0, -1.0, 2.0, np.inf, -np.inf, np.nan])
+    data = vals[rng.integers(0, len(vals), 7 * 9)]
+    for axis in (0, 1):
+        b = ProgramBuilder("arg")
+        x = b.base("float64", (7, 9), data)
+        o = b.base("int64", 9 if axis == 0 else 7)
+        b.emit(op, b.whole(o), b.view(x, 62, (7, 9), (-9, -1)), axis=axis)
+        p = b.build([o])
+        got = oracle.run(p)[o].tolist()
+        m = data.reshape(7, 9)[::-1, ::-1]
+        rows = [list(m[:, j]) for j in range(9)] if axis == 0 else [list(m[i, :]) for i in range(7)]
+        assert got == [_arg_loop(r, op == "ARGMAX_REDUCE") for r in rows]

@@ -319,3 +319,28 @@ def test_stencil_keeps_row_mirror_symmetry_bitwise():
     for q in ("U", "V"):
         a = mem[p.meta[q]].reshape(R, C)
         assert np.array_equal(a, a[::-1])
+
+
+# ------------------------------------------------------------------- kNN
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_knn_matches_sorted_brute_force(dtype):
+    """The k nearest points of every query equal the first k entries of a
+    stable sort of all squared distances (computed here per pair in float64,
+    then rounded like the program's dtype would not change the order for
+    these well-separated draws); duplicated points check the lower-index
+    tie rule."""
+    from workloads import knn, knn_inputs
+    inp = knn_inputs(200, 30, 4, dtype, seed=8)
+    inp["X"][150] = inp["X"][20]          # an exact duplicate: ties go to index 20
+    inp["Q"][3] = inp["X"][20]
+    p = knn(200, 30, 4, 5, dtype, inputs=inp)
+    mem = oracle.run(p)
+    X, Q = inp["X"].astype(np.float64), inp["Q"].astype(np.float64)
+    d2 = [[sum((Q[m, j] - X[n, j]) ** 2 for j in range(4)) for n in range(200)] for m in range(30)]
+    want = [sorted(range(200), key=lambda n: (d2[m][n], n))[:5] for m in range(30)]
+    got = mem[p.meta["idx"]].reshape(30, 5).tolist()
+    assert got == want
+    assert got[3][:2] == [20, 150]
+    dist = mem[p.meta["dist"]].reshape(30, 5)
+    assert np.all(np.diff(dist, axis=1) >= 0)

@@ -11,7 +11,9 @@ from .blackscholes import blackscholes, bs_inputs
 from .shallow_water import shallow_water, sw_inputs
 from .montecarlo import montecarlo_pi, mc_sizes
 from .stencil import gray_scott, stencil_inputs
+from .knn import knn, knn_inputs
 
 __all__ = ["DTYPES", "ITEMSIZE", "NP_DTYPE", "Base", "Const", "Instr", "Program", "ProgramBuilder",
            "View", "c_strides", "jacobi", "jacobi_inputs", "blackscholes", "bs_inputs",
-           "shallow_water", "sw_inputs", "montecarlo_pi", "mc_sizes", "gray_scott", "stencil_inputs"]
+           "shallow_water", "sw_inputs", "montecarlo_pi", "mc_sizes", "gray_scott", "stencil_inputs",
+           "knn", "knn_inputs"]
