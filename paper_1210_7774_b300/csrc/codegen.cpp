@@ -1348,6 +1348,21 @@ std::vector<std::vector<int64_t>> group_smem(const Group& g, int th, int tw, int
 
 constexpr int64_t kGroupSmemLimit = 200 * 1024;
 
+// A group whose runs share one shape and read each other's values only at
+// the same point (no shifts, no halos) is evaluated point by point: every
+// run in turn on the point, the values passed in registers (no shared
+// memory, no block barriers). At most one run may reduce.
+bool group_stacked(const Group& g) {
+  int nred = 0;
+  for (size_t k = 0; k < g.runs.size(); ++k) {
+    if (g.box[k] != std::array<int, 4>{0, 0, 0, 0} || g.runs[k].shape != g.runs.back().shape) return false;
+    for (auto& ld : g.lds[k])
+      if (ld.prod >= 0 && (ld.dr != 0 || ld.dc != 0)) return false;
+    nred += g.runs[k].has_red ? 1 : 0;
+  }
+  return nred <= 1;
+}
+
 std::vector<TileShape> group_shapes(const Group& g) {
   std::vector<TileShape> out;
   for (auto t : std::vector<std::array<int, 3>>{{8, 16, 128}, {16, 32, 256}, {32, 32, 256}, {16, 64, 256},
@@ -1357,12 +1372,154 @@ std::vector<TileShape> group_shapes(const Group& g) {
     ts.tw = t[1];
     ts.block = t[2];
     group_smem(g, ts.th, ts.tw, &ts.smem);
+    if (group_stacked(g)) ts.smem = 0;
     if (ts.smem <= kGroupSmemLimit) out.push_back(ts);
   }
   return out;
 }
 
 }  // namespace
+
+// elements of renamed bases the anchor does not write: copied to the new buffer
+static void emit_copy_through(std::ostringstream& o, const Group& g, const GroupLayout& GL) {
+  const int anchor = (int)g.runs.size() - 1;
+  auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
+  for (size_t rr = 0; rr < g.renamed.size(); ++rr) {
+    const std::string T = ctype(g.runs[anchor].stores[g.renamed_slot[rr]].dtype);
+    const int w = GL.ren[rr];
+    o << "  {\n"
+      << "    const auto src = vbe_ptr<const " << T << ">(" << W(w) << ");\n"
+      << "    const auto dst = vbe_ptr<" << T << ">(" << W(w + 1) << ");\n"
+      << "    const i64 off = " << W(w + 2) << ", P = " << W(w + 3) << ", S0 = " << W(w + 4) << ", S1 = " << W(w + 5)
+      << ", nc = " << W(w + 6) << ";\n"
+      << "    const i64 gap = P - S1, ng = (S0 - 1) * gap;\n"
+      << "    for (i64 q = (i64)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (i64)gridDim.x * blockDim.x) {\n"
+      << "      i64 e;\n"
+      << "      if (q < off) e = q;\n"
+      << "      else if (q - off < ng) { const i64 u = q - off, rw = u / gap; e = off + rw * P + S1 + (u - rw * gap); }\n"
+      << "      else e = off + (S0 - 1) * P + S1 + (q - off - ng);\n"
+      << "      dst[e] = src[e];\n"
+      << "    }\n"
+      << "  }\n";
+  }
+}
+
+// The stacked form (group_stacked): one loop over the tile's points; per
+// point every run in order, values handed on in registers.
+static void emit_stacked(std::ostringstream& o, const Group& g, const GroupLayout& GL,
+                  const std::vector<std::unique_ptr<Gen>>& gens, const std::vector<std::vector<std::string>>& cdecl,
+                  const TileShape& ts) {
+  const int m = (int)g.runs.size(), anchor = m - 1;
+  auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
+  const int TH = ts.th, TW = ts.tw;
+  o << "    const i64 rows = " << W(GL.dims[anchor]) << ", cols = " << W(GL.dims[anchor] + 1) << ";\n"
+    << "    const i64 r0 = i0, c0 = j0;\n"
+    << "    const bool inside = r0 + " << TH << " <= rows && c0 + " << TW << " <= cols;\n";
+  std::vector<std::vector<int64_t>> pats;
+  std::vector<std::pair<int, int>> pat_word;
+  auto mem_slot = [&](const std::string& name, const std::string& T, int w, const Slot& sl) {
+    int q = -1;
+    for (size_t i = 0; i < pats.size(); ++i)
+      if (pats[i] == sl.st) q = (int)i;
+    if (q < 0) {
+      pats.push_back(sl.st);
+      q = (int)pats.size() - 1;
+      pat_word.push_back({q, w});
+    }
+    o << "    const auto " << name << " = vbe_ptr<" << T << ">(" << W(w) << ") + (r0 * " << W(w + 1) << " + c0 * "
+      << W(w + 2) << ");\n";
+    return name + "[ix" + std::to_string(q) + "]";
+  };
+  std::vector<std::vector<std::string>> lv(m), sm(m);
+  for (int k = 0; k < m; ++k) {
+    const Run& r = g.runs[k];
+    for (size_t s = 0; s < r.loads.size(); ++s) {
+      const GroupLoad& ld = g.lds[k][s];
+      if (ld.prod >= 0) {
+        lv[k].push_back("b" + std::to_string(ld.prod) + "_" + std::to_string(ld.prod_store));
+      } else {
+        lv[k].push_back(mem_slot("l" + std::to_string(k) + "p" + std::to_string(s), "const " + std::string(ctype(r.loads[s].dtype)),
+                                 GL.lw[k][s], r.loads[s]));
+      }
+    }
+    for (size_t s = 0; s < r.stores.size(); ++s)
+      sm[k].push_back(k == anchor ? mem_slot("s" + std::to_string(s) + "p", ctype(r.stores[s].dtype), GL.sw[k][s],
+                                             r.stores[s])
+                                  : "");
+    for (size_t q = 0; q < cdecl[k].size(); ++q) {
+      const std::string& d = cdecl[k][q];
+      const size_t eq = d.find(" = ");
+      o << "    const " << d.substr(0, eq) << " c" << k << "_" << q << d.substr(eq) << ";\n";
+    }
+  }
+  for (auto& pw : pat_word) {
+    const std::string q = std::to_string(pw.first);
+    o << "    const int pa" << q << " = (int)" << W(pw.second + 1);
+    if (pats[pw.first][1] != 1) o << ", pb" << q << " = (int)" << W(pw.second + 2);
+    o << ";\n";
+  }
+  int red = -1;
+  for (int k = 0; k < m; ++k)
+    if (g.runs[k].has_red) red = k;
+  if (red >= 0) {
+    gens[red]->o.str("");
+    gens[red]->emit_acc_init("    ");
+    o << gens[red]->o.str();
+  }
+  const int NK = (TH * TW + ts.block - 1) / ts.block;
+  const bool partial = NK * ts.block > TH * TW;
+  auto body = [&](const std::string& ind) {
+    for (auto& pw : pat_word) {
+      const std::string q = std::to_string(pw.first);
+      o << ind << "const int ix" << q << " = li * pa" << q << " + "
+        << (pats[pw.first][1] == 1 ? std::string("lj") : "lj * pb" + q) << ";\n";
+    }
+    for (int k = 0; k < m; ++k) {
+      const Run& r = g.runs[k];
+      for (size_t s = 0; s < r.stores.size(); ++s)
+        o << ind << ctype(r.stores[s].dtype) << " b" << k << "_" << s << ";\n";
+      o << ind << "vbe_elem" << k << "(p, (r0 + li) * cols + (c0 + lj)";
+      for (auto& x : lv[k]) o << ", " << x;
+      for (size_t s = 0; s < r.stores.size(); ++s) o << ", b" << k << "_" << s;
+      if (r.has_red) o << (gens[k]->kahan() ? ", acc, kc" : ", acc");
+      for (size_t q = 0; q < r.consts.size(); ++q) o << ", c" << k << "_" << q;
+      o << ");\n";
+    }
+    for (size_t s = 0; s < g.runs[anchor].stores.size(); ++s)
+      o << ind << sm[anchor][s] << " = b" << anchor << "_" << s << ";\n";
+  };
+  auto loop = [&](bool checked) {
+    o << "#pragma unroll\n"
+      << "      for (int kq = 0; kq < " << NK << "; ++kq) {\n"
+      << "        const int q = threadIdx.x + kq * " << ts.block << ";\n"
+      << "        const int li = q / " << TW << ", lj = q - li * " << TW << ";\n";
+    std::string cond;
+    if (partial) cond = "q < " + std::to_string(TH * TW);
+    if (checked) {
+      if (!cond.empty()) cond += " && ";
+      cond += "r0 + li < rows && c0 + lj < cols";
+    }
+    if (cond.empty()) {
+      body("        ");
+    } else {
+      o << "        if (" << cond << ") {\n";
+      body("          ");
+      o << "        }\n";
+    }
+    o << "      }\n";
+  };
+  o << "    if (inside) {\n";
+  loop(false);
+  o << "    } else {\n";
+  loop(true);
+  o << "    }\n";
+  if (red >= 0) {
+    const int w = GL.red[red];
+    gens[red]->o.str("");
+    gens[red]->emit_full_epilogue("    ", W(w + 1), "blockIdx.x", W(w + 2), "gridDim.x", W(w));
+    o << gens[red]->o.str();
+  }
+}
 
 std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes_out) {
   const int m = (int)g.runs.size();
@@ -1427,6 +1584,13 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
       << "  if ((i64)blockIdx.x < p.w[3]) {\n"
       << "    const i64 ti = (i64)blockIdx.x / p.w[2], tj = (i64)blockIdx.x - ti * p.w[2];\n"
       << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n";
+    if (group_stacked(g)) {
+      emit_stacked(o, g, GL, gens, cdecl, ts);
+      o << "  }\n";
+      emit_copy_through(o, g, GL);
+      o << "}\n";
+      continue;
+    }
     for (int k = 0; k < m; ++k) {
       const Run& r = g.runs[k];
       const int BH = box_rows(g, k, ts.th), BW = box_cols(g, k, ts.tw);
@@ -1551,25 +1715,7 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
       o << "    }\n";
     }
     o << "  }\n";
-    // elements of renamed bases the anchor does not write: copied to the new buffer
-    for (size_t rr = 0; rr < g.renamed.size(); ++rr) {
-      const std::string T = ctype(g.runs[anchor].stores[g.renamed_slot[rr]].dtype);
-      const int w = GL.ren[rr];
-      o << "  {\n"
-        << "    const auto src = vbe_ptr<const " << T << ">(" << W(w) << ");\n"
-        << "    const auto dst = vbe_ptr<" << T << ">(" << W(w + 1) << ");\n"
-        << "    const i64 off = " << W(w + 2) << ", P = " << W(w + 3) << ", S0 = " << W(w + 4) << ", S1 = " << W(w + 5)
-        << ", nc = " << W(w + 6) << ";\n"
-        << "    const i64 gap = P - S1, ng = (S0 - 1) * gap;\n"
-        << "    for (i64 q = (i64)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (i64)gridDim.x * blockDim.x) {\n"
-        << "      i64 e;\n"
-        << "      if (q < off) e = q;\n"
-        << "      else if (q - off < ng) { const i64 u = q - off, rw = u / gap; e = off + rw * P + S1 + (u - rw * gap); }\n"
-        << "      else e = off + (S0 - 1) * P + S1 + (q - off - ng);\n"
-        << "      dst[e] = src[e];\n"
-        << "    }\n"
-        << "  }\n";
-    }
+    emit_copy_through(o, g, GL);
     o << "}\n";
   }
   std::string src = o.str();
