@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <set>
 #include <sstream>
 
 #include "vbe_core.h"
@@ -1276,7 +1277,82 @@ struct GroupLayout {
   std::vector<int> consts, rnd;          // per run: first constant word, first RANDOM word
   std::vector<int> ren;                  // per renamed base: source, destination, offset, pitch, rows, cols, count
   std::vector<int> red;                  // per run: reduction output, partials, counter (-1: no reduction)
+  std::vector<int> stg;                  // per staged base: offset of the reference view, element count
 };
+
+// Inputs staged through shared memory: a base the group reads from memory
+// through several views that differ by small shifts (a stencil's
+// neighbours) is copied once per block, tile plus halo, into shared memory
+// with coalesced row loads; every read of it is then a shared-memory load at
+// a compile-time offset.
+struct StagedSlot {
+  int k, s, dr, dc;  // run, load slot, shift from the reference view
+};
+struct StagedBase {
+  int64_t base = 0;
+  int dtype = 0;
+  int ref_k = 0, ref_s = 0;                // reference view (its pointer and row-stride words)
+  int rlo = 0, rhi = 0, clo = 0, chi = 0;  // union box around the tile, reference coordinates
+  std::vector<StagedSlot> slots;
+};
+
+std::vector<StagedBase> staging_plan(const Group& g) {
+  std::set<int64_t> written;
+  for (auto& r : g.runs)
+    for (auto& st : r.stores) written.insert(st.base);
+  std::vector<StagedBase> out;
+  for (size_t k = 0; k < g.runs.size(); ++k)
+    for (size_t s = 0; s < g.runs[k].loads.size(); ++s) {
+      const Slot& sl = g.runs[k].loads[s];
+      if (g.lds[k][s].prod >= 0 || sl.st.size() != 2 || sl.st[1] != 1 || sl.st[0] <= 16) continue;
+      const bool renamed = std::find(g.renamed.begin(), g.renamed.end(), sl.base) != g.renamed.end();
+      if (written.count(sl.base) && !renamed) continue;  // read in place: no staging
+      if (!g.base_nelem.count(sl.base)) continue;
+      int sb = -1;
+      for (size_t x = 0; x < out.size(); ++x) {
+        const Slot& ref = g.runs[out[x].ref_k].loads[out[x].ref_s];
+        if (out[x].base == sl.base && ref.st == sl.st && ref.dtype == sl.dtype) sb = (int)x;
+      }
+      if (sb < 0) {
+        StagedBase x;
+        x.base = sl.base;
+        x.dtype = sl.dtype;
+        x.ref_k = (int)k;
+        x.ref_s = (int)s;
+        out.push_back(x);
+        sb = (int)out.size() - 1;
+      }
+      const Slot& ref = g.runs[out[sb].ref_k].loads[out[sb].ref_s];
+      const int64_t P = ref.st[0], delta = sl.offset - ref.offset;
+      const int64_t dr = delta >= 0 ? (delta + P / 2) / P : -((-delta + P / 2) / P);
+      const int64_t dc = delta - dr * P;
+      if (std::llabs(dr) > 8 || std::llabs(dc) > 8) continue;
+      out[sb].slots.push_back({(int)k, (int)s, (int)dr, (int)dc});
+    }
+  std::vector<StagedBase> keep;
+  for (auto& x : out) {
+    if (x.slots.size() < 2) continue;
+    x.rlo = x.clo = 1 << 20;
+    x.rhi = x.chi = -(1 << 20);
+    for (auto& q : x.slots) {
+      x.rlo = std::min(x.rlo, g.box[q.k][0] + q.dr);
+      x.rhi = std::max(x.rhi, g.box[q.k][1] + q.dr);
+      x.clo = std::min(x.clo, g.box[q.k][2] + q.dc);
+      x.chi = std::max(x.chi, g.box[q.k][3] + q.dc);
+    }
+    keep.push_back(x);
+  }
+  return keep;
+}
+
+// per run, per load slot: (staged base, slot index) or (-1, -1)
+std::vector<std::vector<std::pair<int, int>>> staged_index(const Group& g, const std::vector<StagedBase>& sp) {
+  std::vector<std::vector<std::pair<int, int>>> ix(g.runs.size());
+  for (size_t k = 0; k < g.runs.size(); ++k) ix[k].assign(g.runs[k].loads.size(), {-1, -1});
+  for (size_t b = 0; b < sp.size(); ++b)
+    for (size_t q = 0; q < sp[b].slots.size(); ++q) ix[sp[b].slots[q].k][sp[b].slots[q].s] = {(int)b, (int)q};
+  return ix;
+}
 
 GroupLayout group_layout(const Group& g) {
   GroupLayout L;
@@ -1320,6 +1396,10 @@ GroupLayout group_layout(const Group& g) {
     L.red.push_back(g.runs[k].has_red ? w : -1);
     if (g.runs[k].has_red) w += 3;
   }
+  for (size_t b = 0; b < staging_plan(g).size(); ++b) {
+    L.stg.push_back(w);
+    w += 2;
+  }
   L.nwords = w;
   return L;
 }
@@ -1342,6 +1422,19 @@ std::vector<std::vector<int64_t>> group_smem(const Group& g, int th, int tw, int
       int64_t pts = (int64_t)box_rows(g, (int)k, th) * box_cols(g, (int)k, tw);
       acc += (pts * itemsize(g.runs[k].stores[s].dtype) + 15) / 16 * 16;
     }
+  *total = acc;
+  return off;
+}
+
+// shared-memory offsets of the staged inputs, placed after *total
+std::vector<int64_t> staged_smem(const std::vector<StagedBase>& sp, int th, int tw, int64_t* total) {
+  std::vector<int64_t> off;
+  int64_t acc = *total;
+  for (auto& b : sp) {
+    off.push_back(acc);
+    const int64_t pts = (int64_t)(th + b.rhi - b.rlo) * (tw + b.chi - b.clo);
+    acc += (pts * itemsize(b.dtype) + 15) / 16 * 16;
+  }
   *total = acc;
   return off;
 }
@@ -1373,6 +1466,7 @@ std::vector<TileShape> group_shapes(const Group& g) {
     ts.block = t[2];
     group_smem(g, ts.th, ts.tw, &ts.smem);
     if (group_stacked(g)) ts.smem = 0;
+    staged_smem(staging_plan(g), ts.th, ts.tw, &ts.smem);
     if (ts.smem <= kGroupSmemLimit) out.push_back(ts);
   }
   return out;
@@ -1408,7 +1502,8 @@ static void emit_copy_through(std::ostringstream& o, const Group& g, const Group
 // point every run in order, values handed on in registers.
 static void emit_stacked(std::ostringstream& o, const Group& g, const GroupLayout& GL,
                   const std::vector<std::unique_ptr<Gen>>& gens, const std::vector<std::vector<std::string>>& cdecl,
-                  const TileShape& ts) {
+                  const TileShape& ts, const std::vector<StagedBase>& sp,
+                  const std::vector<std::vector<std::pair<int, int>>>& six) {
   const int m = (int)g.runs.size(), anchor = m - 1;
   auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
   const int TH = ts.th, TW = ts.tw;
@@ -1435,7 +1530,13 @@ static void emit_stacked(std::ostringstream& o, const Group& g, const GroupLayou
     const Run& r = g.runs[k];
     for (size_t s = 0; s < r.loads.size(); ++s) {
       const GroupLoad& ld = g.lds[k][s];
-      if (ld.prod >= 0) {
+      if (six[k][s].first >= 0) {
+        const StagedBase& B = sp[six[k][s].first];
+        const StagedSlot& q = B.slots[six[k][s].second];
+        const int SC = TW + B.chi - B.clo;
+        lv[k].push_back("sg" + std::to_string(six[k][s].first) + "[li * " + std::to_string(SC) + " + lj + " +
+                        std::to_string((q.dr - B.rlo) * SC + (q.dc - B.clo)) + "]");
+      } else if (ld.prod >= 0) {
         lv[k].push_back("b" + std::to_string(ld.prod) + "_" + std::to_string(ld.prod_store));
       } else {
         lv[k].push_back(mem_slot("l" + std::to_string(k) + "p" + std::to_string(s), "const " + std::string(ctype(r.loads[s].dtype)),
@@ -1578,14 +1679,37 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
   for (const TileShape& ts : shapes) {
     int64_t total = 0;
     auto soff = group_smem(g, ts.th, ts.tw, &total);
+    if (group_stacked(g)) total = 0;
+    const std::vector<StagedBase> sp = staging_plan(g);
+    const auto six = staged_index(g, sp);
+    const std::vector<int64_t> sgoff = staged_smem(sp, ts.th, ts.tw, &total);
     o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@_sg" << ts.th << "x" << ts.tw
       << "(const P p) {\n"
       << "  VBE_DYN_SMEM;\n"
       << "  if ((i64)blockIdx.x < p.w[3]) {\n"
       << "    const i64 ti = (i64)blockIdx.x / p.w[2], tj = (i64)blockIdx.x - ti * p.w[2];\n"
       << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n";
+    // staged inputs: tile plus halo, coalesced along rows, elements outside
+    // the base skipped (their cells are never read)
+    for (size_t b = 0; b < sp.size(); ++b) {
+      const StagedBase& B = sp[b];
+      const std::string T = ctype(B.dtype);
+      const int SR = ts.th + B.rhi - B.rlo, SC = ts.tw + B.chi - B.clo, w = GL.lw[B.ref_k][B.ref_s];
+      o << "    const " << T << "* const sg" << b << " = (const " << T << "*)(vbe_smem + " << sgoff[b] << ");\n"
+        << "    {\n"
+        << "      const auto stp = vbe_ptr<const " << T << ">(" << W(w) << ");\n"
+        << "      const i64 P = " << W(w + 1) << ", soff = " << W(GL.stg[b]) << ", sne = " << W(GL.stg[b] + 1) << ";\n"
+        << "      " << T << "* const sb = (" << T << "*)(vbe_smem + " << sgoff[b] << ");\n"
+        << "      for (int q = threadIdx.x; q < " << SR * SC << "; q += " << ts.block << ") {\n"
+        << "        const int u = q / " << SC << ", v = q - u * " << SC << ";\n"
+        << "        const i64 e = (i0 + (" << B.rlo << ") + u) * P + (j0 + (" << B.clo << ") + v);\n"
+        << "        if (soff + e >= 0 && soff + e < sne) sb[q] = stp[e];\n"
+        << "      }\n"
+        << "    }\n";
+    }
+    if (!sp.empty()) o << "    __syncthreads();\n";
     if (group_stacked(g)) {
-      emit_stacked(o, g, GL, gens, cdecl, ts);
+      emit_stacked(o, g, GL, gens, cdecl, ts, sp, six);
       o << "  }\n";
       emit_copy_through(o, g, GL);
       o << "}\n";
@@ -1621,7 +1745,13 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
       for (size_t s = 0; s < r.loads.size(); ++s) {
         const std::string T = ctype(r.loads[s].dtype), n = std::to_string(s);
         const GroupLoad& ld = g.lds[k][s];
-        if (ld.prod < 0) {
+        if (six[k][s].first >= 0) {
+          const StagedBase& B = sp[six[k][s].first];
+          const StagedSlot& q = B.slots[six[k][s].second];
+          const int SC = ts.tw + B.chi - B.clo;
+          lv.push_back("sg" + std::to_string(six[k][s].first) + "[li * " + std::to_string(SC) + " + lj + " +
+                       std::to_string((g.box[k][0] + q.dr - B.rlo) * SC + (g.box[k][2] + q.dc - B.clo)) + "]");
+        } else if (ld.prod < 0) {
           lv.push_back(mem_slot("l", n, "const " + T, GL.lw[k][s], r.loads[s]));
         } else {
           const int pk = ld.prod;
@@ -1779,6 +1909,12 @@ void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std
     w[q + 4] = R;
     w[q + 5] = C;
     w[q + 6] = g.renamed_nelem[rr] - R * C;
+  }
+  // staged inputs: the reference view's offset in its base and the base's size
+  const std::vector<StagedBase> sp = staging_plan(g);
+  for (size_t b = 0; b < sp.size(); ++b) {
+    w[GL.stg[b]] = g.runs[sp[b].ref_k].loads[sp[b].ref_s].offset;
+    w[GL.stg[b] + 1] = g.base_nelem.at(sp[b].base);
   }
   // reductions: one partial per block, a region and a completion counter per reducing run
   int nq = 0;

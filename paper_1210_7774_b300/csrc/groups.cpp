@@ -184,6 +184,11 @@ std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const 
     g->renamed_slot.push_back(ss);
     g->renamed_nelem.push_back(bit->second.nelem);
   }
+  for (auto& r : g->runs)
+    for (auto& l : r.loads) {
+      auto bit = c->bases.find(l.base);
+      if (bit != c->bases.end()) g->base_nelem[l.base] = bit->second.nelem;
+    }
   // shared memory of the smallest tile shape
   int64_t smem = 0;
   for (int k = 0; k < anchor; ++k) {

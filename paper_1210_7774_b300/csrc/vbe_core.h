@@ -163,6 +163,7 @@ struct Group {
   std::vector<int64_t> renamed;
   std::vector<int> renamed_slot;             // the anchor's store slot of each renamed base
   std::vector<int64_t> renamed_nelem;        // element count of each renamed base
+  std::map<int64_t, int64_t> base_nelem;     // element count of every base the group reads
   int64_t rows(int k) const { return runs[k].shape[0]; }
   int64_t cols(int k) const { return runs[k].shape[1]; }
 };
