@@ -1456,17 +1456,22 @@ bool group_stacked(const Group& g) {
   return nred <= 1;
 }
 
+// Tile shapes the tuner chooses from; two of them also in the staged form
+// (inputs through shared memory), where the group has stencil inputs
 std::vector<TileShape> group_shapes(const Group& g) {
   std::vector<TileShape> out;
-  for (auto t : std::vector<std::array<int, 3>>{{8, 16, 128}, {16, 32, 256}, {32, 32, 256}, {16, 64, 256},
-                                                {32, 64, 256}}) {
+  const bool can_stage = !staging_plan(g).empty();
+  for (auto t : std::vector<std::array<int, 4>>{{8, 16, 128, 0}, {16, 32, 256, 0}, {32, 32, 256, 0}, {16, 64, 256, 0},
+                                                {32, 64, 256, 0}, {32, 32, 256, 1}, {16, 64, 256, 1}}) {
     TileShape ts;
     ts.th = t[0];
     ts.tw = t[1];
     ts.block = t[2];
+    ts.staged = t[3] != 0;
+    if (ts.staged && !can_stage) continue;
     group_smem(g, ts.th, ts.tw, &ts.smem);
     if (group_stacked(g)) ts.smem = 0;
-    staged_smem(staging_plan(g), ts.th, ts.tw, &ts.smem);
+    if (ts.staged) staged_smem(staging_plan(g), ts.th, ts.tw, &ts.smem);
     if (ts.smem <= kGroupSmemLimit) out.push_back(ts);
   }
   return out;
@@ -1680,10 +1685,10 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     int64_t total = 0;
     auto soff = group_smem(g, ts.th, ts.tw, &total);
     if (group_stacked(g)) total = 0;
-    const std::vector<StagedBase> sp = staging_plan(g);
+    const std::vector<StagedBase> sp = ts.staged ? staging_plan(g) : std::vector<StagedBase>();
     const auto six = staged_index(g, sp);
     const std::vector<int64_t> sgoff = staged_smem(sp, ts.th, ts.tw, &total);
-    o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@_sg" << ts.th << "x" << ts.tw
+    o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@" << ts.suffix()
       << "(const P p) {\n"
       << "  VBE_DYN_SMEM;\n"
       << "  if ((i64)blockIdx.x < p.w[3]) {\n"

@@ -751,7 +751,7 @@ GroupPtrs group_ptrs(Ctx* c, const Group& g) {
 
 Launch build_group(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const GroupPtrs& ptr) {
   Launch L;
-  L.entry = G.prefix + "_sg" + std::to_string(ts.th) + "x" + std::to_string(ts.tw);
+  L.entry = G.prefix + ts.suffix();
   L.key = G.key;
   L.fn = kernel_fn(G.kern.get(), L.entry);
   L.block = (unsigned)ts.block;
@@ -790,20 +790,20 @@ std::string group_tune_key(const GroupPrepared& G) {
 TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real, bool may_tune) {
   if (G.shapes.empty()) fail(VBE_ERR_INVALID, "tile-fused group without a tile shape");
   if (c->record) {
-    const char* e = getenv("VBE_RECORD_TILE");
+    const char* e = getenv("VBE_RECORD_TILE");  // "THxTW", or "sTHxTW" for the staged form
     if (e)
       for (auto& ts : G.shapes)
-        if (std::to_string(ts.th) + "x" + std::to_string(ts.tw) == e) return ts;
+        if ((ts.staged ? "s" : "") + std::to_string(ts.th) + "x" + std::to_string(ts.tw) == e) return ts;
     return G.shapes[0];
   }
   std::string tk = group_tune_key(G);
   auto it = c->tune.find(tk);
   if (it != c->tune.end())
     for (auto& ts : G.shapes)
-      if (ts.th == it->second.block && ts.tw == it->second.U) return ts;
+      if (ts.th == it->second.block && ts.tw == it->second.U && (int)ts.staged == it->second.grid_mult) return ts;
   TileShape def = G.shapes[0];
   for (auto& ts : G.shapes)
-    if (ts.th * ts.tw <= 1024 && ts.th * ts.tw >= def.th * def.tw) def = ts;
+    if (!ts.staged && ts.th * ts.tw <= 1024 && ts.th * ts.tw >= def.th * def.tw) def = ts;
   const Group& g = *G.g;
   const int anchor = (int)g.runs.size() - 1;
   if (!(may_tune && (c->cfg.flags & VBE_AUTOTUNE) && g.rows(anchor) * g.cols(anchor) >= (1 << 16))) return def;
@@ -852,9 +852,10 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
   }
   for (auto& b : bufs) dev_free(c, ex, b.first, b.second);
   c->stats.autotunes++;
-  TuneChoice tc;
+  TuneChoice tc;  // the group's choice: tile rows, tile columns, staged form
   tc.block = best.th;
   tc.U = best.tw;
+  tc.grid_mult = best.staged ? 1 : 0;
   c->tune[tk] = tc;
   return best;
 }

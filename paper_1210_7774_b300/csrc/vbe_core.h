@@ -220,7 +220,11 @@ int words_count(const Run& r, const Canon& c);
 // tile-fused groups: source with one kernel per tile shape, and its words
 struct TileShape {
   int th = 0, tw = 0, block = 0;
-  int64_t smem = 0;  // dynamic shared memory bytes
+  bool staged = false;  // stencil inputs copied to shared memory first (else read through L1)
+  int64_t smem = 0;     // dynamic shared memory bytes
+  std::string suffix() const {
+    return std::string(staged ? "_ss" : "_sg") + std::to_string(th) + "x" + std::to_string(tw);
+  }
 };
 std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes);
 void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std::vector<uintptr_t>>& load_ptrs,

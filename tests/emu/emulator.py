@@ -153,7 +153,7 @@ class Emulator:
             if prefix + "_bulk" in names:
                 parts.append(_WRAP_BULK.replace("@P@", prefix))
             for name in names:  # tile-fused groups: one kernel per tile shape
-                if re.search(r"_sg\d+x\d+$", name):
+                if re.search(r"_s[gs]\d+x\d+$", name):
                     parts.append(_WRAP_ENTRY.replace("@E@", name))
             cpp = os.path.join(self.dir, f"emu_{h}.cpp")
             with open(cpp, "w") as f:
@@ -204,7 +204,7 @@ class Emulator:
                                    L["chunk"], L["work"], L["grid"], L["block"])
             else:
                 w = (ctypes.c_longlong * len(L["words"]))(*L["words"])
-                if re.search(r"_sg\d+x\d+$", entry):
+                if re.search(r"_s[gs]\d+x\d+$", entry):
                     fn = getattr(lib, "emu_" + entry)
                     fn.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
                     fn.restype = ctypes.c_longlong

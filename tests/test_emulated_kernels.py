@@ -90,13 +90,14 @@ def test_emulated_shapes_on_stencil_and_packing(shape):
             case.check(got, want)
 
 
-@pytest.mark.parametrize("tile", ["8x16", "16x32", "32x32", "split"])
+@pytest.mark.parametrize("tile", ["8x16", "16x32", "32x32", "s32x32", "s16x64", "split"])
 def test_emulated_tile_groups(tile):
     """Tile-fused groups at several tile shapes (ragged edge tiles, halos
     across tile borders): shallow water (state renamed every step, ghost
-    ring copied across) and the synthetic chains; and the same groups run
-    as their separate kernels (the choice the tuner makes when that is
-    faster)."""
+    ring copied across) and the synthetic chains, with the inputs read
+    through L1 or staged through shared memory ("s" shapes); and the same
+    groups run as their separate kernels (the choice the tuner makes when
+    that is faster)."""
     cases = tile_group_cases()
     for dt in ("float64", "float32"):
         p = shallow_water(40, 2, dt)
