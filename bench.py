@@ -126,6 +126,22 @@ def cpu_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(sec: float, dist=None) -> float:
+    """The slowest rank's per-step time (every rank takes part)."""
+    if not dist:
+        return sec
+    import torch
+    t = torch.tensor([sec], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def aggregate_value(units_per_rank: float, sec_max: float, world: int) -> float:
+    """Whole-job throughput of weak scaling: every rank processes its own
+    units_per_rank per step, the job's step takes the slowest rank's time."""
+    return world * units_per_rank / sec_max
+
+
 def workload_config(n, dtype):
     return {"workload": f"Black-Scholes call+put, {n} options, {dtype}", "options": n,
             "bytes_per_option": 7 * (8 if dtype == "float64" else 4),
@@ -474,17 +490,12 @@ def main():
             print(json.dumps({k: {p: v[p]["sec"] for p in ("fused", "plain") if p in v} for k, v in res.items()}))
         return
     # max over ranks of the per-step time
-    sec = res["float64"]["fused"]["sec"]
-    if dist:
-        import torch
-        t = torch.tensor([sec])
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t[0])
+    sec = max_over_ranks(res["float64"]["fused"]["sec"], dist)
     if rank != 0:
         return
     hbm, src = peaks()
     f64 = res["float64"]
-    value = world * f64["cbytes"] / sec / 1e9
+    value = aggregate_value(f64["cbytes"], sec, world) / 1e9
     achieved = f64["cbytes"] / sec / 1e9
     cpu = None
     if not args.no_cpu_baseline:

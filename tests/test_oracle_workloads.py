@@ -326,9 +326,9 @@ def test_stencil_keeps_row_mirror_symmetry_bitwise():
 @pytest.mark.parametrize("dtype", ["float64", "float32"])
 def test_knn_matches_sorted_brute_force(dtype):
     """The k nearest points of every query equal the first k entries of a
-    stable sort of all squared distances (computed here per pair in float64,
-    then rounded like the program's dtype would not change the order for
-    these well-separated draws); duplicated points check the lower-index
+    stable sort of all squared distances, computed here per pair in plain
+    float64 (for these draws no two candidates are close enough for float32
+    rounding to swap them); an exact duplicate point checks the lower-index
     tie rule."""
     from workloads import knn, knn_inputs
     inp = knn_inputs(200, 30, 4, dtype, seed=8)
