@@ -337,8 +337,11 @@ typedef struct vbe_server vbe_server;
  * as soon as another completes), executes each on its slot's stream, and
  * completes it when its results are on the host. */
 int vbe_server_create(vbe_ctx* ctx, const vbe_server_config* cfg, vbe_server** out);
-/* Enqueue a request; *id identifies it. VBE_ERR_ADMISSION if its footprint
- * alone exceeds the cap, VBE_ERR_BUSY if the queue is full. */
+/* Enqueue a request; *id identifies it. Its footprint is the bytes of all
+ * its bases plus those of every base it writes through some views and reads
+ * through others (which may get a second buffer, see VBE_NO_TILE_FUSION).
+ * VBE_ERR_ADMISSION if the footprint alone exceeds the cap, VBE_ERR_BUSY if
+ * the queue is full. */
 int vbe_server_submit(vbe_server* srv, const vbe_request* req, int64_t* id);
 /* Wait for a request (timeout_ns < 0: forever) and fetch its result record. */
 int vbe_server_wait(vbe_server* srv, int64_t id, int64_t timeout_ns, vbe_request_result* out);

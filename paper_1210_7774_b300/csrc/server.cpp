@@ -96,8 +96,10 @@ void finish_request(vbe_server* s, Req* r) {
     auto it = c.bases.find(h);
     if (it == c.bases.end()) continue;
     if (it->second.dptr && !it->second.external) vbe::dev_free(&c, ex, it->second.dptr, it->second.bytes());
+    if (it->second.shadow) vbe::dev_free(&c, ex, it->second.shadow, it->second.bytes());
     c.bases.erase(it);
   }
+  c.epoch++;
   if (r->ev) cudaEventDestroy(r->ev);
   r->ev = nullptr;
 }
@@ -270,6 +272,32 @@ int vbe_server_submit(vbe_server* s, const vbe_request* req, int64_t* id) {
   for (auto& b : r->bases) {
     if (b.dtype < 0 || b.dtype > 3 || b.nelem < 0) return VBE_ERR_INVALID;
     r->footprint += b.nelem * vbe::itemsize(b.dtype);
+  }
+  // a base the program writes through some views and reads through others
+  // may get a second buffer (a tile-fused group that updates it in place
+  // while reading it around): counted twice
+  {
+    const size_t nb = r->bases.size();
+    std::vector<std::vector<int64_t>> outs(nb), ins(nb);
+    auto base_of = [&](int64_t v) -> int64_t {
+      return (v >= 1 && v <= (int64_t)r->views.size()) ? r->views[v - 1].base : -1;
+    };
+    for (auto& in : r->instrs) {
+      if (in.op == VBE_OP_SYNC || in.op == VBE_OP_DISCARD || in.op == VBE_OP_FREE) continue;
+      int64_t b = base_of(in.out);
+      if (b >= 0 && b < (int64_t)nb) outs[b].push_back(in.out);
+      for (int k = 0; k < 3; ++k) {
+        b = base_of(in.in[k]);
+        if (b >= 0 && b < (int64_t)nb) ins[b].push_back(in.in[k]);
+      }
+    }
+    for (size_t b = 0; b < nb; ++b) {
+      if (outs[b].empty()) continue;
+      bool other = false;
+      for (int64_t v : ins[b])
+        if (std::find(outs[b].begin(), outs[b].end(), v) == outs[b].end()) other = true;
+      if (other) r->footprint += r->bases[b].nelem * vbe::itemsize(r->bases[b].dtype);
+    }
   }
   std::lock_guard<std::mutex> lk(s->m);
   if (s->stop) return VBE_ERR_BUSY;

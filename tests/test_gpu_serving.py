@@ -82,7 +82,12 @@ def test_requests_match_oracle_and_solo_results():
 
 def test_admission_respects_memory_cap_and_rejects_oversize():
     programs = [jacobi_request(64, 2, "float64", s) for s in range(6)]
-    foot = sum(b.nelem * 8 for b in programs[0].bases.values())
+    # the footprint counts every base, and once more each base the request
+    # both reads and writes (the grid: it may get a second buffer)
+    _, solo = serve(programs[:1], slots=1)
+    foot = solo[0].footprint_bytes
+    grid = 64 * 64 * 8
+    assert foot == sum(b.nelem * 8 for b in programs[0].bases.values()) + grid
     # a cap that fits one request at a time: all complete, one by one
     reqs, res = serve(programs, slots=4, cap=foot + 1024, threads=3)
     assert all(r.status == 0 for r in res)
