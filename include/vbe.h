@@ -134,7 +134,10 @@ typedef struct vbe_instr {
 /* ---------------------------------------------------------------- config */
 enum {
   VBE_FUSE = 1u << 0,      /* form kernels from blockable runs (else one launch per bytecode) */
-  VBE_GRAPHS = 1u << 1,    /* capture repeated identical batches as CUDA graphs              */
+  VBE_GRAPHS = 1u << 1,    /* capture repeated identical batches of three or more launches as
+                              CUDA graphs (a batch of one or two launches replays its launch
+                              list: with programmatic dependent launch that costs less than a
+                              graph launch)                                                  */
   VBE_AUTOTUNE = 1u << 2,  /* time launch shapes per kernel signature and keep the fastest  */
   VBE_PACK = 1u << 3,      /* pack consecutive independent same-signature runs in one launch */
   VBE_HOST_ONLY = 1u << 4, /* no device: analysis, planning and code generation only        */
@@ -241,6 +244,8 @@ typedef struct vbe_stats {
   int64_t batches;
   int64_t bytes_allocated;   /* live library allocations                      */
   int64_t peak_bytes;
+  int64_t list_replays;      /* repeated batches replayed from their cached
+                                launch list (no analysis, no graph)          */
 } vbe_stats;
 int vbe_get_stats(vbe_ctx* ctx, vbe_stats* out);
 

@@ -441,6 +441,10 @@ __device__ __forceinline__ bool vbe_mbar_wait(unsigned long long* bar, unsigned 
   return false;
 }
 #define VBE_DYN_SMEM extern __shared__ __align__(128) unsigned char vbe_smem[]
+// programmatic dependent launch: a kernel launched while its predecessor on
+// the stream is still running waits here until that grid has completed and
+// its writes are visible (a no-op for an ordinary launch)
+__device__ __forceinline__ void vbe_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ unsigned long long vbe_umulhi(unsigned long long a, unsigned long long b) {
   return __umul64hi(a, b);
 }
@@ -793,7 +797,8 @@ struct Gen {
   // --------------------------------------------------------- tile kernels
   void emit_tile_kernel(int U) {
     const int nd = c.spec.nd;
-    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_u" << U << "(const P p) {\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_u" << U << "(const P p) {\n"
+      << "  vbe_grid_wait();\n";
     emit_pointers("  ");
     emit_acc_init("  ");
     // inner strides
@@ -893,7 +898,7 @@ struct Gen {
   void emit_bulk_kernel() {
     const int E = c.spec.E;
     o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_bulk(const P p) {\n"
-      << "  VBE_DYN_SMEM;\n";
+      << "  VBE_DYN_SMEM;\n  vbe_grid_wait();\n";
     emit_pointers("  ");
     emit_acc_init("  ");
     o << "  const i64 n = " << W(L.inner) << ", CH = " << W(L.bulk_ch) << ";\n"
@@ -1060,6 +1065,7 @@ struct Gen {
   void emit_packed_kernel(int U) {
     o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_pack_u" << U
       << "(const P* __restrict__ descs, const i64* __restrict__ prefix, int ninst, i64 total, i64 chunk, unsigned* work) {\n"
+      << "  vbe_grid_wait();\n"
       << "  __shared__ i64 s_c;\n"
       << "  for (;;) {\n"
       << "    if (threadIdx.x == 0) s_c = (i64)atomicAdd(work, 1u);\n"
@@ -1110,7 +1116,8 @@ struct Gen {
   void emit_axis_kernel() {
     const int ndk = c.spec.ndk, ndr = c.spec.ndr;
     bool block = c.spec.mode == Mode::AXIS_BLOCK;
-    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_axis(const P p) {\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_axis(const P p) {\n"
+      << "  vbe_grid_wait();\n";
     emit_pointers("  ");
     o << "  const auto rp = vbe_ptr<" << rt() << ">(" << W(L.red_ptr) << ");\n"
       << "  const i64 nout = " << W(L.nout) << ", nred = " << W(L.nred) << ";\n";
@@ -1691,6 +1698,7 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@" << ts.suffix()
       << "(const P p) {\n"
       << "  VBE_DYN_SMEM;\n"
+      << "  vbe_grid_wait();\n"
       << "  if ((i64)blockIdx.x < p.w[3]) {\n"
       << "    const i64 ti = (i64)blockIdx.x / p.w[2], tj = (i64)blockIdx.x - ti * p.w[2];\n"
       << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n";

@@ -357,6 +357,23 @@ void record_launch(Ctx* c, Exec* ex, Launch& L) {
   c->stats.kernel_launches++;
 }
 
+// Every generated kernel starts with griddepcontrol.wait, so it may be
+// launched with programmatic stream serialization: its blocks are scheduled
+// while the previous kernel on the stream drains, and wait there for it.
+cudaError_t launch_pdl(cudaKernel_t fn, unsigned grid, unsigned block, void** args, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, (const void*)fn, args);
+}
+
 void issue(Ctx* c, Exec* ex, Launch& L, bool capturing) {
   if (c->record) {
     record_launch(c, ex, L);
@@ -381,14 +398,14 @@ void issue(Ctx* c, Exec* ex, Launch& L, bool capturing) {
     long long a3 = L.total, a4 = L.chunk;
     void* a5 = work;
     void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
-    cuda_check(cudaLaunchKernel((const void*)L.fn, dim3(L.grid), dim3(L.block), args, 0, s), "launch (packed)");
+    cuda_check(launch_pdl(L.fn, L.grid, L.block, args, 0, s), "launch (packed)");
     if (!capturing) {
       dev_free(c, ex, L.d_descs, L.d_bytes);
       L.d_descs = L.d_prefix = nullptr;
     }
   } else {
     void* args[] = {(void*)L.words.data()};
-    cuda_check(cudaLaunchKernel((const void*)L.fn, dim3(L.grid), dim3(L.block), args, L.smem, s), "launch");
+    cuda_check(launch_pdl(L.fn, L.grid, L.block, args, L.smem, s), "launch");
   }
   if (!capturing) c->stats.kernel_launches++;
 }
@@ -981,6 +998,12 @@ void do_action(Ctx* c, Exec* ex, const HostAction& a) {
 
 }  // namespace
 
+// Batches of fewer launches replay their launch list even with VBE_GRAPHS:
+// with programmatic dependent launch one or two stream launches cost less
+// than a graph launch (measured: a one-kernel Jacobi iteration 6.5 us
+// replayed from its list, 8.3 us from a graph).
+constexpr size_t kGraphMinLaunches = 3;
+
 // Execute one batch on ex's stream. Eager the first time a batch is seen;
 // with VBE_GRAPHS, a batch seen again (same instructions, same views, same
 // base addresses, no FREE) is captured into a CUDA graph and later replayed.
@@ -1037,8 +1060,9 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
         apply_after(*var);
         return;
       }
-      if (!graphs && var->has_eager) {
+      if ((!graphs || (var->has_eager && var->eager.size() < kGraphMinLaunches)) && var->has_eager) {
         for (auto& L : var->eager) issue(c, ex, *L, false);
+        c->stats.list_replays++;
         apply_after(*var);
         return;
       }
@@ -1061,7 +1085,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
     }
     ensure_scratch(c, ex, need, 1 << 16);
   }
-  bool capture = graphs && var && var->seen >= 1;
+  bool capture = graphs && var && var->seen >= 1 && !(var->has_eager && var->eager.size() < kGraphMinLaunches);
 
   // compile the batch's kernels in parallel on first sight
   {
