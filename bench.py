@@ -145,7 +145,9 @@ def aggregate_value(units_per_rank: float, sec_max: float, world: int) -> float:
 def workload_config(n, dtype):
     return {"workload": f"Black-Scholes call+put, {n} options, {dtype}", "options": n,
             "bytes_per_option": 7 * (8 if dtype == "float64" else 4),
-            "l2": "inputs larger than L2 (no flush needed)", "path": "fused + CUDA graph + autotuned launch"}
+            "l2": "inputs larger than L2 (no flush needed)",
+            "path": "fused (one kernel per batch), cached launch replayed with programmatic dependent launch, "
+                    "autotuned launch shape"}
 
 
 # ------------------------------------------------------------------ GPU arm
