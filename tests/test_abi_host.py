@@ -320,3 +320,16 @@ def test_user_operation_registration(fused):
     with pytest.raises(V.VbeError) as e:
         V.vbe_plan(ctx, arr, 1, False)
     assert e.value.code == -3
+
+
+def test_caller_owned_state_is_never_renamed():
+    """A base registered from the caller's memory keeps its address: when a
+    shallow-water step would have to rename it, the chain stays separate
+    kernels (the in-place update then happens in the caller's buffer)."""
+    p = shallow_water(12, 1)
+    with Executor(V.VBE_FUSE | V.VBE_PACK | HOST) as ex:
+        fake = {p.meta["H"]: 0x10000}  # an address the host-only context never dereferences
+        L = ex.load(p, device_ptrs=fake, upload=False)
+        js = json.loads(ex.plan(L, 0))
+        assert not any("group" in i for i in js["items"])
+        assert [len(i["run"]["ops"]) for i in js["items"] if "run" in i] == [6, 6, 9, 21, 21, 18]
