@@ -34,7 +34,7 @@ extern dim3 blockDim, gridDim;
 #define __device__
 #define __forceinline__ inline
 #define SF_CALL __attribute__((noinline))
-#define __launch_bounds__(x)
+#define __launch_bounds__(...)
 #define __shared__ static
 
 struct EmuRange {
