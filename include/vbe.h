@@ -246,6 +246,8 @@ typedef struct vbe_stats {
   int64_t peak_bytes;
   int64_t list_replays;      /* repeated batches replayed from their cached
                                 launch list (no analysis, no graph)          */
+  int64_t tma_group_launches; /* tile-fused groups issued (or captured) in the
+                                tensor-copy form, tuning trials included     */
 } vbe_stats;
 int vbe_get_stats(vbe_ctx* ctx, vbe_stats* out);
 

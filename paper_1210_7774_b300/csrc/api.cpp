@@ -81,6 +81,7 @@ int vbe_init(const vbe_config* cfg, vbe_ctx** out) {
     if (const char* e = getenv("VBE_RECORD_SMS")) c.sm_count = atoi(e);
   }
   if (const char* e = getenv("VBE_STAGING")) c.force_bulk = atoi(e);
+  if (const char* e = getenv("VBE_TILE")) c.force_tile = e;
   c.device = cfg->device;
   if (cfg->cache_dir) {
     // the context keeps its own copy of the path

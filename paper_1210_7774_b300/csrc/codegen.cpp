@@ -463,6 +463,21 @@ __device__ __forceinline__ float vbe_rsqrt_approx(float x) {
 #endif
 )CUDA";
 
+// Tensor-copy helpers, only in sources of groups with the tensor-copy form:
+// a tensor map (an opaque 128-byte, 64-byte aligned descriptor) and a
+// two-dimensional tiled copy of the box at (x, y) into shared memory,
+// completed on an mbarrier; boxes reaching outside the tensor read zeros.
+const char* kTmaPrelude = R"CUDA(
+struct __align__(64) vbe_tmap { unsigned long long v[16]; };
+#ifndef VBE_EMU
+__device__ __forceinline__ void vbe_tma_2d(void* dst, const void* tmap, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(vbe_saddr(dst)), "l"(tmap), "r"(x), "r"(y), "r"(vbe_saddr(bar)) : "memory");
+}
+#endif
+)CUDA";
+
 // float64 divide/sqrt/exp/log on the integer pipes (sf64_tables.h + sf64.cuh)
 #include "_embed_sf64.inc"
 
@@ -1285,6 +1300,7 @@ struct GroupLayout {
   std::vector<int> ren;                  // per renamed base: source, destination, offset, pitch, rows, cols, count
   std::vector<int> red;                  // per run: reduction output, partials, counter (-1: no reduction)
   std::vector<int> stg;                  // per staged base: offset of the reference view, element count
+  int err = -1;                          // error word of the tensor-copy form
 };
 
 // Inputs staged through shared memory: a base the group reads from memory
@@ -1405,8 +1421,9 @@ GroupLayout group_layout(const Group& g) {
   }
   for (size_t b = 0; b < staging_plan(g).size(); ++b) {
     L.stg.push_back(w);
-    w += 2;
+    w += 5;  // reference view's offset, base size; tensor copies: x and y of the box origin, column shift
   }
+  L.err = w++;
   L.nwords = w;
   return L;
 }
@@ -1433,17 +1450,37 @@ std::vector<std::vector<int64_t>> group_smem(const Group& g, int th, int tw, int
   return off;
 }
 
-// shared-memory offsets of the staged inputs, placed after *total
-std::vector<int64_t> staged_smem(const std::vector<StagedBase>& sp, int th, int tw, int64_t* total) {
+// row length of a staged input's shared-memory box: the tile's columns plus
+// halo, and for tensor copies one 16-byte unit more, the copy starting at the
+// 16-byte boundary at or below the box's first column
+int staged_cols(const StagedBase& b, int tw, bool tma) {
+  const int sc = tw + b.chi - b.clo;
+  if (!tma) return sc;
+  const int a = 16 / itemsize(b.dtype);
+  return (sc + a - 1 + a - 1) / a * a;
+}
+
+// shared-memory offsets of the staged inputs, placed after *total (tensor
+// copies: two stages per input, 128-byte aligned; stage 1 at off + stage bytes)
+std::vector<int64_t> staged_smem(const std::vector<StagedBase>& sp, int th, int tw, int64_t* total,
+                                 bool tma = false) {
   std::vector<int64_t> off;
   int64_t acc = *total;
+  const int64_t al = tma ? 128 : 16;
+  acc = (acc + al - 1) / al * al;
   for (auto& b : sp) {
     off.push_back(acc);
-    const int64_t pts = (int64_t)(th + b.rhi - b.rlo) * (tw + b.chi - b.clo);
-    acc += (pts * itemsize(b.dtype) + 15) / 16 * 16;
+    const int64_t pts = (int64_t)(th + b.rhi - b.rlo) * staged_cols(b, tw, tma);
+    acc += (pts * itemsize(b.dtype) + al - 1) / al * al * (tma ? 2 : 1);
   }
+  if (tma) acc += 16;  // two mbarriers
   *total = acc;
   return off;
+}
+
+int64_t staged_stage_bytes(const StagedBase& b, int th, int tw) {
+  const int64_t pts = (int64_t)(th + b.rhi - b.rlo) * staged_cols(b, tw, true);
+  return (pts * itemsize(b.dtype) + 127) / 128 * 128;
 }
 
 constexpr int64_t kGroupSmemLimit = 200 * 1024;
@@ -1463,28 +1500,114 @@ bool group_stacked(const Group& g) {
   return nred <= 1;
 }
 
+// Tensor copies need whole rows (the base a whole number of rows of the
+// row stride), 16-byte row strides, and no reduction (the persistent form
+// keeps no per-tile reduction state).
+bool tma_ok(const Group& g) {
+  for (auto& r : g.runs)
+    if (r.has_red) return false;
+  for (auto& b : staging_plan(g)) {
+    const Slot& ref = g.runs[b.ref_k].loads[b.ref_s];
+    const int64_t P = ref.st[0], ne = g.base_nelem.at(b.base);
+    if ((P * itemsize(b.dtype)) % 16 != 0 || ne % P != 0 || ne / P >= (1ll << 31) || P >= (1ll << 31)) return false;
+  }
+  return true;
+}
+
 // Tile shapes the tuner chooses from; two of them also in the staged form
-// (inputs through shared memory), where the group has stencil inputs
+// (inputs through shared memory) and two in the pipelined tensor-copy form,
+// where the group has stencil inputs
 std::vector<TileShape> group_shapes(const Group& g) {
   std::vector<TileShape> out;
   const bool can_stage = !staging_plan(g).empty();
+  const bool can_tma = can_stage && tma_ok(g);
   for (auto t : std::vector<std::array<int, 4>>{{8, 16, 128, 0}, {16, 32, 256, 0}, {32, 32, 256, 0}, {16, 64, 256, 0},
-                                                {32, 64, 256, 0}, {32, 32, 256, 1}, {16, 64, 256, 1}}) {
+                                                {32, 64, 256, 0}, {32, 32, 256, 1}, {16, 64, 256, 1},
+                                                {32, 32, 256, 2}, {16, 64, 256, 2}}) {
     TileShape ts;
     ts.th = t[0];
     ts.tw = t[1];
     ts.block = t[2];
-    ts.staged = t[3] != 0;
+    ts.staged = t[3] == 1;
+    ts.tma = t[3] == 2;
     if (ts.staged && !can_stage) continue;
+    if (ts.tma && !can_tma) continue;
     group_smem(g, ts.th, ts.tw, &ts.smem);
     if (group_stacked(g)) ts.smem = 0;
-    if (ts.staged) staged_smem(staging_plan(g), ts.th, ts.tw, &ts.smem);
+    if (ts.staged || ts.tma) staged_smem(staging_plan(g), ts.th, ts.tw, &ts.smem, ts.tma);
     if (ts.smem <= kGroupSmemLimit) out.push_back(ts);
   }
   return out;
 }
 
 }  // namespace
+
+// The pipelined tensor-copy form: persistent blocks walk tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; thread 0 issues the next tile's input boxes
+// (one 2-D tensor copy per staged input, into the other of two stages) before
+// waiting for the current tile's, so copies overlap compute. Waits are
+// bounded; a wait that runs out sets the error word, drains the copies in
+// flight (bounded) and stops the block.
+static void emit_tma_prologue(std::ostringstream& o, const Group& g, const GroupLayout& GL, const TileShape& ts,
+                              const std::vector<StagedBase>& sp, const std::vector<int64_t>& sgoff, int64_t total) {
+  auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
+  const int nb = (int)sp.size();
+  int64_t tx = 0;
+  for (auto& b : sp) tx += (int64_t)(ts.th + b.rhi - b.rlo) * staged_cols(b, ts.tw, true) * itemsize(b.dtype);
+  o << "struct __align__(64) PT" << ts.suffix() << " { vbe_tmap tm[" << nb << "]; i64 w[" << GL.nwords << "]; };\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@" << ts.suffix()
+    << "(const __grid_constant__ PT" << ts.suffix() << " pt) {\n"
+    << "  const P& p = *reinterpret_cast<const P*>(pt.w);\n"
+    << "  VBE_DYN_SMEM;\n"
+    << "  vbe_grid_wait();\n"
+    << "  unsigned long long* const bars = (unsigned long long*)(vbe_smem + " << (total - 16) << ");\n"
+    << "  __shared__ int s_ok;\n"
+    << "  if (threadIdx.x == 0) { vbe_mbar_init(&bars[0], 1); vbe_mbar_init(&bars[1], 1); vbe_fence_mbar_init(); }\n"
+    << "  __syncthreads();\n"
+    << "  const i64 ntiles = p.w[3], tpr = p.w[2];\n"
+    << "  unsigned nis0 = 0, nis1 = 0, ndone0 = 0, ndone1 = 0;  // copies issued / completed per stage (thread 0)\n"
+    << "  auto issue = [&](i64 t, int st) {\n"
+    << "    const i64 ti = t / tpr, tj = t - ti * tpr;\n"
+    << "    vbe_mbar_expect_tx(&bars[st], " << tx << "u);\n";
+  for (int b = 0; b < nb; ++b) {
+    const int64_t stage = staged_stage_bytes(sp[b], ts.th, ts.tw);
+    o << "    vbe_tma_2d(vbe_smem + " << sgoff[b] << " + st * " << stage << ", &pt.tm[" << b << "], (int)(tj * " << ts.tw
+      << " + " << W(GL.stg[b] + 2) << "), (int)(ti * " << ts.th << " + " << W(GL.stg[b] + 3) << "), &bars[st]);\n";
+  }
+  o << "    if (st) ++nis1; else ++nis0;\n"
+    << "  };\n"
+    << "  if (threadIdx.x == 0 && (i64)blockIdx.x < ntiles) issue(blockIdx.x, 0);\n"
+    << "  bool failed = false;\n"
+    << "  int kt = 0;\n"
+    << "  for (i64 t = blockIdx.x; t < ntiles; t += gridDim.x, ++kt) {\n"
+    << "    const int st = kt & 1;\n"
+    << "    const i64 ti = t / tpr, tj = t - ti * tpr;\n"
+    << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n"
+    << "    if (threadIdx.x == 0) {\n"
+    << "      if (t + gridDim.x < ntiles) { vbe_fence_proxy_async(); issue(t + gridDim.x, st ^ 1); }\n"
+    << "      s_ok = vbe_mbar_wait(&bars[st], (unsigned)((kt >> 1) & 1));\n"
+    << "      if (s_ok) { if (st) ++ndone1; else ++ndone0; }\n"
+    << "    }\n"
+    << "    __syncthreads();\n"
+    << "    if (!s_ok) { failed = true; break; }\n";
+  for (int b = 0; b < nb; ++b) {
+    const std::string T = ctype(sp[b].dtype);
+    const int64_t stage = staged_stage_bytes(sp[b], ts.th, ts.tw);
+    o << "    const " << T << "* const sg" << b << " = (const " << T << "*)(vbe_smem + " << sgoff[b] << " + st * " << stage
+      << ") + " << W(GL.stg[b] + 4) << ";\n";
+  }
+  (void)g;
+}
+
+static void emit_tma_epilogue(std::ostringstream& o, const GroupLayout& GL) {
+  o << "    __syncthreads();  // the stage and the temporaries are free for the next tile\n"
+    << "  }\n"
+    << "  if (failed && threadIdx.x == 0) {\n"
+    << "    vbe_ptr<volatile unsigned>(p.w[" << GL.err << "])[0] = 1u;\n"
+    << "    for (unsigned q = ndone0; q < nis0; ++q) vbe_mbar_wait(&bars[0], q & 1u);\n"
+    << "    for (unsigned q = ndone1; q < nis1; ++q) vbe_mbar_wait(&bars[1], q & 1u);\n"
+    << "  }\n";
+}
 
 // elements of renamed bases the anchor does not write: copied to the new buffer
 static void emit_copy_through(std::ostringstream& o, const Group& g, const GroupLayout& GL) {
@@ -1545,7 +1668,7 @@ static void emit_stacked(std::ostringstream& o, const Group& g, const GroupLayou
       if (six[k][s].first >= 0) {
         const StagedBase& B = sp[six[k][s].first];
         const StagedSlot& q = B.slots[six[k][s].second];
-        const int SC = TW + B.chi - B.clo;
+        const int SC = staged_cols(B, TW, ts.tma);
         lv[k].push_back("sg" + std::to_string(six[k][s].first) + "[li * " + std::to_string(SC) + " + lj + " +
                         std::to_string((q.dr - B.rlo) * SC + (q.dc - B.clo)) + "]");
       } else if (ld.prod >= 0) {
@@ -1634,6 +1757,24 @@ static void emit_stacked(std::ostringstream& o, const Group& g, const GroupLayou
   }
 }
 
+std::vector<TmaBox> group_tma_boxes(const Group& g, const TileShape& ts) {
+  std::vector<TmaBox> out;
+  for (auto& b : staging_plan(g)) {
+    const Slot& ref = g.runs[b.ref_k].loads[b.ref_s];
+    TmaBox x;
+    x.base = b.base;
+    x.isz = itemsize(b.dtype);
+    x.pitch = ref.st[0];
+    x.rows = g.base_nelem.at(b.base) / ref.st[0];
+    x.box_cols = staged_cols(b, ts.tw, true);
+    x.box_rows = ts.th + b.rhi - b.rlo;
+    x.ref_k = b.ref_k;
+    x.ref_s = b.ref_s;
+    out.push_back(x);
+  }
+  return out;
+}
+
 std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes_out) {
   const int m = (int)g.runs.size();
   const int anchor = m - 1;
@@ -1647,6 +1788,12 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
   }
   o << "// generated by libvbe: tile-fused group of " << m << " runs, " << nsteps << " operations\n";
   o << kPrelude;
+  const std::vector<TileShape> shapes = group_shapes(g);
+  for (auto& ts : shapes)
+    if (ts.tma) {
+      o << kTmaPrelude;
+      break;
+    }
   if (soft)
     o << sf64_include()
       << "__device__ __forceinline__ double vbe_u01s(u64 seed, u64 key, u64 step, u64 m) {\n"
@@ -1687,24 +1834,27 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     gen.o.str("");
   }
   auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
-  std::vector<TileShape> shapes = group_shapes(g);
   for (const TileShape& ts : shapes) {
     int64_t total = 0;
     auto soff = group_smem(g, ts.th, ts.tw, &total);
     if (group_stacked(g)) total = 0;
-    const std::vector<StagedBase> sp = ts.staged ? staging_plan(g) : std::vector<StagedBase>();
+    const std::vector<StagedBase> sp = (ts.staged || ts.tma) ? staging_plan(g) : std::vector<StagedBase>();
     const auto six = staged_index(g, sp);
-    const std::vector<int64_t> sgoff = staged_smem(sp, ts.th, ts.tw, &total);
-    o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@" << ts.suffix()
-      << "(const P p) {\n"
-      << "  VBE_DYN_SMEM;\n"
-      << "  vbe_grid_wait();\n"
-      << "  if ((i64)blockIdx.x < p.w[3]) {\n"
-      << "    const i64 ti = (i64)blockIdx.x / p.w[2], tj = (i64)blockIdx.x - ti * p.w[2];\n"
-      << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n";
+    const std::vector<int64_t> sgoff = staged_smem(sp, ts.th, ts.tw, &total, ts.tma);
+    if (ts.tma) {
+      emit_tma_prologue(o, g, GL, ts, sp, sgoff, total);
+    } else {
+      o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@" << ts.suffix()
+        << "(const P p) {\n"
+        << "  VBE_DYN_SMEM;\n"
+        << "  vbe_grid_wait();\n"
+        << "  if ((i64)blockIdx.x < p.w[3]) {\n"
+        << "    const i64 ti = (i64)blockIdx.x / p.w[2], tj = (i64)blockIdx.x - ti * p.w[2];\n"
+        << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n";
+    }
     // staged inputs: tile plus halo, coalesced along rows, elements outside
     // the base skipped (their cells are never read)
-    for (size_t b = 0; b < sp.size(); ++b) {
+    for (size_t b = 0; b < sp.size() && !ts.tma; ++b) {
       const StagedBase& B = sp[b];
       const std::string T = ctype(B.dtype);
       const int SR = ts.th + B.rhi - B.rlo, SC = ts.tw + B.chi - B.clo, w = GL.lw[B.ref_k][B.ref_s];
@@ -1720,14 +1870,10 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
         << "      }\n"
         << "    }\n";
     }
-    if (!sp.empty()) o << "    __syncthreads();\n";
+    if (!sp.empty() && !ts.tma) o << "    __syncthreads();\n";
     if (group_stacked(g)) {
       emit_stacked(o, g, GL, gens, cdecl, ts, sp, six);
-      o << "  }\n";
-      emit_copy_through(o, g, GL);
-      o << "}\n";
-      continue;
-    }
+    } else {
     for (int k = 0; k < m; ++k) {
       const Run& r = g.runs[k];
       const int BH = box_rows(g, k, ts.th), BW = box_cols(g, k, ts.tw);
@@ -1761,7 +1907,7 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
         if (six[k][s].first >= 0) {
           const StagedBase& B = sp[six[k][s].first];
           const StagedSlot& q = B.slots[six[k][s].second];
-          const int SC = ts.tw + B.chi - B.clo;
+          const int SC = staged_cols(B, ts.tw, ts.tma);
           lv.push_back("sg" + std::to_string(six[k][s].first) + "[li * " + std::to_string(SC) + " + lj + " +
                        std::to_string((g.box[k][0] + q.dr - B.rlo) * SC + (g.box[k][2] + q.dc - B.clo)) + "]");
         } else if (ld.prod < 0) {
@@ -1857,7 +2003,9 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
       if (k != anchor) o << "      __syncthreads();\n";
       o << "    }\n";
     }
-    o << "  }\n";
+    }
+    if (ts.tma) emit_tma_epilogue(o, GL);
+    else o << "  }\n";
     emit_copy_through(o, g, GL);
     o << "}\n";
   }
@@ -1872,7 +2020,8 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
 void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std::vector<uintptr_t>>& load_ptrs,
                       const std::vector<std::vector<uintptr_t>>& store_ptrs,
                       const std::vector<std::pair<uintptr_t, uintptr_t>>& renamed_ptrs,
-                      const std::vector<uintptr_t>& red_ptrs, uintptr_t partials, uintptr_t counters, LaunchArgs* out) {
+                      const std::vector<uintptr_t>& red_ptrs, uintptr_t partials, uintptr_t counters, LaunchArgs* out,
+                      uintptr_t err_word) {
   const int m = (int)g.runs.size();
   const int anchor = m - 1;
   GroupLayout GL = group_layout(g);
@@ -1923,12 +2072,27 @@ void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std
     w[q + 5] = C;
     w[q + 6] = g.renamed_nelem[rr] - R * C;
   }
-  // staged inputs: the reference view's offset in its base and the base's size
+  // staged inputs: the reference view's offset in its base and the base's
+  // size; for tensor copies the box origin relative to the tile origin, its
+  // column rounded down to a 16-byte boundary, and that rounding
   const std::vector<StagedBase> sp = staging_plan(g);
   for (size_t b = 0; b < sp.size(); ++b) {
-    w[GL.stg[b]] = g.runs[sp[b].ref_k].loads[sp[b].ref_s].offset;
+    const Slot& ref = g.runs[sp[b].ref_k].loads[sp[b].ref_s];
+    w[GL.stg[b]] = ref.offset;
     w[GL.stg[b] + 1] = g.base_nelem.at(sp[b].base);
+    const int64_t P = ref.st[0], a = 16 / itemsize(sp[b].dtype);
+    int64_t r_ref = ref.offset / P, c_ref = ref.offset % P;
+    if (c_ref < 0) {
+      c_ref += P;
+      --r_ref;
+    }
+    const int64_t cx = sp[b].clo + c_ref;
+    const int64_t dx = ((cx % a) + a) % a;
+    w[GL.stg[b] + 2] = cx - dx;
+    w[GL.stg[b] + 3] = sp[b].rlo + r_ref;
+    w[GL.stg[b] + 4] = dx;
   }
+  w[GL.err] = (int64_t)err_word;
   // reductions: one partial per block, a region and a completion counter per reducing run
   int nq = 0;
   for (int k = 0; k < m; ++k) {

@@ -1,6 +1,7 @@
 // Runtime: NVRTC compilation and module cache, device memory, launch
 // shapes and their autotuning, batch execution, CUDA-graph replay of
 // repeated batches and packing of independent runs into one launch.
+#include <cuda.h>  // tensor-map types; the encoder comes from the driver entry point
 #include <nvrtc.h>
 #include <sys/stat.h>
 #include <unistd.h>
@@ -310,6 +311,7 @@ struct Launch {
   void* d_descs = nullptr;         // device copies (packed)
   void* d_prefix = nullptr;
   int64_t d_bytes = 0;
+  bool tma = false;                // a tile-fused group in the tensor-copy form
 };
 
 namespace {
@@ -408,6 +410,7 @@ void issue(Ctx* c, Exec* ex, Launch& L, bool capturing) {
     cuda_check(launch_pdl(L.fn, L.grid, L.block, args, L.smem, s), "launch");
   }
   if (!capturing) c->stats.kernel_launches++;
+  if (L.tma) c->stats.tma_group_launches++;
 }
 
 struct RunPtrs {
@@ -766,6 +769,68 @@ GroupPtrs group_ptrs(Ctx* c, const Group& g) {
   return p;
 }
 
+// cuTensorMapEncodeTiled, taken from the driver at run time (no link-time
+// dependency on the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return (EncodeTiledFn)p;
+  }();
+  return fn;
+}
+
+// The tensor maps of a tensor-copy group launch: 16 words each. A recording
+// context writes its own description instead (address, row stride, rows,
+// row bytes, box), which the host emulation of the copy reads.
+std::vector<int64_t> group_tensor_maps(Ctx* c, const Group& g, const TileShape& ts, const GroupPtrs& ptr) {
+  std::vector<int64_t> w;
+  for (const TmaBox& b : group_tma_boxes(g, ts)) {
+    const uintptr_t base = ptr.lp[b.ref_k][b.ref_s];
+    int64_t m[16] = {0};
+    if (c->record) {
+      m[0] = (int64_t)base;
+      m[1] = b.pitch;
+      m[2] = b.rows;
+      m[3] = b.pitch * b.isz;
+      m[4] = b.box_cols;
+      m[5] = b.box_rows;
+      m[6] = b.isz;
+    } else {
+      EncodeTiledFn enc = encode_tiled();
+      if (!enc) fail(VBE_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+      const CUtensorMapDataType dt = b.isz == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                     : (b.isz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64);
+      const cuuint64_t dims[2] = {(cuuint64_t)b.pitch, (cuuint64_t)b.rows};
+      const cuuint64_t strides[1] = {(cuuint64_t)(b.pitch * b.isz)};
+      const cuuint32_t box[2] = {(cuuint32_t)b.box_cols, (cuuint32_t)b.box_rows};
+      const cuuint32_t estr[2] = {1, 1};
+      CUresult r = enc((CUtensorMap*)m, dt, 2, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) fail(VBE_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    }
+    w.insert(w.end(), m, m + 16);
+  }
+  return w;
+}
+
+// tensor copies read whole 16-byte units from 16-byte aligned bases
+bool tma_pointers_ok(const Group& g, const TileShape& ts, const GroupPtrs& ptr) {
+  for (const TmaBox& b : group_tma_boxes(g, ts))
+    if (ptr.lp[b.ref_k][b.ref_s] % 16 != 0) return false;
+  return true;
+}
+
 Launch build_group(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const GroupPtrs& ptr) {
   Launch L;
   L.entry = G.prefix + ts.suffix();
@@ -784,8 +849,19 @@ Launch build_group(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, cons
   const int64_t ntiles = ((ra.shape[0] + ts.th - 1) / ts.th) * ((ra.shape[1] + ts.tw - 1) / ts.tw);
   if (nred * ntiles > ex->scratch.n_partials) fail(VBE_ERR_INVALID, "tile-fused group needs more reduction partials");
   fill_group_words(*G.g, ts, ptr.lp, ptr.sp, ptr.ren, ptr.red, (uintptr_t)ex->scratch.partials,
-                   (uintptr_t)ex->scratch.counters, &a);
+                   (uintptr_t)ex->scratch.counters, &a, (uintptr_t)c->err_word_dev);
   L.grid = (unsigned)std::max<int64_t>(1, a.w[3]);
+  if (ts.tma) {
+    // persistent: as many blocks as fit, tensor maps ahead of the words
+    const int64_t cap = (int64_t)occupancy(L.fn, (int)L.block, L.smem) * c->sm_count;
+    L.grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.w[3], cap));
+    std::vector<int64_t> w = group_tensor_maps(c, *G.g, ts, ptr);
+    w.insert(w.end(), a.w.begin(), a.w.end());
+    while (w.size() % 8) w.push_back(0);  // the parameter block is 64-byte aligned
+    L.words = std::move(w);
+    L.tma = true;
+    return L;
+  }
   L.words = std::move(a.w);
   return L;
 }
@@ -806,21 +882,25 @@ std::string group_tune_key(const GroupPrepared& G) {
 // redirected to scratch buffers
 TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real, bool may_tune) {
   if (G.shapes.empty()) fail(VBE_ERR_INVALID, "tile-fused group without a tile shape");
-  if (c->record) {
-    const char* e = getenv("VBE_RECORD_TILE");  // "THxTW", or "sTHxTW" for the staged form
-    if (e)
-      for (auto& ts : G.shapes)
-        if ((ts.staged ? "s" : "") + std::to_string(ts.th) + "x" + std::to_string(ts.tw) == e) return ts;
-    return G.shapes[0];
-  }
+  // a fixed shape: "THxTW", "sTHxTW" for the staged form, "tTHxTW" for the
+  // tensor-copy form (VBE_RECORD_TILE when recording, else VBE_TILE)
+  const char* e = c->record ? getenv("VBE_RECORD_TILE") : (c->force_tile.empty() ? nullptr : c->force_tile.c_str());
+  if (e)
+    for (auto& ts : G.shapes)
+      if ((ts.tma ? "t" : (ts.staged ? "s" : "")) + std::to_string(ts.th) + "x" + std::to_string(ts.tw) == e &&
+          (c->record || !ts.tma || tma_pointers_ok(*G.g, ts, real)))
+        return ts;
+  if (c->record) return G.shapes[0];
   std::string tk = group_tune_key(G);
   auto it = c->tune.find(tk);
   if (it != c->tune.end())
     for (auto& ts : G.shapes)
-      if (ts.th == it->second.block && ts.tw == it->second.U && (int)ts.staged == it->second.grid_mult) return ts;
+      if (ts.th == it->second.block && ts.tw == it->second.U &&
+          (ts.tma ? 2 : (int)ts.staged) == it->second.grid_mult && (!ts.tma || tma_pointers_ok(*G.g, ts, real)))
+        return ts;
   TileShape def = G.shapes[0];
   for (auto& ts : G.shapes)
-    if (!ts.staged && ts.th * ts.tw <= 1024 && ts.th * ts.tw >= def.th * def.tw) def = ts;
+    if (!ts.staged && !ts.tma && ts.th * ts.tw <= 1024 && ts.th * ts.tw >= def.th * def.tw) def = ts;
   const Group& g = *G.g;
   const int anchor = (int)g.runs.size() - 1;
   if (!(may_tune && (c->cfg.flags & VBE_AUTOTUNE) && g.rows(anchor) * g.cols(anchor) >= (1 << 16))) return def;
@@ -850,6 +930,7 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
   TileShape best = def;
   float best_ms = 1e30f;
   for (const TileShape& ts : G.shapes) {
+    if (ts.tma && !tma_pointers_ok(g, ts, ptr)) continue;
     Launch L = build_group(c, ex, G, ts, ptr);
     issue(c, ex, L, false);  // warm
     c->stats.kernel_launches--;
@@ -872,7 +953,7 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
   TuneChoice tc;  // the group's choice: tile rows, tile columns, staged form
   tc.block = best.th;
   tc.U = best.tw;
-  tc.grid_mult = best.staged ? 1 : 0;
+  tc.grid_mult = best.tma ? 2 : (best.staged ? 1 : 0);
   c->tune[tk] = tc;
   return best;
 }

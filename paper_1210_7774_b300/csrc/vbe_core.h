@@ -217,20 +217,36 @@ void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load
                 uintptr_t err = 0);
 int words_count(const Run& r, const Canon& c);
 
+// tensor-copy boxes of a group's staged inputs for one tile shape: per staged
+// input the base, its element size, row stride (elements), rows of the base
+// and the box (columns, rows)
+struct TmaBox {
+  int64_t base = 0;
+  int isz = 0;
+  int64_t pitch = 0, rows = 0;
+  int box_cols = 0, box_rows = 0;
+  int ref_k = 0, ref_s = 0;  // the view whose pointer word addresses the base
+};
+
+
 // tile-fused groups: source with one kernel per tile shape, and its words
 struct TileShape {
   int th = 0, tw = 0, block = 0;
   bool staged = false;  // stencil inputs copied to shared memory first (else read through L1)
+  bool tma = false;     // persistent form: inputs prefetched by tensor copies, two stages
   int64_t smem = 0;     // dynamic shared memory bytes
   std::string suffix() const {
-    return std::string(staged ? "_ss" : "_sg") + std::to_string(th) + "x" + std::to_string(tw);
+    return std::string(tma ? "_tm" : (staged ? "_ss" : "_sg")) + std::to_string(th) + "x" + std::to_string(tw);
   }
 };
 std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes);
+std::vector<TmaBox> group_tma_boxes(const Group& g, const TileShape& ts);
+// tensor maps go first in a tensor-copy kernel's parameters: 16 words each
 void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std::vector<uintptr_t>>& load_ptrs,
                       const std::vector<std::vector<uintptr_t>>& store_ptrs,
                       const std::vector<std::pair<uintptr_t, uintptr_t>>& renamed_ptrs,
-                      const std::vector<uintptr_t>& red_ptrs, uintptr_t partials, uintptr_t counters, LaunchArgs* out);
+                      const std::vector<uintptr_t>& red_ptrs, uintptr_t partials, uintptr_t counters, LaunchArgs* out,
+                      uintptr_t err_word = 0);
 
 // ----------------------------------------------------------------- context
 struct BaseRec {
@@ -330,6 +346,7 @@ struct Ctx {
   std::vector<std::string> rec_launches;
   std::unordered_map<std::string, std::string> rec_sources;
   int force_bulk = 0;  // VBE_STAGING: stage every eligible run in chunks of this many elements
+  std::string force_tile;  // VBE_TILE: tile shape of every tile-fused group ("32x32", "s32x32", "t32x32")
   // set by staged kernels whose bounded waits ran out (mapped host memory)
   unsigned* err_word = nullptr;
   unsigned* err_word_dev = nullptr;

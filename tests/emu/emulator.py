@@ -41,6 +41,8 @@ extern "C" void emu_set_ranges(const unsigned long long* lohi, int n) {
 }
 extern "C" const char* emu_msg() { return g_bad_msg; }
 static int emu_check_words(int nw) { return nw == (int)(sizeof(P) / 8) ? 0 : -1; }
+template <class F> struct emu_arg;
+template <class T> struct emu_arg<void(T)> { typedef std::remove_cv_t<T> type; };
 """
 
 _WRAP_TILE = """
@@ -79,9 +81,10 @@ extern "C" long long emu_bulk(const long long* w, int nw, unsigned grid, unsigne
 
 _WRAP_ENTRY = """
 extern "C" long long emu_@E@(const long long* w, int nw, unsigned grid, unsigned block) {
-  if (emu_check_words(nw)) return -1;
-  P p;
-  memcpy(&p, w, sizeof(P));
+  typedef emu_arg<decltype(@E@)>::type A;  // P, or the tensor-map block of a tensor-copy kernel
+  if (nw != (int)(sizeof(A) / 8)) return -1;
+  A p;
+  memcpy(&p, w, sizeof(A));
   g_bad = 0;
   emu_grid(grid, block, [&]() { @E@(p); });
   return g_bad.load();
@@ -153,7 +156,7 @@ class Emulator:
             if prefix + "_bulk" in names:
                 parts.append(_WRAP_BULK.replace("@P@", prefix))
             for name in names:  # tile-fused groups: one kernel per tile shape
-                if re.search(r"_s[gs]\d+x\d+$", name):
+                if re.search(r"_(s[gs]|tm)\d+x\d+$", name):
                     parts.append(_WRAP_ENTRY.replace("@E@", name))
             cpp = os.path.join(self.dir, f"emu_{h}.cpp")
             with open(cpp, "w") as f:
@@ -204,7 +207,7 @@ class Emulator:
                                    L["chunk"], L["work"], L["grid"], L["block"])
             else:
                 w = (ctypes.c_longlong * len(L["words"]))(*L["words"])
-                if re.search(r"_s[gs]\d+x\d+$", entry):
+                if re.search(r"_(s[gs]|tm)\d+x\d+$", entry):
                     fn = getattr(lib, "emu_" + entry)
                     fn.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
                     fn.restype = ctypes.c_longlong

@@ -32,6 +32,8 @@ extern dim3 blockDim, gridDim;
 
 #define __global__
 #define __device__
+#define __align__(x) alignas(x)
+#define __grid_constant__
 #define __forceinline__ inline
 #define SF_CALL __attribute__((noinline))
 #define __launch_bounds__(...)
@@ -104,6 +106,28 @@ inline void vbe_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned lo
 }
 
 inline void vbe_grid_wait() {}  // launches run one after another on the host
+
+// a tensor copy, from the description a recording context writes into the
+// map (address, row stride, rows, row bytes, box columns, box rows, element
+// size); elements outside the tensor read as zeros
+inline void vbe_tma_2d(void* dst, const void* tmap, int x, int y, unsigned long long*) {
+  const long long* m = (const long long*)tmap;
+  const char* base = (const char*)m[0];
+  const long long pitch = m[1], rows = m[2], bc = m[4], br = m[5], isz = m[6];
+  char* d = (char*)dst;
+  for (long long r = 0; r < br; ++r)
+    for (long long c = 0; c < bc; ++c) {
+      const long long gx = x + c, gy = y + r;
+      char* out = d + (r * bc + c) * isz;
+      if (gx < 0 || gx >= pitch || gy < 0 || gy >= rows) {
+        memset(out, 0, (size_t)isz);
+        continue;
+      }
+      const char* src = base + (gy * pitch + gx) * isz;
+      if (!emu_ok(src, (size_t)isz)) return;
+      memcpy(out, src, (size_t)isz);
+    }
+}
 
 inline void __syncthreads() { g_block_bar->arrive_and_wait(); }
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }

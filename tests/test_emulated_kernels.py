@@ -90,23 +90,29 @@ def test_emulated_shapes_on_stencil_and_packing(shape):
             case.check(got, want)
 
 
-@pytest.mark.parametrize("tile", ["8x16", "16x32", "32x32", "s32x32", "s16x64", "split"])
+@pytest.mark.parametrize("tile", ["8x16", "16x32", "32x32", "s32x32", "s16x64", "t32x32", "t16x64", "split"])
 def test_emulated_tile_groups(tile):
     """Tile-fused groups at several tile shapes (ragged edge tiles, halos
     across tile borders): shallow water (state renamed every step, ghost
     ring copied across) and the synthetic chains, with the inputs read
-    through L1 or staged through shared memory ("s" shapes); and the same
+    through L1, staged through shared memory ("s" shapes) or brought in by
+    double-buffered tensor copies ("t" shapes); and the same
     groups run as their separate kernels (the choice the tuner makes when
     that is faster)."""
     cases = tile_group_cases()
+    if tile.startswith("t"):  # rows of 16-byte multiples, as tensor copies need
+        cases += tile_group_cases(seed=12, N=37, M=52)
     for dt in ("float64", "float32"):
         p = shallow_water(40, 2, dt)
         cases.append(Case(p.name, p, _exact_check(p)))
     var = "VBE_RECORD_SPLIT" if tile == "split" else "VBE_RECORD_TILE"
     os.environ[var] = tile
+    # one SM for the tensor-copy form: its two persistent blocks each walk
+    # several tiles through both stages
+    shape = (64, 1, 1) if tile.startswith("t") else (64, 1, 2)
     try:
         for case in cases:
-            got = emulate(case.program, MODES["fused"], (64, 1, 2))
+            got = emulate(case.program, MODES["fused"], shape)
             case.check(got, oracle_outputs(case.program))
     finally:
         os.environ.pop(var)

@@ -15,8 +15,8 @@ from paper_1210_7774_b300 import vbe as V  # noqa: E402
 from paper_1210_7774_b300.runner import Executor  # noqa: E402
 
 import oracle  # noqa: E402
-from parity_cases import (F64_REDUCE_RTOL, all_small_cases, assert_close_sum, assert_exact,  # noqa: E402
-                          oracle_outputs, workload_cases)
+from parity_cases import (F64_REDUCE_RTOL, Case, _exact_check, all_small_cases, assert_close_sum,  # noqa: E402
+                          assert_exact, oracle_outputs, tile_group_cases, workload_cases)
 from workloads import (blackscholes, bs_inputs, gray_scott, jacobi, knn, knn_inputs, mc_sizes,  # noqa: E402
                        montecarlo_pi, shallow_water, sw_inputs)
 
@@ -130,6 +130,30 @@ def test_jacobi_paper_size_tile_fused():
     g0 = p.bases[p.meta["grid"]].init
     assert_close_sum(got[p.meta["deltas"]], want[p.meta["deltas"]], np.full(1, 2 * np.abs(g0).sum()),
                      F64_REDUCE_RTOL, "deltas")
+
+
+@pytest.mark.parametrize("tile", ["t32x32", "t16x64", "s32x32", "32x32"])
+def test_tile_group_forms_exact(tile):
+    """Tile-fused groups forced into one tile shape and form (VBE_TILE, read
+    when the context is created): inputs read through L1, staged through
+    shared memory ("s"), or prefetched by double-buffered tensor copies into
+    persistent blocks that walk several tiles each ("t"). Bit-exact with the
+    oracle on the synthetic chains (rows of 16-byte multiples, ragged against
+    every tile), shallow water (state renamed every step) and Gray-Scott at
+    2050 x 1032 (about 2,000 tiles), float64 and float32."""
+    cases = tile_group_cases(seed=12, N=37, M=52)
+    for dt in ("float64", "float32"):
+        for p in (shallow_water(256, 2, dt), gray_scott(2050, 1032, 2, dt)):
+            cases.append(Case(p.name, p, _exact_check(p)))
+    os.environ["VBE_TILE"] = tile
+    try:
+        for case in cases:
+            got = run_gpu(case.program, V.VBE_FUSE | V.VBE_PACK)
+            case.check(got, oracle_outputs(case.program))
+            if tile.startswith("t"):
+                assert got["_stats"]["tma_group_launches"] > 0, case.name
+    finally:
+        os.environ.pop("VBE_TILE")
 
 
 @pytest.mark.parametrize("staging", [0, 2048])
