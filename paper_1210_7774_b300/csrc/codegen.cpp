@@ -475,6 +475,20 @@ __device__ __forceinline__ void vbe_tma_2d(void* dst, const void* tmap, int x, i
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
       ::"r"(vbe_saddr(dst)), "l"(tmap), "r"(x), "r"(y), "r"(vbe_saddr(bar)) : "memory");
 }
+// one arrival on an mbarrier (release: this thread's earlier accesses are
+// ordered before the phase completes)
+__device__ __forceinline__ void vbe_mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(vbe_saddr(bar)) : "memory");
+}
+// barrier `id` over the first n threads of the block (n a multiple of 32)
+__device__ __forceinline__ void vbe_bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+// the same barrier, returning whether v holds in any of the n threads
+__device__ __forceinline__ bool vbe_bar_or(int id, int n, bool v) {
+  unsigned r;
+  asm volatile("{ .reg .pred p, q; setp.ne.u32 p, %1, 0; bar.red.or.pred q, %2, %3, p; selp.u32 %0, 1, 0, q; }"
+               : "=r"(r) : "r"((unsigned)v), "r"(id), "r"(n) : "memory");
+  return r != 0;
+}
 #endif
 )CUDA";
 
@@ -1461,9 +1475,11 @@ int staged_cols(const StagedBase& b, int tw, bool tma) {
 }
 
 // shared-memory offsets of the staged inputs, placed after *total (tensor
-// copies: two stages per input, 128-byte aligned; stage 1 at off + stage bytes)
+// copies: `stages` stages per input, 128-byte aligned, stage s at off + s x
+// stage bytes; then a "full" and an "empty" mbarrier per stage)
 std::vector<int64_t> staged_smem(const std::vector<StagedBase>& sp, int th, int tw, int64_t* total,
-                                 bool tma = false) {
+                                 int stages = 0) {
+  const bool tma = stages > 0;
   std::vector<int64_t> off;
   int64_t acc = *total;
   const int64_t al = tma ? 128 : 16;
@@ -1471,9 +1487,9 @@ std::vector<int64_t> staged_smem(const std::vector<StagedBase>& sp, int th, int 
   for (auto& b : sp) {
     off.push_back(acc);
     const int64_t pts = (int64_t)(th + b.rhi - b.rlo) * staged_cols(b, tw, tma);
-    acc += (pts * itemsize(b.dtype) + al - 1) / al * al * (tma ? 2 : 1);
+    acc += (pts * itemsize(b.dtype) + al - 1) / al * al * (tma ? stages : 1);
   }
-  if (tma) acc += 16;  // two mbarriers
+  if (tma) acc += 16 * stages;
   *total = acc;
   return off;
 }
@@ -1484,6 +1500,11 @@ int64_t staged_stage_bytes(const StagedBase& b, int th, int tw) {
 }
 
 constexpr int64_t kGroupSmemLimit = 200 * 1024;
+
+bool group_stacked(const Group& g);
+// stages of the tensor-copy form: three when the tile's values stay in
+// registers (shared memory holds only the stages), else two
+int tma_stages(const Group& g) { return group_stacked(g) ? 3 : 2; }
 
 // A group whose runs share one shape and read each other's values only at
 // the same point (no shifts, no halos) is evaluated point by point: every
@@ -1534,7 +1555,7 @@ std::vector<TileShape> group_shapes(const Group& g) {
     if (ts.tma && !can_tma) continue;
     group_smem(g, ts.th, ts.tw, &ts.smem);
     if (group_stacked(g)) ts.smem = 0;
-    if (ts.staged || ts.tma) staged_smem(staging_plan(g), ts.th, ts.tw, &ts.smem, ts.tma);
+    if (ts.staged || ts.tma) staged_smem(staging_plan(g), ts.th, ts.tw, &ts.smem, ts.tma ? tma_stages(g) : 0);
     if (ts.smem <= kGroupSmemLimit) out.push_back(ts);
   }
   return out;
@@ -1542,70 +1563,95 @@ std::vector<TileShape> group_shapes(const Group& g) {
 
 }  // namespace
 
-// The pipelined tensor-copy form: persistent blocks walk tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; thread 0 issues the next tile's input boxes
-// (one 2-D tensor copy per staged input, into the other of two stages) before
-// waiting for the current tile's, so copies overlap compute. Waits are
-// bounded; a wait that runs out sets the error word, drains the copies in
-// flight (bounded) and stops the block.
+// The pipelined tensor-copy form, warp-specialised: the block is the
+// compute threads plus one producer warp. Persistent blocks walk tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...; tile k of a block uses stage
+// k mod NS. Lane 0 of the producer warp waits until the compute warps have
+// released a stage ("empty" mbarrier, one arrival per compute warp), then
+// issues the tile's input boxes into it (one 2-D tensor copy per staged
+// input, completing on the stage's "full" mbarrier). Compute threads wait on
+// "full", compute, and their warp releases the stage; they meet at block
+// barriers only where a phase hands values through shared memory. Every
+// wait is bounded; a wait that runs out sets the error word and the thread
+// stops working (compute threads keep releasing stages so that no wait
+// depends on them), and the producer waits, bounded, for its copies in
+// flight before it leaves.
 static void emit_tma_prologue(std::ostringstream& o, const Group& g, const GroupLayout& GL, const TileShape& ts,
                               const std::vector<StagedBase>& sp, const std::vector<int64_t>& sgoff, int64_t total) {
   auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
   const int nb = (int)sp.size();
+  const int NS = tma_stages(g);
+  const int NW = ts.block / 32;  // compute warps
   int64_t tx = 0;
   for (auto& b : sp) tx += (int64_t)(ts.th + b.rhi - b.rlo) * staged_cols(b, ts.tw, true) * itemsize(b.dtype);
+  const std::string err = "vbe_ptr<volatile unsigned>(" + W(GL.err) + ")[0] = 1u";
   o << "struct __align__(64) PT" << ts.suffix() << " { vbe_tmap tm[" << nb << "]; i64 w[" << GL.nwords << "]; };\n"
-    << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@" << ts.suffix()
+    << "extern \"C\" __global__ void __launch_bounds__(" << ts.block + 32 << ") vbe_@TAG@" << ts.suffix()
     << "(const __grid_constant__ PT" << ts.suffix() << " pt) {\n"
     << "  const P& p = *reinterpret_cast<const P*>(pt.w);\n"
     << "  VBE_DYN_SMEM;\n"
     << "  vbe_grid_wait();\n"
-    << "  unsigned long long* const bars = (unsigned long long*)(vbe_smem + " << (total - 16) << ");\n"
-    << "  __shared__ int s_ok;\n"
-    << "  if (threadIdx.x == 0) { vbe_mbar_init(&bars[0], 1); vbe_mbar_init(&bars[1], 1); vbe_fence_mbar_init(); }\n"
+    << "  unsigned long long* const full = (unsigned long long*)(vbe_smem + " << (total - 16 * NS) << ");\n"
+    << "  unsigned long long* const empty = full + " << NS << ";\n"
+    << "  if (threadIdx.x == 0) {\n"
+    << "    for (int s = 0; s < " << NS << "; ++s) { vbe_mbar_init(&full[s], 1); vbe_mbar_init(&empty[s], " << NW
+    << "); }\n"
+    << "    vbe_fence_mbar_init();\n"
+    << "  }\n"
     << "  __syncthreads();\n"
     << "  const i64 ntiles = p.w[3], tpr = p.w[2];\n"
-    << "  unsigned nis0 = 0, nis1 = 0, ndone0 = 0, ndone1 = 0;  // copies issued / completed per stage (thread 0)\n"
-    << "  auto issue = [&](i64 t, int st) {\n"
-    << "    const i64 ti = t / tpr, tj = t - ti * tpr;\n"
-    << "    vbe_mbar_expect_tx(&bars[st], " << tx << "u);\n";
+    << "  if (threadIdx.x >= " << ts.block << ") {\n"
+    << "    if (threadIdx.x == " << ts.block << ") {  // the producer\n"
+    << "      unsigned nis[" << NS << "] = {};  // copies issued per stage\n"
+    << "      int kt = 0;\n"
+    << "      for (i64 t = blockIdx.x; t < ntiles; t += gridDim.x, ++kt) {\n"
+    << "        const int st = kt % " << NS << ";\n"
+    << "        if (kt >= " << NS << " && !vbe_mbar_wait(&empty[st], (unsigned)((kt / " << NS << " - 1) & 1))) { "
+    << err << "; break; }\n"
+    << "        const i64 ti = t / tpr, tj = t - ti * tpr;\n"
+    << "        vbe_fence_proxy_async();\n"
+    << "        vbe_mbar_expect_tx(&full[st], " << tx << "u);\n";
   for (int b = 0; b < nb; ++b) {
     const int64_t stage = staged_stage_bytes(sp[b], ts.th, ts.tw);
-    o << "    vbe_tma_2d(vbe_smem + " << sgoff[b] << " + st * " << stage << ", &pt.tm[" << b << "], (int)(tj * " << ts.tw
-      << " + " << W(GL.stg[b] + 2) << "), (int)(ti * " << ts.th << " + " << W(GL.stg[b] + 3) << "), &bars[st]);\n";
+    o << "        vbe_tma_2d(vbe_smem + " << sgoff[b] << " + st * " << stage << ", &pt.tm[" << b << "], (int)(tj * "
+      << ts.tw << " + " << W(GL.stg[b] + 2) << "), (int)(ti * " << ts.th << " + " << W(GL.stg[b] + 3)
+      << "), &full[st]);\n";
   }
-  o << "    if (st) ++nis1; else ++nis0;\n"
-    << "  };\n"
-    << "  if (threadIdx.x == 0 && (i64)blockIdx.x < ntiles) issue(blockIdx.x, 0);\n"
-    << "  bool failed = false;\n"
-    << "  int kt = 0;\n"
-    << "  for (i64 t = blockIdx.x; t < ntiles; t += gridDim.x, ++kt) {\n"
-    << "    const int st = kt & 1;\n"
-    << "    const i64 ti = t / tpr, tj = t - ti * tpr;\n"
-    << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n"
-    << "    if (threadIdx.x == 0) {\n"
-    << "      if (t + gridDim.x < ntiles) { vbe_fence_proxy_async(); issue(t + gridDim.x, st ^ 1); }\n"
-    << "      s_ok = vbe_mbar_wait(&bars[st], (unsigned)((kt >> 1) & 1));\n"
-    << "      if (s_ok) { if (st) ++ndone1; else ++ndone0; }\n"
+  o << "        ++nis[st];\n"
+    << "      }\n"
+    << "      // the last copies issued into each stage have landed before the block leaves\n"
+    << "      for (int s = 0; s < " << NS << "; ++s)\n"
+    << "        if (nis[s] && !vbe_mbar_wait(&full[s], (nis[s] - 1u) & 1u)) " << err << ";\n"
     << "    }\n"
-    << "    __syncthreads();\n"
-    << "    if (!s_ok) { failed = true; break; }\n";
+    << "  } else {\n"
+    << "    bool failed = false;\n"
+    << "    int kt = 0;\n"
+    << "    for (i64 t = blockIdx.x; t < ntiles; t += gridDim.x, ++kt) {\n"
+    << "      const int st = kt % " << NS << ";\n"
+    << "      if (!failed && !vbe_mbar_wait(&full[st], (unsigned)((kt / " << NS << ") & 1))) { failed = true; " << err
+    << "; }\n";
+  // phases meeting at block barriers must agree on whether to run
+  if (!group_stacked(g)) o << "      failed = vbe_bar_or(1, " << ts.block << ", failed);\n";
+  o << "      if (!failed) {\n"
+    << "    const i64 ti = t / tpr, tj = t - ti * tpr;\n"
+    << "    const i64 i0 = ti * " << ts.th << ", j0 = tj * " << ts.tw << ";\n";
   for (int b = 0; b < nb; ++b) {
     const std::string T = ctype(sp[b].dtype);
     const int64_t stage = staged_stage_bytes(sp[b], ts.th, ts.tw);
     o << "    const " << T << "* const sg" << b << " = (const " << T << "*)(vbe_smem + " << sgoff[b] << " + st * " << stage
       << ") + " << W(GL.stg[b] + 4) << ";\n";
   }
-  (void)g;
 }
 
-static void emit_tma_epilogue(std::ostringstream& o, const GroupLayout& GL) {
-  o << "    __syncthreads();  // the stage and the temporaries are free for the next tile\n"
-    << "  }\n"
-    << "  if (failed && threadIdx.x == 0) {\n"
-    << "    vbe_ptr<volatile unsigned>(p.w[" << GL.err << "])[0] = 1u;\n"
-    << "    for (unsigned q = ndone0; q < nis0; ++q) vbe_mbar_wait(&bars[0], q & 1u);\n"
-    << "    for (unsigned q = ndone1; q < nis1; ++q) vbe_mbar_wait(&bars[1], q & 1u);\n"
+// closes the tile: the warp releases the stage; phases that hand values
+// through shared memory also wait for every compute warp before the next
+// tile overwrites them
+static void emit_tma_epilogue(std::ostringstream& o, const Group& g, const TileShape& ts) {
+  o << "      }\n"
+    << "      __syncwarp();\n"
+    << "      if ((threadIdx.x & 31) == 0) vbe_mbar_arrive(&empty[st]);\n";
+  if (!group_stacked(g)) o << "      vbe_bar_sync(1, " << ts.block << ");\n";
+  o << "    }\n"
     << "  }\n";
 }
 
@@ -1840,7 +1886,7 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     if (group_stacked(g)) total = 0;
     const std::vector<StagedBase> sp = (ts.staged || ts.tma) ? staging_plan(g) : std::vector<StagedBase>();
     const auto six = staged_index(g, sp);
-    const std::vector<int64_t> sgoff = staged_smem(sp, ts.th, ts.tw, &total, ts.tma);
+    const std::vector<int64_t> sgoff = staged_smem(sp, ts.th, ts.tw, &total, ts.tma ? tma_stages(g) : 0);
     if (ts.tma) {
       emit_tma_prologue(o, g, GL, ts, sp, sgoff, total);
     } else {
@@ -2000,11 +2046,11 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
         gens[k]->emit_full_epilogue("      ", W(w + 1), "blockIdx.x", W(w + 2), "gridDim.x", W(w));
         o << gens[k]->o.str();
       }
-      if (k != anchor) o << "      __syncthreads();\n";
+      if (k != anchor) o << (ts.tma ? "      vbe_bar_sync(1, " + std::to_string(ts.block) + ");\n" : "      __syncthreads();\n");
       o << "    }\n";
     }
     }
-    if (ts.tma) emit_tma_epilogue(o, GL);
+    if (ts.tma) emit_tma_epilogue(o, g, ts);
     else o << "  }\n";
     emit_copy_through(o, g, GL);
     o << "}\n";

@@ -836,7 +836,7 @@ Launch build_group(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, cons
   L.entry = G.prefix + ts.suffix();
   L.key = G.key;
   L.fn = kernel_fn(G.kern.get(), L.entry);
-  L.block = (unsigned)ts.block;
+  L.block = (unsigned)(ts.block + (ts.tma ? 32 : 0));  // the tensor-copy form adds a producer warp
   L.smem = (unsigned)ts.smem;
   if (!c->record)
     cuda_check(cudaKernelSetAttributeForDevice(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem,

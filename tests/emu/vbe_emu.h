@@ -9,12 +9,17 @@
 
 #include <atomic>
 #include <barrier>
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 struct dim3 {
@@ -91,26 +96,126 @@ template <class T, int E>
 inline void vbe_vload(const T* p, T (&o)[E]) {  // shared-memory source (unchecked)
   for (int e = 0; e < E; ++e) o[e] = p[e];
 }
-// bulk copies complete at once on the host; the barriers have nothing to wait for
 #define VBE_DYN_SMEM static unsigned char vbe_smem[262144] __attribute__((aligned(128)))
-inline void vbe_mbar_init(unsigned long long*, unsigned) {}
+
+// mbarriers, kept in a table beside the shared memory they would occupy: a
+// phase completes when its expected arrivals have arrived and the bytes of
+// the copies it tracks have landed (copies land when they are issued on the
+// host). Waits poll with a time limit, as the device waits do with an
+// iteration limit, and an arrival on a barrier nobody initialised is an error.
+struct EmuBar {
+  int expected = 0, pending = 0;
+  long long tx = 0;
+  unsigned phase = 0;
+};
+inline std::mutex& emu_bar_mu() {
+  static std::mutex m;
+  return m;
+}
+inline std::unordered_map<const void*, EmuBar>& emu_bars() {
+  static std::unordered_map<const void*, EmuBar> t;
+  return t;
+}
+inline EmuBar* emu_bar(const void* bar) {
+  auto it = emu_bars().find(bar);
+  if (it != emu_bars().end()) return &it->second;
+  if (g_bad.fetch_add(1) == 0) snprintf(g_bad_msg, sizeof g_bad_msg, "mbarrier at %p used before its init", bar);
+  return nullptr;
+}
+inline void emu_bar_settle(EmuBar* b) {
+  if (b->pending < 0 && g_bad.fetch_add(1) == 0)
+    snprintf(g_bad_msg, sizeof g_bad_msg, "more arrivals on an mbarrier phase than it expects");
+  if (b->pending == 0 && b->tx == 0) {
+    ++b->phase;
+    b->pending = b->expected;
+  }
+}
+inline void vbe_mbar_init(unsigned long long* bar, unsigned count) {
+  std::lock_guard<std::mutex> g(emu_bar_mu());
+  emu_bars()[bar] = EmuBar{(int)count, (int)count, 0, 0};
+}
 inline void vbe_fence_mbar_init() {}
 inline void vbe_fence_proxy_async() {}
-inline void vbe_mbar_expect_tx(unsigned long long*, unsigned) {}
-inline bool vbe_mbar_wait(unsigned long long*, unsigned) { return true; }
-inline void vbe_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long*) {
+inline void vbe_mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  std::lock_guard<std::mutex> g(emu_bar_mu());
+  if (EmuBar* b = emu_bar(bar)) {
+    b->tx += bytes;
+    --b->pending;
+    emu_bar_settle(b);
+  }
+}
+inline void vbe_mbar_arrive(unsigned long long* bar) {
+  std::lock_guard<std::mutex> g(emu_bar_mu());
+  if (EmuBar* b = emu_bar(bar)) {
+    --b->pending;
+    emu_bar_settle(b);
+  }
+}
+inline void emu_bar_landed(unsigned long long* bar, long long bytes) {
+  std::lock_guard<std::mutex> g(emu_bar_mu());
+  if (EmuBar* b = emu_bar(bar)) {
+    b->tx -= bytes;
+    if (b->tx < 0 && g_bad.fetch_add(1) == 0)
+      snprintf(g_bad_msg, sizeof g_bad_msg, "copies landed beyond the bytes an mbarrier phase expects");
+    emu_bar_settle(b);
+  }
+}
+inline bool vbe_mbar_wait(unsigned long long* bar, unsigned parity) {
+  const auto until = std::chrono::steady_clock::now() + std::chrono::seconds(60);
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> g(emu_bar_mu());
+      EmuBar* b = emu_bar(bar);
+      if (!b) return false;
+      if ((b->phase & 1u) != (parity & 1u)) return true;
+    }
+    if (std::chrono::steady_clock::now() > until) return false;
+    std::this_thread::yield();
+  }
+}
+inline void vbe_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
   if ((((uintptr_t)dst) | ((uintptr_t)src) | bytes) % 16 != 0 && g_bad.fetch_add(1) == 0)
     snprintf(g_bad_msg, sizeof g_bad_msg, "bulk copy not 16-byte aligned: %p <- %p, %u bytes", dst, src, bytes);
-  if (!emu_ok(src, bytes)) return;
-  memcpy(dst, src, bytes);
+  if (emu_ok(src, bytes)) memcpy(dst, src, bytes);
+  emu_bar_landed(bar, bytes);
 }
+
+// named barriers over the first n threads of a block (one per id and n,
+// reused by every block), optionally or-reducing a predicate
+struct EmuNamedBar {
+  bool acc = false, result = false;
+  std::barrier<std::function<void()>> bar;
+  explicit EmuNamedBar(int n) : bar(n, std::function<void()>([this] { result = acc; acc = false; })) {}
+};
+inline EmuNamedBar& emu_named_bar(int id, int n) {
+  static std::mutex m;
+  static std::map<std::pair<int, int>, std::unique_ptr<EmuNamedBar>> t;
+  std::lock_guard<std::mutex> g(m);
+  auto& e = t[{id, n}];
+  if (!e) e.reset(new EmuNamedBar(n));
+  return *e;
+}
+inline bool vbe_bar_or(int id, int n, bool v) {
+  if ((int)threadIdx.x >= n && g_bad.fetch_add(1) == 0)
+    snprintf(g_bad_msg, sizeof g_bad_msg, "thread outside the %d threads of named barrier %d", n, id);
+  EmuNamedBar& b = emu_named_bar(id, n);
+  if (v) {
+    static std::mutex m;
+    std::lock_guard<std::mutex> g(m);
+    b.acc = true;
+  }
+  b.bar.arrive_and_wait();
+  return b.result;
+}
+inline void vbe_bar_sync(int id, int n) { (void)vbe_bar_or(id, n, false); }
+inline void __syncwarp(unsigned = 0xffffffffu) { g_warp_bar[threadIdx.x >> 5]->arrive_and_wait(); }
 
 inline void vbe_grid_wait() {}  // launches run one after another on the host
 
 // a tensor copy, from the description a recording context writes into the
 // map (address, row stride, rows, row bytes, box columns, box rows, element
 // size); elements outside the tensor read as zeros
-inline void vbe_tma_2d(void* dst, const void* tmap, int x, int y, unsigned long long*) {
+inline void vbe_tma_2d(void* dst, const void* tmap, int x, int y, unsigned long long* bar) {
   const long long* m = (const long long*)tmap;
   const char* base = (const char*)m[0];
   const long long pitch = m[1], rows = m[2], bc = m[4], br = m[5], isz = m[6];
@@ -124,9 +229,9 @@ inline void vbe_tma_2d(void* dst, const void* tmap, int x, int y, unsigned long 
         continue;
       }
       const char* src = base + (gy * pitch + gx) * isz;
-      if (!emu_ok(src, (size_t)isz)) return;
-      memcpy(out, src, (size_t)isz);
+      if (emu_ok(src, (size_t)isz)) memcpy(out, src, (size_t)isz);
     }
+  emu_bar_landed(bar, br * bc * isz);
 }
 
 inline void __syncthreads() { g_block_bar->arrive_and_wait(); }
