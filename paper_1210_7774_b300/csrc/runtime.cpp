@@ -965,6 +965,7 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
 // it) and scratch in place of the anchor's targets, so nothing live changes.
 bool group_split(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const GroupPtrs& real, bool may_tune) {
   if (c->record) return getenv("VBE_RECORD_SPLIT") != nullptr;
+  if (!c->force_tile.empty()) return false;  // a fixed tile shape runs the group kernel
   const std::string sk = group_tune_key(G) + ":split";
   auto it = c->tune.find(sk);
   if (it != c->tune.end()) return it->second.block == 1;

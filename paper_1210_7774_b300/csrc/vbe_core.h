@@ -346,7 +346,7 @@ struct Ctx {
   std::vector<std::string> rec_launches;
   std::unordered_map<std::string, std::string> rec_sources;
   int force_bulk = 0;  // VBE_STAGING: stage every eligible run in chunks of this many elements
-  std::string force_tile;  // VBE_TILE: tile shape of every tile-fused group ("32x32", "s32x32", "t32x32")
+  std::string force_tile;  // VBE_TILE: tile shape of every tile-fused group ("32x32", "s32x32", "t32x32"), never split
   // set by staged kernels whose bounded waits ran out (mapped host memory)
   unsigned* err_word = nullptr;
   unsigned* err_word_dev = nullptr;
