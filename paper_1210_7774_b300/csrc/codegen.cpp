@@ -385,6 +385,28 @@ template <class T> __device__ __forceinline__ void vbe_arg_upd(T& v, i64& i, T x
   const bool take = (xn || vn) ? (xn && (!vn || j < i)) : (better || (x == v && j < i));
   if (take) { v = x; i = j; }
 }
+// float64 orderings on the integer pipes (the FP64 pipe is B300's scarcest):
+// for numbers, the bit pattern with the sign folded (negatives negated)
+// orders like the values and maps -0 and +0 to the same key; a NaN is a
+// pattern above the infinity's once the sign is cleared
+__device__ __forceinline__ bool vbe_disnan(i64 u) { return (u & 0x7fffffffffffffffll) > 0x7ff0000000000000ll; }
+__device__ __forceinline__ i64 vbe_dkey(i64 u) { return u < 0 ? -(u & 0x7fffffffffffffffll) : u; }
+template <> __device__ __forceinline__ double vbe_min<double>(double a, double b) {
+  const i64 ua = __double_as_longlong(a), ub = __double_as_longlong(b);
+  return (vbe_disnan(ua) || (!vbe_disnan(ub) && vbe_dkey(ua) < vbe_dkey(ub))) ? a : b;
+}
+template <> __device__ __forceinline__ double vbe_max<double>(double a, double b) {
+  const i64 ua = __double_as_longlong(a), ub = __double_as_longlong(b);
+  return (vbe_disnan(ua) || (!vbe_disnan(ub) && vbe_dkey(ua) > vbe_dkey(ub))) ? a : b;
+}
+template <> __device__ __forceinline__ void vbe_arg_upd<double>(double& v, i64& i, double x, i64 j, bool maxi) {
+  const i64 ux = __double_as_longlong(x), uv = __double_as_longlong(v);
+  const bool xn = vbe_disnan(ux), vn = vbe_disnan(uv);
+  const i64 kx = vbe_dkey(ux), kv = vbe_dkey(uv);
+  const bool better = maxi ? (kx > kv) : (kx < kv);
+  const bool take = (xn || vn) ? (xn && (!vn || j < i)) : (better || (kx == kv && j < i));
+  if (take) { v = x; i = j; }
+}
 // RANDOM: splitmix64 finaliser of seed + (key + step*m + 1) * golden gamma,
 // top 53 bits scaled to [0, 1)
 __device__ __forceinline__ double vbe_u01(u64 seed, u64 key, u64 step, u64 m) {
@@ -768,11 +790,12 @@ struct Gen {
   std::string W(int k) { return "p.w[" + std::to_string(k) + "]"; }
 
   // argument list for vbe_elem given per-slot value expressions
-  std::string call(const std::string& m, const std::vector<std::string>& lv, const std::vector<std::string>& sv) {
+  std::string call(const std::string& m, const std::vector<std::string>& lv, const std::vector<std::string>& sv,
+                   const std::string& ai = "ri") {
     std::string s = "vbe_elem(p, " + m;
     for (auto& x : lv) s += ", " + x;
     for (auto& x : sv) s += ", " + x;
-    if (arg()) s += ", acc, acci, ri";
+    if (arg()) s += ", acc, acci, " + ai;
     else if (r.has_red) s += kahan() ? ", acc, kc" : ", acc";
     return s + ");";
   }
@@ -1169,37 +1192,61 @@ struct Gen {
     }
     o << "    }\n";
     emit_acc_init("    ");
-    if (block)
-      o << "    for (i64 ri = threadIdx.x; ri < nred; ri += blockDim.x) {\n";
-    else
-      o << "    for (i64 ri = 0; ri < nred; ++ri) {\n";
-    // reduced offsets
+    // reduced offsets of element ri + u * rs (names suffixed by u)
     std::vector<std::pair<std::string, int>> rs;
     for (size_t s = 0; s < r.loads.size(); ++s) rs.push_back({"lr" + std::to_string(s), L.lst[s] + ndk});
     for (size_t s = 0; s < r.stores.size(); ++s) rs.push_back({"sr" + std::to_string(s), L.sst[s] + ndk});
     if (L.idx_st >= 0) rs.push_back({"ir", L.idx_st + ndk});
-    for (auto& k : rs) o << "      i64 " << k.first << " = 0;\n";
-    if (ndr == 1) {
-      for (auto& k : rs) o << "      " << k.first << " = ri * " << W(k.second) << ";\n";
-    } else {
-      o << "      { i64 rr = ri;\n";
-      for (int k = ndr - 1; k >= 0; --k) {
-        o << "        { const i64 ix = rr % " << W(L.dims0 + ndk + k) << "; rr /= " << W(L.dims0 + ndk + k) << ";";
-        for (auto& kk : rs) o << " " << kk.first << " += ix * " << W(kk.second + k) << ";";
-        o << " }\n";
+    auto offsets = [&](const std::string& ind, const std::string& u, const std::string& rix) {
+      for (auto& k : rs) o << ind << "i64 " << k.first << u << " = 0;\n";
+      if (ndr == 1) {
+        for (auto& k : rs) o << ind << k.first << u << " = (" << rix << ") * " << W(k.second) << ";\n";
+      } else {
+        o << ind << "{ i64 rr = " << rix << ";\n";
+        for (int k = ndr - 1; k >= 0; --k) {
+          o << ind << "  { const i64 ix = rr % " << W(L.dims0 + ndk + k) << "; rr /= " << W(L.dims0 + ndk + k) << ";";
+          for (auto& kk : rs) o << " " << kk.first << u << " += ix * " << W(kk.second + k) << ";";
+          o << " }\n";
+        }
+        o << ind << "}\n";
       }
-      o << "      }\n";
+    };
+    // element u of this step: its loads (preloaded values), then the call and its stores
+    auto element = [&](const std::string& ind, const std::string& u, const std::string& rix, bool preloaded) {
+      std::vector<std::string> lv, sv;
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        lv.push_back(preloaded ? "la" + std::to_string(s) + u
+                               : "lp" + std::to_string(s) + "[lk" + std::to_string(s) + " + lr" + std::to_string(s) + u + "]");
+      for (size_t s = 0; s < r.stores.size(); ++s) {
+        o << ind << T(r.stores[s].dtype) << " b" << s << u << ";\n";
+        sv.push_back("b" + std::to_string(s) + u);
+      }
+      o << ind << call(L.idx_st >= 0 ? "ik + ir" + u : "0", lv, sv, rix) << "\n";
+      for (size_t s = 0; s < r.stores.size(); ++s)
+        o << ind << "sp" << s << "[sk" << s << " + sr" << s << u << "] = b" << s << u << ";\n";
+    };
+    // A thread takes the reduced elements ri, ri + rs, ri + 2 rs, ... in
+    // order. Four at a time, their loads issued before the first of them is
+    // combined (a store of one element never touches another element's
+    // inputs: the run's views are disjoint or identical), so four loads are
+    // in flight instead of one; the combining order is unchanged.
+    constexpr int UR = 4;
+    o << "    const i64 rs = " << (block ? "(i64)blockDim.x" : "(i64)1") << ";\n"
+      << "    i64 ri = " << (block ? "(i64)threadIdx.x" : "(i64)0") << ";\n"
+      << "    for (; ri + " << UR - 1 << " * rs < nred; ri += " << UR << " * rs) {\n";
+    for (int u = 0; u < UR; ++u) {
+      const std::string us = "_" + std::to_string(u), rix = "ri + " + std::to_string(u) + " * rs";
+      offsets("      ", us, rix);
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        o << "      const " << T(r.loads[s].dtype) << " la" << s << us << " = lp" << s << "[lk" << s << " + lr" << s << us
+          << "];\n";
     }
-    std::vector<std::string> lv, sv;
-    for (size_t s = 0; s < r.loads.size(); ++s)
-      lv.push_back("lp" + std::to_string(s) + "[lk" + std::to_string(s) + " + lr" + std::to_string(s) + "]");
-    for (size_t s = 0; s < r.stores.size(); ++s) {
-      o << "      " << T(r.stores[s].dtype) << " b" << s << ";\n";
-      sv.push_back("b" + std::to_string(s));
-    }
-    o << "      " << call(L.idx_st >= 0 ? "ik + ir" : "0", lv, sv) << "\n";
-    for (size_t s = 0; s < r.stores.size(); ++s)
-      o << "      sp" << s << "[sk" << s << " + sr" << s << "] = b" << s << ";\n";
+    for (int u = 0; u < UR; ++u)
+      element("      ", "_" + std::to_string(u), "ri + " + std::to_string(u) + " * rs", true);
+    o << "    }\n"
+      << "    for (; ri < nred; ri += rs) {\n";
+    offsets("      ", "", "ri");
+    element("      ", "", "ri", false);
     o << "    }\n";
     if (arg() && block) {
       o << "    { const i64 v = " << block_reduce_name << "(acc, acci); if (threadIdx.x == 0) rp[rk] = v; }\n";

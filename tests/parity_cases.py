@@ -372,6 +372,23 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
             b.emit(op, b.view(o, 0, (), ()), b.whole(xb), axis=0)
             p = b.build([o])
             out.append(Case(p.name, p, _exact_check(p)))
+    # a long reduced axis, inner and outer: a block per output with several
+    # elements of each thread in flight at once, ties, NaNs and infinities
+    for dt in ("float64", "float32", "int64"):
+        rows, cols = 7, 3001
+        x = rng.integers(-3, 4, rows * cols).astype(dt)
+        if dt != "int64":
+            sp = rng.random(x.size) < 0.02
+            x[sp] = lv[rng.integers(0, len(lv), int(sp.sum()))].astype(dt)
+        for op in ("ARGMIN_REDUCE", "ARGMAX_REDUCE", "MIN_REDUCE", "MAX_REDUCE"):
+            for ax, shp in ((1, (rows, cols)), (0, (cols, rows))):
+                b = ProgramBuilder(f"{op}_{dt}_long{ax}")
+                xb = b.base(dt, shp, x)
+                odt = "int64" if op.startswith("ARG") else dt
+                o = b.base(odt, rows)
+                b.emit(op, b.whole(o), b.whole(xb), axis=ax)
+                p = b.build([o])
+                out.append(Case(p.name, p, _exact_check(p)))
     # fused chain with a full reduction and with an axis reduction, plus stores
     for dt in ("float64", "float32"):
         b = ProgramBuilder(f"chain_full_{dt}")
