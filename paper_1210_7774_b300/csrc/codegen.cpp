@@ -418,6 +418,7 @@ __device__ __forceinline__ double vbe_u01(u64 seed, u64 key, u64 step, u64 m) {
 }
 #ifndef VBE_EMU
 template <class T> __device__ __forceinline__ T* vbe_ptr(i64 v) { return reinterpret_cast<T*>(v); }
+template <class T> __device__ __forceinline__ bool vbe_aligned16(const T* p) { return ((u64)p & 15ull) == 0; }
 template <int B> struct vbe_vec;
 template <> struct vbe_vec<16> { typedef uint4 t; };
 template <> struct vbe_vec<8> { typedef uint2 t; };
@@ -1230,6 +1231,34 @@ struct Gen {
     // combined (a store of one element never touches another element's
     // inputs: the run's views are disjoint or identical), so four loads are
     // in flight instead of one; the combining order is unchanged.
+    // A thread per output over a unit-stride reduced dimension (each output
+    // a contiguous row of every input): 16-byte vector loads, the elements
+    // still combined one by one in order. Decided per output at run time
+    // (strides, alignment, length); otherwise the scalar loop below.
+    int visz = r.loads.empty() ? 0 : itemsize(r.loads[0].dtype);
+    for (auto& l : r.loads)
+      if (itemsize(l.dtype) != visz) visz = 0;
+    const bool vec_gen = !block && ndr == 1 && r.stores.empty() && (visz == 4 || visz == 8);
+    if (vec_gen) {
+      const int E = 16 / visz;
+      o << "    bool vec = nred % " << E << " == 0;\n";
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        o << "    vec = vec && " << W(L.lst[s] + ndk) << " == 1 && vbe_aligned16(lp" << s << " + lk" << s << ");\n";
+      o << "    if (vec) {\n"
+        << "      for (i64 ri = 0; ri < nred; ri += " << E << ") {\n";
+      for (size_t s = 0; s < r.loads.size(); ++s)
+        o << "        " << T(r.loads[s].dtype) << " lq" << s << "[" << E << "];\n"
+          << "        vbe_vload(lp" << s << " + (lk" << s << " + ri), lq" << s << ");\n";
+      for (int e = 0; e < E; ++e) {
+        std::vector<std::string> lv;
+        for (size_t s = 0; s < r.loads.size(); ++s) lv.push_back("lq" + std::to_string(s) + "[" + std::to_string(e) + "]");
+        const std::string rix = "ri + " + std::to_string(e);
+        const std::string m = L.idx_st >= 0 ? "ik + (" + rix + ") * " + W(L.idx_st + ndk) : "0";
+        o << "        " << call(m, lv, {}, rix) << "\n";
+      }
+      o << "      }\n"
+        << "    } else {\n";
+    }
     constexpr int UR = 4;
     o << "    const i64 rs = " << (block ? "(i64)blockDim.x" : "(i64)1") << ";\n"
       << "    i64 ri = " << (block ? "(i64)threadIdx.x" : "(i64)0") << ";\n"
@@ -1248,6 +1277,7 @@ struct Gen {
     offsets("      ", "", "ri");
     element("      ", "", "ri", false);
     o << "    }\n";
+    if (vec_gen) o << "    }\n";
     if (arg() && block) {
       o << "    { const i64 v = " << block_reduce_name << "(acc, acci); if (threadIdx.x == 0) rp[rk] = v; }\n";
     } else if (arg()) {

@@ -77,6 +77,10 @@ template <class T>
 inline CP<T> vbe_ptr(long long v) {
   return CP<T>{reinterpret_cast<T*>(v)};
 }
+template <class T>
+inline bool vbe_aligned16(CP<T> p) {
+  return ((uintptr_t)p.p & 15) == 0;
+}
 template <class T, int E>
 inline void vbe_vload(CP<const T> p, T (&o)[E]) {
   if (((uintptr_t)p.p) % (sizeof(T) * E) != 0 && g_bad.fetch_add(1) == 0)
