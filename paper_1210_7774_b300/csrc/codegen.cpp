@@ -1231,31 +1231,64 @@ struct Gen {
     // combined (a store of one element never touches another element's
     // inputs: the run's views are disjoint or identical), so four loads are
     // in flight instead of one; the combining order is unchanged.
-    // A thread per output over a unit-stride reduced dimension (each output
-    // a contiguous row of every input): 16-byte vector loads, the elements
-    // still combined one by one in order. Decided per output at run time
-    // (strides, alignment, length); otherwise the scalar loop below.
+    // Outputs whose reduced dimension is a contiguous, 16-byte aligned row
+    // of every input and output: 16-byte vector loads (and stores) of E
+    // consecutive elements. A thread takes chunks c, c + rs, ... (rs = 1 for
+    // a thread per output, blockDim for a block per output), two chunks in
+    // flight, then the elements past the last whole chunk one by one; a
+    // thread per output thus still combines its elements in order. Decided
+    // per output at run time (strides, alignment); otherwise the scalar
+    // loop below.
     int visz = r.loads.empty() ? 0 : itemsize(r.loads[0].dtype);
     for (auto& l : r.loads)
       if (itemsize(l.dtype) != visz) visz = 0;
-    const bool vec_gen = !block && ndr == 1 && r.stores.empty() && (visz == 4 || visz == 8);
+    for (auto& st : r.stores)
+      if (itemsize(st.dtype) != visz) visz = 0;
+    const bool vec_gen = ndr == 1 && (visz == 4 || visz == 8);
     if (vec_gen) {
       const int E = 16 / visz;
-      o << "    bool vec = nred % " << E << " == 0;\n";
+      const std::string E_ = std::to_string(E);
+      o << "    bool vec = true;\n";
       for (size_t s = 0; s < r.loads.size(); ++s)
         o << "    vec = vec && " << W(L.lst[s] + ndk) << " == 1 && vbe_aligned16(lp" << s << " + lk" << s << ");\n";
+      for (size_t s = 0; s < r.stores.size(); ++s)
+        o << "    vec = vec && " << W(L.sst[s] + ndk) << " == 1 && vbe_aligned16(sp" << s << " + sk" << s << ");\n";
       o << "    if (vec) {\n"
-        << "      for (i64 ri = 0; ri < nred; ri += " << E << ") {\n";
-      for (size_t s = 0; s < r.loads.size(); ++s)
-        o << "        " << T(r.loads[s].dtype) << " lq" << s << "[" << E << "];\n"
-          << "        vbe_vload(lp" << s << " + (lk" << s << " + ri), lq" << s << ");\n";
-      for (int e = 0; e < E; ++e) {
-        std::vector<std::string> lv;
-        for (size_t s = 0; s < r.loads.size(); ++s) lv.push_back("lq" + std::to_string(s) + "[" + std::to_string(e) + "]");
-        const std::string rix = "ri + " + std::to_string(e);
-        const std::string m = L.idx_st >= 0 ? "ik + (" + rix + ") * " + W(L.idx_st + ndk) : "0";
-        o << "        " << call(m, lv, {}, rix) << "\n";
-      }
+        << "      const i64 cs = " << (block ? "(i64)blockDim.x" : "(i64)1") << ", nv = nred / " << E << ";\n"
+        << "      i64 ci = " << (block ? "(i64)threadIdx.x" : "(i64)0") << ";\n";
+      auto chunks = [&](int nu, const std::string& ind) {
+        for (int u = 0; u < nu; ++u) {
+          const std::string us = std::to_string(u), base = "(ci + " + us + " * cs) * " + E_;
+          for (size_t s = 0; s < r.loads.size(); ++s)
+            o << ind << T(r.loads[s].dtype) << " lq" << s << "_" << us << "[" << E << "];\n"
+              << ind << "vbe_vload(lp" << s << " + (lk" << s << " + " << base << "), lq" << s << "_" << us << ");\n";
+        }
+        for (int u = 0; u < nu; ++u) {
+          const std::string us = std::to_string(u), base = "(ci + " + us + " * cs) * " + E_;
+          for (size_t s = 0; s < r.stores.size(); ++s)
+            o << ind << T(r.stores[s].dtype) << " bq" << s << "_" << us << "[" << E << "];\n";
+          for (int e = 0; e < E; ++e) {
+            std::vector<std::string> lv, sv;
+            const std::string es = std::to_string(e);
+            for (size_t s = 0; s < r.loads.size(); ++s) lv.push_back("lq" + std::to_string(s) + "_" + us + "[" + es + "]");
+            for (size_t s = 0; s < r.stores.size(); ++s) sv.push_back("bq" + std::to_string(s) + "_" + us + "[" + es + "]");
+            const std::string rix = base + " + " + es;
+            const std::string m = L.idx_st >= 0 ? "ik + (" + rix + ") * " + W(L.idx_st + ndk) : "0";
+            o << ind << call(m, lv, sv, rix) << "\n";
+          }
+          for (size_t s = 0; s < r.stores.size(); ++s)
+            o << ind << "vbe_vstore(sp" << s << " + (sk" << s << " + " << base << "), bq" << s << "_" << us << ");\n";
+        }
+      };
+      o << "      for (; ci + cs < nv; ci += 2 * cs) {\n";
+      chunks(2, "        ");
+      o << "      }\n"
+        << "      for (; ci < nv; ci += cs) {\n";
+      chunks(1, "        ");
+      o << "      }\n"
+        << "      for (i64 ri = nv * " << E << " + " << (block ? "(i64)threadIdx.x" : "(i64)0") << "; ri < nred; ri += cs) {\n";
+      offsets("        ", "", "ri");
+      element("        ", "", "ri", false);
       o << "      }\n"
         << "    } else {\n";
     }
