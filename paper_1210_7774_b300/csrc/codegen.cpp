@@ -556,6 +556,16 @@ bool uses_soft_f64(const Run& r) {
   return false;
 }
 
+// a float64 constant operand equal to +-2^k, k in [-1022, 1023] (part of a
+// kernel's signature: such products are generated differently)
+bool pow2_const(const Operand& a) {
+  if (a.kind != 1 || a.dtype != VBE_FLOAT64) return false;
+  uint64_t u;
+  memcpy(&u, &a.f, 8);
+  const int e = (int)((u >> 52) & 0x7ff);
+  return (u & 0xFFFFFFFFFFFFFull) == 0 && e != 0 && e != 0x7ff;
+}
+
 bool is_simple_f64(const Step& s) {
   if (s.dt_in != VBE_FLOAT64) return false;
   switch (s.op) {
@@ -603,8 +613,12 @@ struct Gen {
   std::string vt() const { return ctype(r.value_dtype[r.red_value]); }
 
   std::vector<char> soft;  // per step: float64 add/subtract/multiply/compare emulated
+  bool int_heavy = false;  // float64 exp or log on the integer pipes in this run
 
-  Gen(const Run& r_, const Canon& c_) : r(r_), c(c_), L(layout_of(r_, c_)), soft(balance_f64(r_)) {}
+  Gen(const Run& r_, const Canon& c_) : r(r_), c(c_), L(layout_of(r_, c_)), soft(balance_f64(r_)) {
+    for (auto& s : r.steps)
+      if (r.soft_f64 && s.dt_in == VBE_FLOAT64 && (s.op == VBE_OP_EXP || s.op == VBE_OP_LOG)) int_heavy = true;
+  }
 
   bool const_params = false;  // constants arrive as arguments of the element function
   std::string opnd(const Operand& a) {
@@ -652,6 +666,13 @@ struct Gen {
       return call + ")";
     }
     if (sf && s.op == VBE_OP_NEGATIVE) return "vbe_dneg(" + a + ")";
+    // float64 products by a constant power of two: on the integer pipes,
+    // unless the run already keeps them busy with exp/log (measured: a
+    // Black-Scholes kernel got slower, the stencil kernels faster)
+    if (sf && s.op == VBE_OP_MULTIPLY && !int_heavy) {
+      if (pow2_const(s.a[1])) return "vbe_dmul_k(" + a + ", " + b + ")";
+      if (pow2_const(s.a[0])) return "vbe_dmul_k(" + b + ", " + a + ")";
+    }
     if (sf && s.op == VBE_OP_ABSOLUTE) return "vbe_dabs(" + a + ")";
     switch (s.op) {
       case VBE_OP_ADD: return i64t ? "vbe_iadd(" + a + "," + b + ")" : "(" + a + " + " + b + ")";
@@ -1334,7 +1355,7 @@ static std::string signature(const Run& r, const Canon& c) {
   put((int64_t)r.steps.size());
   for (auto& s : r.steps) {
     put(s.op); put(s.dt_out); put(s.dt_in); put(s.nin); put(s.value); put(s.random_idx);
-    for (int a = 0; a < s.nin; ++a) { put(s.a[a].kind); put(s.a[a].idx); put(s.a[a].dtype); }
+    for (int a = 0; a < s.nin; ++a) { put(s.a[a].kind); put(s.a[a].idx); put(s.a[a].dtype); put(pow2_const(s.a[a])); }
   }
   put((int64_t)r.value_dtype.size());
   for (int d : r.value_dtype) put(d);

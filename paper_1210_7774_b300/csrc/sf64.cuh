@@ -179,6 +179,23 @@ __device__ __forceinline__ double vbe_dmul(double a, double b) {
   return __longlong_as_double((sf_i64)(((ua ^ ub) & SF_SIGN) | ((sf_u64)e << 52) | (q & SF_M52)));
 }
 
+// a * c where c is a constant: when c = +-2^k and the product is a normal
+// number (or a is a signed zero) the product is exact and is formed by moving
+// the exponent field on the integer pipes; any other case is the hardware
+// multiply. Whether c is a power of two is uniform across the kernel.
+__device__ __forceinline__ double vbe_dmul_k(double a, double c) {
+  const sf_u64 uc = (sf_u64)__double_as_longlong(c);
+  const int ec = (int)((uc >> 52) & 0x7ff);
+  if ((uc & SF_M52) == 0 && ec != 0 && ec != 0x7ff) {
+    const sf_u64 ua = (sf_u64)__double_as_longlong(a), sg = uc & SF_SIGN;
+    const int ea = (int)((ua >> 52) & 0x7ff), k = ec - 1023;
+    if ((unsigned)(ea + k - 1) < 0x7feu && ea != 0 && ea != 0x7ff)
+      return __longlong_as_double((sf_i64)((ua ^ sg) + ((sf_u64)(sf_i64)k << 52)));
+    if ((ua << 1) == 0) return __longlong_as_double((sf_i64)(ua ^ sg));
+  }
+  return a * c;
+}
+
 // a + b, correctly rounded (round to nearest, ties to even)
 __device__ __forceinline__ double vbe_dadd(double a, double b) {
   sf_u64 ua = (sf_u64)__double_as_longlong(a), ub = (sf_u64)__double_as_longlong(b);

@@ -64,6 +64,23 @@ int main(int argc, char** argv) {
       else if (!strcmp(op, "add")) { got = vbe_dadd(a, b); want = a + b; }
       else { got = vbe_dsub(a, b); want = a - b; }
       if (got == 0 && want == 0 && std::signbit(got) != std::signbit(want)) { got = 1; want = 2; }
+    } else if (!strcmp(op, "mulk")) {
+      // products by constants: powers of two (the integer path) and others
+      a = mode == 0 ? rnd_double(g, -1030, 1030) : rnd_double(g, -60, 60);
+      const int k = (int)(g() % 2101) - 1050;
+      b = std::ldexp((g() & 1) ? -1.0 : 1.0, k < -1074 ? -1074 : k);
+      if (mode == 1) b = std::ldexp((g() & 1) ? -1.0 : 1.0, (int)(g() % 9) - 4);
+      if (mode == 2) a = std::ldexp(1.0 + (double)(g() % 1024) * 0x1p-10, (int)(g() % 40) - 1060);  // subnormal results
+      if (mode == 3) a = std::ldexp(1.0 + (double)(g() % 1024) * 0x1p-10, (int)(g() % 40) + 990);   // overflow edge
+      if (mode == 4) b = rnd_double(g, -8, 8);                                                        // not a power of two
+      if (mode == 5) {
+        const double sp[] = {0.0, -0.0, INFINITY, -INFINITY, NAN, 0x1p-1074, -0x1p-1060, 0x1p1023};
+        a = sp[g() % 8];
+        if (g() & 1) b = sp[g() % 8];
+      }
+      got = vbe_dmul_k(a, b);
+      want = a * b;
+      if (got == 0 && want == 0 && std::signbit(got) != std::signbit(want)) { got = 1; want = 2; }
     } else if (!strcmp(op, "cmp")) {
       const double sp[] = {0.0, -0.0, INFINITY, -INFINITY, NAN, 1.0, -1.0, 0x1p-1074};
       a = mode < 2 ? sp[g() % 8] : rnd_double(g, -5, 5);

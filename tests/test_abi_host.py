@@ -283,6 +283,25 @@ def test_generated_source_is_plain_cuda(fused):
     assert "__fmaf" not in src and "fma(" not in src
 
 
+def test_power_of_two_constants_get_their_own_kernel(fused):
+    """Float64 products by a constant +-2^k are formed by moving the exponent
+    field; whether a constant is such a power is part of the kernel's
+    signature, so two runs that differ only there get different sources."""
+    srcs = {}
+    for c in (0.5, 0.3, -4.0, 2.0 ** -1030):
+        b = ProgramBuilder(f"mulk_{c}")
+        x = b.base("float64", 64, np.arange(64, dtype=np.float64))
+        y = b.base("float64", 64)
+        b.emit("MULTIPLY", b.whole(y), b.whole(x), Const(c))
+        p = b.build([y])
+        L = fused.load(p, upload=False)
+        js = json.loads(fused.plan(L, 0, source=True))
+        srcs[c] = [i["run"]["source"] for i in js["items"] if "run" in i][0]
+    assert "vbe_dmul_k(" in srcs[0.5] and "vbe_dmul_k(" in srcs[-4.0]
+    assert "vbe_dmul_k(" not in srcs[0.3]
+    assert "vbe_dmul_k(" not in srcs[2.0 ** -1030]  # subnormal: not a normal power of two
+
+
 def test_user_operation_registration(fused):
     """Section "Interface": registration of a user-defined operation. The
     body is compiled at registration; the same definition gets the same

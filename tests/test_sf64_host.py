@@ -26,7 +26,7 @@ def checker(tmp_path_factory):
 
 
 @pytest.mark.parametrize("op,n", [("div", 2_000_000), ("sqrt", 2_000_000), ("exp", 1_000_000), ("log", 1_000_000),
-                                  ("mul", 2_000_000), ("add", 2_000_000), ("sub", 2_000_000), ("cmp", 500_000),
+                                  ("mul", 2_000_000), ("mulk", 2_000_000), ("add", 2_000_000), ("sub", 2_000_000), ("cmp", 500_000),
                                   ("u53", 500_000)])
 def test_sf64_against_host_ieee(checker, op, n):
     for seed in (1, 2):
