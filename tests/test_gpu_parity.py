@@ -239,6 +239,71 @@ def test_errors_on_device():
         assert np.array_equal(out, np.sqrt(host))
 
 
+def test_views_beyond_two_to_the_31_elements():
+    """Maximum sizes: float32 views of 2^31 + 4099 elements (8.6 GB each,
+    indices past every 32-bit boundary). x = a / 4 with a = i mod 1024 and
+    y = b with b = (i div 3) mod 512, so z = x * y + x = a (b + 1) / 4 is
+    exact in float32: z bit-exact at sampled indices (both sides of 2^31),
+    the full ADD_REDUCE and the column sums of z viewed as
+    (2^20 + 2) x 2048 (reduced dimension outer, 2^31 + 4096 elements)
+    within the float32 reduction tolerance of exact integer sums."""
+    torch = pytest.importorskip("torch")
+    n = (1 << 31) + 4099
+    R, C = n // 2048, 2048
+    i = torch.arange(n, dtype=torch.int64, device="cuda")
+    x = ((i % 1024).to(torch.float32) * 0.25)
+    y = ((i // 3) % 512).to(torch.float32)
+    del i
+    z = torch.empty(n, dtype=torch.float32, device="cuda")
+    s = torch.zeros(1, dtype=torch.float32, device="cuda")
+    cs = torch.zeros(C, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    with Executor(FUSED, cache_dir=CACHE, stream=torch.cuda.current_stream().cuda_stream) as ex:
+        ctx = ex.ctx
+        f32 = V.DTYPE_CODE["float32"]
+        bx, by, bz = (V.vbe_base_register(ctx, f32, n, t.data_ptr()) for t in (x, y, z))
+        bs = V.vbe_base_register(ctx, f32, 1, s.data_ptr())
+        bc = V.vbe_base_register(ctx, f32, C, cs.data_ptr())
+        vx, vy, vz = (V.vbe_view_create(ctx, b, 0, (n,), (1,)) for b in (bx, by, bz))
+        vs = V.vbe_view_create(ctx, bs, 0, (), ())
+        vz2 = V.vbe_view_create(ctx, bz, 0, (R, C), (C, 1))
+        vc = V.vbe_view_create(ctx, bc, 0, (C,), (1,))
+        arr = (V.vbe_instr * 4)()
+        for e, (op, out, ins, axis) in zip(arr, (("MULTIPLY", vz, (vx, vy), 0), ("ADD", vz, (vz, vx), 0),
+                                                 ("ADD_REDUCE", vs, (vz,), 0), ("ADD_REDUCE", vc, (vz2,), 0))):
+            e.op = V.OPCODES[op]
+            e.const_slot = -1
+            e.out = out
+            for k, v in enumerate(ins):
+                e.in_[k] = v
+            e.axis = axis
+        V.vbe_submit(ctx, arr, 4)
+        torch.cuda.current_stream().synchronize()
+    rng = np.random.default_rng(31)
+    idx = np.unique(np.concatenate([[0, 1, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, n - 1],
+                                    rng.integers(0, n, 2000)]))
+    a, b = idx % 1024, (idx // 3) % 512
+    want = (a * (b + 1)).astype(np.float32) * np.float32(0.25)
+    got = z[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert_exact(got, want, "z at sampled indices")
+
+    def exact_sum(lo, hi, step=1, start=0):
+        # sum of a (b + 1) over i = start + step * k for lo <= k < hi, in int64
+        tot = 0
+        for c0 in range(lo, hi, 1 << 24):
+            k = np.arange(c0, min(hi, c0 + (1 << 24)), dtype=np.int64)
+            ii = start + step * k
+            tot += int(np.sum((ii % 1024) * ((ii // 3) % 512 + 1)))
+        return tot
+    # a (b + 1) repeats with period lcm(1024, 3 * 512) = 3072
+    q, rem = divmod(n, 3072)
+    total = q * exact_sum(0, 3072) + exact_sum(0, rem)
+    assert_close_sum(s.cpu().numpy(), np.array([total / 4.0]), np.array([total / 4.0]), 1e-5, "full sum")
+    cols = rng.choice(C, 12, replace=False)
+    col_want = np.array([exact_sum(0, R, C, int(c)) / 4.0 for c in cols])
+    assert_close_sum(cs.cpu().numpy()[cols], col_want, col_want, 1e-5, "column sums")
+
+
 def test_registered_device_memory():
     torch = pytest.importorskip("torch")
     x = torch.arange(1000, dtype=torch.float64, device="cuda")
