@@ -869,9 +869,11 @@ struct Gen {
   }
 
   // --------------------------------------------------------- tile kernels
-  void emit_tile_kernel(int U) {
+  void emit_tile_kernel(int U, int maxreg = 0) {
     const int nd = c.spec.nd;
-    o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_u" << U << "(const P p) {\n"
+    o << "extern \"C\" __global__ void "
+      << (maxreg ? "__maxnreg__(" + std::to_string(maxreg) + ")" : std::string("__launch_bounds__(1024)")) << " vbe_@TAG@_u"
+      << U << (maxreg ? "r" + std::to_string(maxreg) : std::string()) << "(const P p) {\n"
       << "  vbe_grid_wait();\n";
     emit_pointers("  ");
     emit_acc_init("  ");
@@ -1416,6 +1418,9 @@ static std::string generate_source_uncached(const Run& r, const Canon& c, std::s
   g.emit_block_reduce();
   if (tile_mode(c.spec.mode)) {
     for (int U : {1, 2, 4}) g.emit_tile_kernel(U);
+    if (reg_cap_variants(r))
+      for (int U : {1, 2})
+        for (int cap : kRegCaps) g.emit_tile_kernel(U, cap);
     if (c.spec.vec && g.bulk_slots() > 0) g.emit_bulk_kernel();
     if (c.spec.nd == 1)
       for (int U : {1, 4}) g.emit_packed_kernel(U);

@@ -523,7 +523,7 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
     fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, (uintptr_t)ex->scratch.partials, (uintptr_t)ex->scratch.counters,
                tc.block, 1, &a, CH, (uintptr_t)c->err_word_dev);
   } else if (cn.spec.mode == Mode::ELEM || cn.spec.mode == Mode::FULL) {
-    L.entry = P.prefix + "_u" + std::to_string(tc.U);
+    L.entry = P.prefix + "_u" + std::to_string(tc.U) + (tc.maxreg ? "r" + std::to_string(tc.maxreg) : std::string());
     L.key = P.key;
     L.fn = kernel_fn(P.kern.get(), L.entry);
     L.block = tc.block;
@@ -601,6 +601,16 @@ TuneChoice autotune(Ctx* c, Exec* ex, Prepared& P, const RunPtrs& real) {
       tc.U = U;
       cands.push_back(tc);
     }
+  if (reg_cap_variants(r))
+    for (int block : {256, 512})
+      for (int U : {1, 2})
+        for (int cap : kRegCaps) {
+          TuneChoice tc;
+          tc.block = block;
+          tc.U = U;
+          tc.maxreg = cap;
+          cands.push_back(tc);
+        }
   for (int block : {256, 512})
     for (int ch : {1024, 2048, 4096}) {
       TuneChoice tc;

@@ -265,9 +265,17 @@ struct Kernel {
   std::map<std::string, cudaKernel_t> fn;
 };
 
+// Long runs (many fused bytecodes) also get tile kernels compiled under a
+// per-thread register cap, as tuning candidates: more resident warps to hide
+// the latency of their long dependency chains, against some spilling.
+constexpr int kRegCapMinSteps = 24;
+constexpr int kRegCaps[2] = {40, 48};
+inline bool reg_cap_variants(const Run& r) { return (int)r.steps.size() >= kRegCapMinSteps; }
+
 struct TuneChoice {
   int block = 256;
   int U = 2;
+  int maxreg = 0;      // > 0: the tile kernel compiled with this register cap (U = 1 or 2)
   int bulk_chunk = 0;  // > 0: stage unit-stride inputs through shared memory in chunks of this many elements
   int grid_mult = 0;  // 0: enough CTAs for the work (capped by residency)
 };

@@ -42,6 +42,7 @@ extern dim3 blockDim, gridDim;
 #define __forceinline__ inline
 #define SF_CALL __attribute__((noinline))
 #define __launch_bounds__(...)
+#define __maxnreg__(...)
 #define __shared__ static
 
 struct EmuRange {
