@@ -82,6 +82,10 @@ struct Builder {
   std::vector<int> load_value;            // value id per load slot (unused: loads are operands)
   std::vector<std::pair<ViewDesc, int>> written;  // view -> latest value
   ViewDesc red_view;                      // reduction output view
+  ViewDesc red2_view;                     // paired index reduction output view
+  ViewDesc red_in;                        // the reduced view (when it is a plain view)
+  bool red_in_known = false;
+  int red_instr = -1;                     // batch index of the run's reduction
   std::vector<HostAction> pending;
   int last_instr = -1;
 
@@ -146,6 +150,7 @@ struct Builder {
       for (auto& w : written)
         if (may_overlap(r.in[k], w.first) && !r.in[k].identical(w.first)) return true;
       if (cur.has_red && may_overlap(r.in[k], red_view)) return true;
+      if (cur.has_red2 && may_overlap(r.in[k], red2_view)) return true;
     }
     // (2) output vs the run's inputs and outputs
     for (auto& l : load_views)
@@ -153,6 +158,7 @@ struct Builder {
     for (auto& w : written)
       if (may_overlap(r.out, w.first) && !r.out.identical(w.first)) return true;
     if (cur.has_red && may_overlap(r.out, red_view)) return true;
+    if (cur.has_red2 && may_overlap(r.out, red2_view)) return true;
     return false;
   }
 
@@ -169,6 +175,8 @@ struct Builder {
     cur.shape.assign(shape_view.shape, shape_view.shape + shape_view.ndim);
     load_views.clear();
     written.clear();
+    red_in_known = false;
+    red_instr = -1;
     open = true;
   }
 
@@ -256,15 +264,18 @@ struct Builder {
         x.idx = s.value;
       }
       cur.red_value = x.idx;
+      red_in = r.in[0];
+      red_in_known = true;
     }
     red_view = r.out;
+    red_instr = idx;
     cur.red_out = slot_of(r.out, r.dt_out);
     cur.instrs.push_back(idx);
     last_instr = idx;
   }
 
   bool can_merge_reduction(const RInstr& r, size_t idx) {
-    if (!cur.has_red || r.op != cur.red_op) return false;
+    if (!cur.has_red || r.op != cur.red_op || cur.has_red2) return false;
     if (r.op == VBE_OP_ARGMIN_REDUCE || r.op == VBE_OP_ARGMAX_REDUCE) return false;  // indices do not compose
     if (!r.in[0].identical(red_view)) return false;
     if (live_after(prog, red_view.base, idx)) return false;
@@ -274,6 +285,34 @@ struct Builder {
     for (auto& w : written)
       if (may_overlap(r.out, w.first)) return false;
     return true;
+  }
+
+  // ARGMIN_REDUCE (ARGMAX_REDUCE) right after the run's MIN_REDUCE
+  // (MAX_REDUCE) of the identical view over the same single axis: the index
+  // reduction is the same pass (the minimum's value and its first index)
+  bool can_pair_arg(const RInstr& r) {
+    if (!cur.has_red || cur.has_red2 || !red_in_known || cur.red_axes.size() != 1) return false;
+    const bool mn = cur.red_op == VBE_OP_MIN_REDUCE && r.op == VBE_OP_ARGMIN_REDUCE;
+    const bool mx = cur.red_op == VBE_OP_MAX_REDUCE && r.op == VBE_OP_ARGMAX_REDUCE;
+    if (!(mn || mx) || !r.in[0].identical(red_in) || r.axis != cur.red_axes[0]) return false;
+    // the view still holds the reduced values: nothing in the run wrote it
+    // after the reduction (the reduction is the run's last instruction)
+    if (last_instr != red_instr) return false;
+    for (auto& l : load_views)
+      if (may_overlap(r.out, l)) return false;
+    for (auto& w : written)
+      if (may_overlap(r.out, w.first)) return false;
+    if (may_overlap(r.out, red_view)) return false;
+    return true;
+  }
+
+  void add_arg_pair(const RInstr& r, int idx) {
+    cur.has_red2 = true;
+    cur.red2_op = r.op;
+    cur.red2_out = slot_of(r.out, r.dt_out);
+    red2_view = r.out;
+    cur.instrs.push_back(idx);
+    last_instr = idx;
   }
 
   void run_all() {
@@ -316,6 +355,9 @@ struct Builder {
         if (open && fuse && cur.has_red) {
           if (can_merge_reduction(r, i)) {
             add_reduction(r, (int)i);
+            joined = true;
+          } else if (can_pair_arg(r)) {
+            add_arg_pair(r, (int)i);
             joined = true;
           }
         } else if (open && fuse && shape_is(x)) {
@@ -500,6 +542,7 @@ std::string plan_json(Ctx* c, const std::vector<RInstr>& prog, const Plan& p, bo
       for (size_t k = 0; k < r.red_axes.size(); ++k) os << (k ? "," : "") << r.red_axes[k];
       os << "],\"out\":" << r.red_out.base << "}";
     }
+    if (r.has_red2) os << ",\"reduce2\":{\"op\":\"" << op_name(r.red2_op) << "\",\"out\":" << r.red2_out.base << "}";
     std::vector<uintptr_t> lp(r.loads.size(), 0), sp(r.stores.size(), 0);
     Canon cn = canonicalize(r, true, lp, sp, 0);
     static const char* modes[] = {"elementwise", "full_reduce", "axis_thread", "axis_block"};

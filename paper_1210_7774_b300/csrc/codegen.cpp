@@ -43,6 +43,7 @@ struct Layout {
   int nout = -1, nred = -1;
   std::vector<int> lptr, lst, sptr, sst;
   int red_ptr = -1, red_st = -1, partials = -1, counter = -1;
+  int red2_ptr = -1, red2_st = -1;  // the paired index output (axis kernels)
   int idx_st = -1;
   std::vector<int> rnd;
   int consts = -1;
@@ -82,6 +83,11 @@ Layout layout_of(const Run& r, const Canon& c) {
     if (!tile_mode(c.spec.mode)) {
       L.red_st = w;
       w += c.spec.ndk;
+      if (r.has_red2) {
+        L.red2_ptr = w++;
+        L.red2_st = w;
+        w += c.spec.ndk;
+      }
     } else {
       L.partials = w++;
       L.counter = w++;
@@ -156,7 +162,7 @@ Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& l
     fail(VBE_ERR_INVALID, "internal: reduction output rank");
   // ARGMIN/ARGMAX keep the axis path (an index along the reduced axis)
   bool full = r.has_red && (int)r.red_axes.size() == D && r.red_op != VBE_OP_ARGMIN_REDUCE &&
-              r.red_op != VBE_OP_ARGMAX_REDUCE;
+              r.red_op != VBE_OP_ARGMAX_REDUCE && !r.has_red2;
   if (!r.has_red || full) {
     c.spec.mode = r.has_red ? Mode::FULL : Mode::ELEM;
     std::vector<int64_t> dims = r.shape;
@@ -230,12 +236,14 @@ Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& l
     sr.push_back(pick(s.st, red));
   }
   std::vector<int64_t> outk = r.red_out.st;  // already over the kept dims
+  std::vector<int64_t> outk2 = r.has_red2 ? r.red2_out.st : r.red_out.st;
   std::vector<int64_t> ik = pick(cst, kept), ir = pick(cst, red);
   {
     std::vector<std::vector<int64_t>*> L;
     for (auto& v : lk) L.push_back(&v);
     for (auto& v : sk) L.push_back(&v);
     L.push_back(&outk);
+    if (r.has_red2) L.push_back(&outk2);
     if (r.nrandom) L.push_back(&ik);
     coalesce(kd, L);
   }
@@ -269,6 +277,7 @@ Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& l
     c.spec.store_cls.push_back(cls_of(sr[s].back()));
   }
   c.red_st = outk;
+  if (r.has_red2) c.red2_st = outk2;
   c.idx_st = ik;
   c.idx_st.insert(c.idx_st.end(), ir.begin(), ir.end());
   int64_t nred = 1, nout = 1;
@@ -298,7 +307,8 @@ static int64_t const_bits(const Operand& o) {
 
 void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load_ptrs,
                 const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr, uintptr_t partials,
-                uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out, int64_t chunk, uintptr_t err) {
+                uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out, int64_t chunk, uintptr_t err,
+                uintptr_t red2_ptr) {
   (void)block;
   (void)U;
   Layout L = layout_of(r, c);
@@ -329,6 +339,10 @@ void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load
     w[L.red_ptr] = (int64_t)(red_ptr + (uintptr_t)(r.red_out.offset * itemsize(r.red_dtype)));
     if (L.red_st >= 0)
       for (size_t k = 0; k < c.red_st.size(); ++k) w[L.red_st + k] = c.red_st[k];
+    if (L.red2_ptr >= 0) {
+      w[L.red2_ptr] = (int64_t)(red2_ptr + (uintptr_t)(r.red2_out.offset * 8));
+      for (size_t k = 0; k < c.red2_st.size(); ++k) w[L.red2_st + k] = c.red2_st[k];
+    }
     if (L.partials >= 0) {
       w[L.partials] = (int64_t)partials;
       w[L.counter] = (int64_t)counter;
@@ -607,8 +621,13 @@ struct Gen {
   std::ostringstream o;
   const char* rt() const { return ctype(r.red_dtype); }
   bool kahan() const { return r.has_red && r.red_op == VBE_OP_ADD_REDUCE && r.red_dtype == VBE_FLOAT32; }
-  bool arg() const { return r.has_red && (r.red_op == VBE_OP_ARGMIN_REDUCE || r.red_op == VBE_OP_ARGMAX_REDUCE); }
-  bool argmax() const { return r.has_red && r.red_op == VBE_OP_ARGMAX_REDUCE; }
+  // ARGMIN/ARGMAX, or MIN/MAX paired with them: (value, index) pairs
+  bool arg() const {
+    return r.has_red && (r.red_op == VBE_OP_ARGMIN_REDUCE || r.red_op == VBE_OP_ARGMAX_REDUCE || r.has_red2);
+  }
+  bool argmax() const {
+    return r.has_red && (r.red_op == VBE_OP_ARGMAX_REDUCE || (r.has_red2 && r.red2_op == VBE_OP_ARGMAX_REDUCE));
+  }
   // type of the values an ARGMIN/ARGMAX compares
   std::string vt() const { return ctype(r.value_dtype[r.red_value]); }
 
@@ -753,6 +772,7 @@ struct Gen {
     for (size_t s = 0; s < r.stores.size(); ++s) o << ", " << ctype(r.stores[s].dtype) << "& o" << s;
     if (arg()) {
       o << ", " << vt() << "& acc, i64& acci, const i64 ai";
+      if (r.has_red2) o << ", " << rt() << "& accm";
     } else if (r.has_red) {
       o << ", " << rt() << "& acc";
       if (kahan()) o << ", float& kc";
@@ -766,6 +786,8 @@ struct Gen {
       std::string x = "v" + std::to_string(r.red_value);
       if (arg()) {
         o << "  vbe_arg_upd(acc, acci, " << x << ", ai, " << (argmax() ? "true" : "false") << ");\n";
+        // the paired MIN/MAX keeps its own value, combined as a lone one is
+        if (r.has_red2) o << "  accm = " << comb("accm", x) << ";\n";
       } else if (kahan()) {
         o << "  { const float y = " << x << " - kc; const float t = acc + y; kc = (t - acc) - y; acc = t; }\n";
       } else {
@@ -781,7 +803,7 @@ struct Gen {
       // (value, index) pairs: warp shuffles of both, then one warp over the
       // warps' pairs; returns the index of the block's best pair
       const std::string V = vt(), mx = argmax() ? "true" : "false";
-      o << "__device__ __forceinline__ i64 " << block_reduce_name << "(" << V << " v, i64 i) {\n"
+      o << "__device__ __forceinline__ i64 " << block_reduce_name << "(" << V << " v, i64 i, " << V << "& vout) {\n"
         << "  __shared__ " << V << " shv[32];\n  __shared__ i64 shi[32];\n"
         << "  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;\n"
         << "  for (int off = 16; off > 0; off >>= 1) { const " << V
@@ -793,10 +815,12 @@ struct Gen {
         << "    for (int off = 16; off > 0; off >>= 1) { const " << V
         << " tv = __shfl_down_sync(0xffffffffu, v, off); const i64 ti = __shfl_down_sync(0xffffffffu, i, off);"
         << " vbe_arg_upd(v, i, tv, ti, " << mx << "); }\n  }\n"
+        << "  if (threadIdx.x == 0) vout = v;\n"
         << "  __syncthreads();\n  return i;\n}\n";
-      return;
+      if (!r.has_red2) return;
     }
-    o << "__device__ __forceinline__ " << rt() << " " << block_reduce_name << "(" << rt() << " v) {\n"
+    o << "__device__ __forceinline__ " << rt() << " " << block_reduce_name << (arg() ? "_v" : "") << "(" << rt()
+      << " v) {\n"
       << "  __shared__ " << rt() << " sh[32];\n"
       << "  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;\n"
       << "  for (int off = 16; off > 0; off >>= 1) { " << rt() << " t = __shfl_down_sync(0xffffffffu, v, off); v = "
@@ -817,7 +841,7 @@ struct Gen {
     std::string s = "vbe_elem(p, " + m;
     for (auto& x : lv) s += ", " + x;
     for (auto& x : sv) s += ", " + x;
-    if (arg()) s += ", acc, acci, " + ai;
+    if (arg()) s += ", acc, acci, " + ai + (r.has_red2 ? ", accm" : "");
     else if (r.has_red) s += kahan() ? ", acc, kc" : ", acc";
     return s + ");";
   }
@@ -834,6 +858,7 @@ struct Gen {
     if (!r.has_red) return;
     if (arg()) {
       o << pfx << vt() << " acc = " << red_id() << ";\n" << pfx << "i64 acci = (i64)0x7fffffffffffffffll;\n";
+      if (r.has_red2) o << pfx << rt() << " accm = " << red_id() << ";\n";
       return;
     }
     o << pfx << rt() << " acc = " << red_id() << ";\n";
@@ -1195,6 +1220,7 @@ struct Gen {
     o << "extern \"C\" __global__ void __launch_bounds__(1024) vbe_@TAG@_axis(const P p) {\n"
       << "  vbe_grid_wait();\n";
     emit_pointers("  ");
+    if (r.has_red2) o << "  const auto rp2 = vbe_ptr<i64>(" << W(L.red2_ptr) << ");\n";
     o << "  const auto rp = vbe_ptr<" << rt() << ">(" << W(L.red_ptr) << ");\n"
       << "  const i64 nout = " << W(L.nout) << ", nred = " << W(L.nred) << ";\n";
     if (block)
@@ -1206,6 +1232,7 @@ struct Gen {
     for (size_t s = 0; s < r.loads.size(); ++s) ks.push_back({"lk" + std::to_string(s), L.lst[s]});
     for (size_t s = 0; s < r.stores.size(); ++s) ks.push_back({"sk" + std::to_string(s), L.sst[s]});
     ks.push_back({"rk", L.red_st});
+    if (r.has_red2) ks.push_back({"rk2", L.red2_st});
     if (L.idx_st >= 0) ks.push_back({"ik", L.idx_st});
     for (auto& k : ks) o << "    i64 " << k.first << " = 0;\n";
     o << "    { i64 rr = oi;\n";
@@ -1334,8 +1361,14 @@ struct Gen {
     element("      ", "", "ri", false);
     o << "    }\n";
     if (vec_gen) o << "    }\n";
-    if (arg() && block) {
-      o << "    { const i64 v = " << block_reduce_name << "(acc, acci); if (threadIdx.x == 0) rp[rk] = v; }\n";
+    if (arg() && r.has_red2 && block) {
+      o << "    { " << vt() << " bv; const i64 bi = " << block_reduce_name << "(acc, acci, bv); const " << rt()
+        << " mv = " << block_reduce_name << "_v(accm); if (threadIdx.x == 0) { rp[rk] = mv; rp2[rk2] = bi; } }\n";
+    } else if (arg() && r.has_red2) {
+      o << "    rp[rk] = accm;\n    rp2[rk2] = acci;\n";
+    } else if (arg() && block) {
+      o << "    { " << vt() << " bv; const i64 v = " << block_reduce_name
+        << "(acc, acci, bv); if (threadIdx.x == 0) rp[rk] = v; }\n";
     } else if (arg()) {
       o << "    rp[rk] = acci;\n";
     } else if (block) {
@@ -1366,6 +1399,7 @@ static std::string signature(const Run& r, const Canon& c) {
   put((int64_t)r.stores.size());
   for (size_t q = 0; q < r.stores.size(); ++q) { put(r.stores[q].dtype); put(r.store_value[q]); }
   put(r.has_red); put(r.red_op); put(r.red_dtype); put(r.red_value); put(r.nrandom); put(r.soft_f64);
+  put(r.has_red2); put(r.red2_op);
   put((int64_t)r.consts.size());
   for (auto& o : r.consts) put(o.dtype);
   const Spec& p = c.spec;

@@ -87,6 +87,7 @@ std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const 
     // a reduction over the whole run (both dims) can stay: each of its
     // points must then belong to exactly one tile (checked with the margins)
     if (r.has_red && r.red_axes != std::vector<int>{0, 1}) return nullptr;
+    if (r.has_red2) return nullptr;
     // two strides per view, small enough for 32-bit offsets inside a tile
     for (auto* v : {&r.loads, &r.stores})
       for (auto& s : *v)

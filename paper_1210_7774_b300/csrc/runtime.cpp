@@ -415,7 +415,7 @@ void issue(Ctx* c, Exec* ex, Launch& L, bool capturing) {
 
 struct RunPtrs {
   std::vector<uintptr_t> lp, sp;
-  uintptr_t rp = 0;
+  uintptr_t rp = 0, rp2 = 0;  // reduction output, paired index output
 };
 
 RunPtrs run_ptrs(Ctx* c, const Run& r) {
@@ -423,6 +423,7 @@ RunPtrs run_ptrs(Ctx* c, const Run& r) {
   for (auto& s : r.loads) p.lp.push_back(base_ptr(c, s.base));
   for (auto& s : r.stores) p.sp.push_back(base_ptr(c, s.base));
   if (r.has_red) p.rp = base_ptr(c, r.red_out.base);
+  if (r.has_red2) p.rp2 = base_ptr(c, r.red2_out.base);
   return p;
 }
 
@@ -436,6 +437,7 @@ void allocate_outputs(Ctx* c, Exec* ex, const Run& r) {
   };
   for (auto& s : r.stores) need(s.base);
   if (r.has_red) need(r.red_out.base);
+  if (r.has_red2) need(r.red2_out.base);
   for (auto& s : r.loads) {
     BaseRec& br = c->bases[s.base];
     if (!br.dptr) fail(VBE_ERR_UNINIT, "a run reads base " + std::to_string(s.base) + " which was never written");
@@ -553,7 +555,7 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
       int64_t cap = (int64_t)occupancy(L.fn, 128) * c->sm_count;
       L.grid = (unsigned)std::max<int64_t>(1, std::min((nout + 127) / 128, cap));
     }
-    fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, 0, 0, L.block, 1, &a);
+    fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, 0, 0, L.block, 1, &a, 0, 0, ptr.rp2);
   }
   L.words = std::move(a.w);
   return L;
@@ -703,6 +705,8 @@ bool independent(const Run& a, const Run& b, Ctx* c) {
   };
   if (a.has_red) wa.push_back(view_of(a.red_out, kept(a)));
   if (b.has_red) wb.push_back(view_of(b.red_out, kept(b)));
+  if (a.has_red2) wa.push_back(view_of(a.red2_out, kept(a)));
+  if (b.has_red2) wb.push_back(view_of(b.red2_out, kept(b)));
   for (auto& x : wb) {
     for (auto& y : ra) if (may_overlap(x, y)) return false;
     for (auto& y : wa) if (may_overlap(x, y)) return false;
@@ -1218,6 +1222,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
           fail(VBE_ERR_UNINIT, "the batch reads base " + std::to_string(s.base) + " before anything wrote it");
       for (auto& s : it.run.stores) avail.insert(s.base);
       if (it.run.has_red) avail.insert(it.run.red_out.base);
+      if (it.run.has_red2) avail.insert(it.run.red2_out.base);
     }
   }
   // capture needs every store target (and second buffer) allocated already
@@ -1234,6 +1239,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       for (auto& s : it.run.stores)
         if (!c->bases[s.base].dptr) capture = false;
       if (it.run.has_red && !c->bases[it.run.red_out.base].dptr) capture = false;
+      if (it.run.has_red2 && !c->bases[it.run.red2_out.base].dptr) capture = false;
     }
   }
 

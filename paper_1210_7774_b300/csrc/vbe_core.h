@@ -129,6 +129,11 @@ struct Run {
   int red_op = 0, red_dtype = 0, red_value = -1;
   std::vector<int> red_axes;  // run dims that are reduced (sorted)
   Slot red_out;               // strides over the kept dims, in order
+  // MIN_REDUCE (MAX_REDUCE) followed by ARGMIN_REDUCE (ARGMAX_REDUCE) of the
+  // same view over the same axis: one pass writes both (red2_out: int64)
+  bool has_red2 = false;
+  int red2_op = 0;
+  Slot red2_out;
   std::vector<int> instrs;    // batch indices
   int nrandom = 0;
   std::vector<Operand> consts;  // constant operands, passed as parameter words
@@ -198,6 +203,7 @@ struct Canon {  // a run in the form the generated kernel consumes
   std::vector<int64_t> dims;          // ELEM/FULL dims, or kept dims then reduced dims
   std::vector<std::vector<int64_t>> lst, sst;  // per slot strides over dims
   std::vector<int64_t> red_st;        // reduction output strides over kept dims
+  std::vector<int64_t> red2_st;       // the paired index output's strides over kept dims
   std::vector<int64_t> idx_st;        // RANDOM linear index strides over dims
   int64_t total = 0;
 };
@@ -214,7 +220,7 @@ struct LaunchArgs {
 void fill_words(const Run& r, const Canon& c, const std::vector<uintptr_t>& load_ptrs,
                 const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr, uintptr_t partials,
                 uintptr_t counter, int64_t block, int64_t U, LaunchArgs* out, int64_t chunk = 0,
-                uintptr_t err = 0);
+                uintptr_t err = 0, uintptr_t red2_ptr = 0);
 int words_count(const Run& r, const Canon& c);
 
 // tensor-copy boxes of a group's staged inputs for one tile shape: per staged

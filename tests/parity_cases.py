@@ -389,6 +389,35 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
                 b.emit(op, b.whole(o), b.whole(xb), axis=ax)
                 p = b.build([o])
                 out.append(Case(p.name, p, _exact_check(p)))
+    # MIN_REDUCE (MAX_REDUCE) followed by ARGMIN_REDUCE (ARGMAX_REDUCE) of the
+    # same view over the same axis, run as one pass: ties, NaNs, infinities
+    # and zeros of both signs; thread and block per output. Indices bit-exact;
+    # the minimum's value exact up to the sign of a zero minimum, which
+    # depends on the combining order (as for any reduction)
+    for dt in ("float64", "float32", "int64"):
+        for shp, ax in (((7, 3001), 1), ((3001, 7), 0), ((9, 33, 70), 2), ((9, 33, 70), 0)):
+            n = int(np.prod(shp))
+            x = rng.integers(-2, 3, n).astype(dt)
+            if dt != "int64":
+                x[rng.random(n) < 0.3] = -0.0
+                sp = rng.random(n) < 0.01
+                x[sp] = lv[rng.integers(0, len(lv), int(sp.sum()))].astype(dt)
+            oshape = tuple(s_ for k, s_ in enumerate(shp) if k != ax)
+            for mop, aop in (("MIN_REDUCE", "ARGMIN_REDUCE"), ("MAX_REDUCE", "ARGMAX_REDUCE")):
+                b = ProgramBuilder(f"{mop}_{aop}_{dt}_{len(shp)}d_ax{ax}")
+                xb = b.base(dt, shp, x)
+                mv = b.base(dt, oshape)
+                ix = b.base("int64", oshape)
+                b.emit(mop, b.whole(mv), b.whole(xb), axis=ax)
+                b.emit(aop, b.whole(ix), b.whole(xb), axis=ax)
+                p = b.build([mv, ix])
+
+                def pchk(got, want, mv=mv, ix=ix, p=p):
+                    assert_exact(got[ix], want[ix], p.name + " indices")
+                    g, w = got[mv], want[mv]
+                    same = (g == w) | (np.isnan(g) & np.isnan(w)) if g.dtype.kind == "f" else g == w
+                    assert np.all(same), f"{p.name} values: {np.sum(~same)} mismatches"
+                out.append(Case(p.name, p, pchk))
     # fused chain with a full reduction and with an axis reduction, plus stores
     for dt in ("float64", "float32"):
         b = ProgramBuilder(f"chain_full_{dt}")

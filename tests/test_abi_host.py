@@ -283,6 +283,31 @@ def test_generated_source_is_plain_cuda(fused):
     assert "__fmaf" not in src and "fma(" not in src
 
 
+def test_min_and_argmin_of_one_view_share_a_pass(fused):
+    """kNN: each round's MIN_REDUCE and the ARGMIN_REDUCE of the same view
+    and axis right after it are one run (one read of the distances), in the
+    first round and after the masking; the plain path keeps them apart."""
+    from workloads import knn
+    p = knn(300, 20, 8, 3)
+    L = fused.load(p, upload=False)
+    runs, _ = runs_of(fused, L)
+    paired = [r for r in runs if "reduce2" in r]
+    assert len(paired) == 3
+    assert all(r["reduce"]["op"] == "MIN_REDUCE" and r["reduce2"]["op"] == "ARGMIN_REDUCE" for r in paired)
+    assert all(r["mode"].startswith("axis") for r in paired)
+    # a MIN over one view and an ARGMIN over another are not paired
+    b = ProgramBuilder("unpaired")
+    x = b.base("float64", (4, 50), np.arange(200, dtype=np.float64))
+    y = b.base("float64", (4, 50), np.arange(200, dtype=np.float64)[::-1].copy())
+    m = b.base("float64", 4)
+    i = b.base("int64", 4)
+    b.emit("MIN_REDUCE", b.whole(m), b.whole(x), axis=1)
+    b.emit("ARGMIN_REDUCE", b.whole(i), b.whole(y), axis=1)
+    L = fused.load(b.build([m, i]), upload=False)
+    runs, _ = runs_of(fused, L)
+    assert not any("reduce2" in r for r in runs) and len(runs) == 2
+
+
 def test_power_of_two_constants_get_their_own_kernel(fused):
     """Float64 products by a constant +-2^k are formed by moving the exponent
     field; whether a constant is such a power is part of the kernel's
