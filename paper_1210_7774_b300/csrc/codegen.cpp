@@ -1692,11 +1692,12 @@ bool group_stacked(const Group& g) {
 }
 
 // Tensor copies need whole rows (the base a whole number of rows of the
-// row stride), 16-byte row strides, and no reduction (the persistent form
-// keeps no per-tile reduction state).
+// row stride) and 16-byte row strides; a reduction only in a group whose
+// values stay in registers (its persistent blocks accumulate over all their
+// tiles and combine once, after the tile loop).
 bool tma_ok(const Group& g) {
   for (auto& r : g.runs)
-    if (r.has_red) return false;
+    if (r.has_red && !group_stacked(g)) return false;
   for (auto& b : staging_plan(g)) {
     const Slot& ref = g.runs[b.ref_k].loads[b.ref_s];
     const int64_t P = ref.st[0], ne = g.base_nelem.at(b.base);
@@ -1747,7 +1748,8 @@ std::vector<TileShape> group_shapes(const Group& g) {
 // depends on them), and the producer waits, bounded, for its copies in
 // flight before it leaves.
 static void emit_tma_prologue(std::ostringstream& o, const Group& g, const GroupLayout& GL, const TileShape& ts,
-                              const std::vector<StagedBase>& sp, const std::vector<int64_t>& sgoff, int64_t total) {
+                              const std::vector<StagedBase>& sp, const std::vector<int64_t>& sgoff, int64_t total,
+                              const std::string& pre) {
   auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
   const int nb = (int)sp.size();
   const int NS = tma_stages(g);
@@ -1769,6 +1771,7 @@ static void emit_tma_prologue(std::ostringstream& o, const Group& g, const Group
     << "    vbe_fence_mbar_init();\n"
     << "  }\n"
     << "  __syncthreads();\n"
+    << pre
     << "  const i64 ntiles = p.w[3], tpr = p.w[2];\n"
     << "  if (threadIdx.x >= " << ts.block << ") {\n"
     << "    if (threadIdx.x == " << ts.block << ") {  // the producer\n"
@@ -1913,7 +1916,7 @@ static void emit_stacked(std::ostringstream& o, const Group& g, const GroupLayou
   int red = -1;
   for (int k = 0; k < m; ++k)
     if (g.runs[k].has_red) red = k;
-  if (red >= 0) {
+  if (red >= 0 && !ts.tma) {  // the tensor-copy form accumulates across its tiles
     gens[red]->o.str("");
     gens[red]->emit_acc_init("    ");
     o << gens[red]->o.str();
@@ -1965,7 +1968,7 @@ static void emit_stacked(std::ostringstream& o, const Group& g, const GroupLayou
   o << "    } else {\n";
   loop(true);
   o << "    }\n";
-  if (red >= 0) {
+  if (red >= 0 && !ts.tma) {
     const int w = GL.red[red];
     gens[red]->o.str("");
     gens[red]->emit_full_epilogue("    ", W(w + 1), "blockIdx.x", W(w + 2), "gridDim.x", W(w));
@@ -2058,7 +2061,16 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     const auto six = staged_index(g, sp);
     const std::vector<int64_t> sgoff = staged_smem(sp, ts.th, ts.tw, &total, ts.tma ? tma_stages(g) : 0);
     if (ts.tma) {
-      emit_tma_prologue(o, g, GL, ts, sp, sgoff, total);
+      // a reduction accumulates over all of a block's tiles (every thread,
+      // the producer warp's at the identity) and is combined after the loop
+      std::string pre;
+      for (int k = 0; k < m; ++k)
+        if (g.runs[k].has_red) {
+          gens[k]->o.str("");
+          gens[k]->emit_acc_init("  ");
+          pre = gens[k]->o.str();
+        }
+      emit_tma_prologue(o, g, GL, ts, sp, sgoff, total, pre);
     } else {
       o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << ") vbe_@TAG@" << ts.suffix()
         << "(const P p) {\n"
@@ -2220,7 +2232,16 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
       o << "    }\n";
     }
     }
-    if (ts.tma) emit_tma_epilogue(o, g, ts);
+    if (ts.tma) {
+      emit_tma_epilogue(o, g, ts);
+      for (int k = 0; k < m; ++k)
+        if (g.runs[k].has_red) {
+          const int w = GL.red[k];
+          gens[k]->o.str("");
+          gens[k]->emit_full_epilogue("  ", W(w + 1), "blockIdx.x", W(w + 2), "gridDim.x", W(w));
+          o << gens[k]->o.str();
+        }
+    }
     else o << "  }\n";
     emit_copy_through(o, g, GL);
     o << "}\n";

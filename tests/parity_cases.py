@@ -491,17 +491,23 @@ def knn_check(p, rows=None):
     return check
 
 
-def workload_cases(scale="small"):
-    out = []
-    n = 24 if scale == "small" else 256
-    p = jacobi(n, 3 if scale == "small" else 10)
+def jacobi_case(n, iters):
+    """Jacobi on an n x n grid: the grid bit-exact, the deltas within the
+    reduction tolerance."""
+    p = jacobi(n, iters)
 
     def jchk(got, want, p=p):
         assert_exact(got[p.meta["grid"]], want[p.meta["grid"]], "jacobi grid")
         g0 = p.bases[p.meta["grid"]].init.reshape(n, n)
         assert_close_sum(got[p.meta["deltas"]], want[p.meta["deltas"]],
                          np.full(want[p.meta["deltas"]].size, np.sum(np.abs(g0)) * 2), F64_REDUCE_RTOL, "jacobi deltas")
-    out.append(Case(p.name, p, jchk))
+    return Case(p.name, p, jchk)
+
+
+def workload_cases(scale="small"):
+    out = []
+    n = 24 if scale == "small" else 256
+    out.append(jacobi_case(n, 3 if scale == "small" else 10))
     nb = 3000 if scale == "small" else 100_000
     for dt, rtol in (("float64", 1e-12), ("float32", 1e-5)):
         p = blackscholes(nb, dt, seed=11)

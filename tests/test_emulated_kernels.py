@@ -17,7 +17,8 @@ from paper_1210_7774_b300 import vbe as V  # noqa: E402
 from paper_1210_7774_b300.runner import Executor  # noqa: E402
 
 from emu.emulator import Emulator  # noqa: E402
-from parity_cases import Case, _exact_check, all_small_cases, oracle_outputs, tile_group_cases  # noqa: E402
+from parity_cases import (Case, _exact_check, all_small_cases, jacobi_case, oracle_outputs,  # noqa: E402
+                          tile_group_cases)
 from workloads import shallow_water  # noqa: E402
 
 CASES = all_small_cases()
@@ -102,6 +103,7 @@ def test_emulated_tile_groups(tile):
     cases = tile_group_cases()
     if tile.startswith("t"):  # rows of 16-byte multiples, as tensor copies need
         cases += tile_group_cases(seed=12, N=37, M=52)
+        cases.append(jacobi_case(66, 3))  # stencil, reductions and copy back: a group with a whole-run reduction
     for dt in ("float64", "float32"):
         p = shallow_water(40, 2, dt)
         cases.append(Case(p.name, p, _exact_check(p)))

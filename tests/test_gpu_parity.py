@@ -16,7 +16,7 @@ from paper_1210_7774_b300.runner import Executor  # noqa: E402
 
 import oracle  # noqa: E402
 from parity_cases import (F64_REDUCE_RTOL, Case, _exact_check, all_small_cases, assert_close_sum,  # noqa: E402
-                          assert_exact, oracle_outputs, tile_group_cases, workload_cases)
+                          assert_exact, jacobi_case, oracle_outputs, tile_group_cases, workload_cases)
 from workloads import (blackscholes, bs_inputs, gray_scott, jacobi, knn, knn_inputs, mc_sizes,  # noqa: E402
                        montecarlo_pi, shallow_water, sw_inputs)
 
@@ -139,9 +139,10 @@ def test_tile_group_forms_exact(tile):
     shared memory ("s"), or prefetched by double-buffered tensor copies into
     persistent blocks that walk several tiles each ("t"). Bit-exact with the
     oracle on the synthetic chains (rows of 16-byte multiples, ragged against
-    every tile), shallow water (state renamed every step) and Gray-Scott at
-    2050 x 1032 (about 2,000 tiles), float64 and float32."""
-    cases = tile_group_cases(seed=12, N=37, M=52)
+    every tile), Jacobi 514^2 (a group with a whole-run reduction: deltas
+    within the reduction tolerance), shallow water (state renamed every step)
+    and Gray-Scott at 2050 x 1032 (about 2,000 tiles), float64 and float32."""
+    cases = tile_group_cases(seed=12, N=37, M=52) + [jacobi_case(514, 3)]
     for dt in ("float64", "float32"):
         for p in (shallow_water(256, 2, dt), gray_scott(2050, 1032, 2, dt)):
             cases.append(Case(p.name, p, _exact_check(p)))
