@@ -325,9 +325,10 @@ def other_workload(args, local):
 
     if args.workload == "jacobi":
         from workloads import jacobi
+        only_paper = args.paths == "paper_size"  # profiling: the 7168^2 part alone
         p = jacobi(256, 10)
         cbytes = 256 * 256 * 8 + 254 * 254 * 8  # read the grid, write the interior, per iteration
-        for name, flags in modes.items():
+        for name, flags in ({} if only_paper else modes).items():
             # host-bound at this size: enough warm-up for the host path to settle
             sec, st = timed_batches(p, flags, 100, warmup=20)
             out[name] = {"us_per_iteration": sec / 10 * 1e6, "GB/s": cbytes * 10 / sec / 1e9}
@@ -475,7 +476,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtypes", default="float64,float32", help="profiling: restrict the dtypes run")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
-    ap.add_argument("--paths", default="fused,plain", help="profiling: restrict the paths run")
+    ap.add_argument("--paths", default="fused,plain", help="profiling: restrict the paths run (jacobi: paper_size runs the 7168^2 part alone)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
