@@ -1994,7 +1994,120 @@ std::vector<TmaBox> group_tma_boxes(const Group& g, const TileShape& ts) {
   return out;
 }
 
+// Everything a group's source depends on, as a key: the runs (views with
+// their bases numbered by first appearance, operations, constants,
+// reductions), the shifts, margins, renamed bases and base sizes. Planning
+// the same group again (every iteration of a solver, every request of a
+// shape) then reuses its source instead of generating it anew.
+static std::string group_key(const Group& g) {
+  std::string k;
+  std::vector<int64_t> ids;
+  auto put = [&](int64_t v) { k.append((const char*)&v, sizeof v); };
+  auto bid = [&](int64_t b) {
+    for (size_t i = 0; i < ids.size(); ++i)
+      if (ids[i] == b) return (int64_t)i;
+    ids.push_back(b);
+    return (int64_t)ids.size() - 1;
+  };
+  auto slot = [&](const Slot& sl) {
+    put(bid(sl.base));
+    put(sl.offset);
+    put(sl.dtype);
+    put((int64_t)sl.st.size());
+    for (auto v : sl.st) put(v);
+  };
+  auto operand = [&](const Operand& a) {
+    int64_t fb;
+    memcpy(&fb, &a.f, 8);
+    put(a.kind);
+    put(a.idx);
+    put(a.dtype);
+    put(a.i);
+    put(fb);
+  };
+  put((int64_t)g.runs.size());
+  for (auto& r : g.runs) {
+    put((int64_t)r.shape.size());
+    for (auto v : r.shape) put(v);
+    put((int64_t)r.loads.size());
+    for (auto& sl : r.loads) slot(sl);
+    put((int64_t)r.stores.size());
+    for (auto& sl : r.stores) slot(sl);
+    for (int v : r.store_value) put(v);
+    put((int64_t)r.steps.size());
+    for (auto& st : r.steps) {
+      put(st.op); put(st.dt_out); put(st.dt_in); put(st.nin); put(st.value); put(st.random_idx);
+      for (int a = 0; a < st.nin; ++a) operand(st.a[a]);
+    }
+    put((int64_t)r.value_dtype.size());
+    for (int d : r.value_dtype) put(d);
+    put(r.has_red); put(r.red_op); put(r.red_dtype); put(r.red_value);
+    put((int64_t)r.red_axes.size());
+    for (int a : r.red_axes) put(a);
+    if (r.has_red) slot(r.red_out);
+    put(r.has_red2); put(r.red2_op);
+    if (r.has_red2) slot(r.red2_out);
+    put(r.nrandom);
+    put((int64_t)r.consts.size());
+    for (auto& o : r.consts) operand(o);
+    put(r.soft_f64);
+  }
+  for (auto& b : g.box)
+    for (int v : b) put(v);
+  for (auto& l : g.lds) {
+    put((int64_t)l.size());
+    for (auto& x : l) { put(x.prod); put(x.prod_store); put(x.dr); put(x.dc); }
+  }
+  for (auto& c : g.consumed) {
+    put((int64_t)c.size());
+    for (char x : c) put(x);
+  }
+  put((int64_t)g.renamed.size());
+  for (size_t i = 0; i < g.renamed.size(); ++i) {
+    put(bid(g.renamed[i]));
+    put(g.renamed_slot[i]);
+    put(g.renamed_nelem[i]);
+  }
+  put((int64_t)g.base_nelem.size());
+  for (int64_t b : ids) {
+    auto it = g.base_nelem.find(b);
+    put(it == g.base_nelem.end() ? -1 : it->second);
+  }
+  return k;
+}
+
+static std::string generate_group_source_uncached(const Group& g, std::string* entry_prefix,
+                                                  std::vector<TileShape>* shapes_out);
+
 std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes_out) {
+  struct Entry {
+    std::string src, prefix;
+    std::vector<TileShape> shapes;
+  };
+  static std::mutex mu;
+  static std::unordered_map<std::string, Entry> memo;
+  const std::string key = group_key(g);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) {
+      if (entry_prefix) *entry_prefix = it->second.prefix;
+      if (shapes_out) *shapes_out = it->second.shapes;
+      return it->second.src;
+    }
+  }
+  Entry e;
+  e.src = generate_group_source_uncached(g, &e.prefix, &e.shapes);
+  if (entry_prefix) *entry_prefix = e.prefix;
+  if (shapes_out) *shapes_out = e.shapes;
+  std::lock_guard<std::mutex> lk(mu);
+  if (memo.size() > 1024) memo.clear();
+  memo[key] = e;
+  return e.src;
+}
+
+static std::string generate_group_source_uncached(const Group& g, std::string* entry_prefix,
+                                                  std::vector<TileShape>* shapes_out) {
   const int m = (int)g.runs.size();
   const int anchor = m - 1;
   GroupLayout GL = group_layout(g);
