@@ -1414,25 +1414,31 @@ static std::string generate_source_uncached(const Run& r, const Canon& c, std::s
 
 // Generated sources are memoised by signature: a serving loop or a long
 // batch plans many runs of a few signatures.
-std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix) {
+std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix, std::string* key_out) {
+  struct Entry {
+    std::string src, prefix, key;
+  };
   static std::mutex mu;
-  static std::unordered_map<std::string, std::pair<std::string, std::string>> memo;
+  static std::unordered_map<std::string, Entry> memo;
   const std::string key = signature(r, c);
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = memo.find(key);
     if (it != memo.end()) {
-      if (entry_prefix) *entry_prefix = it->second.second;
-      return it->second.first;
+      if (entry_prefix) *entry_prefix = it->second.prefix;
+      if (key_out) *key_out = it->second.key;
+      return it->second.src;
     }
   }
-  std::string prefix;
-  std::string src = generate_source_uncached(r, c, &prefix);
+  Entry e;
+  e.src = generate_source_uncached(r, c, &e.prefix);
+  e.key = src_key(e.src);
+  if (entry_prefix) *entry_prefix = e.prefix;
+  if (key_out) *key_out = e.key;
   std::lock_guard<std::mutex> lk(mu);
   if (memo.size() > 4096) memo.clear();
-  memo[key] = {src, prefix};
-  if (entry_prefix) *entry_prefix = prefix;
-  return src;
+  memo[key] = e;
+  return e.src;
 }
 
 static std::string generate_source_uncached(const Run& r, const Canon& c, std::string* entry_prefix) {
@@ -2079,9 +2085,10 @@ static std::string group_key(const Group& g) {
 static std::string generate_group_source_uncached(const Group& g, std::string* entry_prefix,
                                                   std::vector<TileShape>* shapes_out);
 
-std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes_out) {
+std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes_out,
+                                  std::string* key_out) {
   struct Entry {
-    std::string src, prefix;
+    std::string src, prefix, key;
     std::vector<TileShape> shapes;
   };
   static std::mutex mu;
@@ -2093,13 +2100,16 @@ std::string generate_group_source(const Group& g, std::string* entry_prefix, std
     if (it != memo.end()) {
       if (entry_prefix) *entry_prefix = it->second.prefix;
       if (shapes_out) *shapes_out = it->second.shapes;
+      if (key_out) *key_out = it->second.key;
       return it->second.src;
     }
   }
   Entry e;
   e.src = generate_group_source_uncached(g, &e.prefix, &e.shapes);
+  e.key = src_key(e.src);
   if (entry_prefix) *entry_prefix = e.prefix;
   if (shapes_out) *shapes_out = e.shapes;
+  if (key_out) *key_out = e.key;
   std::lock_guard<std::mutex> lk(mu);
   if (memo.size() > 1024) memo.clear();
   memo[key] = e;

@@ -54,7 +54,7 @@ static std::vector<char> nvrtc_compile(const std::string& src, std::string* log)
   return cubin;
 }
 
-static std::string src_key(const std::string& src) {
+std::string src_key(const std::string& src) {
   return hex64(hash64(src.data(), src.size(), 1)) + hex64(hash64(src.data(), src.size(), 0x5bd1e995ull));
 }
 
@@ -88,14 +88,15 @@ std::vector<char> compile_cached(Ctx* c, const std::string& src, bool* compiled)
 
 // Compile, in parallel threads, every source not loaded yet (first sight
 // of a batch), then load the modules.
-void precompile(Ctx* c, const std::vector<std::string>& srcs) {
-  std::vector<std::string> todo;
+void precompile(Ctx* c, const std::vector<std::string>& srcs, const std::vector<std::string>* keys) {
+  std::vector<std::string> todo, todo_keys;
   std::set<std::string> seen;
-  for (auto& s : srcs) {
-    std::string k = src_key(s);
+  for (size_t i = 0; i < srcs.size(); ++i) {
+    const std::string k = keys ? (*keys)[i] : src_key(srcs[i]);
     if (c->kernels.count(k) || seen.count(k)) continue;
     seen.insert(k);
-    todo.push_back(s);
+    todo.push_back(srcs[i]);
+    todo_keys.push_back(k);
   }
   if (todo.size() <= 1) return;
   std::vector<std::vector<char>> bins(todo.size());
@@ -131,12 +132,12 @@ void precompile(Ctx* c, const std::vector<std::string>& srcs) {
     auto k = std::make_shared<Kernel>();
     cuda_check(cudaLibraryLoadData(&k->lib, bins[i].data(), nullptr, nullptr, 0, nullptr, nullptr, 0),
                "cudaLibraryLoadData");
-    c->kernels[src_key(todo[i])] = k;
+    c->kernels[todo_keys[i]] = k;
   }
 }
 
-std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src) {
-  std::string key = src_key(src);
+std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src, const std::string* key_in) {
+  const std::string key = key_in ? *key_in : src_key(src);
   auto it = c->kernels.find(key);
   if (it != c->kernels.end()) return it->second;
   if (c->record) {
@@ -489,7 +490,7 @@ struct Prepared {
   std::string prefix;  // kernel name prefix
 };
 
-std::string tune_key(const std::string& src, const Canon& cn) {
+std::string tune_key(const std::string& key, const Canon& cn) {
   // tuned per signature and per size class (log2 of the element count)
   int lg = 0;
   int64_t n = std::max<int64_t>(1, cn.total);
@@ -497,7 +498,7 @@ std::string tune_key(const std::string& src, const Canon& cn) {
     n >>= 1;
     ++lg;
   }
-  return src_key(src) + ":" + std::to_string(lg);
+  return key + ":" + std::to_string(lg);
 }
 
 Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const RunPtrs& ptr) {
@@ -660,7 +661,7 @@ TuneChoice choose(Ctx* c, Exec* ex, Prepared& P, const RunPtrs& ptr, bool may_tu
     tc.bulk_chunk = c->force_bulk;
     return tc;
   }
-  std::string tk = tune_key(P.src, P.canon);
+  std::string tk = tune_key(P.key, P.canon);
   auto it = c->tune.find(tk);
   if (it != c->tune.end()) return it->second;
   TuneChoice tc;
@@ -888,7 +889,7 @@ std::string group_tune_key(const GroupPrepared& G) {
     n >>= 1;
     ++lg;
   }
-  return src_key(G.src) + ":" + std::to_string(lg);
+  return G.key + ":" + std::to_string(lg);
 }
 
 // the tile shape: fixed in record mode (VBE_RECORD_TILE=THxTW), else timed
@@ -1020,9 +1021,8 @@ bool group_split(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const 
     if (k == anchor)
       for (size_t s = 0; s < r.stores.size(); ++s) rp.sp[s] = scratch_for(r.stores[s], r.shape);
     P.canon = canonicalize(r, true, rp.lp, rp.sp, rp.rp);
-    P.src = generate_source(r, P.canon, &P.prefix);
-    P.key = src_key(P.src);
-    P.kern = get_kernel(c, P.src);
+    P.src = generate_source(r, P.canon, &P.prefix, &P.key);
+    P.kern = get_kernel(c, P.src, &P.key);
     TuneChoice tc = choose(c, ex, P, rp, true);
     sep.push_back(build_single(c, ex, P, tc, rp));
   }
@@ -1185,10 +1185,11 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
 
   // compile the batch's kernels in parallel on first sight
   {
-    std::vector<std::string> srcs;
+    std::vector<std::string> srcs, keys;
     for (auto& it : plan.items) {
       if (it.kind == 2) {
-        srcs.push_back(generate_group_source(*it.group, nullptr, nullptr));
+        keys.emplace_back();
+        srcs.push_back(generate_group_source(*it.group, nullptr, nullptr, &keys.back()));
         continue;
       }
       if (it.kind != 0) continue;
@@ -1196,9 +1197,10 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       for (auto& s : it.run.loads) pp.lp.push_back((uintptr_t)c->bases[s.base].dptr);
       for (auto& s : it.run.stores) pp.sp.push_back((uintptr_t)c->bases[s.base].dptr);
       Canon cn = canonicalize(it.run, true, pp.lp, pp.sp, 0);
-      srcs.push_back(generate_source(it.run, cn, nullptr));
+      keys.emplace_back();
+      srcs.push_back(generate_source(it.run, cn, nullptr, &keys.back()));
     }
-    if (!c->record) precompile(c, srcs);
+    if (!c->record) precompile(c, srcs, &keys);
   }
   // first pass: allocation order and reads of never-written bases
   {
@@ -1269,9 +1271,8 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       allocate_group(c, ex, g);
       GroupPrepared G;
       G.g = &g;
-      G.src = generate_group_source(g, &G.prefix, &G.shapes);
-      G.key = src_key(G.src);
-      G.kern = get_kernel(c, G.src);
+      G.src = generate_group_source(g, &G.prefix, &G.shapes, &G.key);
+      G.kern = get_kernel(c, G.src, &G.key);
       GroupPtrs ptr = group_ptrs(c, g);
       TileShape ts = choose_group(c, ex, G, ptr, !capture);
       if (group_split(c, ex, G, ts, ptr, !capture)) {
@@ -1284,9 +1285,8 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
           P.run = &r;
           RunPtrs rp = run_ptrs(c, r);
           P.canon = canonicalize(r, true, rp.lp, rp.sp, rp.rp);
-          P.src = generate_source(r, P.canon, &P.prefix);
-          P.key = src_key(P.src);
-          P.kern = get_kernel(c, P.src);
+          P.src = generate_source(r, P.canon, &P.prefix, &P.key);
+          P.kern = get_kernel(c, P.src, &P.key);
           TuneChoice tc = choose(c, ex, P, rp, !capture);
           Launch L = build_single(c, ex, P, tc, rp);
           if (capture) {
@@ -1326,9 +1326,8 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
     P.run = &r;
     RunPtrs ptr = run_ptrs(c, r);
     P.canon = canonicalize(r, true, ptr.lp, ptr.sp, ptr.rp);
-    P.src = generate_source(r, P.canon, &P.prefix);
-    P.key = src_key(P.src);
-    P.kern = get_kernel(c, P.src);
+    P.src = generate_source(r, P.canon, &P.prefix, &P.key);
+    P.kern = get_kernel(c, P.src, &P.key);
     bool tile = P.canon.spec.mode == Mode::ELEM || P.canon.spec.mode == Mode::FULL;
     // packing: following runs with the same kernel that share no data
     std::vector<size_t> group{i};

@@ -210,7 +210,9 @@ struct Canon {  // a run in the form the generated kernel consumes
 
 Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& load_ptrs,
                    const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr);
-std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix);
+// key_out: the source's cache key (src_key), kept with the memoised source
+std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix, std::string* key_out = nullptr);
+std::string src_key(const std::string& src);  // two 64-bit hashes of the source text
 std::vector<std::pair<const char*, const char*>> nvrtc_headers();  // (include name, text)
 
 // words of the kernel parameter block, in the order the generated code reads them
@@ -245,7 +247,8 @@ struct TileShape {
     return std::string(tma ? "_tm" : (staged ? "_ss" : "_sg")) + std::to_string(th) + "x" + std::to_string(tw);
   }
 };
-std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes);
+std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes,
+                                  std::string* key_out = nullptr);
 std::vector<TmaBox> group_tma_boxes(const Group& g, const TileShape& ts);
 // tensor maps go first in a tensor-copy kernel's parameters: 16 words each
 void fill_group_words(const Group& g, const TileShape& ts, const std::vector<std::vector<uintptr_t>>& load_ptrs,
@@ -375,8 +378,9 @@ std::string plan_json(Ctx* c, const std::vector<RInstr>& prog, const Plan& p, bo
 
 // runtime
 void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_graph);
-std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src);
-void precompile(Ctx* c, const std::vector<std::string>& srcs);
+// key: the source's src_key when the caller has it (saves hashing the text again)
+std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src, const std::string* key = nullptr);
+void precompile(Ctx* c, const std::vector<std::string>& srcs, const std::vector<std::string>* keys = nullptr);
 void* dev_alloc(Ctx* c, Exec* ex, int64_t bytes);
 void dev_free(Ctx* c, Exec* ex, void* p, int64_t bytes);
 void ensure_scratch(Ctx* c, Exec* ex, int64_t partials, int64_t counters);
