@@ -202,58 +202,75 @@ namespace {
 struct NormDim {
   int64_t s, n;
 };
-bool normalise(const ViewDesc& v, int64_t* off, std::vector<NormDim>* dims) {
+// dims: at most VBE_MAX_NDIM entries, sorted by decreasing stride
+bool normalise(const ViewDesc& v, int64_t* off, NormDim* dims, int* nd) {
   *off = v.offset;
-  dims->clear();
+  int n = 0;
   for (int k = 0; k < v.ndim; ++k) {
     if (v.shape[k] <= 1 || v.strides[k] == 0) continue;
-    int64_t s = v.strides[k];
-    if (s < 0) {
-      *off += (v.shape[k] - 1) * s;
-      s = -s;
+    int64_t st = v.strides[k];
+    if (st < 0) {
+      *off += (v.shape[k] - 1) * st;
+      st = -st;
     }
-    dims->push_back({s, v.shape[k]});
+    // insertion by decreasing stride (ndim is small)
+    int j = n++;
+    while (j > 0 && dims[j - 1].s < st) {
+      dims[j] = dims[j - 1];
+      --j;
+    }
+    dims[j] = {st, v.shape[k]};
   }
-  std::sort(dims->begin(), dims->end(), [](const NormDim& a, const NormDim& b) { return a.s > b.s; });
-  for (size_t k = 1; k < dims->size(); ++k)
-    if ((*dims)[k].s == (*dims)[k - 1].s) return false;
+  *nd = n;
+  for (int k = 1; k < n; ++k)
+    if (dims[k].s == dims[k - 1].s) return false;
   return true;
 }
 }  // namespace
 
-bool may_overlap(const ViewDesc& a, const ViewDesc& b) {
-  if (a.base != b.base) return false;
-  if (a.hi < a.lo || b.hi < b.lo) return false;
-  if (a.hi < b.lo || b.hi < a.lo) return false;
+// The same-base, intersecting-range case of may_overlap (the cheap tests are
+// inline in the header). No allocation: every array is bounded by the
+// number of dimensions.
+bool may_overlap_same_base(const ViewDesc& a, const ViewDesc& b) {
   int64_t oa, ob;
-  std::vector<NormDim> da, db;
-  if (!normalise(a, &oa, &da) || !normalise(b, &ob, &db)) return true;
-  std::set<int64_t, std::greater<int64_t>> ss;
-  for (auto& d : da) ss.insert(d.s);
-  for (auto& d : db) ss.insert(d.s);
-  ss.insert(1);
-  std::vector<int64_t> s(ss.begin(), ss.end());
-  for (size_t k = 1; k < s.size(); ++k)
+  NormDim da[VBE_MAX_NDIM], db[VBE_MAX_NDIM];
+  int na, nb;
+  if (!normalise(a, &oa, da, &na) || !normalise(b, &ob, db, &nb)) return true;
+  // the union of both stride sets and 1, in decreasing order
+  int64_t s[2 * VBE_MAX_NDIM + 1];
+  int ns = 0;
+  auto add = [&](int64_t v) {
+    int j = 0;
+    while (j < ns && s[j] > v) ++j;
+    if (j < ns && s[j] == v) return;
+    for (int q = ns; q > j; --q) s[q] = s[q - 1];
+    s[j] = v;
+    ++ns;
+  };
+  for (int k = 0; k < na; ++k) add(da[k].s);
+  for (int k = 0; k < nb; ++k) add(db[k].s);
+  add(1);
+  for (int k = 1; k < ns; ++k)
     if (s[k - 1] % s[k] != 0) return true;
   // digit intervals of each view
-  auto box = [&](int64_t off, const std::vector<NormDim>& d, std::vector<std::pair<int64_t, int64_t>>* out) {
-    out->assign(s.size(), {0, 0});
+  auto box = [&](int64_t off, const NormDim* d, int nd, int64_t* lo, int64_t* hi) {
     int64_t rem = off;
-    for (size_t k = 0; k < s.size(); ++k) {
-      int64_t c = rem / s[k];
+    for (int k = 0; k < ns; ++k) {
+      const int64_t c = rem / s[k];
       rem -= c * s[k];
       int64_t ext = 1;
-      for (auto& dd : d)
-        if (dd.s == s[k]) ext = dd.n;
-      (*out)[k] = {c, c + ext - 1};
+      for (int q = 0; q < nd; ++q)
+        if (d[q].s == s[k]) ext = d[q].n;
+      lo[k] = c;
+      hi[k] = c + ext - 1;
       if (k > 0 && c + ext - 1 >= s[k - 1] / s[k]) return false;  // carries
     }
     return true;
   };
-  std::vector<std::pair<int64_t, int64_t>> ba, bb;
-  if (!box(oa, da, &ba) || !box(ob, db, &bb)) return true;
-  for (size_t k = 0; k < s.size(); ++k)
-    if (ba[k].second < bb[k].first || bb[k].second < ba[k].first) return false;
+  int64_t alo[2 * VBE_MAX_NDIM + 1], ahi[2 * VBE_MAX_NDIM + 1], blo[2 * VBE_MAX_NDIM + 1], bhi[2 * VBE_MAX_NDIM + 1];
+  if (!box(oa, da, na, alo, ahi) || !box(ob, db, nb, blo, bhi)) return true;
+  for (int k = 0; k < ns; ++k)
+    if (ahi[k] < blo[k] || bhi[k] < alo[k]) return false;
   return true;
 }
 

@@ -51,8 +51,15 @@ struct ViewDesc {
   bool self_overlapping() const;
 };
 
-// false only when the two views provably reach no common element
-bool may_overlap(const ViewDesc& a, const ViewDesc& b);
+// false only when the two views provably reach no common element (the
+// cheap tests inline: analysis calls this for every pair it considers)
+bool may_overlap_same_base(const ViewDesc& a, const ViewDesc& b);
+inline bool may_overlap(const ViewDesc& a, const ViewDesc& b) {
+  if (a.base != b.base) return false;
+  if (a.hi < a.lo || b.hi < b.lo) return false;
+  if (a.hi < b.lo || b.hi < a.lo) return false;
+  return may_overlap_same_base(a, b);
+}
 
 // ------------------------------------------------------------ instructions
 enum OpKind { K_ARITH, K_DIV, K_FUNARY, K_SUNARY, K_CMP, K_SELECT, K_CAST, K_COPY, K_RANDOM,
