@@ -308,6 +308,24 @@ def test_min_and_argmin_of_one_view_share_a_pass(fused):
     assert not any("reduce2" in r for r in runs) and len(runs) == 2
 
 
+def test_group_sources_are_shared_by_identical_groups(fused):
+    """A tile-fused group's generated source depends on its structure, not on
+    which base handles it uses: two Jacobi programs of one size, the second
+    loaded after unrelated bases (other handles), plan the same source; a
+    different grid size may change it (sizes are part of the key)."""
+    def group_source(p):
+        L = fused.load(p, upload=False)
+        js = json.loads(fused.plan(L, 0, source=True))
+        srcs = [i["group"]["source"] for i in js["items"] if "group" in i]
+        assert len(srcs) == 1
+        return srcs[0]
+    a = group_source(jacobi(64, 1))
+    fused.load(blackscholes(100), upload=False)  # takes handles in between
+    b = group_source(jacobi(64, 1))
+    assert a == b
+    assert "_tm32x32" in a  # the tensor-copy form with the whole-run reduction
+
+
 def test_power_of_two_constants_get_their_own_kernel(fused):
     """Float64 products by a constant +-2^k are formed by moving the exponent
     field; whether a constant is such a power is part of the kernel's
