@@ -391,11 +391,12 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
                 out.append(Case(p.name, p, _exact_check(p)))
     # MIN_REDUCE (MAX_REDUCE) followed by ARGMIN_REDUCE (ARGMAX_REDUCE) of the
     # same view over the same axis, run as one pass: ties, NaNs, infinities
-    # and zeros of both signs; thread and block per output. Indices bit-exact;
+    # and zeros of both signs; thread and block per output (rows of 8: a
+    # thread per output with 16-byte vector loads). Indices bit-exact;
     # the minimum's value exact up to the sign of a zero minimum, which
     # depends on the combining order (as for any reduction)
     for dt in ("float64", "float32", "int64"):
-        for shp, ax in (((7, 3001), 1), ((3001, 7), 0), ((9, 33, 70), 2), ((9, 33, 70), 0)):
+        for shp, ax in (((7, 3001), 1), ((3001, 7), 0), ((9, 33, 70), 2), ((9, 33, 70), 0), ((600, 8), 1)):
             n = int(np.prod(shp))
             x = rng.integers(-2, 3, n).astype(dt)
             if dt != "int64":
@@ -404,7 +405,7 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
                 x[sp] = lv[rng.integers(0, len(lv), int(sp.sum()))].astype(dt)
             oshape = tuple(s_ for k, s_ in enumerate(shp) if k != ax)
             for mop, aop in (("MIN_REDUCE", "ARGMIN_REDUCE"), ("MAX_REDUCE", "ARGMAX_REDUCE")):
-                b = ProgramBuilder(f"{mop}_{aop}_{dt}_{len(shp)}d_ax{ax}")
+                b = ProgramBuilder(f"{mop}_{aop}_{dt}_{'x'.join(map(str, shp))}_ax{ax}")
                 xb = b.base(dt, shp, x)
                 mv = b.base(dt, oshape)
                 ix = b.base("int64", oshape)
