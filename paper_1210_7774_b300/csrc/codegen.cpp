@@ -620,7 +620,11 @@ struct Gen {
   Layout L;
   std::ostringstream o;
   const char* rt() const { return ctype(r.red_dtype); }
-  bool kahan() const { return r.has_red && r.red_op == VBE_OP_ADD_REDUCE && r.red_dtype == VBE_FLOAT32; }
+  bool kahan() const {
+    return r.has_red && r.red_op == VBE_OP_ADD_REDUCE && r.red_dtype == VBE_FLOAT32 && !plain_sum;
+  }
+  // the float32 sum's plain variant (axis kernels, short reduced extents)
+  bool plain_sum = false;
   // ARGMIN/ARGMAX, or MIN/MAX paired with them: (value, index) pairs
   bool arg() const {
     return r.has_red && (r.red_op == VBE_OP_ARGMIN_REDUCE || r.red_op == VBE_OP_ARGMAX_REDUCE || r.has_red2);
@@ -838,7 +842,7 @@ struct Gen {
   // argument list for vbe_elem given per-slot value expressions
   std::string call(const std::string& m, const std::vector<std::string>& lv, const std::vector<std::string>& sv,
                    const std::string& ai = "ri") {
-    std::string s = "vbe_elem(p, " + m;
+    std::string s = (plain_sum ? "vbe_elem_p(p, " : "vbe_elem(p, ") + m;
     for (auto& x : lv) s += ", " + x;
     for (auto& x : sv) s += ", " + x;
     if (arg()) s += ", acc, acci, " + ai + (r.has_red2 ? ", accm" : "");
@@ -1243,6 +1247,7 @@ struct Gen {
     }
     o << "    }\n";
     emit_acc_init("    ");
+    auto emit_loops = [&]() {
     // reduced offsets of element ri + u * rs (names suffixed by u)
     std::vector<std::pair<std::string, int>> rs;
     for (size_t s = 0; s < r.loads.size(); ++s) rs.push_back({"lr" + std::to_string(s), L.lst[s] + ndk});
@@ -1361,6 +1366,21 @@ struct Gen {
     element("      ", "", "ri", false);
     o << "    }\n";
     if (vec_gen) o << "    }\n";
+    };
+    if (kahan()) {
+      // A float32 sum of n terms in order is within (n - 1) x 2^-24 of the
+      // sum of magnitudes, inside the reduction tolerance (1e-5 of it) for
+      // n <= 128: short reduced extents skip the compensation
+      o << "    if (nred <= 128) {\n";
+      plain_sum = true;
+      emit_loops();
+      plain_sum = false;
+      o << "    } else {\n";
+      emit_loops();
+      o << "    }\n";
+    } else {
+      emit_loops();
+    }
     if (arg() && r.has_red2 && block) {
       o << "    { " << vt() << " bv; const i64 bi = " << block_reduce_name << "(acc, acci, bv); const " << rt()
         << " mv = " << block_reduce_name << "_v(accm); if (threadIdx.x == 0) { rp[rk] = mv; rp2[rk2] = bi; } }\n";
@@ -1455,6 +1475,15 @@ static std::string generate_source_uncached(const Run& r, const Canon& c, std::s
         << "  return vbe_u53_to_unit((z ^ (z >> 31)) >> 11);\n}\n";
   g.o << user_op_defs({&r});
   g.emit_elem();
+  if (!tile_mode(c.spec.mode) && g.kahan()) {  // the axis kernel's plain-sum variant
+    g.plain_sum = true;
+    g.emit_struct = false;
+    g.elem_name = "vbe_elem_p";
+    g.emit_elem();
+    g.elem_name = "vbe_elem";
+    g.emit_struct = true;
+    g.plain_sum = false;
+  }
   g.emit_block_reduce();
   if (tile_mode(c.spec.mode)) {
     for (int U : {1, 2, 4}) g.emit_tile_kernel(U);
