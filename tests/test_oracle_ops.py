@@ -437,3 +437,106 @@ def test_argmin_argmax_first_occurrence_and_nan(op):
         m = data.reshape(7, 9)[::-1, ::-1]
         rows = [list(m[:, j]) for j in range(9)] if axis == 0 else [list(m[i, :]) for i in range(7)]
         assert got == [_arg_loop(r, op == "ARGMAX_REDUCE") for r in rows]
+
+
+# ------------------------------------------------- SYNC / DISCARD / FREE
+#
+# Section "Vector Engine Manager": sync asks for read access, so the copy the
+# host reads must be the most recent one (the oracle's host memory is the
+# only copy: the values stay as they are); discard declares every other copy
+# invalid (the oracle's base has no defined contents until it is written
+# again, which it shows as a sentinel: NaN for floats, a fixed int64, True
+# for bool); release (FREE) ends the base (any later use is an error).
+
+def _ctl_program(ctl, dtype="float64", via_subview=False):
+    b = ProgramBuilder("ctl")
+    init = np.arange(12, dtype=np.float64).reshape(3, 4) * 1.5 - 4.0
+    if dtype == "int64":
+        init = np.arange(12, dtype=np.int64).reshape(3, 4) * 7 - 30
+    x = b.base(dtype, (3, 4), init)
+    y = b.base(dtype, (3, 4))
+    b.emit("ADD", b.whole(y), b.whole(x), b.whole(x))
+    # the control instruction names its base through any view of it
+    cv = b.view(y, 5, (2, 2), (4, 1)) if via_subview else b.whole(y)
+    b.emit(ctl, cv)
+    return b, x, y, init
+
+
+@pytest.mark.parametrize("via_subview", [False, True])
+@pytest.mark.parametrize("dtype", ["float64", "int64"])
+def test_sync_leaves_values_unchanged(dtype, via_subview):
+    b, x, y, init = _ctl_program("SYNC", dtype, via_subview)
+    z = b.base(dtype, (3, 4))
+    b.emit("COPY", b.whole(z), b.whole(y))
+    mem = oracle.run(b.build([y, z]))
+    want = [v + v for v in init.reshape(-1).tolist()]
+    assert mem[y].tolist() == want and mem[z].tolist() == want
+    assert mem[x].tolist() == init.reshape(-1).tolist()
+
+
+@pytest.mark.parametrize("via_subview", [False, True])
+def test_discard_makes_every_element_undefined(via_subview):
+    """A read after DISCARD sees no stale value: every element of the base,
+    including those outside the naming view, reads as the sentinel."""
+    b, x, y, init = _ctl_program("DISCARD", "float64", via_subview)
+    z = b.base("float64", (3, 4))
+    b.emit("COPY", b.whole(z), b.whole(y))
+    mem = oracle.run(b.build([y, z]))
+    assert all(math.isnan(v) for v in mem[z].tolist())
+    assert all(math.isnan(v) for v in mem[y].tolist())
+    assert mem[x].tolist() == init.reshape(-1).tolist()  # other bases untouched
+
+
+def test_discard_int_and_bool_sentinels():
+    b, x, y, init = _ctl_program("DISCARD", "int64")
+    mem = oracle.run(b.build([y]))
+    assert mem[y].tolist() == [-(2**63) + 12345] * 12
+    b = ProgramBuilder("ctlb")
+    f = b.base("float64", (5,), np.array([1.0, -1.0, 0.0, 2.0, -3.0]))
+    m = b.base("bool", (5,))
+    b.emit("GREATER", b.whole(m), b.whole(f), Const(0.0))
+    b.emit("DISCARD", b.whole(m))
+    assert oracle.run(b.build([m]))[m].tolist() == [True] * 5
+
+
+def test_write_after_discard_is_live_again():
+    b, x, y, init = _ctl_program("DISCARD")
+    b.emit("MULTIPLY", b.whole(y), b.whole(x), Const(3.0))
+    mem = oracle.run(b.build([y]))
+    assert mem[y].tolist() == [v * 3.0 for v in init.reshape(-1).tolist()]
+
+
+@pytest.mark.parametrize("use", ["read", "write", "SYNC", "DISCARD", "FREE"])
+def test_any_use_after_free_raises(use):
+    b, x, y, init = _ctl_program("FREE")
+    z = b.base("float64", (3, 4))
+    if use == "read":
+        b.emit("COPY", b.whole(z), b.whole(y))
+    elif use == "write":
+        b.emit("COPY", b.whole(y), b.whole(x))
+    else:
+        b.emit(use, b.whole(y))
+    with pytest.raises(oracle.OracleError):
+        oracle.run(b.build([z]))
+
+
+def test_free_removes_only_its_base():
+    b, x, y, init = _ctl_program("FREE")
+    mem = oracle.run(b.build([x]))
+    assert y not in mem
+    assert mem[x].tolist() == init.reshape(-1).tolist()
+
+
+def test_control_of_a_base_never_created_raises():
+    b = ProgramBuilder("ctl0")
+    x = b.base("float64", (4,), np.zeros(4))
+    for op in ("SYNC", "DISCARD", "FREE"):
+        p = b.build([x])
+        p.instrs = [oracle_instr(op, 999)]
+        with pytest.raises(oracle.OracleError):
+            oracle.run(p)
+
+
+def oracle_instr(op, bid):
+    from workloads.program import Instr
+    return Instr(op, View(bid, 0, (4,), (1,)))
