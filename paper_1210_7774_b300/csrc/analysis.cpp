@@ -303,6 +303,12 @@ struct Builder {
     for (auto& w : written)
       if (may_overlap(r.out, w.first)) return false;
     if (may_overlap(r.out, red_view)) return false;
+    // a reduction that wrote into its own input has changed the values the
+    // index must be taken from: in program order the ARGMIN reads them after
+    // the MIN's store, so the pair would answer from stale values (staging
+    // of a partially overlapping input already gives such a reduction a
+    // private copy to read; this check does not rely on that)
+    if (may_overlap(red_view, red_in)) return false;
     return true;
   }
 

@@ -419,6 +419,20 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
                     same = (g == w) | (np.isnan(g) & np.isnan(w)) if g.dtype.kind == "f" else g == w
                     assert np.all(same), f"{p.name} values: {np.sum(~same)} mismatches"
                 out.append(Case(p.name, p, pchk))
+    # a MIN_REDUCE (MAX_REDUCE) written into its own input's first column,
+    # then the ARGMIN_REDUCE (ARGMAX_REDUCE) of that input: in program order
+    # the index is taken over the updated rows (the first element now holds
+    # each row's extreme, so the index is 0 unless an earlier tie or NaN)
+    for dt in ("float64", "int64"):
+        for mop, aop in (("MIN_REDUCE", "ARGMIN_REDUCE"), ("MAX_REDUCE", "ARGMAX_REDUCE")):
+            b = ProgramBuilder(f"{mop}_into_input_then_{aop}_{dt}")
+            rows, cols = 37, 301
+            xb = b.base(dt, (rows, cols), rng.integers(-1000, 1000, rows * cols).astype(dt))
+            ix = b.base("int64", rows)
+            b.emit(mop, b.view(xb, 0, (rows,), (cols,)), b.whole(xb), axis=1)
+            b.emit(aop, b.whole(ix), b.whole(xb), axis=1)
+            p = b.build([xb, ix])
+            out.append(Case(p.name, p, _exact_check(p)))
     # fused chain with a full reduction and with an axis reduction, plus stores
     for dt in ("float64", "float32"):
         b = ProgramBuilder(f"chain_full_{dt}")

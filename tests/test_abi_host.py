@@ -306,6 +306,16 @@ def test_min_and_argmin_of_one_view_share_a_pass(fused):
     L = fused.load(b.build([m, i]), upload=False)
     runs, _ = runs_of(fused, L)
     assert not any("reduce2" in r for r in runs) and len(runs) == 2
+    # a MIN written into its own input (x[:, 0]) changes the rows the ARGMIN
+    # then reads: the two are not paired (the MIN reads a private copy of x)
+    b = ProgramBuilder("min_into_input")
+    x = b.base("float64", (4, 50), np.arange(200, dtype=np.float64))
+    i = b.base("int64", 4)
+    b.emit("MIN_REDUCE", b.view(x, 0, (4,), (50,)), b.whole(x), axis=1)
+    b.emit("ARGMIN_REDUCE", b.whole(i), b.whole(x), axis=1)
+    L = fused.load(b.build([x, i]), upload=False)
+    runs, _ = runs_of(fused, L)
+    assert not any("reduce2" in r for r in runs)
 
 
 def test_group_sources_are_shared_by_identical_groups(fused):
