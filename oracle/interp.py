@@ -28,7 +28,10 @@ Readings where the paper is silent (each listed in the design notes):
   defined);
 * MAXIMUM(a, b) is ``a`` if ``a > b`` or ``a`` is NaN, else ``b`` (NumPy's
   ``maximum``: NaN propagates, a tie of signed zeros gives ``b``); MINIMUM
-  likewise with ``<``; MIN/MAX_REDUCE fold the same rule.
+  likewise with ``<``; MIN/MAX_REDUCE fold the same rule, except that when
+  the extreme is a zero present with both signs the sign of the result
+  depends on the combining order (NumPy's reduction of a contiguous axis
+  does not combine sequentially), so it is not part of the result.
 """
 from __future__ import annotations
 

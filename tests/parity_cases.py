@@ -393,8 +393,10 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
     # same view over the same axis, run as one pass: ties, NaNs, infinities
     # and zeros of both signs; thread and block per output (rows of 8: a
     # thread per output with 16-byte vector loads). Indices bit-exact;
-    # the minimum's value exact up to the sign of a zero minimum, which
-    # depends on the combining order (as for any reduction)
+    # the minimum's value exact, except the sign of a zero minimum where
+    # zeros of both signs tie: either zero is the minimum, and which one a
+    # fold returns depends on its combining order (the oracle's NumPy
+    # reduction included), so that sign is not compared
     for dt in ("float64", "float32", "int64"):
         for shp, ax in (((7, 3001), 1), ((3001, 7), 0), ((9, 33, 70), 2), ((9, 33, 70), 0), ((600, 8), 1)):
             n = int(np.prod(shp))
