@@ -72,12 +72,20 @@ enum {
   VBE_OP_ADD = 1,         /* [2] int64/f32/f64; int64 wraps modulo 2^64   */
   VBE_OP_SUBTRACT = 2,    /* [2]                                          */
   VBE_OP_MULTIPLY = 3,    /* [2]                                          */
-  VBE_OP_DIVIDE = 4,      /* [2] f32/f64 only, IEEE round-to-nearest      */
+  VBE_OP_DIVIDE = 4,      /* [2] f32/f64 only, IEEE round-to-nearest (f64:
+                             integer-pipe routine, correctly rounded, or
+                             the FP64 pipe under VBE_NATIVE_F64)          */
   VBE_OP_MAXIMUM = 5,     /* [2] a if (a > b or a is NaN) else b          */
   VBE_OP_MINIMUM = 6,     /* [2] a if (a < b or a is NaN) else b          */
-  VBE_OP_SQRT = 7,        /* [1] f32/f64, correctly rounded               */
-  VBE_OP_EXP = 8,         /* [1] f32/f64, CUDA exp/expf                   */
-  VBE_OP_LOG = 9,         /* [1] f32/f64, CUDA log/logf                   */
+  VBE_OP_SQRT = 7,        /* [1] f32/f64, correctly rounded (f64: integer-
+                             pipe routine, or the FP64 pipe under
+                             VBE_NATIVE_F64)                              */
+  VBE_OP_EXP = 8,         /* [1] f32: CUDA expf; f64: the library's own
+                             table-driven exp on the integer pipes (within
+                             1 ulp), or CUDA exp under VBE_NATIVE_F64      */
+  VBE_OP_LOG = 9,         /* [1] f32: CUDA logf; f64: the library's own
+                             table-driven log (within 1 ulp), or CUDA log
+                             under VBE_NATIVE_F64                         */
   VBE_OP_ABSOLUTE = 10,   /* [1] int64/f32/f64                            */
   VBE_OP_NEGATIVE = 11,   /* [1] int64/f32/f64                            */
   VBE_OP_LESS = 12,       /* [2] same-dtype inputs, bool output           */
@@ -285,7 +293,10 @@ int vbe_op_register(vbe_ctx* ctx, const char* name, const char* body, int32_t ni
  * first call on a device looks up the array's device address: make it
  * before any stream capture. Calls share the array: calls that overlap on
  * the GPU race; serialise them. Summation order depends only on n.
- * VBE_ERR_CUDA if a CUDA call fails. No context is needed. */
+ * VBE_ERR_CUDA if a CUDA call fails: a CUDA error already pending on the
+ * calling thread is reported before anything is enqueued and left pending;
+ * a failure of this call's own launch is reported and cleared. No context
+ * is needed. */
 int vbe_reduce_add_f64_noalloc(const double* x, int64_t n, double* out, void* stream);
 
 /* ------------------------------------------------------------ serving */

@@ -17,6 +17,11 @@
 // that first call before any stream capture. Every call shares the one
 // array, so calls that overlap on the GPU (different streams, or several
 // host threads) race and give wrong sums; serialise them.
+//
+// CUDA errors: an error already pending on the calling thread (left by
+// earlier, unrelated work) is reported as VBE_ERR_CUDA before anything is
+// enqueued and is left pending for its owner to read; an error of this
+// call's own launch is reported as VBE_ERR_CUDA and cleared.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -90,6 +95,8 @@ __global__ void __launch_bounds__(kBlock) sum_chunks(const double* __restrict__ 
 extern "C" int vbe_reduce_add_f64_noalloc(const double* x, int64_t n, double* out, void* stream) {
   if (n < 0 || out == nullptr || (n > 0 && x == nullptr)) return VBE_ERR_INVALID;
   if (n > kMaxChunks * kChunk) return VBE_ERR_INVALID;  // beyond the scratch: 2^30 elements
+  // an earlier error belongs to someone else: report it, do not clear it
+  if (cudaPeekAtLastError() != cudaSuccess) return VBE_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VBE_ERR_CUDA;
   void* scratch = nullptr;
@@ -116,5 +123,6 @@ extern "C" int vbe_reduce_add_f64_noalloc(const double* x, int64_t n, double* ou
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = nchunks < 4LL * sms ? nchunks : 4LL * sms;
   sum_chunks<<<(unsigned)grid, kBlock, 0, s>>>(x, n, nchunks, out, static_cast<unsigned char*>(scratch));
+  // nothing was pending before this call, so an error here is this launch's
   return cudaGetLastError() == cudaSuccess ? VBE_OK : VBE_ERR_CUDA;
 }
