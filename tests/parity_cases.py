@@ -421,6 +421,31 @@ def reduction_cases(shape=(9, 33, 70), seed=2):
                     same = (g == w) | (np.isnan(g) & np.isnan(w)) if g.dtype.kind == "f" else g == w
                     assert np.all(same), f"{p.name} values: {np.sum(~same)} mismatches"
                 out.append(Case(p.name, p, pchk))
+    # float32 axis sums at the switch between plain sums (at most 128 terms
+    # per output) and compensated ones (129 and more), on data that makes
+    # every addition round the same way: 1.0 first, then terms just under
+    # half an ulp of 1.0, so a plain sum in order loses each of them. The
+    # bound for any order of n - 1 additions is (n - 1) * 2^-24 * sum|x|
+    # (about 7.6e-6 at n = 128), inside the 1e-5 tolerance
+    tiny = np.float32(np.float64(2.0 ** -24) * (1 - 2.0 ** -10))
+    for nred in (128, 129):
+        for ax in (1, 0):
+            rows = 67
+            blk = np.full((rows, nred), tiny, dtype=np.float32)
+            blk[:, 0] = 1.0
+            blk[1::2, 0] = tiny
+            blk[1::2, -1] = 1.0  # odd rows: the large term last
+            x = blk if ax == 1 else np.ascontiguousarray(blk.T)
+            b = ProgramBuilder(f"ADD_REDUCE_float32_round_{nred}_ax{ax}")
+            xb = b.base("float32", x.shape, x)
+            o = b.base("float32", rows)
+            b.emit("ADD_REDUCE", b.whole(o), b.whole(xb), axis=ax)
+            p = b.build([o])
+            scale = _abs_sum(x, ax).reshape(-1)
+
+            def rchk(got, want, o=o, scale=scale, p=p):
+                assert_close_sum(got[o], want[o], scale, F32_REDUCE_RTOL, p.name)
+            out.append(Case(p.name, p, rchk))
     # a MIN_REDUCE (MAX_REDUCE) written into its own input's first column,
     # then the ARGMIN_REDUCE (ARGMAX_REDUCE) of that input: in program order
     # the index is taken over the updated rows (the first element now holds
