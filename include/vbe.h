@@ -256,6 +256,9 @@ typedef struct vbe_stats {
                                 launch list (no analysis, no graph)          */
   int64_t tma_group_launches; /* tile-fused groups issued (or captured) in the
                                 tensor-copy form, tuning trials included     */
+  int64_t packed_launches;   /* launches (graph replays included) of packed
+                                kernels: several independent runs executed by
+                                one persistent launch (VBE_PACK)              */
 } vbe_stats;
 int vbe_get_stats(vbe_ctx* ctx, vbe_stats* out);
 

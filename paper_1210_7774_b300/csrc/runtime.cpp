@@ -358,6 +358,7 @@ void record_launch(Ctx* c, Exec* ex, Launch& L) {
   }
   c->rec_launches.push_back(j + "}");
   c->stats.kernel_launches++;
+  if (L.packed) c->stats.packed_launches++;
 }
 
 // Every generated kernel starts with griddepcontrol.wait, so it may be
@@ -411,6 +412,7 @@ void issue(Ctx* c, Exec* ex, Launch& L, bool capturing) {
     cuda_check(launch_pdl(L.fn, L.grid, L.block, args, L.smem, s), "launch");
   }
   if (!capturing) c->stats.kernel_launches++;
+  if (!capturing && L.packed) c->stats.packed_launches++;
   if (L.tma) c->stats.tma_group_launches++;
 }
 
@@ -1153,6 +1155,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
         cuda_check(cudaGraphLaunch(var->exec, ex->stream), "cudaGraphLaunch");
         c->stats.graph_launches++;
         c->stats.kernel_launches += var->launches;
+        c->stats.packed_launches += var->packed_launches;
         apply_after(*var);
         return;
       }
@@ -1495,10 +1498,12 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   var->graph = graph;
   var->keep = keep;
   var->launches = (int64_t)recorded.size();
+  var->packed_launches = std::count_if(recorded.begin(), recorded.end(), [](const Launch& L) { return L.packed; });
   c->stats.graph_captures++;
   cuda_check(cudaGraphLaunch(gexec, ex->stream), "cudaGraphLaunch");
   c->stats.graph_launches++;
   c->stats.kernel_launches += var->launches;
+  c->stats.packed_launches += var->packed_launches;
 }
 
 }  // namespace vbe

@@ -321,6 +321,7 @@ struct CachedVariant {
   cudaGraph_t graph = nullptr;
   std::vector<void*> keep;  // device buffers the graph references
   int64_t launches = 0;
+  int64_t packed_launches = 0;  // of which packed (several independent runs in one launch)
   std::vector<std::pair<int64_t, std::pair<void*, void*>>> after;  // renamed base -> (buffer, second buffer)
   uint64_t last_use = 0;
 };

@@ -82,7 +82,7 @@ def jacobi_request(n: int, iters: int, dtype: str, seed: int):
         b.discard(t, d, r)
     b.sync(full, delta)
     p = b.build([full, delta])
-    p.meta.update(kind="jacobi", cells=n * n, iters=iters)
+    p.meta.update(kind="jacobi", cells=n * n, iters=iters, grid=full, delta=delta)
     return p
 
 
@@ -134,7 +134,7 @@ def blackscholes_request(n: int, dtype: str, seed: int):
     b.discard(*(v.base for v in tv.values()), c.base, *(v.base for v in ins.values()))
     b.sync(call, put)
     p = b.build([call, put])
-    p.meta.update(kind="blackscholes", options=n)
+    p.meta.update(kind="blackscholes", options=n, S=S.base, K=K.base)
     return p
 
 
