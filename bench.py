@@ -189,30 +189,78 @@ def measured_counters(name, khash):
         return None
 
 
-# B300: 148 SMs; the FP64 pipe retires 2 lanes per clock per SM (1/64 of the
-# FP32 rate; 1.97/clk/SM measured by ncu on the Black-Scholes kernel)
-FP64_LANES_PER_SM_CLK = 2
-SMS = 148
+def measure_fp64_peak(V, torch, local, stream):
+    """The FP64 pipe's rate, measured on this GPU by the library's throughput
+    kernel (8 independent chains per thread, 8 blocks of 256 threads per SM):
+    fused multiply-add, add and multiply, each the median of 5 launches of
+    about 30 ms after one warm-up launch, with the SM clocks sampled
+    meanwhile. ``peak`` is the fastest of the three medians (one FP64
+    instruction per lane either way)."""
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    scratch = torch.empty(2048 * sms, dtype=torch.float64, device=f"cuda:{local}")
+    ck = Clocks(local)
+    ck.start()
+    res = {}
+    for op in ("dfma", "dadd", "dmul"):
+        V.vbe_measure_fp64_rate(op, 512, scratch.data_ptr(), stream)
+        vals = [V.vbe_measure_fp64_rate(op, 8192, scratch.data_ptr(), stream) for _ in range(5)]
+        res[op] = statistics.median(vals) / 1e9
+    clocks = ck.stop()
+    peak = max(res.values())
+    mhz = clocks.get("sm_mhz") or 2032.0
+    return {"peak": peak, "unit": "G FP64-inst/s", "dfma": res["dfma"], "dadd": res["dadd"], "dmul": res["dmul"],
+            "sms": sms, "per_sm_per_clk": peak * 1e9 / (sms * mhz * 1e6), "clocks": clocks,
+            "how": "library throughput kernel (vbe_measure_fp64_rate): 8 chains/thread, 8x256 threads/SM, "
+                   "median of 5 launches of 8192 rounds, CUDA events"}
 
 
-def roofline_f64(achieved_gbs, hbm, src, counters, n, sec, clk_mhz):
+FP64_PIPE_OPS = {"ADD", "SUBTRACT", "MULTIPLY", "MAXIMUM", "MINIMUM", "LESS", "LESS_EQUAL", "GREATER",
+                 "GREATER_EQUAL", "EQUAL", "NOT_EQUAL"}
+
+
+def fp64_bytecode_ops(program, lo=0, hi=None):
+    """Float64 operations of the bytecodes in ``program.instrs[lo:hi]`` that
+    must run on the FP64 pipe: element counts of the float64 add, subtract,
+    multiply, min/max and compare bytecodes and of float64 sums, products by
+    a constant +-2^k excluded (the library does those exactly on the integer
+    pipes, as it does divide, sqrt, exp and log). This is the scheme's own
+    ALU work, before any recomputation a kernel form adds."""
+    from workloads.program import Const, View
+    n = 0
+    for ins in program.instrs[lo:hi]:
+        views = [x for x in ins.ins if isinstance(x, View)]
+        if ins.op == "ADD_REDUCE" and views and program.bases[views[0].base].dtype == "float64":
+            n += views[0].size
+            continue
+        if ins.op not in FP64_PIPE_OPS or not views or program.bases[views[0].base].dtype != "float64":
+            continue
+        if ins.op == "MULTIPLY" and any(isinstance(x, Const) and x.value != 0 and
+                                        float(abs(x.value)) == 2.0 ** int(np.round(np.log2(abs(x.value))))
+                                        for x in ins.ins):
+            continue
+        n += ins.out.size
+    return n
+
+
+def roofline_f64(achieved_gbs, hbm, src, counters, n, sec, fp64, clk_mhz):
     hbm_part = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
                 "peak_source": src}
     if not counters or "fp64_inst_per_unit" not in counters:
         hbm_part["traffic"] = counters["dram_bytes_per_launch"] if counters else None
         return hbm_part
-    peak = SMS * FP64_LANES_PER_SM_CLK * clk_mhz * 1e6 / 1e9
+    peak = fp64["peak"]
     ach = counters["fp64_inst_per_unit"] * n / sec / 1e9
     out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G FP64-inst/s", "frac": ach / peak,
-           "peak_source": f"derived: {SMS} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes/clk x {clk_mhz:.0f} MHz",
+           "peak_source": "measured in this run (vbe_measure_fp64_rate; see fp64_peak)",
            "work": f"{counters['fp64_inst_per_unit']:.1f} FP64 instructions per option (ncu, this kernel)",
            "traffic": counters["dram_bytes_per_launch"], "hbm": hbm_part}
     if "inst_per_unit" in counters:
         # all instructions against the issue rate (4 schedulers x 32 lanes per SM)
-        ipeak = SMS * 128 * clk_mhz * 1e6 / 1e12
+        ipeak = fp64["sms"] * 128 * clk_mhz * 1e6 / 1e12
         iach = counters["inst_per_unit"] * n / sec / 1e12
         out["issue"] = {"achieved": iach, "peak": ipeak, "unit": "T thread-inst/s", "frac": iach / ipeak,
-                        "work": f"{counters['inst_per_unit']:.0f} instructions per option"}
+                        "work": f"{counters['inst_per_unit']:.0f} instructions per option",
+                        "peak_source": f"derived: {fp64['sms']} SMs x 128 lanes/clk x {clk_mhz:.0f} MHz"}
     return out
 
 
@@ -238,7 +286,7 @@ def gpu_blackscholes(args, rank, world, local):
     n = args.options
     cache = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
     flags_fused = V.VBE_FUSE | V.VBE_GRAPHS | V.VBE_AUTOTUNE | V.VBE_PACK
-    res = {}
+    res = {"_fp64": measure_fp64_peak(V, torch, local, stream), "_ctx": (V, torch, local, stream)}
     for dtype in args.dtypes.split(","):
         inp = bs_inputs(n, dtype, seed=1210_7774 + 2 + rank)
         prog = blackscholes(n, dtype, inputs=inp)
@@ -286,6 +334,167 @@ def gpu_blackscholes(args, rank, world, local):
         out["cbytes"] = cbytes
         res[dtype] = out
     return res, dist
+
+
+# ------------------------------------------------- per-configuration keys
+
+def _oracle_seconds(program, reps=1):
+    import oracle
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.run(program)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return best
+
+
+def _oracle_job(args):
+    """One oracle run in a worker process (a spawn pool): the program is
+    rebuilt there from its generator and arguments."""
+    kind, params = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    if kind == "mc":
+        from workloads import montecarlo_pi
+        p = montecarlo_pi(sizes=np.array(params["sizes"]), keys=params["keys"])
+    else:
+        from workloads.serving import request_program
+        p = request_program(kind, params)
+    t0 = time.perf_counter()
+    oracle.run(p)
+    return time.perf_counter() - t0
+
+
+def _pool_rate(jobs, units):
+    """Wall-clock rate of the oracle over all host cores: ``jobs`` run by a
+    spawn process pool with one worker per usable core."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+        list(pool.map(_oracle_job, jobs[:cores]))  # workers started and warm
+        t0 = time.perf_counter()
+        list(pool.map(_oracle_job, jobs))
+        wall = time.perf_counter() - t0
+    return units / wall, cores, wall
+
+
+def config_subkeys(args, V, torch, local, stream, hbm, fp64):
+    """One sub-key per configuration beside the headline: Jacobi 256^2,
+    shallow water 4096^2 float64 (50 steps), Monte-Carlo pi (256 instances)
+    and the serving loop, each fused against the per-bytecode path on this
+    GPU with the oracle timed beside it (``cpu_baseline``)."""
+    from paper_1210_7774_b300.runner import Executor
+    from workloads import jacobi, mc_sizes, montecarlo_pi, shallow_water
+    cache = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
+    F = V.VBE_FUSE | V.VBE_AUTOTUNE | V.VBE_PACK
+    G = V.VBE_GRAPHS
+
+    def timed(program, flags, reps, warmup=3):
+        with Executor(flags, device=local, stream=stream, cache_dir=cache) as ex:
+            L = ex.load(program)
+            nb = len(L.batches)
+            st0 = ex.stats()
+
+            def step():
+                for k in range(nb):
+                    ex.submit(L, k)
+            sec = time_steps(step, reps, warmup, torch)
+            st1 = ex.stats()
+        per = reps + warmup
+        return sec, {k: (st1[k] - st0[k]) / per for k in ("kernel_launches", "graph_launches", "list_replays",
+                                                             "packed_launches")}
+
+    out = {}
+    # --- Jacobi 256^2 float64, 10 iterations (launch-bound: the grid is L2-resident)
+    p = jacobi(256, 10)
+    cb = 256 * 256 * 8 + 254 * 254 * 8
+    jr = {}
+    for name, flags in (("fused_graphs", F | G), ("plain_graphs", G), ("plain", 0)):
+        sec, st = timed(p, flags, 100, warmup=20)
+        jr[name] = {"us_per_iteration": sec / 10 * 1e6, "GB/s": cb * 10 / sec / 1e9,
+                    "launches_per_iteration": st["kernel_launches"] / 10}
+    osec = _oracle_seconds(p, 3)
+    jr.update(speedup_vs_plain=jr["plain"]["us_per_iteration"] / jr["fused_graphs"]["us_per_iteration"],
+              speedup_vs_plain_graphs=jr["plain_graphs"]["us_per_iteration"] / jr["fused_graphs"]["us_per_iteration"],
+              note="256x256 float64, 10 iterations of 9 bytecodes; the 0.5 MB grid stays in L2, so launch latency "
+                   "bounds it, not HBM",
+              cpu_baseline={"value": osec / 10 * 1e6, "unit": "us/iteration", "cores": 1, "kind": "oracle",
+                            "sample": "the whole configuration (10 iterations), best of 3"})
+    out["jacobi_256_f64_10it"] = jr
+    # --- shallow water 4096^2 float64, 50 steps
+    N, steps = 4096, 50
+    p = shallow_water(N, steps)
+    cb = 6 * 8 * N * N
+    lo, hi = p.meta["batches"][1]
+    ops = fp64_bytecode_ops(p, lo, hi)
+    sw = {}
+    for name, flags in (("fused_graphs", F | G), ("plain_graphs", G)):
+        sec, st = timed(p, flags, 2 if name == "fused_graphs" else 1, warmup=1)
+        ms = sec / steps * 1e3
+        sw[name] = {"ms_per_step": ms, "GB/s": cb / (ms / 1e3) / 1e9, "hbm_fraction": cb / (ms / 1e3) / 1e9 / hbm,
+                    "launches_per_step": st["kernel_launches"] / steps}
+    ms = sw["fused_graphs"]["ms_per_step"]
+    floor_ms = ops / (fp64["peak"] * 1e9) * 1e3
+    sw["speedup_vs_plain"] = sw["plain_graphs"]["ms_per_step"] / ms
+    sw["roofline"] = {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e9, "peak": fp64["peak"],
+                      "unit": "G FP64-inst/s", "frac": floor_ms / ms,
+                      "work": f"{ops / (N * N):.2f} float64 add/subtract/multiply operations per cell per step "
+                              "(the bytecodes' own, products by 2^k excluded)",
+                      "floor_ms_per_step": floor_ms,
+                      "hbm": {"achieved": cb / (ms / 1e3) / 1e9, "peak": hbm, "frac": cb / (ms / 1e3) / 1e9 / hbm,
+                              "bytes_per_cell": 48}}
+    ps = shallow_water(1024, 1)
+    osec = _oracle_seconds(ps)
+    sw["cpu_baseline"] = {"value": 6 * 8 * 1024 * 1024 / osec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                          "ms_per_step_at_4096": osec * (N * N) / (1024 * 1024) * 1e3,
+                          "sample": f"one step of 1024x1024 ({osec:.1f} s), scaled by cells"}
+    out["shallow_water_4096_f64_50st"] = sw
+    # --- Monte-Carlo pi, 256 instances in one packed launch
+    sizes = mc_sizes(256)
+    p = montecarlo_pi(sizes=sizes)
+    samples = int(sizes.sum())
+    mc = {}
+    for name, flags in (("packed", F), ("unpacked", V.VBE_FUSE | V.VBE_AUTOTUNE), ("plain", 0)):
+        sec, st = timed(p, flags, 3 if name != "plain" else 1, warmup=2 if name != "plain" else 1)
+        mc[name] = {"ms_per_step": sec * 1e3, "samples_per_s": samples / sec,
+                    "launches_per_step": st["kernel_launches"], "packed_launches_per_step": st["packed_launches"]}
+    ops = fp64_bytecode_ops(p)
+    mc["speedup_vs_plain"] = mc["plain"]["ms_per_step"] / mc["packed"]["ms_per_step"]
+    mc["roofline"] = {"bound": "alu", "achieved": ops / (mc["packed"]["ms_per_step"] / 1e3) / 1e9,
+                      "peak": fp64["peak"], "unit": "G FP64-inst/s",
+                      "frac": ops / (mc["packed"]["ms_per_step"] / 1e3) / 1e9 / fp64["peak"],
+                      "work": f"{ops / samples:.1f} float64 operations per sample (2 multiplies, add, compare)"}
+    order = np.argsort(sizes)
+    pick = order[:192]  # a bounded sample: the 192 smallest instances
+    sub = montecarlo_pi(sizes=sizes[pick], keys=pick)
+    osec = _oracle_seconds(sub)
+    ns = int(sizes[pick].sum())
+    jobs = [("mc", {"sizes": [int(sizes[k])], "keys": [int(k)]}) for k in pick]
+    prate, cores, wall = _pool_rate(jobs, ns)
+    mc["cpu_baseline"] = {"value": ns / osec, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                          "sample": f"the 192 smallest instances ({ns} samples, {osec:.1f} s)",
+                          "all_cores": {"value": prate, "cores": cores,
+                                        "sample": f"the same instances, one per task, spawn process pool ({wall:.1f} s)"}}
+    mc["samples"] = samples
+    out["montecarlo_pi_256"] = mc
+    # --- serving loop
+    sv = serving_bench(args, V, local)
+    from workloads.serving import request_mix
+    mix = request_mix(64, seed=1210_7774 + 55)
+    jobs = [(k, prm) for k, prm in mix]
+    t0 = time.perf_counter()
+    for j in jobs[:8]:
+        _oracle_job(j)
+    one = time.perf_counter() - t0
+    prate, cores, wall = _pool_rate(jobs, len(jobs))
+    sv["cpu_baseline"] = {"value": 8 / one, "unit": "requests/s", "cores": 1, "kind": "oracle",
+                          "sample": f"8 requests of the same mix (another seed), {one:.1f} s",
+                          "all_cores": {"value": prate, "cores": cores,
+                                        "sample": f"64 requests of that mix, spawn process pool ({wall:.1f} s)"}}
+    out["serving_64_clients"] = sv
+    return out
 
 
 # ------------------------------------------------------ the other workloads
@@ -480,6 +689,8 @@ def main():
     ap.add_argument("--options", type=int, default=1 << 24)
     ap.add_argument("--ref-sample", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the per-configuration sub-keys (Jacobi, shallow water, MC, serving)")
     ap.add_argument("--dtypes", default="float64,float32", help="profiling: restrict the dtypes run")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--paths", default="fused,plain", help="profiling: restrict the paths run (jacobi: paper_size runs the 7168^2 part alone)")
@@ -495,6 +706,8 @@ def main():
     clocks.start()
     res, dist = gpu_blackscholes(args, rank, world, local)
     ck = clocks.stop()
+    fp64 = res.pop("_fp64")
+    V, torch, _, stream = res.pop("_ctx")
     if args.dtypes != "float64,float32" or args.paths != "fused,plain":
         if rank == 0:  # a restricted profiling run prints only its timings
             print(json.dumps({k: {p: v[p]["sec"] for p in ("fused", "plain") if p in v} for k, v in res.items()}))
@@ -535,13 +748,19 @@ def main():
                                      "dram_bytes_per_launch"),
                                  "kernel_hash": f32["kernel_hash"]}},
         "roofline": dict(roofline_f64(achieved, hbm, src, measured_counters("blackscholes_f64", f64["kernel_hash"]),
-                                      args.options, sec, ck.get("sm_mhz") or 2032.0),
+                                      args.options, sec, fp64, ck.get("sm_mhz") or 2032.0),
                          kernel_hash=f64["kernel_hash"]),
+        "fp64_peak": fp64,
         "e2e": f64["e2e"],
         "gpu_launches": int(round(f64["fused"]["launches_per_step"] * args.steps)),
         "clocks": ck,
         "cpu_baseline": cpu,
     }
+    if not args.no_configs and world == 1:
+        ck2 = Clocks(local)
+        ck2.start()
+        line["configs"] = config_subkeys(args, V, torch, local, stream, hbm, fp64)
+        line["configs"]["clocks"] = ck2.stop()
     print(json.dumps(line), flush=True)
 
 

@@ -302,6 +302,17 @@ int vbe_op_register(vbe_ctx* ctx, const char* name, const char* body, int32_t ni
  * is needed. */
 int vbe_reduce_add_f64_noalloc(const double* x, int64_t n, double* out, void* stream);
 
+/* Measurement aid (no counterpart in the paper): the FP64 pipe's rate on
+ * the current device, in float64 operations per second (one fused
+ * multiply-add, add or multiply per lane per operation: op = 0, 1 or 2),
+ * from a throughput kernel of `iters` rounds of 8 independent chains per
+ * thread over 8 blocks of 256 threads per SM, timed with CUDA events on
+ * `stream` (a cudaStream_t or NULL); waits for the kernel. `scratch` is
+ * device memory for 2048 * SMs doubles, which the kernel overwrites. The
+ * float64 workloads' ALU roofline divides by this rate. VBE_ERR_INVALID
+ * for bad arguments, VBE_ERR_CUDA if a CUDA call fails. */
+int vbe_measure_fp64_rate(int32_t op, int64_t iters, double* out_per_s, double* scratch, void* stream);
+
 /* ------------------------------------------------------------ serving */
 /* A request is a self-contained program executed by the server loop:
  * bases (with optional host input and result buffers), views over them

@@ -118,6 +118,7 @@ _SIGS = {
     "vbe_server_destroy": [_P],
     "vbe_op_register": [_P, ctypes.c_char_p, ctypes.c_char_p, c_int32, c_int32, POINTER(c_int32)],
     "vbe_reduce_add_f64_noalloc": [c_void_p, c_int64, c_void_p, c_void_p],
+    "vbe_measure_fp64_rate": [c_int32, c_int64, POINTER(ctypes.c_double), c_void_p, c_void_p],
 }
 EXPORTED = tuple(_SIGS)
 for _name, _args in _SIGS.items():
@@ -281,3 +282,15 @@ def vbe_reduce_add_f64_noalloc(x_ptr: int, n: int, out_ptr: int, stream: int | N
     code = lib.vbe_reduce_add_f64_noalloc(x_ptr, n, out_ptr, stream or None)
     if code < 0:
         raise VbeError(code, "vbe_reduce_add_f64_noalloc")
+
+
+FP64_RATE_OPS = {"dfma": 0, "dadd": 1, "dmul": 2}
+
+
+def vbe_measure_fp64_rate(op: str, iters: int, scratch_ptr: int, stream: int | None = None) -> float:
+    """float64 operations per second of the FP64 pipe (throughput kernel)."""
+    out = ctypes.c_double(0.0)
+    code = lib.vbe_measure_fp64_rate(FP64_RATE_OPS[op], iters, byref(out), scratch_ptr, stream or None)
+    if code < 0:
+        raise VbeError(code, "vbe_measure_fp64_rate")
+    return out.value
