@@ -221,6 +221,62 @@ int vbe_discard(vbe_ctx* ctx, vbe_base base);
 /* Release a base (and its views) after the work enqueued so far. */
 int vbe_free(vbe_ctx* ctx, vbe_base base);
 
+/* ------------------------------------------------------- host mirrors */
+/* The data-ownership scheme of section "Vector Engine Manager" for a base
+ * that also has a copy in host memory (the paper's "shared memory" copy):
+ * the library keeps track of which copies hold the base's current value and
+ * who may write it. Rules, as this library applies them:
+ *  1. The host asks for access: vbe_mirror_sync for read access,
+ *     vbe_mirror_release for write access (vbe_mirror_discard when it has
+ *     already overwritten its copy). It keeps no ownership state itself.
+ *  2. A submitted batch may read every input and write every output it
+ *     names: before it runs, a mirrored base whose current value only the
+ *     mirror holds is copied to the device (unless the batch's first use of
+ *     it overwrites every element); afterwards the mirror of a base the batch
+ *     wrote is stale, and the host holds write access to no base it named.
+ *  3. An in-batch SYNC of a mirrored base copies the device copy back to the
+ *     mirror at that point (the mirror is current once the batch completes);
+ *     an in-batch DISCARD drops the device copy (the mirror, if current,
+ *     then holds the value; otherwise no copy does). Such a batch is executed
+ *     afresh at every submit (never replayed from a graph). A batch that
+ *     reads a mirrored base after discarding it, while the mirror holds its
+ *     value, is rejected (VBE_ERR_INVALID): write it first. A batch that
+ *     reads a mirrored base whose value no copy holds is rejected
+ *     (VBE_ERR_UNINIT).
+ *  4. The library tracks ownership (vbe_mirror_state); it reads and writes
+ *     the mirror only in the calls above and in rule 2 and 3 copies.
+ * The mirror is caller-owned memory of exactly the base's size; it must stay
+ * valid until vbe_free (or vbe_finalize). The host must not write it without
+ * write access, nor read it without read access: the library cannot see such
+ * accesses. vbe_base_upload into a mirrored base makes the device copy
+ * current and the mirror stale. */
+enum {
+  VBE_MIRROR_DEVICE = 1,     /* the device copy holds the current value      */
+  VBE_MIRROR_HOST = 2,       /* the mirror holds the current value            */
+  VBE_MIRROR_HOST_WRITE = 4  /* the host holds write access (owns the base)   */
+};
+/* Attach host memory `host` (nbytes == the base's size) as the base's mirror.
+ * It declares that the mirror holds the base's current value and that the
+ * host has write access (as after a discard); the device copy, if any, is
+ * no longer current. Waits for work already enqueued. Errors:
+ * VBE_ERR_INVALID (size, null pointer, a registered base, a second mirror). */
+int vbe_mirror_attach(vbe_ctx* ctx, vbe_base base, void* host, int64_t nbytes);
+/* Read access (sync): waits for all enqueued work; on return the mirror holds
+ * the base's current value (copied from the device if it did not). Errors:
+ * VBE_ERR_INVALID (no mirror), VBE_ERR_UNINIT (no copy holds a value: the
+ * base was discarded). */
+int vbe_mirror_sync(vbe_ctx* ctx, vbe_base base);
+/* Write access (release): as vbe_mirror_sync, then the device copy is no
+ * longer current and the host owns the base; the next batch that uses it
+ * reads the mirror. */
+int vbe_mirror_release(vbe_ctx* ctx, vbe_base base);
+/* Discard: the host declares that its mirror holds the base's current value
+ * (it has overwritten it) and that every other copy is invalid; no copy is
+ * made. Waits for enqueued work first, so no copy back is still in flight. */
+int vbe_mirror_discard(vbe_ctx* ctx, vbe_base base);
+/* *state = VBE_MIRROR_* bits of the base as of the calls made so far. */
+int vbe_mirror_state(vbe_ctx* ctx, vbe_base base, int32_t* state);
+
 /* Describe, as JSON, how vbe_submit would execute a batch: the kernels
  * (runs) it forms, the instructions of each, which values stay in registers
  * and which are stored, and the generated CUDA source when

@@ -7,7 +7,9 @@ the CUDA path (it depends only on the seeded workload generators, which hold
 none of the method's arithmetic).
 
 ``oracle.run(program)`` executes the program's bytecodes one at a time, in
-order, with NumPy-ufunc semantics (see ``oracle.interp``). RANDOM follows the
+order, with NumPy-ufunc semantics (see ``oracle.interp``).
+``oracle.OwnershipModel`` adds a host copy to bases and follows the
+sync / release / discard ownership rules (see ``oracle.ownership``). RANDOM follows the
 counter form of splitmix64 (``oracle.splitmix``). Every function is pinned
 by tests against values fixed by mathematics or by brute force, not by
 itself: IEEE correct rounding via exact rationals, transcendentals via
@@ -15,6 +17,7 @@ mpmath, views via explicit index loops, the workloads via closed forms,
 invariants and pure-Python loops on tiny inputs.
 """
 from .interp import Memory, OracleError, execute, run
+from .ownership import OwnershipModel
 from .splitmix import GAMMA, mix64, random_u01
 
-__all__ = ["Memory", "OracleError", "execute", "run", "GAMMA", "mix64", "random_u01"]
+__all__ = ["Memory", "OracleError", "execute", "run", "OwnershipModel", "GAMMA", "mix64", "random_u01"]

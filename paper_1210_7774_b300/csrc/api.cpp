@@ -39,6 +39,161 @@ namespace vbe {
 std::vector<char> compile_cached(Ctx* c, const std::string& src, bool* compiled);
 }
 
+namespace {
+
+// ---------------------------------------------------------- host mirrors
+//
+// The data-ownership scheme of section "Vector Engine Manager" for a base
+// with a host mirror. Rule 2: a batch may write every output and read every
+// input it names, so before it runs the device copy of each mirrored base
+// it uses must be current (uploaded from the mirror when only the mirror
+// is), and afterwards the mirror of every base it wrote is stale and the
+// host holds no write access to any base it named. Rule 3: an in-batch SYNC
+// copies the device copy back to the mirror; an in-batch DISCARD drops the
+// device copy. Rules 1 and 4: the host asks for read access (sync) or write
+// access (release, or discard when it has already updated its copy), and
+// the library tracks which copy is current.
+
+struct Ref {
+  int64_t base;
+  int kind;  // 0 read, 1 write, 2 SYNC, 3 DISCARD, 4 FREE
+  bool covers = false;  // a write that covers every element of the base
+};
+
+// the references an instruction makes to bases, reads before its write
+void instr_refs(Ctx& c, const vbe_instr& in, std::vector<Ref>* out) {
+  out->clear();
+  auto base_of = [&](int64_t vh) -> const vbe::ViewDesc* {
+    auto it = c.views.find(vh);
+    return it == c.views.end() ? nullptr : &it->second;
+  };
+  const int op = in.op;
+  if (op == VBE_OP_SYNC || op == VBE_OP_DISCARD || op == VBE_OP_FREE) {
+    if (auto v = base_of(in.out))
+      out->push_back({v->base, op == VBE_OP_SYNC ? 2 : (op == VBE_OP_DISCARD ? 3 : 4)});
+    return;
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (k == in.const_slot || in.in[k] == 0) continue;
+    if (auto v = base_of(in.in[k])) out->push_back({v->base, 0});
+  }
+  if (auto v = base_of(in.out)) {
+    auto b = c.bases.find(v->base);
+    bool covers = b != c.bases.end() && v->size() == b->second.nelem && !v->self_overlapping();
+    out->push_back({v->base, 1, covers});
+  }
+}
+
+// Before a batch: upload every mirrored base whose value only the mirror
+// holds and which the batch reads (or writes only in part) before writing
+// it whole; decide which in-batch SYNCs copy back. A read of a mirrored base
+// after its DISCARD in the same batch, while the mirror holds its value,
+// would need an upload in mid-batch and is rejected.
+void mirror_before(Ctx& c, vbe::Exec* ex, const vbe_instr* prog, int64_t n) {
+  c.mirror_syncs.clear();
+  bool any = false;
+  for (auto& kv : c.bases)
+    if (kv.second.mirror) any = true;
+  if (!any || !prog) return;
+  std::unordered_map<int64_t, std::pair<bool, bool>> sim;  // base -> (device valid, host valid)
+  std::vector<int64_t> upload;
+  std::vector<Ref> refs;
+  for (int64_t i = 0; i < n; ++i) {
+    instr_refs(c, prog[i], &refs);
+    for (auto& r : refs) {
+      auto b = c.bases.find(r.base);
+      if (b == c.bases.end() || !b->second.mirror) continue;
+      auto s = sim.find(r.base);
+      if (s == sim.end()) {
+        s = sim.emplace(r.base, std::make_pair(b->second.dev_valid, b->second.host_valid)).first;
+        bool needs_old = r.kind == 0 || r.kind == 2 || (r.kind == 1 && !r.covers);
+        if (!s->second.first && s->second.second && needs_old) {
+          upload.push_back(r.base);
+          s->second.first = true;
+        }
+      }
+      bool& dv = s->second.first;
+      bool& hv = s->second.second;
+      switch (r.kind) {
+        case 0:
+          if (!dv && hv)
+            vbe::fail(VBE_ERR_INVALID, "the batch reads mirrored base " + std::to_string(r.base) +
+                                           " after discarding it while the host copy holds its value");
+          if (!dv)
+            vbe::fail(VBE_ERR_UNINIT, "the batch reads mirrored base " + std::to_string(r.base) +
+                                          ", whose value no copy holds (it was discarded)");
+          break;
+        case 1: dv = true; hv = false; break;
+        case 2:
+          c.mirror_syncs[r.base].push_back(dv);
+          if (dv) hv = true;
+          break;
+        case 3: dv = false; break;
+        default: break;
+      }
+    }
+  }
+  for (int64_t b : upload) {
+    vbe::BaseRec& br = c.bases[b];
+    if (!br.dptr) br.dptr = vbe::dev_alloc(&c, ex, br.bytes());
+    vbe::stream_copy(&c, ex, br.dptr, br.mirror, br.bytes(), false);
+    br.dev_valid = true;
+    br.written = true;
+  }
+}
+
+// After a batch was enqueued: which copies are current, and host access.
+void mirror_after(Ctx& c, const vbe_instr* prog, int64_t n) {
+  std::vector<Ref> refs;
+  for (int64_t i = 0; i < n; ++i) {
+    instr_refs(c, prog[i], &refs);
+    for (auto& r : refs) {
+      auto b = c.bases.find(r.base);
+      if (b == c.bases.end() || !b->second.mirror) continue;
+      vbe::BaseRec& br = b->second;
+      br.host_write = false;
+      if (r.kind == 1) {
+        br.dev_valid = true;
+        br.host_valid = false;
+      } else if (r.kind == 2) {
+        if (br.dev_valid) br.host_valid = true;
+      } else if (r.kind == 3) {
+        br.dev_valid = false;
+      }
+    }
+  }
+  c.mirror_syncs.clear();
+}
+
+vbe::BaseRec& mirrored(Ctx& c, vbe_base base) {
+  auto it = c.bases.find(base);
+  if (it == c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
+  if (!it->second.mirror) vbe::fail(VBE_ERR_INVALID, "base has no host mirror");
+  return it->second;
+}
+
+// wait for everything enqueued so far (so no copy back to a mirror or
+// kernel is still in flight)
+void drain(Ctx& c) {
+  if (!c.record) vbe::cuda_check(cudaStreamSynchronize(c.exec.stream), "sync");
+  vbe::check_error_word(&c);
+}
+
+// read access: the mirror holds the current value on return
+void mirror_read(Ctx& c, vbe::BaseRec& br) {
+  drain(c);
+  if (br.host_valid) return;
+  if (!br.dev_valid || !br.dptr)
+    vbe::fail(VBE_ERR_UNINIT, "no copy of the base holds a value (it was discarded or never written)");
+  if (br.bytes() > 0) {
+    if (c.record) memcpy(br.mirror, br.dptr, (size_t)br.bytes());
+    else vbe::cuda_check(cudaMemcpy(br.mirror, br.dptr, (size_t)br.bytes(), cudaMemcpyDeviceToHost), "mirror sync");
+  }
+  br.host_valid = true;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* vbe_strerror(int code) {
@@ -183,6 +338,12 @@ int vbe_base_upload(vbe_ctx* ctx, vbe_base base, const void* host, int64_t nbyte
   if (nbytes > 0 && !host) vbe::fail(VBE_ERR_INVALID, "null host pointer");
   if (!it->second.dptr) it->second.dptr = vbe::dev_alloc(&c, &c.exec, it->second.bytes());
   it->second.written = true;
+  if (it->second.mirror) {
+    drain(c);  // no copy back to the mirror may still be in flight
+    it->second.dev_valid = true;
+    it->second.host_valid = false;
+    it->second.host_write = false;
+  }
   if (c.record) {
     if (nbytes > 0) memcpy(it->second.dptr, host, (size_t)nbytes);
     return VBE_OK;
@@ -242,7 +403,10 @@ int vbe_submit(vbe_ctx* ctx, const vbe_instr* prog, int64_t n, vbe_ticket* ticke
   API_BEGIN
   if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
   Ctx& c = ctx->c;
+  if (c.host_only && !c.record) vbe::fail(VBE_ERR_NO_DEVICE, "host-only context");
+  mirror_before(c, &c.exec, prog, n);
   vbe::exec_batch(&c, &c.exec, prog, n, true);
+  mirror_after(c, prog, n);
   if (ticket && c.record) *ticket = 0;
   if (ticket && !c.record) {
     if (c.ticket_ring.empty()) c.ticket_ring.assign(Ctx::kTicketRing, nullptr);
@@ -287,6 +451,16 @@ int vbe_sync(vbe_ctx* ctx, vbe_base base, void* host_dst, int64_t nbytes) {
   auto it = c.bases.find(base);
   if (it == c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
   if (nbytes < 0 || nbytes > it->second.bytes()) vbe::fail(VBE_ERR_INVALID, "bad size");
+  if (it->second.mirror && !it->second.dev_valid) {
+    // only the host mirror holds the value
+    drain(c);
+    if (!it->second.host_valid) vbe::fail(VBE_ERR_UNINIT, "no copy of the base holds a value");
+    if (nbytes > 0) {
+      if (!host_dst) vbe::fail(VBE_ERR_INVALID, "null host pointer");
+      memcpy(host_dst, it->second.mirror, (size_t)nbytes);
+    }
+    return VBE_OK;
+  }
   if (nbytes > 0 && !it->second.dptr) vbe::fail(VBE_ERR_UNINIT, "base was never written");
   if (c.record) {
     if (nbytes > 0) memcpy(host_dst, it->second.dptr, (size_t)nbytes);
@@ -309,6 +483,65 @@ int vbe_discard(vbe_ctx* ctx, vbe_base base) {
   auto it = ctx->c.bases.find(base);
   if (it == ctx->c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
   it->second.written = false;
+  it->second.dev_valid = false;
+  API_END
+}
+
+int vbe_mirror_attach(vbe_ctx* ctx, vbe_base base, void* host, int64_t nbytes) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  auto it = c.bases.find(base);
+  if (it == c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
+  if (nbytes != it->second.bytes()) vbe::fail(VBE_ERR_INVALID, "mirror size must equal the base size");
+  if (!host && nbytes > 0) vbe::fail(VBE_ERR_INVALID, "null host pointer");
+  if (it->second.external) vbe::fail(VBE_ERR_INVALID, "a registered base cannot have a host mirror");
+  if (it->second.mirror) vbe::fail(VBE_ERR_INVALID, "base already has a host mirror");
+  drain(c);  // work already enqueued on the base is finished
+  it->second.mirror = host ? host : (void*)&it->second;  // an empty base needs no memory
+  it->second.host_valid = true;
+  it->second.dev_valid = false;
+  it->second.host_write = true;
+  API_END
+}
+
+int vbe_mirror_sync(vbe_ctx* ctx, vbe_base base) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  mirror_read(c, mirrored(c, base));
+  API_END
+}
+
+int vbe_mirror_release(vbe_ctx* ctx, vbe_base base) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  vbe::BaseRec& br = mirrored(c, base);
+  mirror_read(c, br);
+  br.dev_valid = false;
+  br.host_write = true;
+  API_END
+}
+
+int vbe_mirror_discard(vbe_ctx* ctx, vbe_base base) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  vbe::BaseRec& br = mirrored(c, base);
+  drain(c);
+  br.host_valid = true;
+  br.dev_valid = false;
+  br.host_write = true;
+  API_END
+}
+
+int vbe_mirror_state(vbe_ctx* ctx, vbe_base base, int32_t* state) {
+  API_BEGIN
+  if (!ctx || !state) vbe::fail(VBE_ERR_INVALID, "null argument");
+  vbe::BaseRec& br = mirrored(ctx->c, base);
+  *state = (br.dev_valid ? VBE_MIRROR_DEVICE : 0) | (br.host_valid ? VBE_MIRROR_HOST : 0) |
+           (br.host_write ? VBE_MIRROR_HOST_WRITE : 0);
   API_END
 }
 

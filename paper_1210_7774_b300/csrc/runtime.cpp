@@ -339,6 +339,23 @@ std::string words_json(const std::vector<int64_t>& w) {
   return s + "]";
 }
 
+}  // namespace
+
+void stream_copy(Ctx* c, Exec* ex, void* dst, const void* src, int64_t bytes, bool to_host) {
+  if (bytes <= 0) return;
+  if (c->record) {
+    // executed by whoever runs the recorded launches, in order with them
+    c->rec_launches.push_back("{\"copy\":true,\"dst\":" + std::to_string((uintptr_t)dst) + ",\"src\":" +
+                              std::to_string((uintptr_t)src) + ",\"bytes\":" + std::to_string(bytes) + "}");
+    return;
+  }
+  cuda_check(cudaMemcpyAsync(dst, src, (size_t)bytes, to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice,
+                             ex->stream),
+             to_host ? "copy to the host mirror" : "copy from the host mirror");
+}
+
+namespace {
+
 void record_launch(Ctx* c, Exec* ex, Launch& L) {
   std::string j = "{\"key\":\"" + L.key + "\",\"entry\":\"" + L.entry + "\",\"grid\":" +
                   std::to_string(L.grid) + ",\"block\":" + std::to_string(L.block) + ",\"smem\":" +
@@ -1082,6 +1099,17 @@ std::vector<std::pair<int64_t, uintptr_t>> fingerprint(Ctx* c, const std::vector
 void do_action(Ctx* c, Exec* ex, const HostAction& a) {
   auto it = c->bases.find(a.base);
   if (it == c->bases.end()) return;
+  if (a.kind == 2 && it->second.mirror) {
+    // a SYNC of a base with a host mirror copies the device copy back to
+    // the mirror at this point of the batch (rule 3 of the ownership
+    // scheme), unless the device copy holds no current value there
+    auto q = c->mirror_syncs.find(a.base);
+    bool copy = q != c->mirror_syncs.end() && !q->second.empty() && q->second.front();
+    if (q != c->mirror_syncs.end() && !q->second.empty()) q->second.pop_front();
+    if (copy && it->second.dptr && it->second.bytes() > 0)
+      stream_copy(c, ex, it->second.mirror, it->second.dptr, it->second.bytes(), true);
+    return;
+  }
   if (a.kind == 0) {  // FREE
     if (it->second.dptr && !it->second.external) dev_free(c, ex, it->second.dptr, it->second.bytes());
     if (it->second.shadow) dev_free(c, ex, it->second.shadow, it->second.bytes());
@@ -1124,11 +1152,17 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
   std::vector<RInstr> rp_local;
   if (!known) rp_local = resolve_batch(c, prog, n);
   const std::vector<RInstr>& rp = known ? known->rp : rp_local;
-  bool has_free = false;
-  for (auto& r : rp)
-    if (r.op == VBE_OP_FREE) has_free = true;
-  bool graphs = allow_graph && (c->cfg.flags & VBE_GRAPHS) && !has_free && !c->record;
-  bool cacheable = may_cache && !has_free;
+  // a batch with FREE, or with a SYNC or DISCARD of a base that has a host
+  // mirror (they act on the host copy), is executed afresh every time
+  bool one_shot = false;
+  for (auto& r : rp) {
+    if (r.op == VBE_OP_FREE) one_shot = true;
+    if ((r.op == VBE_OP_SYNC || r.op == VBE_OP_DISCARD) && c->bases.count(r.out.base) &&
+        c->bases[r.out.base].mirror)
+      one_shot = true;
+  }
+  bool graphs = allow_graph && (c->cfg.flags & VBE_GRAPHS) && !one_shot && !c->record;
+  bool cacheable = may_cache && !one_shot;
   static uint64_t use_clock = 0;
   CachedBatch* cb = nullptr;
   CachedVariant* var = nullptr;

@@ -273,6 +273,13 @@ struct BaseRec {
   bool external = false;
   bool written = false;
   bool internal = false;  // created by the library (staging)
+  // host mirror (vbe_mirror_attach): the caller's copy of the base in host
+  // memory, kept in step with the device copy by the sync / release /
+  // discard rules of the ownership scheme
+  void* mirror = nullptr;
+  bool dev_valid = true;    // the device copy holds the base's current value
+  bool host_valid = false;  // the host mirror holds it
+  bool host_write = false;  // the host holds write access (it owns the base)
   int64_t bytes() const { return nelem * itemsize(dtype); }
 };
 
@@ -372,6 +379,9 @@ struct Ctx {
   std::unordered_map<std::string, std::string> rec_sources;
   int force_bulk = 0;  // VBE_STAGING: stage every eligible run in chunks of this many elements
   std::string force_tile;  // VBE_TILE: tile shape of every tile-fused group ("32x32", "s32x32", "t32x32"), never split
+  // per mirrored base, in instruction order: whether each in-batch SYNC of
+  // the current batch copies the device copy back to the mirror
+  std::unordered_map<int64_t, std::deque<bool>> mirror_syncs;
   // set by staged kernels whose bounded waits ran out (mapped host memory)
   unsigned* err_word = nullptr;
   unsigned* err_word_dev = nullptr;
@@ -397,6 +407,8 @@ void init_error_word(Ctx* c);
 void release_error_word(Ctx* c);
 bool take_error_word(Ctx* c);  // true (and cleared) when a staged kernel reported a failed wait
 void check_error_word(Ctx* c);  // fails with VBE_ERR_TIMEOUT when take_error_word is true
+// a host <-> device copy in stream order (recorded as a copy on VBE_RECORD contexts)
+void stream_copy(Ctx* c, Exec* ex, void* dst, const void* src, int64_t bytes, bool to_host);
 uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull);
 uint64_t hash64(const void* data, size_t n, uint64_t seed);
 std::string hex64(uint64_t v);

@@ -119,6 +119,11 @@ _SIGS = {
     "vbe_op_register": [_P, ctypes.c_char_p, ctypes.c_char_p, c_int32, c_int32, POINTER(c_int32)],
     "vbe_reduce_add_f64_noalloc": [c_void_p, c_int64, c_void_p, c_void_p],
     "vbe_measure_fp64_rate": [c_int32, c_int64, POINTER(ctypes.c_double), c_void_p, c_void_p],
+    "vbe_mirror_attach": [_P, c_int64, c_void_p, c_int64],
+    "vbe_mirror_sync": [_P, c_int64],
+    "vbe_mirror_release": [_P, c_int64],
+    "vbe_mirror_discard": [_P, c_int64],
+    "vbe_mirror_state": [_P, c_int64, POINTER(c_int32)],
 }
 EXPORTED = tuple(_SIGS)
 for _name, _args in _SIGS.items():
@@ -294,3 +299,28 @@ def vbe_measure_fp64_rate(op: str, iters: int, scratch_ptr: int, stream: int | N
     if code < 0:
         raise VbeError(code, "vbe_measure_fp64_rate")
     return out.value
+
+
+MIRROR_DEVICE, MIRROR_HOST, MIRROR_HOST_WRITE = 1, 2, 4
+
+
+def vbe_mirror_attach(ctx, base: int, host_ptr: int, nbytes: int) -> None:
+    _check(lib.vbe_mirror_attach(ctx, base, host_ptr, nbytes), ctx)
+
+
+def vbe_mirror_sync(ctx, base: int) -> None:
+    _check(lib.vbe_mirror_sync(ctx, base), ctx)
+
+
+def vbe_mirror_release(ctx, base: int) -> None:
+    _check(lib.vbe_mirror_release(ctx, base), ctx)
+
+
+def vbe_mirror_discard(ctx, base: int) -> None:
+    _check(lib.vbe_mirror_discard(ctx, base), ctx)
+
+
+def vbe_mirror_state(ctx, base: int) -> int:
+    st = c_int32(0)
+    _check(lib.vbe_mirror_state(ctx, base, byref(st)), ctx)
+    return st.value

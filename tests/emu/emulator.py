@@ -198,6 +198,11 @@ class Emulator:
             flat += [addr, addr + nbytes]
         ranges = (ctypes.c_ulonglong * max(1, len(flat)))(*flat)
         for L in js["launches"]:
+            if L.get("copy"):
+                # a host <-> device copy in stream order (device memory is host
+                # memory on a recording context)
+                ctypes.memmove(L["dst"], L["src"], L["bytes"])
+                continue
             lib = self.module(js["sources"][L["key"]])
             lib.emu_set_ranges(ranges, len(flat) // 2)
             entry = L["entry"]
