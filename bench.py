@@ -380,6 +380,22 @@ def _pool_rate(jobs, units):
     return units / wall, cores, wall
 
 
+def _mcore_seconds(program, reps=2):
+    """Best wall time of the mcore engine (the paper's multi-core blocked
+    Vector Engine, restated in C++) on every usable core, after one
+    untimed run."""
+    import mcore
+    prep = mcore.Prepared(program)
+    prep.run()
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        prep.run()
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return best, mcore.cores()
+
+
 def config_subkeys(args, V, torch, local, stream, hbm, fp64):
     """One sub-key per configuration beside the headline: Jacobi 256^2,
     shallow water 4096^2 float64 (50 steps), Monte-Carlo pi (256 instances)
@@ -422,6 +438,9 @@ def config_subkeys(args, V, torch, local, stream, hbm, fp64):
                    "bounds it, not HBM",
               cpu_baseline={"value": osec / 10 * 1e6, "unit": "us/iteration", "cores": 1, "kind": "oracle",
                             "sample": "the whole configuration (10 iterations), best of 3"})
+    msec, mcores = _mcore_seconds(p)
+    jr["cpu_mcore"] = {"value": msec / 10 * 1e6, "unit": "us/iteration", "cores": mcores, "kind": "mcore",
+                       "sample": "the whole configuration (10 iterations), best of 2"}
     out["jacobi_256_f64_10it"] = jr
     # --- shallow water 4096^2 float64, 50 steps
     N, steps = 4096, 50
@@ -450,6 +469,11 @@ def config_subkeys(args, V, torch, local, stream, hbm, fp64):
     sw["cpu_baseline"] = {"value": 6 * 8 * 1024 * 1024 / osec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                           "ms_per_step_at_4096": osec * (N * N) / (1024 * 1024) * 1e3,
                           "sample": f"one step of 1024x1024 ({osec:.1f} s), scaled by cells"}
+    ps = shallow_water(2048, 2)
+    msec, mcores = _mcore_seconds(ps)
+    sw["cpu_mcore"] = {"value": 6 * 8 * 2048 * 2048 * 2 / msec / 1e9, "unit": "GB/s", "cores": mcores,
+                       "kind": "mcore", "ms_per_step_at_4096": msec / 2 * (N * N) / (2048 * 2048) * 1e3,
+                       "sample": f"two steps of 2048x2048 ({msec:.2f} s), scaled by cells"}
     out["shallow_water_4096_f64_50st"] = sw
     # --- Monte-Carlo pi, 256 instances in one packed launch
     sizes = mc_sizes(256)
@@ -477,6 +501,9 @@ def config_subkeys(args, V, torch, local, stream, hbm, fp64):
                           "sample": f"the 192 smallest instances ({ns} samples, {osec:.1f} s)",
                           "all_cores": {"value": prate, "cores": cores,
                                         "sample": f"the same instances, one per task, spawn process pool ({wall:.1f} s)"}}
+    msec, mcores = _mcore_seconds(sub)
+    mc["cpu_mcore"] = {"value": ns / msec, "unit": "samples/s", "cores": mcores, "kind": "mcore",
+                       "sample": f"the 192 smallest instances ({ns} samples, {msec:.2f} s)"}
     mc["samples"] = samples
     out["montecarlo_pi_256"] = mc
     # --- serving loop
@@ -493,6 +520,17 @@ def config_subkeys(args, V, torch, local, stream, hbm, fp64):
                           "sample": f"8 requests of the same mix (another seed), {one:.1f} s",
                           "all_cores": {"value": prate, "cores": cores,
                                         "sample": f"64 requests of that mix, spawn process pool ({wall:.1f} s)"}}
+    import mcore
+    from workloads.serving import request_program
+    progs = [request_program(k, prm) for k, prm in jobs[:8]]
+    for q in progs[:2]:
+        mcore.run(q)
+    t0 = time.perf_counter()
+    for q in progs:
+        mcore.run(q)
+    msec = time.perf_counter() - t0
+    sv["cpu_mcore"] = {"value": len(progs) / msec, "unit": "requests/s", "cores": mcore.cores(), "kind": "mcore",
+                       "sample": f"the same 8 requests, one after another, each on every core ({msec:.1f} s)"}
     out["serving_64_clients"] = sv
     return out
 
@@ -720,7 +758,7 @@ def main():
     f64 = res["float64"]
     value = aggregate_value(f64["cbytes"], sec, world) / 1e9
     achieved = f64["cbytes"] / sec / 1e9
-    cpu = None
+    cpu = cpu_mcore = None
     if not args.no_cpu_baseline:
         import oracle
         from workloads import blackscholes
@@ -730,6 +768,11 @@ def main():
         dt = time.perf_counter() - t0
         cpu = {"value": prog.compulsory_bytes() / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.ref_sample} options of the same workload, float64, one pass ({dt:.1f} s)"}
+        pm = blackscholes(4 * args.ref_sample, "float64")
+        msec, mcores = _mcore_seconds(pm)
+        cpu_mcore = {"value": pm.compulsory_bytes() / msec / 1e9, "unit": "GB/s", "cores": mcores, "kind": "mcore",
+                     "sample": f"{4 * args.ref_sample} options of the same workload, float64, best of 2 "
+                               f"({msec:.2f} s)"}
     f32 = res["float32"]
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -755,6 +798,7 @@ def main():
         "gpu_launches": int(round(f64["fused"]["launches_per_step"] * args.steps)),
         "clocks": ck,
         "cpu_baseline": cpu,
+        "cpu_mcore": cpu_mcore,
     }
     if not args.no_configs and world == 1:
         ck2 = Clocks(local)
