@@ -299,6 +299,18 @@ int vbe_views_may_overlap(vbe_ctx* ctx, vbe_view a, vbe_view b, int32_t* out);
  * protocol as vbe_plan. */
 int vbe_debug_take_launches(vbe_ctx* ctx, char* buf, int64_t cap, int64_t* needed);
 
+/* Test hook for failure detection (no counterpart in the paper): from now
+ * on, kernels this context compiles give their compute threads at most
+ * `polls` polls (0: none) when they wait for data staged by bulk or tensor
+ * copies, so that those waits run out and the kernel takes its failure
+ * path: it sets the context's error word, stops computing, lets its
+ * producer and drain waits (which keep their full limit) see every copy it
+ * issued land, and exits; the next vbe_wait / vbe_sync returns
+ * VBE_ERR_TIMEOUT and the batch's results are invalid. polls < 0 restores
+ * the normal limit (2^24 polls). Waits for enqueued work first and drops
+ * the context's cached launches. VBE_ERR_INVALID if polls > 2^24. */
+int vbe_debug_set_wait_polls(vbe_ctx* ctx, int64_t polls);
+
 typedef struct vbe_stats {
   int64_t kernel_launches;   /* launches of generated kernels                 */
   int64_t graph_launches;    /* CUDA graph replays                            */

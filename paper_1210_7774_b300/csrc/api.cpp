@@ -423,7 +423,10 @@ int vbe_wait(vbe_ctx* ctx, vbe_ticket ticket, int64_t timeout_ns) {
   API_BEGIN
   if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
   Ctx& c = ctx->c;
-  if (c.record && ticket == 0) return VBE_OK;
+  if (c.record && ticket == 0) {
+    vbe::check_error_word(&c);  // a recorded kernel's bounded wait may have run out
+    return VBE_OK;
+  }
   if (ticket <= 0 || ticket >= c.next_ticket || c.ticket_ring.empty()) vbe::fail(VBE_ERR_INVALID, "unknown ticket");
   cudaEvent_t ev = c.ticket_ring[ticket % Ctx::kTicketRing];
   if (timeout_ns < 0) {
@@ -679,6 +682,20 @@ int vbe_debug_take_launches(vbe_ctx* ctx, char* buf, int64_t cap, int64_t* neede
     buf[js.size()] = '\0';
     c.rec_launches.clear();
   }
+  API_END
+}
+
+int vbe_debug_set_wait_polls(vbe_ctx* ctx, int64_t polls) {
+  API_BEGIN
+  if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
+  Ctx& c = ctx->c;
+  if (polls > (int64_t)(1u << 24)) vbe::fail(VBE_ERR_INVALID, "at most 2^24 polls");
+  if (!c.host_only) vbe::cuda_check(cudaStreamSynchronize(c.exec.stream), "sync");
+  c.cwait = polls < 0 ? -1 : polls;
+  // cached launches hold kernels compiled with the previous limit
+  for (auto& kv : c.batches)
+    for (auto& v : kv.second.v) vbe::release_variant(v);
+  c.batches.clear();
   API_END
 }
 

@@ -421,6 +421,12 @@ template <> __device__ __forceinline__ void vbe_arg_upd<double>(double& v, i64& 
   const bool take = (xn || vn) ? (xn && (!vn || j < i)) : (better || (kx == kv && j < i));
   if (take) { v = x; i = j; }
 }
+// polls of a compute thread's wait for its staged data (the waits of a
+// producer and of the final drain always allow 2^24); a context may lower it
+// (vbe_debug_set_wait_polls) to make those waits run out in a test
+#ifndef VBE_CWAIT
+#define VBE_CWAIT (1u << 24)
+#endif
 // RANDOM: splitmix64 finaliser of seed + (key + step*m + 1) * golden gamma,
 // top 53 bits scaled to [0, 1)
 __device__ __forceinline__ double vbe_u01(u64 seed, u64 key, u64 step, u64 m) {
@@ -468,14 +474,18 @@ __device__ __forceinline__ void vbe_bulk_g2s(void* dst, const void* src, unsigne
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(vbe_saddr(dst)), "l"(src), "r"(bytes), "r"(vbe_saddr(bar)) : "memory");
 }
-__device__ __forceinline__ bool vbe_mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (unsigned it = 0; it < (1u << 24); ++it) {
+// at most `polls` polls: false when the phase has not completed by then
+__device__ __forceinline__ bool vbe_mbar_wait_n(unsigned long long* bar, unsigned parity, unsigned polls) {
+  for (unsigned it = 0; it < polls; ++it) {
     unsigned ok;
     asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
                  : "=r"(ok) : "r"(vbe_saddr(bar)), "r"(parity) : "memory");
     if (ok) return true;
   }
   return false;
+}
+__device__ __forceinline__ bool vbe_mbar_wait(unsigned long long* bar, unsigned parity) {
+  return vbe_mbar_wait_n(bar, parity, 1u << 24);
 }
 #define VBE_DYN_SMEM extern __shared__ __align__(128) unsigned char vbe_smem[]
 // programmatic dependent launch: a kernel launched while its predecessor on
@@ -1050,7 +1060,7 @@ struct Gen {
       << "  int k = 0;\n"
       << "  for (i64 cc = blockIdx.x; cc < nfull; cc += gridDim.x, ++k) {\n"
       << "    const int st = k & 1;\n"
-      << "    if (threadIdx.x == 0) { s_ok = vbe_mbar_wait(&bars[st], (unsigned)((k >> 1) & 1)); if (s_ok) inflight &= ~(1u << st); }\n"
+      << "    if (threadIdx.x == 0) { s_ok = vbe_mbar_wait_n(&bars[st], (unsigned)((k >> 1) & 1), VBE_CWAIT); if (s_ok) inflight &= ~(1u << st); }\n"
       << "    __syncthreads();\n"
       << "    if (!s_ok) { failed = true; break; }\n"
       << "    for (i64 vi = threadIdx.x; vi < CH / " << E << "; vi += bd) {\n";
@@ -1800,10 +1810,12 @@ static void emit_tma_prologue(std::ostringstream& o, const Group& g, const Group
     << "  vbe_grid_wait();\n"
     << "  unsigned long long* const full = (unsigned long long*)(vbe_smem + " << (total - 16 * NS) << ");\n"
     << "  unsigned long long* const empty = full + " << NS << ";\n"
+    << "  __shared__ volatile int s_abort;  // set by compute threads whose wait ran out\n"
     << "  if (threadIdx.x == 0) {\n"
     << "    for (int s = 0; s < " << NS << "; ++s) { vbe_mbar_init(&full[s], 1); vbe_mbar_init(&empty[s], " << NW
     << "); }\n"
     << "    vbe_fence_mbar_init();\n"
+    << "    s_abort = 0;\n"
     << "  }\n"
     << "  __syncthreads();\n"
     << pre
@@ -1816,6 +1828,9 @@ static void emit_tma_prologue(std::ostringstream& o, const Group& g, const Group
     << "        const int st = kt % " << NS << ";\n"
     << "        if (kt >= " << NS << " && !vbe_mbar_wait(&empty[st], (unsigned)((kt / " << NS << " - 1) & 1))) { "
     << err << "; break; }\n"
+    << "        // compute threads that gave up release stages without waiting for\n"
+    << "        // their copies: issue nothing more, so a stage never has two in flight\n"
+    << "        if (kt >= " << NS << " && s_abort) break;\n"
     << "        const i64 ti = t / tpr, tj = t - ti * tpr;\n"
     << "        vbe_fence_proxy_async();\n"
     << "        vbe_mbar_expect_tx(&full[st], " << tx << "u);\n";
@@ -1836,8 +1851,8 @@ static void emit_tma_prologue(std::ostringstream& o, const Group& g, const Group
     << "    int kt = 0;\n"
     << "    for (i64 t = blockIdx.x; t < ntiles; t += gridDim.x, ++kt) {\n"
     << "      const int st = kt % " << NS << ";\n"
-    << "      if (!failed && !vbe_mbar_wait(&full[st], (unsigned)((kt / " << NS << ") & 1))) { failed = true; " << err
-    << "; }\n";
+    << "      if (!failed && !vbe_mbar_wait_n(&full[st], (unsigned)((kt / " << NS << ") & 1), VBE_CWAIT)) { "
+    << "failed = true; s_abort = 1; " << err << "; }\n";
   // phases meeting at block barriers must agree on whether to run
   if (!group_stacked(g)) o << "      failed = vbe_bar_or(1, " << ts.block << ", failed);\n";
   o << "      if (!failed) {\n"

@@ -86,16 +86,27 @@ std::vector<char> compile_cached(Ctx* c, const std::string& src, bool* compiled)
   return cubin;
 }
 
+// the source a context compiles: with a wait limit set for tests, the
+// limit is defined ahead of the text (and so is part of the cache key)
+static bool with_wait_limit(const Ctx* c, const std::string& src, std::string* src2, std::string* key2) {
+  if (c->cwait < 0) return false;
+  *src2 = "#define VBE_CWAIT " + std::to_string(c->cwait) + "u\n" + src;
+  *key2 = src_key(*src2);
+  return true;
+}
+
 // Compile, in parallel threads, every source not loaded yet (first sight
 // of a batch), then load the modules.
 void precompile(Ctx* c, const std::vector<std::string>& srcs, const std::vector<std::string>* keys) {
   std::vector<std::string> todo, todo_keys;
   std::set<std::string> seen;
   for (size_t i = 0; i < srcs.size(); ++i) {
-    const std::string k = keys ? (*keys)[i] : src_key(srcs[i]);
+    std::string src2, key2;
+    const bool adj = with_wait_limit(c, srcs[i], &src2, &key2);
+    const std::string k = adj ? key2 : (keys ? (*keys)[i] : src_key(srcs[i]));
     if (c->kernels.count(k) || seen.count(k)) continue;
     seen.insert(k);
-    todo.push_back(srcs[i]);
+    todo.push_back(adj ? src2 : srcs[i]);
     todo_keys.push_back(k);
   }
   if (todo.size() <= 1) return;
@@ -136,12 +147,18 @@ void precompile(Ctx* c, const std::vector<std::string>& srcs, const std::vector<
   }
 }
 
-std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src, const std::string* key_in) {
-  const std::string key = key_in ? *key_in : src_key(src);
+std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src_in, const std::string* key_in) {
+  std::string src2, key2;
+  const bool adj = with_wait_limit(c, src_in, &src2, &key2);
+  const std::string& src = adj ? src2 : src_in;
+  const std::string key = adj ? key2 : (key_in ? *key_in : src_key(src_in));
   auto it = c->kernels.find(key);
   if (it != c->kernels.end()) return it->second;
   if (c->record) {
     c->rec_sources[key] = src;
+    // with a wait limit set, launches of this source are recorded under the
+    // key of the text actually compiled
+    if (adj) c->rec_alias[key_in ? *key_in : src_key(src_in)] = key;
     auto k = std::make_shared<Kernel>();
     c->kernels[key] = k;
     return k;
@@ -357,7 +374,12 @@ void stream_copy(Ctx* c, Exec* ex, void* dst, const void* src, int64_t bytes, bo
 namespace {
 
 void record_launch(Ctx* c, Exec* ex, Launch& L) {
-  std::string j = "{\"key\":\"" + L.key + "\",\"entry\":\"" + L.entry + "\",\"grid\":" +
+  std::string key = L.key;
+  if (c->cwait >= 0) {
+    auto a = c->rec_alias.find(L.key);
+    if (a != c->rec_alias.end()) key = a->second;
+  }
+  std::string j = "{\"key\":\"" + key + "\",\"entry\":\"" + L.entry + "\",\"grid\":" +
                   std::to_string(L.grid) + ",\"block\":" + std::to_string(L.block) + ",\"smem\":" +
                   std::to_string(L.smem);
   if (L.packed) {

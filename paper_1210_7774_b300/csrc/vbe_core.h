@@ -377,7 +377,11 @@ struct Ctx {
   std::map<uintptr_t, size_t> host_allocs;
   std::vector<std::string> rec_launches;
   std::unordered_map<std::string, std::string> rec_sources;
+  std::unordered_map<std::string, std::string> rec_alias;  // source key -> key with the test wait limit
   int force_bulk = 0;  // VBE_STAGING: stage every eligible run in chunks of this many elements
+  // vbe_debug_set_wait_polls: >= 0 replaces the compute threads' wait limit
+  // (VBE_CWAIT) in every kernel this context compiles from then on
+  int64_t cwait = -1;
   std::string force_tile;  // VBE_TILE: tile shape of every tile-fused group ("32x32", "s32x32", "t32x32"), never split
   // per mirrored base, in instruction order: whether each in-batch SYNC of
   // the current batch copies the device copy back to the mirror

@@ -124,6 +124,7 @@ _SIGS = {
     "vbe_mirror_release": [_P, c_int64],
     "vbe_mirror_discard": [_P, c_int64],
     "vbe_mirror_state": [_P, c_int64, POINTER(c_int32)],
+    "vbe_debug_set_wait_polls": [_P, c_int64],
 }
 EXPORTED = tuple(_SIGS)
 for _name, _args in _SIGS.items():
@@ -324,3 +325,9 @@ def vbe_mirror_state(ctx, base: int) -> int:
     st = c_int32(0)
     _check(lib.vbe_mirror_state(ctx, base, byref(st)), ctx)
     return st.value
+
+
+def vbe_debug_set_wait_polls(ctx, polls: int) -> None:
+    """Test hook: compute threads' staged-data waits allow ``polls`` polls in
+    kernels compiled from now on (negative: the normal limit)."""
+    _check(lib.vbe_debug_set_wait_polls(ctx, polls), ctx)

@@ -32,6 +32,8 @@ char g_bad_msg[256];
 std::barrier<>* g_block_bar = nullptr;
 std::vector<std::unique_ptr<std::barrier<>>> g_warp_bar;
 unsigned long long g_xchg[1024];
+int g_emu_drop = 0;
+extern "C" void emu_set_drop(int d) { g_emu_drop = d; }
 """
 
 _WRAP_COMMON = """
@@ -115,7 +117,9 @@ class Emulator:
         self.launches = 0
 
     def _key(self, src: str) -> str:
-        return hashlib.sha1((src + self._emu_h).encode()).hexdigest()[:20]  # the source names the headers' hash
+        # the source names the soft float64 headers' hash; the emulation
+        # header and the wrappers are part of every module too
+        return hashlib.sha1((src + self._emu_h + _GLOBALS + _WRAP_COMMON).encode()).hexdigest()[:20]
 
     @property
     def _emu_h(self) -> str:
@@ -191,7 +195,9 @@ class Emulator:
         self.mods[h] = lib
         return lib
 
-    def run(self, record_json: str) -> int:
+    def run(self, record_json: str, drop_copies: bool = False) -> int:
+        """Execute the recorded launches in order; ``drop_copies``: bulk and
+        tensor copies never land (every wait on them runs out)."""
         js = json.loads(record_json)
         flat = []
         for addr, nbytes in js["allocs"]:
@@ -205,6 +211,7 @@ class Emulator:
                 continue
             lib = self.module(js["sources"][L["key"]])
             lib.emu_set_ranges(ranges, len(flat) // 2)
+            lib.emu_set_drop(1 if drop_copies else 0)
             entry = L["entry"]
             if L.get("packed"):
                 ctypes.c_uint.from_address(L["work"]).value = 0

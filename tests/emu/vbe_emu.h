@@ -165,8 +165,12 @@ inline void emu_bar_landed(unsigned long long* bar, long long bytes) {
     emu_bar_settle(b);
   }
 }
+// g_emu_drop: bulk and tensor copies never land (a copy that never
+// completes), and every wait gives up after 50 ms instead of 60 s
+extern int g_emu_drop;
 inline bool vbe_mbar_wait(unsigned long long* bar, unsigned parity) {
-  const auto until = std::chrono::steady_clock::now() + std::chrono::seconds(60);
+  const auto until = std::chrono::steady_clock::now() +
+                     (g_emu_drop ? std::chrono::milliseconds(50) : std::chrono::milliseconds(60000));
   for (;;) {
     {
       std::lock_guard<std::mutex> g(emu_bar_mu());
@@ -178,9 +182,16 @@ inline bool vbe_mbar_wait(unsigned long long* bar, unsigned parity) {
     std::this_thread::yield();
   }
 }
+// a wait of at most `polls` polls: zero polls give up at once, as on the
+// device; otherwise the time-limited wait above
+inline bool vbe_mbar_wait_n(unsigned long long* bar, unsigned parity, unsigned polls) {
+  if (polls == 0) return false;
+  return vbe_mbar_wait(bar, parity);
+}
 inline void vbe_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
   if ((((uintptr_t)dst) | ((uintptr_t)src) | bytes) % 16 != 0 && g_bad.fetch_add(1) == 0)
     snprintf(g_bad_msg, sizeof g_bad_msg, "bulk copy not 16-byte aligned: %p <- %p, %u bytes", dst, src, bytes);
+  if (g_emu_drop) return;
   if (emu_ok(src, bytes)) memcpy(dst, src, bytes);
   emu_bar_landed(bar, bytes);
 }
@@ -221,6 +232,7 @@ inline void vbe_grid_wait() {}  // launches run one after another on the host
 // map (address, row stride, rows, row bytes, box columns, box rows, element
 // size); elements outside the tensor read as zeros
 inline void vbe_tma_2d(void* dst, const void* tmap, int x, int y, unsigned long long* bar) {
+  if (g_emu_drop) return;
   const long long* m = (const long long*)tmap;
   const char* base = (const char*)m[0];
   const long long pitch = m[1], rows = m[2], bc = m[4], br = m[5], isz = m[6];
