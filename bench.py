@@ -328,12 +328,82 @@ def gpu_blackscholes(args, rank, world, local):
                     e2e_step()
                 torch.cuda.synchronize()
                 e2e_sec = (time.perf_counter() - t0) / e2e_steps
-                out["e2e"] = {"value": cbytes / e2e_sec / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                              "d2h_bytes_per_step": d2h}
-            ex.close()
+                out["e2e_serial"] = {"value": cbytes / e2e_sec / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                                     "d2h_bytes_per_step": d2h,
+                                     "how": "one context: upload the inputs, submit, sync the outputs, in turn"}
+                ex.close()
+                if dtype == "float64":
+                    out["e2e"] = e2e_pipelined(V, Executor, prog, dtype, flags_fused, local, cache, args, torch)
+            if ex.ctx:
+                ex.close()
         out["cbytes"] = cbytes
         res[dtype] = out
     return res, dist
+
+
+def e2e_pipelined(V, Executor, prog, dtype, flags, local, cache, args, torch, workers=4):
+    """End to end through the C ABI with the copies overlapped: the options
+    are split over ``workers`` contexts (each with its own stream), each
+    driven by a host thread that uploads its share of the inputs from pinned
+    memory (vbe_base_upload), submits the batch and reads its results back
+    (vbe_sync). The calls block their own thread only, so while one share's
+    inputs go to the device another's results come back and a third computes:
+    both directions of the host link are busy at once. A step is every
+    share's upload, batch and read-back; its time is the wall clock of the
+    slowest thread."""
+    import threading
+
+    from workloads import blackscholes
+    n = prog.meta["n"]
+    cuts = np.linspace(0, n, workers + 1).astype(np.int64)
+    ins = {k: prog.bases[i].init for k, i in prog.meta["input_ids"].items()}
+    shares = []
+    for w in range(workers):
+        lo, hi = int(cuts[w]), int(cuts[w + 1])
+        p = blackscholes(hi - lo, dtype, inputs={k: v[lo:hi] for k, v in ins.items()})
+        ex = Executor(flags, device=local, cache_dir=cache)
+        L = ex.load(p)
+        host_in = {bid: torch.from_numpy(b.init).pin_memory() for bid, b in p.bases.items() if b.init is not None}
+        host_out = {bid: torch.empty(p.bases[bid].nelem, dtype=getattr(torch, dtype)).pin_memory()
+                    for bid in p.outputs}
+        shares.append((ex, L, host_in, host_out))
+    h2d = sum(t.numel() * t.element_size() for sh in shares for t in sh[2].values())
+    d2h = sum(t.numel() * t.element_size() for sh in shares for t in sh[3].values())
+    cbytes = prog.compulsory_bytes()
+
+    def one(sh):
+        ex, L, host_in, host_out = sh
+        for bid, t in host_in.items():
+            V.vbe_base_upload(ex.ctx, L.base[bid], t.data_ptr(), t.numel() * t.element_size())
+        ex.submit(L, 0)
+        for bid, t in host_out.items():
+            V.vbe_sync(ex.ctx, L.base[bid], t.data_ptr(), t.numel() * t.element_size())
+
+    def run_steps(k):
+        barrier = threading.Barrier(workers)
+
+        def worker(sh):
+            torch.cuda.set_device(local)
+            for _ in range(k):
+                barrier.wait()  # every share's step starts together
+                one(sh)
+        th = [threading.Thread(target=worker, args=(sh,)) for sh in shares]
+        t0 = time.perf_counter()
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return time.perf_counter() - t0
+
+    run_steps(2)  # warm-up (tuning, first launches)
+    steps = max(3, args.steps // 4)
+    sec = run_steps(steps) / steps
+    for sh in shares:
+        sh[0].close()
+    return {"value": cbytes / sec / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "workers": workers,
+            "how": f"{workers} contexts, one host thread each, over equal shares of the options: pinned inputs "
+                   "uploaded, batch submitted, results synced back, each thread in turn; the threads overlap"}
 
 
 # ------------------------------------------------- per-configuration keys
@@ -667,7 +737,7 @@ def serving_bench(args, V, local):
     res = {}
     for name, flags in (("fused", V.VBE_FUSE | V.VBE_PACK), ("plain", 0)):
         ctx = V.vbe_init(local, flags, 0, None, cache)
-        srv = V.vbe_server_create(ctx, 16, 60 << 30, flags)
+        srv = V.vbe_server_create(ctx, 16, 60 << 30, flags, workers=args.serve_workers)
         # every request is built and packed (views, bytecodes, result buffers
         # not yet touched) before the clock starts, so the Python load
         # generator stays off the measured path; the clients only submit,
@@ -675,20 +745,27 @@ def serving_bench(args, V, local):
         progs = [request_program(*m) for m in mix]
         reqs = [Request(p) for p in progs]
         # capacity: after a pass over 256 requests of the same mix (kernel
-        # compilation), a closed loop over 512 further requests that have not
-        # been seen (another seed), so per-size work is paid as it is in the
-        # timed run
+        # compilation), a closed loop of the 64 clients over 512 further
+        # requests that have not been seen (another seed), so per-size work is
+        # paid as it is in the timed run: each client submits its next
+        # request as soon as its previous one is back
         extra = [Request(request_program(*m)) for m in request_mix(768, seed=1210_7774 + 99)]
         for batch in (extra[:256], extra[256:]):
+            def closed(c, batch=batch):
+                for i in range(c, len(batch), 64):
+                    V.vbe_server_wait(srv, V.vbe_server_submit(srv, batch[i].req), -1)
+            th = [threading.Thread(target=closed, args=(c,)) for c in range(64)]
             t0 = time.perf_counter()
-            ids = [V.vbe_server_submit(srv, r.req) for r in batch]
-            for i in ids:
-                V.vbe_server_wait(srv, i, -1)
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
             cap = len(batch) / (time.perf_counter() - t0)
         del extra
         rate = 0.7 * cap if name == "fused" else res["fused"]["arrival_rate"]
         arrivals = poisson_arrivals(n_req, rate)
         lat = [None] * n_req
+        parts = [None] * n_req  # (queued, planning, device and copies) per request, ms
         nclients = 64
         start = time.perf_counter() + 0.2
 
@@ -701,6 +778,8 @@ def serving_bench(args, V, local):
                 r = V.vbe_server_wait(srv, rid, -1)
                 reqs[i] = None
                 lat[i] = (r.t_done_ns - r.t_arrive_ns) / 1e6
+                parts[i] = ((r.t_admit_ns - r.t_arrive_ns) / 1e6, (r.t_issued_ns - r.t_admit_ns) / 1e6,
+                            (r.t_done_ns - r.t_issued_ns) / 1e6)
 
         th = [threading.Thread(target=client, args=(c,)) for c in range(nclients)]
         for t in th:
@@ -711,9 +790,16 @@ def serving_bench(args, V, local):
         V.vbe_server_destroy(srv)
         V.vbe_finalize(ctx)
         lat = np.array(lat)
+        pa = np.array(parts)
         res[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "throughput_req_s": n_req / wall, "capacity_req_s": cap, "arrival_rate": rate}
+                     "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50)),
+                     "throughput_req_s": n_req / wall, "capacity_req_s": cap, "arrival_rate": rate,
+                     "breakdown_ms": {k: {"p50": float(np.percentile(pa[:, q], 50)),
+                                          "p99": float(np.percentile(pa[:, q], 99))}
+                                      for q, k in enumerate(("queued", "host_planning", "device_and_copies"))}}
     res["requests"] = n_req
+    res["server"] = {"slots": 16, "workers": args.serve_workers, "mem_cap_bytes": 60 << 30, "clients": 64,
+                     "rate": "0.7 x the fused capacity, for both paths"}
     return res
 
 
@@ -731,6 +817,7 @@ def main():
                     help="leave out the per-configuration sub-keys (Jacobi, shallow water, MC, serving)")
     ap.add_argument("--dtypes", default="float64,float32", help="profiling: restrict the dtypes run")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
+    ap.add_argument("--serve-workers", type=int, default=4, help="serving: scheduler threads of the server")
     ap.add_argument("--paths", default="fused,plain", help="profiling: restrict the paths run (jacobi: paper_size runs the 7168^2 part alone)")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -795,6 +882,7 @@ def main():
                          kernel_hash=f64["kernel_hash"]),
         "fp64_peak": fp64,
         "e2e": f64["e2e"],
+        "e2e_serial": f64["e2e_serial"],
         "gpu_launches": int(round(f64["fused"]["launches_per_step"] * args.steps)),
         "clocks": ck,
         "cpu_baseline": cpu,

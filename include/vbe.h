@@ -417,6 +417,9 @@ typedef struct vbe_server_config {
   int32_t max_queue;      /* pending requests accepted before VBE_ERR_BUSY */
   uint64_t mem_cap_bytes; /* admission cap on the sum of request footprints */
   uint32_t flags;         /* VBE_FUSE etc. for request execution             */
+  int32_t workers;        /* scheduler threads (0 means 1), each with its own
+                             context on the same device and a share of the
+                             slots; they plan and launch requests in parallel */
 } vbe_server_config;
 
 typedef struct vbe_request_result {
@@ -425,17 +428,24 @@ typedef struct vbe_request_result {
   int64_t footprint_bytes;
   double t_arrive_ns;     /* submit time (steady clock)                     */
   double t_admit_ns;      /* admitted (slot + memory available)             */
-  double t_done_ns;       /* results copied to the host buffers             */
+  double t_done_ns;       /* results copied to the host buffers (by the
+                             vbe_server_wait call that fetched them)       */
+  double t_issued_ns;     /* the request's kernels and result copies were
+                             enqueued (t_issued - t_admit: host planning)  */
 } vbe_request_result;
 
 typedef struct vbe_server vbe_server;
 
 /* Start a server on a context (which it then owns for execution; do not
- * submit on the context directly while the server runs). A scheduler
- * thread admits queued requests while a slot is free and the admitted
+ * submit on the context directly while the server runs). Scheduler threads
+ * (`workers`; the first uses ctx, the others contexts of their own with
+ * ctx's device, flags and cache directory) admit queued requests in
+ * arrival order while one of their slots is free and the admitted
  * footprints fit mem_cap_bytes (continuous batching: a request is admitted
- * as soon as another completes), executes each on its slot's stream, and
- * completes it when its results are on the host. */
+ * as soon as another completes), execute each on its slot's stream, and
+ * complete it when its results are in pinned staging. Each worker holds the
+ * server's lock only to move requests between the queue, its slots and the
+ * finished state. */
 int vbe_server_create(vbe_ctx* ctx, const vbe_server_config* cfg, vbe_server** out);
 /* Enqueue a request; *id identifies it. Its footprint is the bytes of all
  * its bases plus those of every base it writes through some views and reads
@@ -443,7 +453,9 @@ int vbe_server_create(vbe_ctx* ctx, const vbe_server_config* cfg, vbe_server** o
  * VBE_ERR_ADMISSION if the footprint alone exceeds the cap, VBE_ERR_BUSY if
  * the queue is full. */
 int vbe_server_submit(vbe_server* srv, const vbe_request* req, int64_t* id);
-/* Wait for a request (timeout_ns < 0: forever) and fetch its result record. */
+/* Wait for a request (timeout_ns < 0: forever), copy its results into the
+ * request's result buffers (in the calling thread) and fetch its result
+ * record. A request's results reach its buffers only through this call. */
 int vbe_server_wait(vbe_server* srv, int64_t id, int64_t timeout_ns, vbe_request_result* out);
 /* Drain, stop the scheduler, release everything. */
 int vbe_server_destroy(vbe_server* srv);

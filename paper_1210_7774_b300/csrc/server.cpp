@@ -6,10 +6,12 @@
 // (requests) arrive concurrently. A scheduler thread owns the context. It
 // admits queued requests in arrival order while a slot (a stream with its
 // own reduction scratch) is free and the admitted footprints fit the
-// memory cap, executes each request's batch on its slot's stream, copies
-// the results into pinned staging memory, and on completion hands them to
-// the client. A request is admitted as soon as another completes, so work
-// from different requests overlaps on the device.
+// memory cap, executes each request's batch on its slot's stream, queues
+// the results' copies into pinned staging memory, and on completion
+// releases the request's device memory and wakes its client, which copies
+// the results into its own buffers in its own thread. A request is admitted
+// as soon as another completes, so work from different requests overlaps
+// on the device.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -25,9 +27,13 @@ double now_ns() {
       .count();
 }
 
+// pinned host buffers for results, reused; taken by the scheduler and
+// given back by the clients that copied out of them
 struct PinnedPool {
+  std::mutex mu;
   std::multimap<size_t, void*> free_;
   void* get(size_t n) {
+    std::lock_guard<std::mutex> lk(mu);
     auto it = free_.lower_bound(n);
     if (it != free_.end() && it->first <= 2 * n + 4096) {
       void* p = it->second;
@@ -39,7 +45,10 @@ struct PinnedPool {
     sizes[p] = n;
     return p;
   }
-  void put(void* p) { free_.insert({sizes[p], p}); }
+  void put(void* p) {
+    std::lock_guard<std::mutex> lk(mu);
+    free_.insert({sizes[p], p});
+  }
   std::unordered_map<void*, size_t> sizes;
   ~PinnedPool() {
     for (auto& kv : sizes) cudaFreeHost(kv.first);
@@ -63,34 +72,38 @@ struct Req {
 
 }  // namespace
 
-struct vbe_server {
+// a scheduler thread with its own context and slots
+struct Worker {
   vbe_ctx* ctx = nullptr;
-  vbe_server_config cfg{};
+  bool owns_ctx = false;
   std::vector<vbe::Exec> slots;
   std::vector<Req*> slot_req;
+  int inflight = 0;
+  std::thread th;
+};
+
+struct vbe_server {
+  vbe_server_config cfg{};
+  std::vector<std::unique_ptr<Worker>> workers;
   std::deque<Req*> queue;
   std::unordered_map<int64_t, std::unique_ptr<Req>> reqs;
   int64_t used = 0;
   int64_t next_id = 1;
   std::mutex m;
   std::condition_variable cv_done, cv_work;
-  std::thread th;
   bool stop = false;
   PinnedPool pinned;
-  int inflight = 0;
+  int inflight = 0;  // over all workers
 };
 
 namespace {
 
-void finish_request(vbe_server* s, Req* r) {
-  vbe::Ctx& c = s->ctx->c;
-  vbe::Exec* ex = &s->slots[r->slot];
-  for (auto& st : r->staging) {
-    const vbe_req_base& b = r->bases[st.first];
-    memcpy(b.result, st.second, (size_t)(b.nelem * vbe::itemsize(b.dtype)));
-    s->pinned.put(st.second);
-  }
-  r->staging.clear();
+// Release a finished request's device memory and handles (scheduler
+// thread). Its results stay in pinned staging until the client that waits
+// for it copies them out (in its own thread, see vbe_server_wait).
+void finish_request(Worker* w, Req* r) {
+  vbe::Ctx& c = w->ctx->c;
+  vbe::Exec* ex = &w->slots[r->slot];
   for (auto v : r->vh) c.views.erase(v);
   for (auto h : r->bh) {
     auto it = c.bases.find(h);
@@ -104,9 +117,9 @@ void finish_request(vbe_server* s, Req* r) {
   r->ev = nullptr;
 }
 
-void admit(vbe_server* s, Req* r, int slot) {
-  vbe::Ctx& c = s->ctx->c;
-  vbe::Exec* ex = &s->slots[slot];
+void admit(vbe_server* s, Worker* w, Req* r, int slot) {
+  vbe::Ctx& c = w->ctx->c;
+  vbe::Exec* ex = &w->slots[slot];
   r->slot = slot;
   r->res.t_admit_ns = now_ns();
   try {
@@ -168,68 +181,95 @@ void admit(vbe_server* s, Req* r, int slot) {
     }
     vbe::cuda_check(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming), "event");
     vbe::cuda_check(cudaEventRecord(r->ev, ex->stream), "event record");
+    r->res.t_issued_ns = now_ns();
     r->res.status = VBE_OK;
   } catch (const vbe::Error& e) {
     r->res.status = e.code;
     c.last_error = e.msg;
     cudaStreamSynchronize(ex->stream);
-    finish_request(s, r);
-    r->done = true;
-    r->res.t_done_ns = now_ns();
-    s->used -= r->footprint;
-    s->slot_req[slot] = nullptr;
+    finish_request(w, r);
+    for (auto& st : r->staging) s->pinned.put(st.second);
+    r->staging.clear();
     return;
   }
-  s->slot_req[slot] = r;
-  s->inflight++;
 }
 
-void loop(vbe_server* s) {
-  vbe::cuda_check(cudaSetDevice(s->ctx->c.device), "cudaSetDevice");
-  std::unique_lock<std::mutex> lk(s->m);
+// A scheduler thread. It holds the server's lock only to move requests
+// between the queue, its slots and the finished state; planning, launching
+// and releasing run outside it (only this thread touches its context), so
+// clients submitting and waiting, and the other workers, are never held up
+// behind that host work. It admits at most two requests per round, so that
+// completions are noticed between plannings.
+void worker_loop(vbe_server* s, Worker* w) {
+  vbe::cuda_check(cudaSetDevice(w->ctx->c.device), "cudaSetDevice");
+  std::vector<Req*> done, admitted;
+  std::vector<int> admitted_slot;
   for (;;) {
-    bool progressed = false;
-    // completions
-    for (size_t k = 0; k < s->slots.size(); ++k) {
-      Req* r = s->slot_req[k];
-      if (!r) continue;
-      cudaError_t e = cudaEventQuery(r->ev);
-      if (e == cudaErrorNotReady) continue;
-      if (e != cudaSuccess) r->res.status = VBE_ERR_CUDA;
-      else if (vbe::take_error_word(&s->ctx->c)) r->res.status = VBE_ERR_TIMEOUT;
-      finish_request(s, r);
-      r->res.t_done_ns = now_ns();
-      r->done = true;
-      s->used -= r->footprint;
-      s->slot_req[k] = nullptr;
-      s->inflight--;
-      progressed = true;
+    done.clear();
+    admitted.clear();
+    admitted_slot.clear();
+    {
+      std::unique_lock<std::mutex> lk(s->m);
+      // completions (their device work is finished)
+      for (size_t k = 0; k < w->slots.size(); ++k) {
+        Req* r = w->slot_req[k];
+        if (!r || !r->ev) continue;
+        cudaError_t e = cudaEventQuery(r->ev);
+        if (e == cudaErrorNotReady) continue;
+        if (e != cudaSuccess) r->res.status = VBE_ERR_CUDA;
+        else if (vbe::take_error_word(&w->ctx->c)) r->res.status = VBE_ERR_TIMEOUT;
+        done.push_back(r);
+        w->slot_req[k] = nullptr;
+        w->inflight--;
+        s->inflight--;
+      }
+      // admissions, in arrival order, while a slot is free and memory fits
+      while (!s->queue.empty() && admitted.size() < 2) {
+        Req* r = s->queue.front();
+        int free_slot = -1;
+        for (size_t k = 0; k < w->slots.size(); ++k)
+          if (!w->slot_req[k]) {
+            free_slot = (int)k;
+            break;
+          }
+        if (free_slot < 0) break;
+        if (s->cfg.mem_cap_bytes && s->used + r->footprint > (int64_t)s->cfg.mem_cap_bytes) break;
+        s->queue.pop_front();
+        s->used += r->footprint;
+        w->slot_req[free_slot] = r;  // reserved; its event is recorded by admit()
+        w->inflight++;
+        s->inflight++;
+        admitted.push_back(r);
+        admitted_slot.push_back(free_slot);
+      }
+      if (done.empty() && admitted.empty()) {
+        if (s->stop && s->queue.empty() && w->inflight == 0) break;
+        if (w->inflight > 0 || !s->queue.empty()) s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        else s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        continue;
+      }
     }
-    if (progressed) s->cv_done.notify_all();
-    // admissions, in arrival order
-    while (!s->queue.empty()) {
-      Req* r = s->queue.front();
-      int free_slot = -1;
-      for (size_t k = 0; k < s->slots.size(); ++k)
-        if (!s->slot_req[k]) {
-          free_slot = (int)k;
-          break;
+    for (Req* r : done) finish_request(w, r);
+    for (size_t i = 0; i < admitted.size(); ++i) admit(s, w, admitted[i], admitted_slot[i]);
+    {
+      std::lock_guard<std::mutex> lk(s->m);
+      for (Req* r : done) {
+        r->done = true;
+        s->used -= r->footprint;
+      }
+      for (size_t i = 0; i < admitted.size(); ++i) {
+        Req* r = admitted[i];
+        if (r->res.status != VBE_OK) {  // rejected while planning: finished already
+          r->done = true;
+          s->used -= r->footprint;
+          w->slot_req[admitted_slot[i]] = nullptr;
+          w->inflight--;
+          s->inflight--;
         }
-      if (free_slot < 0) break;
-      if (s->cfg.mem_cap_bytes && s->used + r->footprint > (int64_t)s->cfg.mem_cap_bytes) break;
-      s->queue.pop_front();
-      s->used += r->footprint;
-      admit(s, r, free_slot);
-      if (r->done) s->cv_done.notify_all();
-      progressed = true;
+      }
     }
-    if (s->stop && s->queue.empty() && s->inflight == 0) break;
-    if (!progressed) {
-      if (s->inflight > 0)
-        s->cv_work.wait_for(lk, std::chrono::microseconds(20));
-      else
-        s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
-    }
+    s->cv_done.notify_all();
+    if (!done.empty()) s->cv_work.notify_all();  // memory freed: other workers may admit
   }
 }
 
@@ -238,26 +278,50 @@ void loop(vbe_server* s) {
 extern "C" {
 
 int vbe_server_create(vbe_ctx* ctx, const vbe_server_config* cfg, vbe_server** out) {
-  if (!ctx || !cfg || !out || cfg->slots <= 0) return VBE_ERR_INVALID;
+  if (!ctx || !cfg || !out || cfg->slots <= 0 || cfg->workers < 0) return VBE_ERR_INVALID;
   if (ctx->c.host_only) return VBE_ERR_NO_DEVICE;
+  const int nw = std::max(1, std::min<int>(cfg->workers, cfg->slots));
   auto* s = new vbe_server();
-  s->ctx = ctx;
   s->cfg = *cfg;
-  s->ctx->c.cfg.flags = (s->ctx->c.cfg.flags & ~(uint32_t)(VBE_FUSE | VBE_PACK | VBE_AUTOTUNE)) |
-                        (cfg->flags & (VBE_FUSE | VBE_PACK | VBE_AUTOTUNE));
-  s->slots.resize(cfg->slots);
-  s->slot_req.assign(cfg->slots, nullptr);
+  const uint32_t fl = cfg->flags & (VBE_FUSE | VBE_PACK | VBE_AUTOTUNE);
   try {
-    for (auto& e : s->slots) {
-      vbe::cuda_check(cudaStreamCreateWithFlags(&e.stream, cudaStreamNonBlocking), "cudaStreamCreate");
-      vbe::ensure_scratch(&ctx->c, &e, 1 << 20, 1 << 16);
+    for (int k = 0; k < nw; ++k) {
+      auto w = std::make_unique<Worker>();
+      if (k == 0) {
+        w->ctx = ctx;
+      } else {
+        vbe_config wc = ctx->c.cfg;
+        wc.stream = nullptr;
+        wc.cache_dir = ctx->c.cfg.cache_dir;
+        int rc = vbe_init(&wc, &w->ctx);
+        if (rc != VBE_OK) vbe::fail(rc, "worker context");
+        w->owns_ctx = true;
+      }
+      w->ctx->c.cfg.flags = (w->ctx->c.cfg.flags & ~(uint32_t)(VBE_FUSE | VBE_PACK | VBE_AUTOTUNE)) | fl;
+      // slots dealt round robin over the workers
+      const int ns = cfg->slots / nw + (k < cfg->slots % nw ? 1 : 0);
+      w->slots.resize(ns);
+      w->slot_req.assign(ns, nullptr);
+      for (auto& e : w->slots) {
+        vbe::cuda_check(cudaStreamCreateWithFlags(&e.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        vbe::ensure_scratch(&w->ctx->c, &e, 1 << 20, 1 << 16);
+      }
+      s->workers.push_back(std::move(w));
     }
   } catch (const vbe::Error& e) {
     ctx->c.last_error = e.msg;
+    for (auto& w : s->workers) {
+      for (auto& x : w->slots)
+        if (x.stream) {
+          vbe::release_exec(&w->ctx->c, &x);
+          cudaStreamDestroy(x.stream);
+        }
+      if (w->owns_ctx) vbe_finalize(w->ctx);
+    }
     delete s;
     return e.code;
   }
-  s->th = std::thread(loop, s);
+  for (auto& w : s->workers) w->th = std::thread(worker_loop, s, w.get());
   *out = s;
   return VBE_OK;
 }
@@ -325,10 +389,20 @@ int vbe_server_wait(vbe_server* s, int64_t id, int64_t timeout_ns, vbe_request_r
   } else if (!s->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), pred)) {
     return VBE_ERR_TIMEOUT;
   }
-  if (out) *out = r->res;
-  int st = r->res.status;
+  std::unique_ptr<Req> own = std::move(it->second);
   s->reqs.erase(it);
-  return st;
+  lk.unlock();
+  // the results, from pinned staging into the client's buffers, in this
+  // (the client's) thread and outside the server's lock
+  for (auto& stg : r->staging) {
+    const vbe_req_base& b = r->bases[stg.first];
+    if (r->res.status == VBE_OK) memcpy(b.result, stg.second, (size_t)(b.nelem * vbe::itemsize(b.dtype)));
+    s->pinned.put(stg.second);
+  }
+  r->staging.clear();
+  r->res.t_done_ns = now_ns();
+  if (out) *out = r->res;
+  return r->res.status;
 }
 
 int vbe_server_destroy(vbe_server* s) {
@@ -338,11 +412,15 @@ int vbe_server_destroy(vbe_server* s) {
     s->stop = true;
     s->cv_work.notify_all();
   }
-  if (s->th.joinable()) s->th.join();
-  for (auto& e : s->slots) {
-    cudaStreamSynchronize(e.stream);
-    vbe::release_exec(&s->ctx->c, &e);
-    cudaStreamDestroy(e.stream);
+  for (auto& w : s->workers)
+    if (w->th.joinable()) w->th.join();
+  for (auto& w : s->workers) {
+    for (auto& e : w->slots) {
+      cudaStreamSynchronize(e.stream);
+      vbe::release_exec(&w->ctx->c, &e);
+      cudaStreamDestroy(e.stream);
+    }
+    if (w->owns_ctx) vbe_finalize(w->ctx);
   }
   delete s;
   return VBE_OK;

@@ -75,12 +75,14 @@ class vbe_request(Structure):
 
 
 class vbe_server_config(Structure):
-    _fields_ = [("slots", c_int32), ("max_queue", c_int32), ("mem_cap_bytes", c_uint64), ("flags", c_uint32)]
+    _fields_ = [("slots", c_int32), ("max_queue", c_int32), ("mem_cap_bytes", c_uint64), ("flags", c_uint32),
+                ("workers", c_int32)]
 
 
 class vbe_request_result(Structure):
     _fields_ = [("status", c_int32), ("reserved", c_int32), ("footprint_bytes", c_int64),
-                ("t_arrive_ns", c_double), ("t_admit_ns", c_double), ("t_done_ns", c_double)]
+                ("t_arrive_ns", c_double), ("t_admit_ns", c_double), ("t_done_ns", c_double),
+                ("t_issued_ns", c_double)]
 
 
 assert ctypes.sizeof(vbe_instr) == 80 and ctypes.sizeof(vbe_config) == 32
@@ -261,8 +263,8 @@ def vbe_strerror(code: int) -> str:
     return lib.vbe_strerror(code).decode()
 
 
-def vbe_server_create(ctx, slots: int, mem_cap_bytes: int, flags: int, max_queue: int = 0):
-    cfg = vbe_server_config(slots, max_queue, mem_cap_bytes, flags)
+def vbe_server_create(ctx, slots: int, mem_cap_bytes: int, flags: int, max_queue: int = 0, workers: int = 1):
+    cfg = vbe_server_config(slots, max_queue, mem_cap_bytes, flags, workers)
     s = c_void_p()
     _check(lib.vbe_server_create(ctx, byref(cfg), byref(s)), ctx)
     return s

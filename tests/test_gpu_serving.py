@@ -36,9 +36,9 @@ def small_mix(n):
     return out
 
 
-def serve(programs, slots=4, cap=8 << 30, threads=8):
+def serve(programs, slots=4, cap=8 << 30, threads=8, workers=1):
     ctx = V.vbe_init(0, FLAGS, 0, None, CACHE)
-    srv = V.vbe_server_create(ctx, slots, cap, FLAGS)
+    srv = V.vbe_server_create(ctx, slots, cap, FLAGS, workers=workers)
     reqs = [Request(p) for p in programs]
     results = [None] * len(reqs)
 
@@ -57,10 +57,13 @@ def serve(programs, slots=4, cap=8 << 30, threads=8):
     return reqs, results
 
 
-def test_requests_match_oracle_and_solo_results():
+@pytest.mark.parametrize("workers", [1, 3])
+def test_requests_match_oracle_and_solo_results(workers):
+    """With one scheduler thread, and with three (each with its own context
+    and slots, planning in parallel)."""
     mix = small_mix(40)
     programs = [request_program(k, p) for k, p in mix]
-    reqs, res = serve(programs)
+    reqs, res = serve(programs, slots=6, workers=workers)
     assert all(r.status == 0 for r in res)
     assert all(r.t_arrive_ns <= r.t_admit_ns <= r.t_done_ns for r in res)
     # each result equals the same request run alone (bitwise: kernels and
@@ -112,7 +115,7 @@ def test_full_size_mix_matches_oracle():
                         ("blackscholes", dict(n=4 << 20, dtype="float32", seed=72)),
                         ("blackscholes", dict(n=4 << 20, dtype="float64", seed=73))]
     programs = [request_program(k, p) for k, p in mix]
-    reqs, res = serve(programs, slots=16, cap=60 << 30, threads=16)
+    reqs, res = serve(programs, slots=16, cap=60 << 30, threads=16, workers=4)
     assert all(x.status == 0 for x in res)
     for r in reqs:
         check_against_oracle(r)
@@ -126,8 +129,9 @@ def test_admission_respects_memory_cap_and_rejects_oversize():
     foot = solo[0].footprint_bytes
     grid = 64 * 64 * 8
     assert foot == sum(b.nelem * 8 for b in programs[0].bases.values()) + grid
-    # a cap that fits one request at a time: all complete, one by one
-    reqs, res = serve(programs, slots=4, cap=foot + 1024, threads=3)
+    # a cap that fits one request at a time: all complete, one by one, also
+    # with several workers admitting from the one queue
+    reqs, res = serve(programs, slots=4, cap=foot + 1024, threads=3, workers=2)
     assert all(r.status == 0 for r in res)
     spans = sorted((r.t_admit_ns, r.t_done_ns) for r in res)
     for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
