@@ -453,9 +453,12 @@ int vbe_server_create(vbe_ctx* ctx, const vbe_server_config* cfg, vbe_server** o
  * VBE_ERR_ADMISSION if the footprint alone exceeds the cap, VBE_ERR_BUSY if
  * the queue is full. */
 int vbe_server_submit(vbe_server* srv, const vbe_request* req, int64_t* id);
-/* Wait for a request (timeout_ns < 0: forever), copy its results into the
- * request's result buffers (in the calling thread) and fetch its result
- * record. A request's results reach its buffers only through this call. */
+/* Wait for a request's results (timeout_ns < 0: forever) and fetch its
+ * result record. A result buffer in page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister) receives its copy directly from the device; any other
+ * is filled from pinned staging by this call, in the calling thread, so a
+ * request's results are in its buffers when this call returns VBE_OK. The
+ * request's device memory may be released after the call returns. */
 int vbe_server_wait(vbe_server* srv, int64_t id, int64_t timeout_ns, vbe_request_result* out);
 /* Drain, stop the scheduler, release everything. */
 int vbe_server_destroy(vbe_server* srv);

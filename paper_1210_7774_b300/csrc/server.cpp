@@ -6,12 +6,13 @@
 // (requests) arrive concurrently. A scheduler thread owns the context. It
 // admits queued requests in arrival order while a slot (a stream with its
 // own reduction scratch) is free and the admitted footprints fit the
-// memory cap, executes each request's batch on its slot's stream, queues
-// the results' copies into pinned staging memory, and on completion
-// releases the request's device memory and wakes its client, which copies
-// the results into its own buffers in its own thread. A request is admitted
-// as soon as another completes, so work from different requests overlaps
-// on the device.
+// memory cap, executes each request's batch on its slot's stream, and
+// queues the results' copies: straight into the client's buffers when they
+// are page-locked, else into pinned staging. A host callback after the
+// copies wakes the client, which copies staged results into its own buffers
+// in its own thread; the worker later sees the slot's event and releases the
+// request's device memory. A request is admitted as soon as another
+// completes, so work from different requests overlaps on the device.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -56,6 +57,8 @@ struct PinnedPool {
 };
 
 struct Req {
+  vbe_server* srv = nullptr;
+  const unsigned* err_word = nullptr;  // the executing context's error word (mapped host memory)
   int64_t id = 0;
   std::vector<vbe_req_base> bases;
   std::vector<vbe_req_view> views;
@@ -68,6 +71,10 @@ struct Req {
   std::vector<int64_t> vh;  // view handles
   std::vector<std::pair<int, void*>> staging;  // (base index, pinned buffer)
   cudaEvent_t ev = nullptr;
+  bool ready = false;    // results are in host memory (set by a stream host callback)
+  bool taken = false;    // a client's wait has started taking the results
+  bool cb_enqueued = false;  // the results callback is on the stream (it may set ready)
+  bool fetched = false;  // ... and is finished with the request (it may be deleted)
 };
 
 }  // namespace
@@ -117,10 +124,38 @@ void finish_request(Worker* w, Req* r) {
   r->ev = nullptr;
 }
 
+// Stream host callback after a request's result copies: its client may
+// take the results now, before the worker notices the completion and
+// releases the request's device memory. (No CUDA calls here.)
+void CUDART_CB on_results_ready(void* arg) {
+  Req* r = static_cast<Req*>(arg);
+  vbe_server* s = r->srv;
+  {
+    std::lock_guard<std::mutex> lk(s->m);
+    // a staged kernel of the context gave up a wait: the results may be
+    // invalid (the word is cleared later by the worker's completion check;
+    // a request finishing on the same context meanwhile is failed too)
+    if (r->err_word && *(volatile const unsigned*)r->err_word) r->res.status = VBE_ERR_TIMEOUT;
+    r->ready = true;
+  }
+  s->cv_done.notify_all();
+}
+
+// pinned (page-locked) host memory: a result can be copied there directly
+bool is_pinned(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // the query's own error, not a pending one: checked above by the caller
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
 void admit(vbe_server* s, Worker* w, Req* r, int slot) {
   vbe::Ctx& c = w->ctx->c;
   vbe::Exec* ex = &w->slots[slot];
   r->slot = slot;
+  r->err_word = c.err_word;
   r->res.t_admit_ns = now_ns();
   try {
     for (auto& b : r->bases) {
@@ -175,11 +210,20 @@ void admit(vbe_server* s, Worker* w, Req* r, int slot) {
       size_t n = (size_t)br.bytes();
       if (!n) continue;
       if (!br.dptr) vbe::fail(VBE_ERR_UNINIT, "request result base was never written");
+      if (is_pinned(b.result)) {
+        // the client's buffer is page-locked: the copy lands there directly
+        vbe::cuda_check(cudaMemcpyAsync(b.result, br.dptr, n, cudaMemcpyDeviceToHost, ex->stream), "request result");
+        continue;
+      }
       void* p = s->pinned.get(n);
       r->staging.push_back({(int)i, p});
       vbe::cuda_check(cudaMemcpyAsync(p, br.dptr, n, cudaMemcpyDeviceToHost, ex->stream), "request result");
     }
+    // the client is woken by the callback; the event (after it) tells the
+    // worker that the slot's work, callback included, is finished
     vbe::cuda_check(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming), "event");
+    vbe::cuda_check(cudaLaunchHostFunc(ex->stream, on_results_ready, r), "results callback");
+    r->cb_enqueued = true;
     vbe::cuda_check(cudaEventRecord(r->ev, ex->stream), "event record");
     r->res.t_issued_ns = now_ns();
     r->res.status = VBE_OK;
@@ -188,8 +232,10 @@ void admit(vbe_server* s, Worker* w, Req* r, int slot) {
     c.last_error = e.msg;
     cudaStreamSynchronize(ex->stream);
     finish_request(w, r);
-    for (auto& st : r->staging) s->pinned.put(st.second);
-    r->staging.clear();
+    if (!r->cb_enqueued) {  // else the callback may have woken the client, who returns them
+      for (auto& st : r->staging) s->pinned.put(st.second);
+      r->staging.clear();
+    }
     return;
   }
 }
@@ -256,6 +302,7 @@ void worker_loop(vbe_server* s, Worker* w) {
       for (Req* r : done) {
         r->done = true;
         s->used -= r->footprint;
+        if (r->fetched) s->reqs.erase(r->id);  // its client is gone already
       }
       for (size_t i = 0; i < admitted.size(); ++i) {
         Req* r = admitted[i];
@@ -368,6 +415,7 @@ int vbe_server_submit(vbe_server* s, const vbe_request* req, int64_t* id) {
   if (s->cfg.mem_cap_bytes && r->footprint > (int64_t)s->cfg.mem_cap_bytes) return VBE_ERR_ADMISSION;
   if (s->cfg.max_queue > 0 && (int64_t)s->queue.size() >= s->cfg.max_queue) return VBE_ERR_BUSY;
   r->id = s->next_id++;
+  r->srv = s;
   r->res.t_arrive_ns = now_ns();
   r->res.footprint_bytes = r->footprint;
   *id = r->id;
@@ -383,26 +431,33 @@ int vbe_server_wait(vbe_server* s, int64_t id, int64_t timeout_ns, vbe_request_r
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return VBE_ERR_INVALID;
   Req* r = it->second.get();
-  auto pred = [&] { return r->done; };
+  if (r->taken) return VBE_ERR_INVALID;
+  // results in host memory (ready), or finished without them (done: an error)
+  auto pred = [&] { return r->ready || r->done; };
   if (timeout_ns < 0) {
     s->cv_done.wait(lk, pred);
   } else if (!s->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), pred)) {
     return VBE_ERR_TIMEOUT;
   }
-  std::unique_ptr<Req> own = std::move(it->second);
-  s->reqs.erase(it);
+  r->taken = true;
+  const bool ready = r->ready;
+  vbe_request_result res = r->res;
   lk.unlock();
   // the results, from pinned staging into the client's buffers, in this
   // (the client's) thread and outside the server's lock
   for (auto& stg : r->staging) {
     const vbe_req_base& b = r->bases[stg.first];
-    if (r->res.status == VBE_OK) memcpy(b.result, stg.second, (size_t)(b.nelem * vbe::itemsize(b.dtype)));
+    if (ready) memcpy(b.result, stg.second, (size_t)(b.nelem * vbe::itemsize(b.dtype)));
     s->pinned.put(stg.second);
   }
   r->staging.clear();
-  r->res.t_done_ns = now_ns();
-  if (out) *out = r->res;
-  return r->res.status;
+  res.t_done_ns = now_ns();
+  if (!ready && res.status == VBE_OK) res.status = VBE_ERR_CUDA;
+  lk.lock();
+  r->fetched = true;
+  if (r->done) s->reqs.erase(id);  // else the worker erases it when it finishes
+  if (out) *out = res;
+  return res.status;
 }
 
 int vbe_server_destroy(vbe_server* s) {

@@ -220,6 +220,25 @@ class Request:
             e.key = ins.key & ((1 << 64) - 1)
             e.step = ins.step
         self.req = V.vbe_request(self.bases, len(ids), len(views), self.views, self.instrs, n)
+        self._ids = ids
+
+    def result_bytes(self) -> int:
+        """Bytes of all result buffers, each rounded up to 64 bytes."""
+        return sum((a.nbytes + 63) // 64 * 64 for a in self.results.values())
+
+    def bind_results(self, arena: np.ndarray) -> None:
+        """Point the request's result buffers into ``arena`` (a uint8 array of
+        at least result_bytes(); e.g. page-locked memory, which the server
+        then fills straight from the device). ``results`` become views of it."""
+        off = 0
+        for i, bid in enumerate(self._ids):
+            if bid not in self.results:
+                continue
+            a = self.results[bid]
+            view = arena[off:off + a.nbytes].view(a.dtype)
+            self.results[bid] = view
+            self.bases[i].result = view.ctypes.data
+            off += (a.nbytes + 63) // 64 * 64
 
 
 def run_program(program: Program, flags: int = V.VBE_FUSE | V.VBE_GRAPHS | V.VBE_AUTOTUNE | V.VBE_PACK,
