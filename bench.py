@@ -748,7 +748,7 @@ def serving_bench(args, V, local):
         nb = sum((p.bases[b].nelem * np.dtype(NP_DTYPE[p.bases[b].dtype]).itemsize + 63) // 64 * 64
                  for b in p.outputs)
         need[i % nclients] = max(need[i % nclients], nb)
-    extra_mix = request_mix(768, seed=1210_7774 + 99)
+    extra_mix = request_mix(1280, seed=1210_7774 + 99)
     for i, m in enumerate(extra_mix):
         p = request_program(*m)
         nb = sum((p.bases[b].nelem * np.dtype(NP_DTYPE[p.bases[b].dtype]).itemsize + 63) // 64 * 64
@@ -764,7 +764,7 @@ def serving_bench(args, V, local):
         # wait and drop the request (its result memory) when it is done
         reqs = [Request(p) for p in progs_all]
         # capacity: after a pass over 256 requests of the same mix (kernel
-        # compilation), a closed loop of the 64 clients over 512 further
+        # compilation), a closed loop of the 64 clients over 1024 further
         # requests that have not been seen (another seed), so per-size work is
         # paid as it is in the timed run: each client submits its next
         # request as soon as its previous one is back
@@ -839,7 +839,7 @@ def main():
                     help="leave out the per-configuration sub-keys (Jacobi, shallow water, MC, serving)")
     ap.add_argument("--dtypes", default="float64,float32", help="profiling: restrict the dtypes run")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
-    ap.add_argument("--serve-workers", type=int, default=4, help="serving: scheduler threads of the server")
+    ap.add_argument("--serve-workers", type=int, default=8, help="serving: scheduler threads of the server")
     ap.add_argument("--paths", default="fused,plain", help="profiling: restrict the paths run (jacobi: paper_size runs the 7168^2 part alone)")
     args = ap.parse_args()
     rank, world, local = dist_env()

@@ -90,11 +90,8 @@ void instr_refs(Ctx& c, const vbe_instr& in, std::vector<Ref>* out) {
 // after its DISCARD in the same batch, while the mirror holds its value,
 // would need an upload in mid-batch and is rejected.
 void mirror_before(Ctx& c, vbe::Exec* ex, const vbe_instr* prog, int64_t n) {
+  if (c.n_mirrors == 0 || !prog) return;
   c.mirror_syncs.clear();
-  bool any = false;
-  for (auto& kv : c.bases)
-    if (kv.second.mirror) any = true;
-  if (!any || !prog) return;
   std::unordered_map<int64_t, std::pair<bool, bool>> sim;  // base -> (device valid, host valid)
   std::vector<int64_t> upload;
   std::vector<Ref> refs;
@@ -144,6 +141,7 @@ void mirror_before(Ctx& c, vbe::Exec* ex, const vbe_instr* prog, int64_t n) {
 
 // After a batch was enqueued: which copies are current, and host access.
 void mirror_after(Ctx& c, const vbe_instr* prog, int64_t n) {
+  if (c.n_mirrors == 0 || !prog) return;
   std::vector<Ref> refs;
   for (int64_t i = 0; i < n; ++i) {
     instr_refs(c, prog[i], &refs);
@@ -502,6 +500,7 @@ int vbe_mirror_attach(vbe_ctx* ctx, vbe_base base, void* host, int64_t nbytes) {
   if (it->second.mirror) vbe::fail(VBE_ERR_INVALID, "base already has a host mirror");
   drain(c);  // work already enqueued on the base is finished
   it->second.mirror = host ? host : (void*)&it->second;  // an empty base needs no memory
+  c.n_mirrors++;
   it->second.host_valid = true;
   it->second.dev_valid = false;
   it->second.host_write = true;

@@ -386,6 +386,7 @@ struct Ctx {
   // per mirrored base, in instruction order: whether each in-batch SYNC of
   // the current batch copies the device copy back to the mirror
   std::unordered_map<int64_t, std::deque<bool>> mirror_syncs;
+  int64_t n_mirrors = 0;  // bases given a host mirror so far (0: submits skip the mirror rules)
   // set by staged kernels whose bounded waits ran out (mapped host memory)
   unsigned* err_word = nullptr;
   unsigned* err_word_dev = nullptr;
