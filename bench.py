@@ -333,7 +333,8 @@ def gpu_blackscholes(args, rank, world, local):
                                      "how": "one context: upload the inputs, submit, sync the outputs, in turn"}
                 ex.close()
                 if dtype == "float64":
-                    out["e2e"] = e2e_pipelined(V, Executor, prog, dtype, flags_fused, local, cache, args, torch)
+                    out["e2e"] = e2e_pipelined(V, Executor, prog, dtype, flags_fused, local, cache, args, torch,
+                                               workers=args.e2e_workers)
             if ex.ctx:
                 ex.close()
         out["cbytes"] = cbytes
@@ -348,9 +349,11 @@ def e2e_pipelined(V, Executor, prog, dtype, flags, local, cache, args, torch, wo
     memory (vbe_base_upload), submits the batch and reads its results back
     (vbe_sync). The calls block their own thread only, so while one share's
     inputs go to the device another's results come back and a third computes:
-    both directions of the host link are busy at once. A step is every
-    share's upload, batch and read-back; its time is the wall clock of the
-    slowest thread."""
+    both directions of the host link are busy at once. The threads start
+    together and run their steps without waiting for one another (so they
+    drift apart and their copies interleave); a step is every share's
+    upload, batch and read-back, and its time is the wall clock until the
+    last thread has finished all its steps, divided by the steps."""
     import threading
 
     from workloads import blackscholes
@@ -384,8 +387,8 @@ def e2e_pipelined(V, Executor, prog, dtype, flags, local, cache, args, torch, wo
 
         def worker(sh):
             torch.cuda.set_device(local)
+            barrier.wait()  # the shares start together, then run their steps freely
             for _ in range(k):
-                barrier.wait()  # every share's step starts together
                 one(sh)
         th = [threading.Thread(target=worker, args=(sh,)) for sh in shares]
         t0 = time.perf_counter()
@@ -501,6 +504,13 @@ def config_subkeys(args, V, torch, local, stream, hbm, fp64):
         sec, st = timed(p, flags, 100, warmup=20)
         jr[name] = {"us_per_iteration": sec / 10 * 1e6, "GB/s": cb * 10 / sec / 1e9,
                     "launches_per_iteration": st["kernel_launches"] / 10}
+    # the whole 10-iteration program as one batch (the paper's Bridge hands
+    # over everything recorded up to a flush): one graph of ten kernels
+    p1 = jacobi(256, 10, one_batch=True)
+    sec, st = timed(p1, F | G, 100, warmup=20)
+    jr["fused_graphs_one_batch"] = {"us_per_iteration": sec / 10 * 1e6, "GB/s": cb * 10 / sec / 1e9,
+                                    "launches_per_iteration": st["kernel_launches"] / 10,
+                                    "note": "one submit per 10 iterations"}
     osec = _oracle_seconds(p, 3)
     jr.update(speedup_vs_plain=jr["plain"]["us_per_iteration"] / jr["fused_graphs"]["us_per_iteration"],
               speedup_vs_plain_graphs=jr["plain_graphs"]["us_per_iteration"] / jr["fused_graphs"]["us_per_iteration"],
@@ -840,6 +850,8 @@ def main():
     ap.add_argument("--dtypes", default="float64,float32", help="profiling: restrict the dtypes run")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--serve-workers", type=int, default=8, help="serving: scheduler threads of the server")
+    ap.add_argument("--e2e-workers", type=int, default=4,
+                    help="end-to-end: contexts (and host threads) the options are split over")
     ap.add_argument("--paths", default="fused,plain", help="profiling: restrict the paths run (jacobi: paper_size runs the 7168^2 part alone)")
     args = ap.parse_args()
     rank, world, local = dist_env()

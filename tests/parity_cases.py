@@ -533,10 +533,12 @@ def knn_check(p, rows=None):
     return check
 
 
-def jacobi_case(n, iters):
+def jacobi_case(n, iters, one_batch=False):
     """Jacobi on an n x n grid: the grid bit-exact, the deltas within the
-    reduction tolerance."""
-    p = jacobi(n, iters)
+    reduction tolerance (with ``one_batch``: every iteration in one batch)."""
+    p = jacobi(n, iters, one_batch=one_batch)
+    if one_batch:
+        p.name += "_one_batch"
 
     def jchk(got, want, p=p):
         assert_exact(got[p.meta["grid"]], want[p.meta["grid"]], "jacobi grid")
@@ -550,6 +552,7 @@ def workload_cases(scale="small"):
     out = []
     n = 24 if scale == "small" else 256
     out.append(jacobi_case(n, 3 if scale == "small" else 10))
+    out.append(jacobi_case(n, 3 if scale == "small" else 10, one_batch=True))  # the program as one batch
     nb = 3000 if scale == "small" else 100_000
     for dt, rtol in (("float64", 1e-12), ("float32", 1e-5)):
         p = blackscholes(nb, dt, seed=11)

@@ -73,7 +73,7 @@ MEDIUM = workload_cases("medium")
 def test_medium_workload_parity(case, mode):
     got = run_gpu(case.program, MODES[mode], staging=STAGING.get(mode, 0))
     case.check(got, oracle_outputs(case.program))
-    if mode == "fused_graphs" and case.name.startswith(("jacobi", "shallow")):
+    if mode == "fused_graphs" and case.name.startswith(("jacobi", "shallow")) and not case.name.endswith("one_batch"):
         # repeated iterations replay a graph (or, for a batch of one or two
         # launches, its cached launch list)
         assert got["_stats"]["graph_launches"] + got["_stats"]["list_replays"] > 0

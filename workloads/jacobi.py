@@ -42,11 +42,14 @@ def jacobi_inputs(n: int, dtype: str = "float64", seed: int = SEED + 1,
 
 
 def jacobi(n: int = 256, iters: int = 10, dtype: str = "float64",
-           seed: int = SEED + 1, init: str = "random", linear=(1, 2, 3), history: bool = False):
+           seed: int = SEED + 1, init: str = "random", linear=(1, 2, 3), history: bool = False,
+           one_batch: bool = False):
     """The Jacobi program. Outputs: the grid and ``deltas``: the scalar delta
     of the last iteration (every iteration overwrites it, so all iterations
     are the same batch), or with ``history`` the delta of each iteration.
-    ``meta['batches']`` lists one instruction range per iteration."""
+    ``meta['batches']`` lists one instruction range per iteration, or with
+    ``one_batch`` a single range: the whole program is one batch, as the
+    paper's Bridge hands over everything recorded up to a flush."""
     b = ProgramBuilder(f"jacobi{n}_{dtype}_{iters}it")
     grid = jacobi_inputs(n, dtype, seed, init, linear)
     full = b.base(dtype, (n, n), grid)
@@ -78,6 +81,8 @@ def jacobi(n: int = 256, iters: int = 10, dtype: str = "float64",
     b.sync(full, deltas)
     p = b.build([full, deltas])
     batches[-1] = (batches[-1][0], len(p.instrs))
+    if one_batch:
+        batches = [(0, len(p.instrs))]
     p.meta.update(batches=batches, n=n, iters=iters, dtype=dtype, grid=full, deltas=deltas,
                   elements_per_iter=m * m)
     return p
