@@ -523,8 +523,18 @@ void apply_reduce(const Ins& I, int64_t lo, int64_t hi) {
     Val r{0, 0};
     bool rf = fin;
     if (I.op == ADD_REDUCE) {
-      if (fin) {
-        double acc = 0.0;  // float32 sums accumulate in float64 too
+      if (x.dtype == MC_FLOAT64) {
+        const double* px = reinterpret_cast<const double*>(x.data) + ex;
+        double acc = 0.0;
+        for (int64_t m = 0; m < n; ++m) acc += px[m * st];
+        r.f = acc;
+      } else if (x.dtype == MC_FLOAT32) {
+        const float* px = reinterpret_cast<const float*>(x.data) + ex;
+        double acc = 0.0;  // float32 sums accumulate in float64
+        for (int64_t m = 0; m < n; ++m) acc += (double)px[m * st];
+        r.f = acc;
+      } else if (fin) {
+        double acc = 0.0;
         for (int64_t m = 0; m < n; ++m) acc += get(I.in[0], x.dtype, ex + m * st).f;
         r.f = acc;
       } else {
