@@ -3,6 +3,7 @@ point the header declares; the analysis and the code generator work on a
 host-only context (no GPU): fusion decisions, staging of partially
 overlapping operands, validation errors, the overlap test against NumPy,
 and NVRTC compilation of every kernel the workloads need."""
+import ctypes
 import json
 import os
 import re
@@ -405,3 +406,10 @@ def test_caller_owned_state_is_never_renamed():
         js = json.loads(ex.plan(L, 0))
         assert not any("group" in i for i in js["items"])
         assert [len(i["run"]["ops"]) for i in js["items"] if "run" in i] == [6, 6, 9, 21, 21, 18]
+
+
+def test_fp64_rate_probe_rejects_bad_arguments():
+    """vbe_measure_fp64_rate validates its arguments before touching a device."""
+    for op, iters, scratch in ((3, 10, 16), (-1, 10, 16), (0, 0, 16), (0, 10, 0)):
+        code = V.lib.vbe_measure_fp64_rate(op, iters, ctypes.byref(ctypes.c_double()), scratch or None, None)
+        assert code == -1, (op, iters, scratch)
