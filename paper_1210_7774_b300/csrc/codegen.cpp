@@ -490,13 +490,11 @@ __device__ __forceinline__ bool vbe_mbar_wait(unsigned long long* bar, unsigned 
 #define VBE_DYN_SMEM extern __shared__ __align__(128) unsigned char vbe_smem[]
 // programmatic dependent launch: a kernel launched while its predecessor on
 // the stream is still running waits here until that grid has completed and
-// its writes are visible (a no-op for an ordinary launch); it then lets its
-// own successor be scheduled, whose blocks start as this grid's last ones
-// run and wait here in turn before they touch memory
-__device__ __forceinline__ void vbe_grid_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// its writes are visible (a no-op for an ordinary launch). Kernels do not
+// trigger their successors early: measured, that slowed the persistent
+// tensor-copy kernels (the successor's blocks took resources while the
+// predecessor still ran) and gained nothing elsewhere.
+__device__ __forceinline__ void vbe_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ unsigned long long vbe_umulhi(unsigned long long a, unsigned long long b) {
   return __umul64hi(a, b);
 }
