@@ -43,6 +43,15 @@ typedef long long sf_i64;
 #define SF_H52 0x0010000000000000ull
 #define SF_SIGN 0x8000000000000000ull
 
+// The native operations, for the cases the integer routines below leave to
+// the FP64 pipe (special operands, results outside the normal range). They
+// are kept out of line so that none of their code is scheduled into the
+// integer paths.
+__device__ SF_CALL double vbe_ddiv_native(double a, double b) { return a / b; }
+__device__ SF_CALL double vbe_dsqrt_native(double a) { return sqrt(a); }
+__device__ SF_CALL double vbe_dexp_native(double x) { return exp(x); }
+__device__ SF_CALL double vbe_dlog_native(double x) { return log(x); }
+
 // ------------------------------------------------------------ division
 
 __device__ SF_CALL double vbe_ddiv(double a, double b) {
@@ -52,22 +61,22 @@ __device__ SF_CALL double vbe_ddiv(double a, double b) {
   // a zero numerator over a normal or infinite divisor: a signed zero
   // (frequent in practice, e.g. momenta of a fluid at rest)
   if ((ua << 1) == 0 && eb != 0 && ((ub << 12) == 0 || eb != 0x7ff)) return __longlong_as_double((sf_i64)sign);
-  if (ea == 0 || ea == 0x7ff || eb == 0 || eb == 0x7ff) return a / b;
+  if (ea == 0 || ea == 0x7ff || eb == 0 || eb == 0x7ff) return vbe_ddiv_native(a, b);
   const sf_u64 ma = (ua & SF_M52) | SF_H52, mb = (ub & SF_M52) | SF_H52;
   if ((ub & SF_M52) == 0) {  // b = +-2^k: the quotient is exact
     const int er = ea - eb + 1023;
-    if (er < 1 || er > 2046) return a / b;
+    if (er < 1 || er > 2046) return vbe_ddiv_native(a, b);
     return __longlong_as_double((sf_i64)(sign | ((sf_u64)er << 52) | (ua & SF_M52)));
   }
   const int s = ma < mb ? 53 : 52;
   int er = ea - eb + 1023 - (s - 52);
-  if (er < 1 || er > 2046) return a / b;
+  if (er < 1 || er > 2046) return vbe_ddiv_native(a, b);
   // x = 1/d, d = mb / 2^53 in (0.5, 1); X = x 2^62 (Q2.62), D = d 2^64 (Q0.64)
   const sf_u64 D = mb << 11;
   const float df = __uint_as_float((126u << 23) | (unsigned)((mb >> 29) & 0x7fffffu));
   const unsigned xb = __float_as_uint(vbe_rcp_approx(df));
   const int xe = (int)(xb >> 23) - 88;
-  if (xe < 30 || xe > 41) return a / b;
+  if (xe < 30 || xe > 41) return vbe_ddiv_native(a, b);
   sf_u64 X = (sf_u64)((xb & 0x7fffffu) | 0x800000u) << xe;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
@@ -97,7 +106,7 @@ __device__ SF_CALL double vbe_ddiv(double a, double b) {
   if (q == (SF_H52 << 1)) {
     q = SF_H52;
     er += 1;
-    if (er > 2046) return a / b;
+    if (er > 2046) return vbe_ddiv_native(a, b);
   }
   return __longlong_as_double((sf_i64)(sign | ((sf_u64)er << 52) | (q & SF_M52)));
 }
@@ -107,7 +116,7 @@ __device__ SF_CALL double vbe_ddiv(double a, double b) {
 __device__ SF_CALL double vbe_dsqrt(double a) {
   const sf_u64 ua = (sf_u64)__double_as_longlong(a);
   const int ea = (int)((ua >> 52) & 0x7ff);
-  if ((ua & SF_SIGN) || ea == 0 || ea == 0x7ff) return sqrt(a);
+  if ((ua & SF_SIGN) || ea == 0 || ea == 0x7ff) return vbe_dsqrt_native(a);
   sf_u64 m = (ua & SF_M52) | SF_H52;  // a = m 2^(ea - 1075)
   int e = ea - 1023;                   // a = (m 2^-52) 2^e
   if (e & 1) {
@@ -120,7 +129,7 @@ __device__ SF_CALL double vbe_dsqrt(double a) {
   const float tf = __uint_as_float(((127u + hb) << 23) | (unsigned)((m >> (29 + hb)) & 0x7fffffu));
   const unsigned yb = __float_as_uint(vbe_rsqrt_approx(tf));
   const int ye = (int)(yb >> 23) - 88;
-  if (ye < 30 || ye > 41) return sqrt(a);
+  if (ye < 30 || ye > 41) return vbe_dsqrt_native(a);
   sf_u64 Y = (sf_u64)((yb & 0x7fffffu) | 0x800000u) << ye;  // y = 1/sqrt(t) in (0.5, 1], Q2.62
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
@@ -145,7 +154,7 @@ __device__ SF_CALL double vbe_dsqrt(double a) {
   }
   if (rem > (sf_i64)q) q += 1;  // (q + 1/2)^2 = q^2 + q + 1/4 is never an integer: no ties
   const int er = e / 2 + 1023;
-  if (q == (SF_H52 << 1)) return sqrt(a);  // cannot happen for a normal input; stay safe
+  if (q == (SF_H52 << 1)) return vbe_dsqrt_native(a);  // cannot happen for a normal input; stay safe
   return __longlong_as_double((sf_i64)(((sf_u64)er << 52) | (q & SF_M52)));
 }
 
@@ -335,7 +344,7 @@ __device__ __forceinline__ bool sf_pack(sf_u64 v, int scale_exp, sf_u64 sign, do
 __device__ SF_CALL double vbe_dexp(double x) {
   const sf_u64 ux = (sf_u64)__double_as_longlong(x);
   const int ex = (int)((ux >> 52) & 0x7ff);
-  if (ex < 1023 - 40 || ex > 1031) return exp(x);  // |x| < 2^-40, |x| >= 512, inf, nan
+  if (ex < 1023 - 40 || ex > 1031) return vbe_dexp_native(x);  // |x| < 2^-40, |x| >= 512, inf, nan
   // k ~ round(x 64 / ln2) in single precision (off by at most one)
   const float xf = __uint_as_float((unsigned)((ux >> 32) & 0x80000000u) |
                                    ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)((ux >> 29) & 0x7fffffu));
@@ -365,7 +374,7 @@ __device__ SF_CALL double vbe_dexp(double x) {
   const int j = k & 63, m = k >> 6;
   const sf_u64 V = vbe_umulhi(VBE_EXP2_TAB[j], (sf_u64)P);
   double out;
-  if (!sf_pack(V, m - 61, 0, &out)) return exp(x);
+  if (!sf_pack(V, m - 61, 0, &out)) return vbe_dexp_native(x);
   return out;
 }
 
@@ -396,7 +405,7 @@ __device__ __forceinline__ sf_i128 sf_from_i64(sf_i64 v) {
 __device__ SF_CALL double vbe_dlog(double x) {
   const sf_u64 ux = (sf_u64)__double_as_longlong(x);
   const int ex = (int)((ux >> 52) & 0x7ff);
-  if ((ux & SF_SIGN) || ex == 0 || ex == 0x7ff) return log(x);
+  if ((ux & SF_SIGN) || ex == 0 || ex == 0x7ff) return vbe_dlog_native(x);
   const sf_u64 M = (ux & SF_M52) | SF_H52;
   int e = ex - 1023;
   // x = 2^e m with m in [0.75, 1.5); Mq = m 2^63; m - 1 = Fint 2^-fs exactly
@@ -421,7 +430,7 @@ __device__ SF_CALL double vbe_dlog(double x) {
     const sf_u64 af = (sf_u64)(Fint < 0 ? -Fint : Fint);
     const int z = vbe_clz64(af);
     double out;
-    if (!sf_pack(vbe_umulhi(af << z, (sf_u64)Q), 2 - fs - z, Fint < 0 ? SF_SIGN : 0, &out)) return log(x);
+    if (!sf_pack(vbe_umulhi(af << z, (sf_u64)Q), 2 - fs - z, Fint < 0 ? SF_SIGN : 0, &out)) return vbe_dlog_native(x);
     return out;
   }
   const int i = jj - 96;
@@ -438,7 +447,7 @@ __device__ SF_CALL double vbe_dlog(double x) {
   S = sf_add(S, sf_from_i64(L1));
   const sf_u64 sign = S.hi < 0 ? SF_SIGN : 0;
   if (sign) S = sf_neg(S);
-  if (S.hi == 0 && S.lo == 0) return log(x);
+  if (S.hi == 0 && S.lo == 0) return vbe_dlog_native(x);
   double out;
   bool ok;
   if (S.hi != 0) {
@@ -448,7 +457,7 @@ __device__ SF_CALL double vbe_dlog(double x) {
   } else {
     ok = sf_pack(S.lo, -64, sign, &out);
   }
-  return ok ? out : log(x);
+  return ok ? out : vbe_dlog_native(x);
 }
 
 #endif  // VBE_SF64_CUH
