@@ -52,10 +52,23 @@ __device__ SF_CALL double vbe_dsqrt_native(double a) { return sqrt(a); }
 __device__ SF_CALL double vbe_dexp_native(double x) { return exp(x); }
 __device__ SF_CALL double vbe_dlog_native(double x) { return log(x); }
 
+// The bits of a double, opaque to the compiler: a test on them (a zero
+// numerator, say) would otherwise be turned back into a float64 compare on
+// the FP64 pipe (measured: one such compare per divide).
+__device__ __forceinline__ sf_u64 sf_bits(double a) {
+#ifdef __CUDA_ARCH__
+  sf_u64 u;
+  asm("mov.b64 %0, %1;" : "=l"(u) : "d"(a));
+  return u;
+#else
+  return (sf_u64)__double_as_longlong(a);
+#endif
+}
+
 // ------------------------------------------------------------ division
 
 __device__ SF_CALL double vbe_ddiv(double a, double b) {
-  const sf_u64 ua = (sf_u64)__double_as_longlong(a), ub = (sf_u64)__double_as_longlong(b);
+  const sf_u64 ua = sf_bits(a), ub = sf_bits(b);
   const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
   const sf_u64 sign = (ua ^ ub) & SF_SIGN;
   // a zero numerator over a normal or infinite divisor: a signed zero
