@@ -610,8 +610,9 @@ bool is_simple_f64(const Step& s) {
 // pipes as the native one does on the FP64 pipe, and its longer dependency
 // chain hides latency worse. So by default only divide, square root, exp,
 // log, the RANDOM conversion and sign operations are emulated; the
-// environment variable VBE_F64_SIMPLE=mul|all moves multiplies and
-// compares, or every simple step, to the integer pipes for experiments.
+// environment variable VBE_F64_SIMPLE=cmp|mul|all moves compares,
+// multiplies and compares, or every simple step, to the integer pipes for
+// experiments.
 // Either choice gives the same (correctly rounded) results.
 std::vector<char> balance_f64(const Run& r) {
   std::vector<char> soft(r.steps.size(), 0);
@@ -623,6 +624,7 @@ std::vector<char> balance_f64(const Run& r) {
     if (!is_simple_f64(s)) continue;
     if (policy == "all") soft[i] = 1;
     if (policy == "mul" && s.op != VBE_OP_ADD && s.op != VBE_OP_SUBTRACT) soft[i] = 1;
+    if (policy == "cmp" && s.op >= VBE_OP_LESS && s.op <= VBE_OP_NOT_EQUAL) soft[i] = 1;
   }
   return soft;
 }
