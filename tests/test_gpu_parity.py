@@ -340,13 +340,17 @@ def test_registered_device_memory():
 
 
 def test_fp64_rate_probe_is_plausible():
-    """The FP64 pipe's rate from the throughput kernel: the three operations
-    agree within 5 %, and the rate lies between 1/128 and 1/32 of the FP32
+    """The FP64 pipe's rate from the throughput kernel (median of three
+    launches after a warm-up): the three operations agree within 5 %, and
+    the rate lies between 1/128 and 1/32 of the FP32
     lanes' rate at the boost clock (B300's FP64 pipe: about 1/76)."""
     torch = pytest.importorskip("torch")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     scratch = torch.empty(2048 * sms, dtype=torch.float64, device="cuda")
-    rates = [V.vbe_measure_fp64_rate(op, 2048, scratch.data_ptr()) for op in ("dfma", "dadd", "dmul")]
+    rates = []
+    for op in ("dfma", "dadd", "dmul"):
+        V.vbe_measure_fp64_rate(op, 512, scratch.data_ptr())  # warm-up launch
+        rates.append(sorted(V.vbe_measure_fp64_rate(op, 2048, scratch.data_ptr()) for _ in range(3))[1])
     assert max(rates) <= 1.05 * min(rates), rates
     fp32 = sms * 128 * 2.032e9
     assert fp32 / 128 < rates[0] < fp32 / 32, rates
