@@ -637,6 +637,12 @@ def other_workload(args, local):
     modes = {"fused_graphs": F | V.VBE_GRAPHS, "fused": F, "plain": 0, "plain_graphs": V.VBE_GRAPHS}
     out = {"workload": args.workload}
 
+    def group_forms(st):
+        # tile-fused group launches by form (tuning trials included); VBE_TILE
+        # in the environment fixes the form
+        return {"tensor_copy": st["tma_group_launches"], "row_sweep": st["sweep_group_launches"],
+                "forced": os.environ.get("VBE_TILE") or None}
+
     def timed_batches(program, flags, reps, warmup=2):
         ex = Executor(flags, device=local, stream=stream, cache_dir=cache)
         L = ex.load(program)
@@ -685,7 +691,7 @@ def other_workload(args, local):
             for name in names:
                 sec, st = timed_batches(p, modes[name], 2)
                 res[name] = {"ms_per_step": sec / 50 * 1e3, "GB/s": cbytes / sec / 1e9,
-                             "hbm_fraction": cbytes / sec / 1e9 / hbm}
+                             "hbm_fraction": cbytes / sec / 1e9 / hbm, "group_forms": group_forms(st)}
             if "plain_graphs" in res and "fused_graphs" in res:
                 res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_step"] / res["fused_graphs"]["ms_per_step"]
             out[dtype] = res
@@ -701,7 +707,7 @@ def other_workload(args, local):
             for name in ("fused_graphs", "fused_graphs_untiled", "plain_graphs"):
                 sec, st = timed_batches(p, modes[name], 3)
                 res[name] = {"ms_per_step": sec / steps * 1e3, "GB/s": cbytes / sec / 1e9,
-                             "hbm_fraction": cbytes / sec / 1e9 / hbm}
+                             "hbm_fraction": cbytes / sec / 1e9 / hbm, "group_forms": group_forms(st)}
             res["speedup_vs_plain"] = res["plain_graphs"]["ms_per_step"] / res["fused_graphs"]["ms_per_step"]
             out[dtype] = res
         out["note"] = "Gray-Scott reaction-diffusion, 10240x1024, 10 steps (the paper's synthetic-stencil size)"

@@ -327,6 +327,9 @@ typedef struct vbe_stats {
   int64_t packed_launches;   /* launches (graph replays included) of packed
                                 kernels: several independent runs executed by
                                 one persistent launch (VBE_PACK)              */
+  int64_t sweep_group_launches; /* tile-fused groups issued (or captured) in
+                                the row-sweep form (one warp per column strip
+                                walking the rows), tuning trials included    */
 } vbe_stats;
 int vbe_get_stats(vbe_ctx* ctx, vbe_stats* out);
 

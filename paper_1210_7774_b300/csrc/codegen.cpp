@@ -25,6 +25,8 @@
 // Every reduction order depends only on the launch shape, never on timing,
 // so a result is reproducible for a given signature and size.
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <set>
@@ -1756,9 +1758,160 @@ bool tma_ok(const Group& g) {
   return true;
 }
 
+// ------------------------------------------------------- row-sweep form
+//
+// One warp owns a strip of WO anchor columns and R anchor rows and walks the
+// rows top to bottom. Every node of the group (a staged input, or a run)
+// handles one row per step, at a fixed lead: at step t it produces row
+// i0 + t + rhi of its own box (rhi: the node's bottom margin), so that every
+// row a later node reads at that step is already produced, this step or an
+// earlier one. A node keeps the last `depth` rows it produced in registers,
+// as many as its consumers still read, so every point of every run is
+// evaluated once, with no halo recomputed above or below (the first steps of
+// a strip, before its anchor row 0, produce the rows the first anchor rows
+// need). Lane l of node n holds column j0 + s_n + l; a consumer reading a
+// producer at column shift dc takes the value from lane l + s_l + dc - s_n
+// by a warp shuffle (none where that is 0). The lane shifts s_n are chosen
+// to need as few shuffles as possible. WO is 32 minus the widest column
+// margin, so the lanes of every node cover its box; the lanes outside it
+// compute values nobody reads, and never touch memory.
+struct SweepNode {
+  int rlo = 0, rhi = 0, clo = 0, chi = 0;  // margins around the anchor tile
+  int s = 0;                               // lane shift
+  std::vector<int> depth;                  // per value (staged: one; run: per store slot): rows kept
+};
+struct SweepLoad {
+  int node = -1, value = 0;  // producer node and value (-1: read from memory)
+  int d = 0, delta = 0;      // rows back in the producer's history, lane shift of the shuffle
+};
+struct SweepPlan {
+  bool ok = false;
+  int wo = 0, t0 = 0;                     // anchor columns per warp, first step (<= 0)
+  int nsb = 0;                            // staged inputs first, then the runs
+  std::vector<SweepNode> nodes;
+  std::vector<std::vector<SweepLoad>> ld;  // per run, per load slot
+};
+
+constexpr int kSweepMaxHistoryBytes = 384;  // register history per thread
+
+SweepPlan sweep_plan(const Group& g) {
+  SweepPlan P;
+  const int m = (int)g.runs.size();
+  for (auto& r : g.runs)
+    if (r.has_red || r.has_red2) return P;
+  const std::vector<StagedBase> sp = staging_plan(g);
+  if (group_stacked(g) && sp.empty()) return P;  // no shifts anywhere: the stacked form is this already
+  const auto six = staged_index(g, sp);
+  P.nsb = (int)sp.size();
+  for (auto& b : sp) {
+    SweepNode n;
+    n.rlo = b.rlo;
+    n.rhi = b.rhi;
+    n.clo = b.clo;
+    n.chi = b.chi;
+    n.depth.assign(1, 1);
+    P.nodes.push_back(n);
+  }
+  for (int k = 0; k < m; ++k) {
+    SweepNode n;
+    n.rlo = g.box[k][0];
+    n.rhi = g.box[k][1];
+    n.clo = g.box[k][2];
+    n.chi = g.box[k][3];
+    n.depth.assign(g.runs[k].stores.size(), 1);
+    P.nodes.push_back(n);
+  }
+  int spread = 0;
+  P.t0 = 0;
+  for (auto& n : P.nodes) {
+    spread = std::max(spread, n.chi - n.clo);
+    P.t0 = std::min(P.t0, n.rlo - n.rhi);
+  }
+  P.wo = 32 - spread;
+  if (P.wo < 16) return P;
+  // loads served by nodes: history depth, and the edges the shifts align
+  struct Edge { int l, n, dc, w; };
+  std::vector<Edge> edges;
+  P.ld.resize(m);
+  for (int k = 0; k < m; ++k) {
+    const int me = P.nsb + k;
+    P.ld[k].resize(g.runs[k].loads.size());
+    for (size_t s = 0; s < g.runs[k].loads.size(); ++s) {
+      SweepLoad& L = P.ld[k][s];
+      int dr = 0, dc = 0;
+      if (six[k][s].first >= 0) {
+        const StagedSlot& q = sp[six[k][s].first].slots[six[k][s].second];
+        L.node = six[k][s].first;
+        L.value = 0;
+        dr = q.dr;
+        dc = q.dc;
+      } else if (g.lds[k][s].prod >= 0) {
+        L.node = P.nsb + g.lds[k][s].prod;
+        L.value = g.lds[k][s].prod_store;
+        dr = g.lds[k][s].dr;
+        dc = g.lds[k][s].dc;
+      } else {
+        continue;  // read from memory at the point itself
+      }
+      SweepNode& n = P.nodes[L.node];
+      L.d = n.rhi - P.nodes[me].rhi - dr;
+      if (L.d < 0) return P;  // cannot happen with margins taken from the consumers
+      n.depth[L.value] = std::max(n.depth[L.value], L.d + 1);
+      edges.push_back({me, L.node, dc, itemsize(g.runs[k].loads[s].dtype) > 4 ? 2 : 1});
+    }
+  }
+  int64_t hist = 0;
+  for (int b = 0; b < P.nsb; ++b) hist += (int64_t)(P.nodes[b].depth[0] + 2) * itemsize(sp[b].dtype);
+  for (int k = 0; k < m; ++k)
+    for (size_t s = 0; s < g.runs[k].stores.size(); ++s)
+      if (g.consumed[k][s]) hist += (int64_t)P.nodes[P.nsb + k].depth[s] * itemsize(g.runs[k].stores[s].dtype);
+  if (hist > kSweepMaxHistoryBytes) return P;
+  // lane shifts: node n may take s in [wo - 32 + chi, clo] (its box on the
+  // lanes); coordinate descent on the number of shuffled values
+  const int N = (int)P.nodes.size();
+  for (auto& n : P.nodes) n.s = n.clo;
+  auto cost = [&](int x) {
+    int c = 0;
+    for (auto& e : edges)
+      if ((e.l == x || e.n == x) && P.nodes[e.l].s + e.dc - P.nodes[e.n].s != 0) c += e.w;
+    return c;
+  };
+  for (int pass = 0; pass < 16; ++pass) {
+    bool changed = false;
+    for (int x = 0; x < N; ++x) {
+      SweepNode& n = P.nodes[x];
+      const int cur = n.s;
+      int best = cur, bc = cost(x);
+      for (int v = P.wo - 32 + n.chi; v <= n.clo; ++v) {
+        n.s = v;
+        const int c = cost(x);
+        if (c < bc) {
+          bc = c;
+          best = v;
+        }
+      }
+      n.s = best;
+      changed = changed || best != cur;
+    }
+    if (!changed) break;
+  }
+  for (int k = 0; k < m; ++k) {
+    const int me = P.nsb + k;
+    for (size_t s = 0; s < g.runs[k].loads.size(); ++s) {
+      SweepLoad& L = P.ld[k][s];
+      if (L.node < 0) continue;
+      const int dc = six[k][s].first >= 0 ? sp[six[k][s].first].slots[six[k][s].second].dc : g.lds[k][s].dc;
+      L.delta = P.nodes[me].s + dc - P.nodes[L.node].s;
+    }
+  }
+  P.ok = true;
+  return P;
+}
+
 // Tile shapes the tuner chooses from; two of them also in the staged form
 // (inputs through shared memory) and two in the pipelined tensor-copy form,
-// where the group has stencil inputs
+// where the group has stencil inputs; and the row-sweep form at three strip
+// lengths where the group allows it
 std::vector<TileShape> group_shapes(const Group& g) {
   std::vector<TileShape> out;
   const bool can_stage = !staging_plan(g).empty();
@@ -1779,6 +1932,16 @@ std::vector<TileShape> group_shapes(const Group& g) {
     if (ts.staged || ts.tma) staged_smem(staging_plan(g), ts.th, ts.tw, &ts.smem, ts.tma ? tma_stages(g) : 0);
     if (ts.smem <= kGroupSmemLimit) out.push_back(ts);
   }
+  const SweepPlan sw = sweep_plan(g);
+  if (sw.ok)
+    for (int R : {32, 64, 128}) {
+      TileShape ts;
+      ts.th = R;
+      ts.tw = sw.wo;
+      ts.block = 256;
+      ts.sweep = true;
+      out.push_back(ts);
+    }
   return out;
 }
 
@@ -2031,6 +2194,228 @@ static void emit_stacked(std::ostringstream& o, const Group& g, const GroupLayou
   }
 }
 
+// lane shifts of the row-sweep form (bool through int: shuffles move 32 or 64 bits)
+const char* kSweepPrelude = R"CUDA(
+template <class T> __device__ __forceinline__ T vbe_lane_dn(T v, unsigned d) { return __shfl_down_sync(0xffffffffu, v, d); }
+template <class T> __device__ __forceinline__ T vbe_lane_up(T v, unsigned d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ bool vbe_lane_dn(bool v, unsigned d) { return __shfl_down_sync(0xffffffffu, (int)v, d) != 0; }
+__device__ __forceinline__ bool vbe_lane_up(bool v, unsigned d) { return __shfl_up_sync(0xffffffffu, (int)v, d) != 0; }
+)CUDA";
+
+// A constant of a group's source as an exact literal (group sources are
+// already keyed by their constants' values): hexadecimal floating literals
+// for finite values, the bit pattern otherwise.
+static std::string const_literal(const Operand& a) {
+  char buf[64];
+  switch (a.dtype) {
+    case VBE_FLOAT64:
+      if (std::isfinite(a.f)) {
+        snprintf(buf, sizeof buf, "(%a)", a.f);
+        return buf;
+      }
+      return "__longlong_as_double(" + std::to_string(const_bits(a)) + "ll)";
+    case VBE_FLOAT32: {
+      const float f = (float)a.f;
+      if (std::isfinite(f)) {
+        snprintf(buf, sizeof buf, "(%af)", (double)f);
+        return buf;
+      }
+      return "__int_as_float(" + std::to_string((int)(uint32_t)const_bits(a)) + ")";
+    }
+    case VBE_BOOL:
+      return a.i ? "true" : "false";
+    default:
+      snprintf(buf, sizeof buf, "((long long)0x%llxull)", (unsigned long long)a.i);
+      return buf;
+  }
+}
+
+// The row-sweep form (sweep_plan): warp gw takes strip (ti, tj) of the
+// anchor, rows i0 .. i0 + R - 1 and columns j0 .. j0 + WO - 1. Staged inputs
+// are loaded PF rows ahead of their use, so that a row's loads are in flight
+// while the rows before it are computed. Steps t0 .. -1 fill the histories;
+// steps 0 .. R - 1 produce one anchor row each. Every lane runs every step
+// (warp shuffles need the whole warp); loads and stores are guarded by the
+// lane's column lying in its node's box, and rows always lie in the runs'
+// shapes (the margins come from what the consumers read).
+//
+// Each history (and each staged input's prefetch ring) is a ring of
+// registers whose size is a power of two; the step loop is unrolled by the
+// largest ring size U, so that at step t the value of t - d sits in a fixed
+// register and nothing is moved between registers. Strides and constants are
+// literals (the group's source is keyed by them), so the row offsets of an
+// unrolled block fold into the loads' and stores' immediate offsets, and one
+// pointer per stream advances once per block.
+static void emit_sweep(std::ostringstream& o, const Group& g, const GroupLayout& GL, const TileShape& ts) {
+  const SweepPlan P = sweep_plan(g);
+  const std::vector<StagedBase> sp = staging_plan(g);
+  const int m = (int)g.runs.size(), anchor = m - 1, NW = ts.block / 32, R = ts.th, WO = ts.tw;
+  const int PF = 2;
+  // 32-bit groups: four blocks per SM (64 registers a thread); left to the
+  // compiler, they got 48 and re-derived values inside the loop instead
+  // (measured: 204 against 189 instructions per cell on shallow water)
+  bool wide = false;
+  for (auto& r : g.runs) {
+    for (auto& sl : r.loads) wide = wide || itemsize(sl.dtype) > 4;
+    for (auto& sl : r.stores) wide = wide || itemsize(sl.dtype) > 4;
+  }
+  const int minb = wide ? 0 : 4;
+  const int nn = (int)P.nodes.size();
+  auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
+  auto I = [](int64_t v) { return std::to_string(v); };
+  auto pow2 = [](int v) {
+    int r = 1;
+    while (r < v) r <<= 1;
+    return r;
+  };
+  std::vector<std::vector<int>> ring(nn);
+  int U = 1;
+  for (int n = 0; n < nn; ++n) {
+    for (int d : P.nodes[n].depth) ring[n].push_back(pow2(n < P.nsb ? PF + d : d));
+    for (int r : ring[n]) U = std::max(U, r);
+  }
+  // the register holding value v of node n produced at step q (any integer)
+  auto reg = [&](int n, int v, int q) {
+    const int S = ring[n][v];
+    return "r" + I(n) + "_" + I(v) + "_" + I(((q % S) + S) % S);
+  };
+  auto strides = [](const Slot& sl) { return std::make_pair(sl.st[0], sl.st[1]); };
+  o << "extern \"C\" __global__ void __launch_bounds__(" << ts.block << (minb ? ", " + std::to_string(minb) : std::string()) << ") vbe_@TAG@" << ts.suffix()
+    << "(const P p) {\n"
+    << "  vbe_grid_wait();\n"
+    << "  const i64 gw = (i64)blockIdx.x * " << NW << " + (threadIdx.x >> 5);\n"
+    << "  if (gw < p.w[3]) {  // the whole warp or none of it\n"
+    << "    const int lane = threadIdx.x & 31;\n"
+    << "    const i64 ti = gw / p.w[2], tj = gw - ti * p.w[2];\n"
+    << "    const i64 i0 = ti * " << R << ", j0 = tj * " << WO << ";\n"
+    << "    const int reff = (int)min((i64)" << R << ", p.w[0] - i0), weff = (int)min((i64)" << WO
+    << ", p.w[1] - j0);\n";
+  for (int n = 0; n < nn; ++n) {
+    const SweepNode& N = P.nodes[n];
+    o << "    const int x" << n << " = lane + (" << N.s << ");\n"
+      << "    const bool ok" << n << " = x" << n << " >= " << N.clo << " && x" << n << " < weff + " << N.chi << ";\n";
+  }
+  // staged inputs: pointer at the row of step 0, ring registers, the first PF rows
+  for (int b = 0; b < P.nsb; ++b) {
+    const StagedBase& B = sp[b];
+    const SweepNode& N = P.nodes[b];
+    const std::string T = ctype(B.dtype);
+    const int64_t Pr = g.runs[B.ref_k].loads[B.ref_s].st[0];
+    o << "    auto sq" << b << " = vbe_ptr<const " << T << ">(" << W(GL.lw[B.ref_k][B.ref_s]) << ") + ((i0 + "
+      << N.rhi << ") * " << Pr << "ll + j0 + x" << b << ");\n"
+      << "    " << T;
+    for (int r = 0; r < ring[b][0]; ++r) o << (r ? ", " : " ") << "r" << b << "_0_" << r << " = 0";
+    o << ";\n";
+    for (int q = P.t0; q < P.t0 + PF; ++q)
+      if (q + N.rhi >= N.rlo)
+        o << "    if (ok" << b << (q > 0 ? " && " + I(q) + " < reff" : "") << ") " << reg(b, 0, q) << " = sq" << b
+          << "[" << I(q * Pr) << "ll];\n";
+  }
+  // runs: memory pointers at the row of step 0, rings of the values they hand on
+  for (int k = 0; k < m; ++k) {
+    const Run& r = g.runs[k];
+    const int n = P.nsb + k;
+    for (size_t s = 0; s < r.loads.size(); ++s) {
+      if (P.ld[k][s].node >= 0) continue;
+      auto st = strides(r.loads[s]);
+      o << "    auto lq" << k << "_" << s << " = vbe_ptr<const " << ctype(r.loads[s].dtype) << ">("
+        << W(GL.lw[k][s]) << ") + ((i0 + " << P.nodes[n].rhi << ") * " << st.first << "ll + (j0 + x" << n << ") * "
+        << st.second << "ll);\n";
+    }
+    for (size_t s = 0; s < r.stores.size(); ++s) {
+      const std::string T = ctype(r.stores[s].dtype);
+      if (k == anchor) {
+        auto st = strides(r.stores[s]);
+        o << "    auto oq" << s << " = vbe_ptr<" << T << ">(" << W(GL.sw[k][s]) << ") + (i0 * " << st.first
+          << "ll + (j0 + x" << n << ") * " << st.second << "ll);\n";
+      } else {
+        o << "    " << T;
+        for (int q = 0; q < ring[n][s]; ++q) o << (q ? ", " : " ") << "r" << n << "_" << s << "_" << q << " = 0";
+        o << ";\n";
+      }
+    }
+  }
+  // one step: q the step index modulo the rings (its registers), rel the
+  // row offset from the pointers, t its index at run time; check: whether
+  // a load PF steps ahead may run past the strip
+  auto advance = [&](int64_t rows, const std::string& ind) {
+    for (int b = 0; b < P.nsb; ++b)
+      o << ind << "sq" << b << " = sq" << b << " + " << I(rows * g.runs[sp[b].ref_k].loads[sp[b].ref_s].st[0])
+        << "ll;\n";
+    for (int k = 0; k < m; ++k)
+      for (size_t s = 0; s < g.runs[k].loads.size(); ++s)
+        if (P.ld[k][s].node < 0)
+          o << ind << "lq" << k << "_" << s << " = lq" << k << "_" << s << " + "
+            << I(rows * g.runs[k].loads[s].st[0]) << "ll;\n";
+    for (size_t s = 0; s < g.runs[anchor].stores.size(); ++s)
+      o << ind << "oq" << s << " = oq" << s << " + " << I(rows * g.runs[anchor].stores[s].st[0]) << "ll;\n";
+  };
+  auto step = [&](int q, int rel, const std::string& t, bool fill, bool check, const std::string& ind) {
+    for (int b = 0; b < P.nsb; ++b) {
+      const SweepNode& N = P.nodes[b];
+      if (fill && q + PF + N.rhi < N.rlo) continue;  // a row above the input's box
+      const int64_t Pr = g.runs[sp[b].ref_k].loads[sp[b].ref_s].st[0];
+      const bool guard = fill ? q + PF > 0 : check;
+      o << ind << "if (ok" << b << (guard ? " && " + t + " + " + I(PF) + " < reff" : "") << ") "
+        << reg(b, 0, q + PF) << " = sq" << b << "[" << I((int64_t)(rel + PF) * Pr) << "ll];\n";
+    }
+    for (int k = 0; k < m; ++k) {
+      const Run& r = g.runs[k];
+      const int n = P.nsb + k;
+      const SweepNode& N = P.nodes[n];
+      if (fill && q < N.rlo - N.rhi) continue;  // rows above this run's box
+      o << ind << "{  // run " << k << "\n"
+        << ind << "  const i64 rr = i0 + (" << t << " + " << N.rhi << "), cc = j0 + x" << n << ";\n";
+      for (size_t s = 0; s < r.loads.size(); ++s) {
+        const std::string T = ctype(r.loads[s].dtype), a = "a" + I((int)s);
+        const SweepLoad& L = P.ld[k][s];
+        if (L.node < 0) {
+          o << ind << "  const " << T << " " << a << " = ok" << n << " ? lq" << k << "_" << s << "["
+            << I((int64_t)rel * r.loads[s].st[0]) << "ll] : (" << T << ")0;\n";
+          continue;
+        }
+        std::string x = reg(L.node, L.value, q - L.d);
+        if (L.delta > 0) x = "vbe_lane_dn(" + x + ", " + I(L.delta) + "u)";
+        if (L.delta < 0) x = "vbe_lane_up(" + x + ", " + I(-L.delta) + "u)";
+        o << ind << "  const " << T << " " << a << " = " << x << ";\n";
+      }
+      for (size_t s = 0; s < r.stores.size(); ++s) o << ind << "  " << ctype(r.stores[s].dtype) << " b" << s << ";\n";
+      o << ind << "  vbe_elem" << k << "(p, rr * " << r.shape[1] << "ll + cc";
+      for (size_t s = 0; s < r.loads.size(); ++s) o << ", a" << s;
+      for (size_t s = 0; s < r.stores.size(); ++s) o << ", b" << s;
+      for (auto& cst : r.consts) o << ", " << const_literal(cst);
+      o << ");\n";
+      if (k == anchor) {
+        o << ind << "  if (ok" << n << ") {\n";
+        for (size_t s = 0; s < r.stores.size(); ++s)
+          o << ind << "    oq" << s << "[" << I((int64_t)rel * r.stores[s].st[0]) << "ll] = b" << s << ";\n";
+        o << ind << "  }\n";
+      } else {
+        for (size_t s = 0; s < r.stores.size(); ++s) o << ind << "  " << reg(n, (int)s, q) << " = b" << s << ";\n";
+      }
+      o << ind << "}\n";
+    }
+  };
+  for (int t = P.t0; t < 0; ++t) {
+    o << "    {  // fill step " << t << "\n";
+    step(t, t, I(t), true, false, "      ");
+    o << "    }\n";
+  }
+  o << "    int tb = 0;\n"
+    << "    for (; tb + " << U << " <= reff; tb += " << U << ") {\n";
+  for (int j = 0; j < U; ++j) step(j, j, "tb + " + I(j), false, j + PF >= U, "      ");
+  advance(U, "      ");  // every stream moves on by U rows
+  o << "    }\n";
+  for (int j = 0; j + 1 < U; ++j) {  // the last steps of a ragged strip
+    o << "    if (tb + " << j << " < reff) {\n";
+    step(j, j, "tb + " + I(j), false, true, "      ");
+    o << "    }\n";
+  }
+  o << "  }\n";
+  emit_copy_through(o, g, GL);
+  o << "}\n";
+}
+
 std::vector<TmaBox> group_tma_boxes(const Group& g, const TileShape& ts) {
   std::vector<TmaBox> out;
   for (auto& b : staging_plan(g)) {
@@ -2185,6 +2570,11 @@ static std::string generate_group_source_uncached(const Group& g, std::string* e
       o << kTmaPrelude;
       break;
     }
+  for (auto& ts : shapes)
+    if (ts.sweep) {
+      o << kSweepPrelude;
+      break;
+    }
   if (soft)
     o << sf64_include()
       << "__device__ __forceinline__ double vbe_u01s(u64 seed, u64 key, u64 step, u64 m) {\n"
@@ -2226,6 +2616,10 @@ static std::string generate_group_source_uncached(const Group& g, std::string* e
   }
   auto W = [](int k) { return "p.w[" + std::to_string(k) + "]"; };
   for (const TileShape& ts : shapes) {
+    if (ts.sweep) {
+      emit_sweep(o, g, GL, ts);
+      continue;
+    }
     int64_t total = 0;
     auto soff = group_smem(g, ts.th, ts.tw, &total);
     if (group_stacked(g)) total = 0;

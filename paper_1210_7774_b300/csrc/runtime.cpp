@@ -330,6 +330,7 @@ struct Launch {
   void* d_prefix = nullptr;
   int64_t d_bytes = 0;
   bool tma = false;                // a tile-fused group in the tensor-copy form
+  bool sweep = false;              // a tile-fused group in the row-sweep form
 };
 
 namespace {
@@ -398,6 +399,7 @@ void record_launch(Ctx* c, Exec* ex, Launch& L) {
   c->rec_launches.push_back(j + "}");
   c->stats.kernel_launches++;
   if (L.packed) c->stats.packed_launches++;
+  if (L.sweep) c->stats.sweep_group_launches++;
 }
 
 // Every generated kernel starts with griddepcontrol.wait, so it may be
@@ -453,6 +455,7 @@ void issue(Ctx* c, Exec* ex, Launch& L, bool capturing) {
   if (!capturing) c->stats.kernel_launches++;
   if (!capturing && L.packed) c->stats.packed_launches++;
   if (L.tma) c->stats.tma_group_launches++;
+  if (L.sweep) c->stats.sweep_group_launches++;
 }
 
 struct RunPtrs {
@@ -907,6 +910,11 @@ Launch build_group(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, cons
   fill_group_words(*G.g, ts, ptr.lp, ptr.sp, ptr.ren, ptr.red, (uintptr_t)ex->scratch.partials,
                    (uintptr_t)ex->scratch.counters, &a, (uintptr_t)c->err_word_dev);
   L.grid = (unsigned)std::max<int64_t>(1, a.w[3]);
+  if (ts.sweep) {  // one warp per strip
+    const int64_t nw = ts.block / 32;
+    L.grid = (unsigned)std::max<int64_t>(1, (a.w[3] + nw - 1) / nw);
+    L.sweep = true;
+  }
   if (ts.tma) {
     // persistent: as many blocks as fit, tensor maps ahead of the words
     const int64_t cap = (int64_t)occupancy(L.fn, (int)L.block, L.smem) * c->sm_count;
@@ -939,24 +947,25 @@ std::string group_tune_key(const GroupPrepared& G) {
 TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real, bool may_tune) {
   if (G.shapes.empty()) fail(VBE_ERR_INVALID, "tile-fused group without a tile shape");
   // a fixed shape: "THxTW", "sTHxTW" for the staged form, "tTHxTW" for the
-  // tensor-copy form (VBE_RECORD_TILE when recording, else VBE_TILE)
+  // tensor-copy form, "rR" for the row-sweep form with strips of R rows
+  // (VBE_RECORD_TILE when recording, else VBE_TILE)
   const char* e = c->record ? getenv("VBE_RECORD_TILE") : (c->force_tile.empty() ? nullptr : c->force_tile.c_str());
   if (e)
-    for (auto& ts : G.shapes)
-      if ((ts.tma ? "t" : (ts.staged ? "s" : "")) + std::to_string(ts.th) + "x" + std::to_string(ts.tw) == e &&
-          (c->record || !ts.tma || tma_pointers_ok(*G.g, ts, real)))
-        return ts;
+    for (auto& ts : G.shapes) {
+      const std::string name = ts.letter() + std::to_string(ts.th) + (ts.sweep ? "" : "x" + std::to_string(ts.tw));
+      if (name == e && (c->record || !ts.tma || tma_pointers_ok(*G.g, ts, real))) return ts;
+    }
   if (c->record) return G.shapes[0];
   std::string tk = group_tune_key(G);
   auto it = c->tune.find(tk);
   if (it != c->tune.end())
     for (auto& ts : G.shapes)
-      if (ts.th == it->second.block && ts.tw == it->second.U &&
-          (ts.tma ? 2 : (int)ts.staged) == it->second.grid_mult && (!ts.tma || tma_pointers_ok(*G.g, ts, real)))
+      if (ts.th == it->second.block && ts.tw == it->second.U && ts.form() == it->second.grid_mult &&
+          (!ts.tma || tma_pointers_ok(*G.g, ts, real)))
         return ts;
   TileShape def = G.shapes[0];
   for (auto& ts : G.shapes)
-    if (!ts.staged && !ts.tma && ts.th * ts.tw <= 1024 && ts.th * ts.tw >= def.th * def.tw) def = ts;
+    if (!ts.staged && !ts.tma && !ts.sweep && ts.th * ts.tw <= 1024 && ts.th * ts.tw >= def.th * def.tw) def = ts;
   const Group& g = *G.g;
   const int anchor = (int)g.runs.size() - 1;
   if (!(may_tune && (c->cfg.flags & VBE_AUTOTUNE) && g.rows(anchor) * g.cols(anchor) >= (1 << 16))) return def;
@@ -1006,10 +1015,10 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
   }
   for (auto& b : bufs) dev_free(c, ex, b.first, b.second);
   c->stats.autotunes++;
-  TuneChoice tc;  // the group's choice: tile rows, tile columns, staged form
+  TuneChoice tc;  // the group's choice: tile rows, tile columns, form
   tc.block = best.th;
   tc.U = best.tw;
-  tc.grid_mult = best.tma ? 2 : (best.staged ? 1 : 0);
+  tc.grid_mult = best.form();
   c->tune[tk] = tc;
   return best;
 }

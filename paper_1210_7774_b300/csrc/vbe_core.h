@@ -249,10 +249,17 @@ struct TileShape {
   int th = 0, tw = 0, block = 0;
   bool staged = false;  // stencil inputs copied to shared memory first (else read through L1)
   bool tma = false;     // persistent form: inputs prefetched by tensor copies, two stages
+  // row-sweep form: one warp per strip of tw anchor columns walks th rows,
+  // values kept in registers across rows and exchanged by warp shuffles
+  bool sweep = false;
   int64_t smem = 0;     // dynamic shared memory bytes
   std::string suffix() const {
-    return std::string(tma ? "_tm" : (staged ? "_ss" : "_sg")) + std::to_string(th) + "x" + std::to_string(tw);
+    return std::string(sweep ? "_rs" : (tma ? "_tm" : (staged ? "_ss" : "_sg"))) + std::to_string(th) + "x" +
+           std::to_string(tw);
   }
+  // the form's letter in VBE_TILE / VBE_RECORD_TILE: "r" sweep, "t" tensor copies, "s" staged
+  const char* letter() const { return sweep ? "r" : (tma ? "t" : (staged ? "s" : "")); }
+  int form() const { return sweep ? 3 : (tma ? 2 : (int)staged); }
 };
 std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes,
                                   std::string* key_out = nullptr);

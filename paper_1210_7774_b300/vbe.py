@@ -56,7 +56,8 @@ class vbe_config(Structure):
 class vbe_stats(Structure):
     _fields_ = [(n, c_int64) for n in ("kernel_launches", "graph_launches", "graph_captures", "compiles",
                                        "autotunes", "batches", "bytes_allocated", "peak_bytes",
-                                       "list_replays", "tma_group_launches", "packed_launches")]
+                                       "list_replays", "tma_group_launches", "packed_launches",
+                                       "sweep_group_launches")]
 
 
 class vbe_req_base(Structure):

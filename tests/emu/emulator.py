@@ -105,6 +105,10 @@ extern "C" long long emu_axis(const long long* w, int nw, unsigned grid, unsigne
 """
 
 
+# bump when build() changes how it finds entries or picks wrappers
+_WRAPPER_RULES = "entries: launch bounds with an optional minimum of blocks; group forms sg ss tm rs"
+
+
 class EmulationError(AssertionError):
     pass
 
@@ -118,8 +122,9 @@ class Emulator:
 
     def _key(self, src: str) -> str:
         # the source names the soft float64 headers' hash; the emulation
-        # header and the wrappers are part of every module too
-        return hashlib.sha1((src + self._emu_h + _GLOBALS + _WRAP_COMMON).encode()).hexdigest()[:20]
+        # header, the wrappers and the rules that pick the wrappers are part
+        # of every module too
+        return hashlib.sha1((src + self._emu_h + _GLOBALS + _WRAP_COMMON + _WRAPPER_RULES).encode()).hexdigest()[:20]
 
     @property
     def _emu_h(self) -> str:
@@ -147,7 +152,7 @@ class Emulator:
         so = os.path.join(self.dir, f"emu_{h}.so")
         if not os.path.exists(so):
             parts = [f'#include "{EMU_H}"', "#include <type_traits>", _GLOBALS, src, _WRAP_COMMON]
-            names = re.findall(r"__global__ void __launch_bounds__\(\d+\) (\w+)\(", src)
+            names = re.findall(r"__global__ void __launch_bounds__\(\d+(?:, \d+)?\) (\w+)\(", src)
             prefix = names[0].rsplit("_", 1)[0] if names else "vbe"
             if prefix.endswith("_pack"):
                 prefix = prefix[:-5]
@@ -160,7 +165,7 @@ class Emulator:
             if prefix + "_bulk" in names:
                 parts.append(_WRAP_BULK.replace("@P@", prefix))
             for name in names:  # tile-fused groups: one kernel per tile shape
-                if re.search(r"_(s[gs]|tm)\d+x\d+$", name):
+                if re.search(r"_(s[gs]|tm|rs)\d+x\d+$", name):
                     parts.append(_WRAP_ENTRY.replace("@E@", name))
             cpp = os.path.join(self.dir, f"emu_{h}.cpp")
             with open(cpp, "w") as f:
@@ -219,7 +224,7 @@ class Emulator:
                                    L["chunk"], L["work"], L["grid"], L["block"])
             else:
                 w = (ctypes.c_longlong * len(L["words"]))(*L["words"])
-                if re.search(r"_(s[gs]|tm)\d+x\d+$", entry):
+                if re.search(r"_(s[gs]|tm|rs)\d+x\d+$", entry):
                     fn = getattr(lib, "emu_" + entry)
                     fn.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
                     fn.restype = ctypes.c_longlong

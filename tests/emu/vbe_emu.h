@@ -274,6 +274,20 @@ inline T __shfl_down_sync(unsigned, T v, int off) {
   return r;
 }
 
+template <class T>
+inline T __shfl_up_sync(unsigned, T v, int off) {
+  static_assert(sizeof(T) <= 8, "shuffle width");
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long bits = 0;
+  memcpy(&bits, &v, sizeof(T));
+  g_xchg[threadIdx.x] = bits;
+  g_warp_bar[w]->arrive_and_wait();
+  T r = v;
+  if (lane >= (unsigned)off) memcpy(&r, &g_xchg[w * 32 + lane - off], sizeof(T));
+  g_warp_bar[w]->arrive_and_wait();
+  return r;
+}
+
 inline double __longlong_as_double(long long v) {
   double d;
   memcpy(&d, &v, 8);

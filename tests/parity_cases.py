@@ -299,10 +299,15 @@ def tile_group_cases(seed=11, N=37, M=45):
     for dt in ("float32", "float64"):
         info = np.finfo(dt)
         sp = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, info.tiny / 8, -info.tiny / 1024, info.max / 2, 1.5,
-                       -3.0], dt)
+                       -3.0, 2.0 ** -60, -(2.0 ** -61), 2.0 ** 70, 2.0 ** 40], dt)
         num = rng.standard_normal(N * M).astype(dt)
         num[rng.random(N * M) < 0.6] = 0.0
         num[rng.random(N * M) < 0.1] = -0.0
+        # tiny numerators, log-uniform from the smallest subnormal to 2^-56
+        # (the float32 divide scales those below 2^-60)
+        lo = np.log2(info.smallest_subnormal)
+        pick = rng.random(N * M) < 0.15
+        num[pick] = (np.exp2(rng.uniform(lo, -56.0, pick.sum())) * rng.choice([-1.0, 1.0], pick.sum())).astype(dt)
         den = rng.standard_normal(N * M).astype(dt)
         pick = rng.random(N * M) < 0.3
         den[pick] = sp[rng.integers(0, len(sp), pick.sum())]

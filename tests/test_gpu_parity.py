@@ -132,16 +132,19 @@ def test_jacobi_paper_size_tile_fused():
                      F64_REDUCE_RTOL, "deltas")
 
 
-@pytest.mark.parametrize("tile", ["t32x32", "t16x64", "s32x32", "32x32"])
+@pytest.mark.parametrize("tile", ["t32x32", "t16x64", "s32x32", "32x32", "r32", "r128"])
 def test_tile_group_forms_exact(tile):
     """Tile-fused groups forced into one tile shape and form (VBE_TILE, read
     when the context is created): inputs read through L1, staged through
-    shared memory ("s"), or prefetched by double-buffered tensor copies into
-    persistent blocks that walk several tiles each ("t"). Bit-exact with the
-    oracle on the synthetic chains (rows of 16-byte multiples, ragged against
-    every tile), Jacobi 514^2 (a group with a whole-run reduction: deltas
-    within the reduction tolerance), shallow water (state renamed every step)
-    and Gray-Scott at 2050 x 1032 (about 2,000 tiles), float64 and float32."""
+    shared memory ("s"), prefetched by double-buffered tensor copies into
+    persistent blocks that walk several tiles each ("t"), or swept down the
+    rows by one warp per column strip, values in registers and handed
+    across columns by warp shuffles ("r", strips of 32 or 128 rows).
+    Bit-exact with the oracle on the synthetic chains (rows of 16-byte
+    multiples, ragged against every tile), Jacobi 514^2 (a group with a
+    whole-run reduction: deltas within the reduction tolerance; no row-sweep
+    form), shallow water (state renamed every step) and Gray-Scott at
+    2050 x 1032 (about 2,000 tiles), float64 and float32."""
     cases = tile_group_cases(seed=12, N=37, M=52) + [jacobi_case(514, 3)]
     for dt in ("float64", "float32"):
         for p in (shallow_water(256, 2, dt), gray_scott(2050, 1032, 2, dt)):
@@ -153,6 +156,8 @@ def test_tile_group_forms_exact(tile):
             case.check(got, oracle_outputs(case.program))
             if tile.startswith("t"):
                 assert got["_stats"]["tma_group_launches"] > 0, case.name
+            if tile.startswith("r") and not case.name.startswith("jacobi"):
+                assert got["_stats"]["sweep_group_launches"] > 0, case.name
     finally:
         os.environ.pop("VBE_TILE")
 
