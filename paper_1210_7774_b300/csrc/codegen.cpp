@@ -382,12 +382,14 @@ __device__ __forceinline__ i64 vbe_iabs(i64 a) { return a < 0 ? vbe_ineg(a) : a;
 template <class T> __device__ __forceinline__ T vbe_max(T a, T b) { return (a > b || a != a) ? a : b; }
 // IEEE division with zero numerators kept off the hardware sequence's slow
 // path (tile-fused stencil kernels: state fields such as the momenta of a
-// fluid at rest are mostly zeros). For a == 0 the quotient is a * (1 / b'),
-// b' = b * 2^64 (so that 1 / b' cannot overflow for a subnormal b): the
-// signed zero, or NaN for b = 0 or NaN, exactly as a / b.
+// fluid at rest are mostly zeros). For a == 0 the quotient is a * (2^-64 / b):
+// 2^-64 / b is finite and non-zero for every finite non-zero b, subnormal b
+// included, so the product is the zero with the sign of a / b; it is NaN
+// for b = 0 (2^-64 / 0 = inf) or NaN, and a zero for an infinite b, exactly
+// as a / b.
 template <class T> __device__ __forceinline__ T vbe_zdiv(T a, T b) {
   const bool z = a == (T)0;
-  const T q = (z ? (T)1 : a) / (z ? b * (T)18446744073709551616.0 : b);
+  const T q = (z ? (T)0x1p-64 : a) / b;
   return z ? a * q : q;
 }
 template <class T> __device__ __forceinline__ T vbe_min(T a, T b) { return (a < b || a != a) ? a : b; }
@@ -1934,7 +1936,7 @@ std::vector<TileShape> group_shapes(const Group& g) {
   }
   const SweepPlan sw = sweep_plan(g);
   if (sw.ok)
-    for (int R : {32, 64, 128}) {
+    for (int R : {24, 32, 64}) {
       TileShape ts;
       ts.th = R;
       ts.tw = sw.wo;

@@ -132,14 +132,14 @@ def test_jacobi_paper_size_tile_fused():
                      F64_REDUCE_RTOL, "deltas")
 
 
-@pytest.mark.parametrize("tile", ["t32x32", "t16x64", "s32x32", "32x32", "r32", "r128"])
+@pytest.mark.parametrize("tile", ["t32x32", "t16x64", "s32x32", "32x32", "r24", "r64"])
 def test_tile_group_forms_exact(tile):
     """Tile-fused groups forced into one tile shape and form (VBE_TILE, read
     when the context is created): inputs read through L1, staged through
     shared memory ("s"), prefetched by double-buffered tensor copies into
     persistent blocks that walk several tiles each ("t"), or swept down the
     rows by one warp per column strip, values in registers and handed
-    across columns by warp shuffles ("r", strips of 32 or 128 rows).
+    across columns by warp shuffles ("r", strips of 24 or 64 rows).
     Bit-exact with the oracle on the synthetic chains (rows of 16-byte
     multiples, ragged against every tile), Jacobi 514^2 (a group with a
     whole-run reduction: deltas within the reduction tolerance; no row-sweep
