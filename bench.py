@@ -493,7 +493,7 @@ def config_subkeys(args, V, torch, local, stream, hbm, fp64):
             st1 = ex.stats()
         per = reps + warmup
         return sec, {k: (st1[k] - st0[k]) / per for k in ("kernel_launches", "graph_launches", "list_replays",
-                                                             "packed_launches")}
+                                                             "packed_launches", "sweep_group_launches")}
 
     out = {}
     # --- Jacobi 256^2 float64, 10 iterations (launch-bound: the grid is L2-resident)
@@ -554,6 +554,18 @@ def config_subkeys(args, V, torch, local, stream, hbm, fp64):
     sw["cpu_mcore"] = {"value": 6 * 8 * 2048 * 2048 * 2 / msec / 1e9, "unit": "GB/s", "cores": mcores,
                        "kind": "mcore", "ms_per_step_at_4096": msec / 2 * (N * N) / (2048 * 2048) * 1e3,
                        "sample": f"two steps of 2048x2048 ({msec:.2f} s), scaled by cells"}
+    # the same program in float32, where the memory roofline is within reach
+    # (fused path only: its plain path is timed by --workload shallow_water)
+    p32 = shallow_water(N, steps, "float32")
+    sec, st = timed(p32, F | G, 2, warmup=1)
+    ms32 = sec / steps * 1e3
+    cb32 = 6 * 4 * N * N
+    sw["float32"] = {"ms_per_step": ms32, "GB/s": cb32 / (ms32 / 1e3) / 1e9,
+                     "roofline": {"bound": "hbm", "achieved": cb32 / (ms32 / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                  "frac": cb32 / (ms32 / 1e3) / 1e9 / hbm, "bytes_per_cell": 24},
+                     "launches_per_step": st["kernel_launches"] / steps,
+                     # graph replays are not counted: whether the form was issued (or captured) at all
+                     "row_sweep_form": st["sweep_group_launches"] > 0}
     out["shallow_water_4096_f64_50st"] = sw
     # --- Monte-Carlo pi, 256 instances in one packed launch
     sizes = mc_sizes(256)

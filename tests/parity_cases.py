@@ -263,8 +263,10 @@ def tile_group_cases(seed=11, N=37, M=45):
     """Chains of two-dimensional runs handing temporaries to each other at
     small shifts (tile-fused into one kernel): an in-place anchor that each
     point reads only through its own view (no renaming), with RANDOM and
-    constants in the producer; and a three-run chain with shifts in both
-    dimensions writing a separate base. Sizes are ragged for every tile."""
+    constants in the producer; a three-run chain with shifts in both
+    dimensions writing a separate base; int64 and bool temporaries read
+    diagonally; divides with special operands. Sizes are ragged for every
+    tile."""
     rng = np.random.default_rng(seed)
     out = []
     b = ProgramBuilder("tile_group_inplace")
@@ -292,6 +294,20 @@ def tile_group_cases(seed=11, N=37, M=45):
     b.emit("SUBTRACT", b.sub2d(o, 0, N - 2, 0, M - 2), b.sub2d(t2, 1, N - 1, 1, M - 1),
            b.sub2d(t2, 0, N - 2, 0, M - 2))
     b.free(t1, t2)
+    p = b.build([o])
+    out.append(Case(p.name, p, _exact_check(p)))
+    # int64 and bool temporaries handed on at row and column shifts (a mask
+    # and a SELECT reading them diagonally)
+    b = ProgramBuilder("tile_group_int64_bool")
+    a = b.base("int64", (N, M), rng.integers(-1000, 1000, N * M))
+    o = b.base("int64", (N, M), np.zeros(N * M, np.int64))
+    t = b.base("int64", (N - 1, M - 1))
+    msk = b.base("bool", (N - 1, M - 1))
+    b.emit("ADD", b.whole(t), b.sub2d(a, 0, N - 1, 0, M - 1), b.sub2d(a, 1, N, 1, M))
+    b.emit("GREATER", b.whole(msk), b.whole(t), Const(0))
+    b.emit("SELECT", b.sub2d(o, 0, N - 2, 0, M - 2), b.sub2d(msk, 1, N - 1, 0, M - 2), b.sub2d(t, 0, N - 2, 1, M - 1),
+           b.sub2d(t, 1, N - 1, 1, M - 1))
+    b.discard(t, msk)
     p = b.build([o])
     out.append(Case(p.name, p, _exact_check(p)))
     # divisions with zero numerators and special divisors (zero, subnormal,
