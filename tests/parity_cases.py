@@ -310,6 +310,23 @@ def tile_group_cases(seed=11, N=37, M=45):
     b.discard(t, msk)
     p = b.build([o])
     out.append(Case(p.name, p, _exact_check(p)))
+    # a producer read 3 rows and 5 columns away (deep histories in the
+    # row-sweep form), a stencil input with a 10-column spread, a transposed
+    # view and a broadcast row read directly from memory
+    b = ProgramBuilder("tile_group_deep_shifts")
+    a = b.base("float64", (N, M), rng.standard_normal(N * M))
+    bt = b.base("float64", (M, N), rng.standard_normal(N * M))
+    row = b.base("float64", (M,), rng.standard_normal(M))
+    o = b.base("float64", (N, M), np.zeros(N * M))
+    t = b.base("float64", (N - 3, M - 5))
+    b.emit("MULTIPLY", b.whole(t), b.sub2d(a, 0, N - 3, 0, M - 5), b.sub2d(a, 3, N, 5, M))
+    b.emit("ADD", b.whole(t), b.whole(t), b.view(bt, 0, (N - 3, M - 5), (1, N)))
+    ov = b.sub2d(o, 0, N - 6, 0, M - 10)
+    b.emit("SUBTRACT", ov, b.sub2d(t, 0, N - 6, 0, M - 10), b.sub2d(t, 3, N - 3, 5, M - 5))
+    b.emit("ADD", ov, ov, b.view(row, 0, (N - 6, M - 10), (0, 1)))
+    b.discard(t)
+    p = b.build([o])
+    out.append(Case(p.name, p, _exact_check(p)))
     # divisions with zero numerators and special divisors (zero, subnormal,
     # huge, infinite, NaN) inside a tile-fused group
     for dt in ("float32", "float64"):
