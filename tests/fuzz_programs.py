@@ -1,0 +1,127 @@
+"""Seeded random bytecode programs for differential testing against the oracle.
+
+A program works on a few small 9 x 11 bases (float64, int64, bool) through
+random views of them: sub-blocks, rows or columns reversed (negative
+strides), transposed (column stride 1, row stride 11), every other row,
+broadcast rows (zero stride, inputs only), so consecutive instructions
+overlap, alias in place, partially overlap their own inputs and depend on
+each other through every kind of view; this is what the paper's blockable
+rule and the library's fusion breaks, staging and pairing have to get
+right. The bytecodes are the exact ones (add, subtract, multiply, divide,
+maximum, minimum, negative, absolute, square root, compares, select, copy,
+cast of small integers, min/max/argmin/argmax reductions over either axis,
+int64 sums), so every result must equal the oracle's bit for bit; the one
+documented relaxation is the sign of a zero chosen by a MIN/MAX reduction
+from tied signed zeros. Reductions write bases that no later instruction
+reads, so no reordering tolerance is needed anywhere.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from parity_cases import Case, assert_exact
+from workloads import Const, ProgramBuilder
+
+R, C = 9, 11
+SHAPES = [(3, 4), (4, 7), (5, 5), (9, 2), (2, 11), (1, 6), (6, 1), (9, 11), (7, 9)]
+
+
+def _view(b, rng, bid, h, w, broadcast_ok):
+    """A random view of shape (h, w) of the R x C base ``bid``."""
+    for _ in range(50):
+        kind = int(rng.integers(0, 6 if broadcast_ok else 5))
+        if kind == 0 and h <= R and w <= C:  # sub-block
+            r0, c0 = rng.integers(0, R - h + 1), rng.integers(0, C - w + 1)
+            return b.view(bid, r0 * C + c0, (h, w), (C, 1))
+        if kind == 1 and h <= R and w <= C:  # columns reversed
+            r0, c0 = rng.integers(0, R - h + 1), rng.integers(0, C - w + 1)
+            return b.view(bid, r0 * C + c0 + w - 1, (h, w), (C, -1))
+        if kind == 2 and h <= R and w <= C:  # rows reversed
+            r0, c0 = rng.integers(0, R - h + 1), rng.integers(0, C - w + 1)
+            return b.view(bid, (r0 + h - 1) * C + c0, (h, w), (-C, 1))
+        if kind == 3 and h <= C and w <= R:  # transposed: (i, j) -> base[r0 + j, c0 + i]
+            r0, c0 = rng.integers(0, R - w + 1), rng.integers(0, C - h + 1)
+            return b.view(bid, r0 * C + c0, (h, w), (1, C))
+        if kind == 4 and 2 * (h - 1) < R and w <= C:  # every other row
+            r0, c0 = rng.integers(0, R - 2 * (h - 1)), rng.integers(0, C - w + 1)
+            return b.view(bid, r0 * C + c0, (h, w), (2 * C, 1))
+        if kind == 5 and w <= C:  # one row, broadcast down
+            r0, c0 = rng.integers(0, R), rng.integers(0, C - w + 1)
+            return b.view(bid, r0 * C + c0, (h, w), (0, 1))
+    raise AssertionError("no view fits")
+
+
+def random_program(seed: int):
+    rng = np.random.default_rng(1000 + seed)
+    b = ProgramBuilder(f"fuzz{seed}")
+    n = R * C
+    F = [b.base("float64", (R, C), rng.standard_normal(n) * np.exp2(rng.integers(-3, 4, n))) for _ in range(3)]
+    I = [b.base("int64", (R, C), rng.integers(-50, 50, n)) for _ in range(2)]
+    B = b.base("bool", (R, C), rng.random(n) < 0.5)
+    red = b.base("float64", (64,), np.zeros(64))
+    redi = b.base("int64", (64,), np.zeros(64, np.int64))
+
+    def fv(h, w, bc=True):
+        return _view(b, rng, F[rng.integers(0, 3)], h, w, bc)
+
+    def iv(h, w, bc=True):
+        return _view(b, rng, I[rng.integers(0, 2)], h, w, bc)
+
+    def red_out(bid, m):
+        return b.view(bid, int(rng.integers(0, 64 - m + 1)), (m,), (1,))
+
+    for _ in range(int(rng.integers(8, 21))):
+        h, w = SHAPES[rng.integers(0, len(SHAPES))]
+        k = int(rng.integers(0, 10))
+        if k <= 2:  # float binary
+            op = ["ADD", "SUBTRACT", "MULTIPLY", "DIVIDE", "MAXIMUM", "MINIMUM"][rng.integers(0, 6)]
+            y = Const(float(np.round(rng.standard_normal(), 3))) if rng.random() < 0.25 else fv(h, w)
+            b.emit(op, fv(h, w, False), fv(h, w), y)
+        elif k == 3:  # float unary
+            op = ["NEGATIVE", "ABSOLUTE", "COPY"][rng.integers(0, 3)]
+            b.emit(op, fv(h, w, False), fv(h, w))
+        elif k == 4:  # square root of a magnitude, in place
+            o = fv(h, w, False)
+            b.emit("ABSOLUTE", o, fv(h, w))
+            b.emit("SQRT", o, o)
+        elif k == 5:  # int64
+            op = ["ADD", "SUBTRACT", "MAXIMUM", "MINIMUM"][rng.integers(0, 4)]
+            b.emit(op, iv(h, w, False), iv(h, w), iv(h, w) if rng.random() < 0.7 else Const(int(rng.integers(-9, 9))))
+        elif k == 6:  # compare, then select
+            cmpop = ["LESS", "GREATER", "LESS_EQUAL", "EQUAL"][rng.integers(0, 4)]
+            m = _view(b, rng, B, h, w, False)
+            b.emit(cmpop, m, fv(h, w), fv(h, w))
+            b.emit("SELECT", fv(h, w, False), _view(b, rng, B, h, w, True), fv(h, w), fv(h, w))
+        elif k == 7:  # casts of small integers both ways
+            b.emit("CAST", fv(h, w, False), iv(h, w))
+            if rng.random() < 0.5:
+                b.emit("CAST", iv(h, w, False), _view(b, rng, B, h, w, True))
+        elif k == 8:  # min/max/argmin/argmax reductions (sometimes a MIN then ARGMIN pair)
+            ax = int(rng.integers(0, 2))
+            m = (h, w)[1 - ax]
+            x = fv(h, w)
+            op = ["MIN_REDUCE", "MAX_REDUCE"][rng.integers(0, 2)]
+            b.emit(op, red_out(red, m), x, axis=ax)
+            if rng.random() < 0.6:
+                b.emit("ARGMIN_REDUCE" if op == "MIN_REDUCE" else "ARGMAX_REDUCE", red_out(redi, m), x, axis=ax)
+        else:  # int64 sums (exact)
+            ax = int(rng.integers(0, 2))
+            b.emit("ADD_REDUCE", red_out(redi, (h, w)[1 - ax]), iv(h, w), axis=ax)
+    outs = F + I + [B, red, redi]
+    p = b.build(outs)
+
+    def check(got, want):
+        for bid in outs:
+            if bid == red:
+                # MIN/MAX of tied signed zeros may return either zero (see
+                # the readings of the paper): values compared, NaN as NaN
+                g, wv = np.asarray(got[bid]), np.asarray(want[bid])
+                same = (g == wv) | (np.isnan(g) & np.isnan(wv))
+                assert np.all(same), f"{p.name} reductions: got {g[~same][:4]} want {wv[~same][:4]}"
+            else:
+                assert_exact(got[bid], want[bid], f"{p.name} base {bid}")
+    return Case(p.name, p, check)
+
+
+def fuzz_cases(seeds):
+    return [random_program(s) for s in seeds]

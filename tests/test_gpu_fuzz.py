@@ -1,0 +1,53 @@
+"""Random exact programs (``fuzz_programs``) on the GPU against the oracle,
+bit for bit: fused with packing, fused with graph replay (each program run
+twice, so the second run replays), staged and plain. The views alias, overlap
+in place and partially overlap their own inputs, so every fusion break, the
+staging of overlapping operands and the MIN/ARGMIN pairing are exercised on
+shapes the hand-written cases do not have."""
+import os
+
+import pytest
+
+from paper_1210_7774_b300 import build
+
+build.build()
+
+from paper_1210_7774_b300 import vbe as V  # noqa: E402
+from paper_1210_7774_b300.runner import Executor  # noqa: E402
+
+import oracle  # noqa: E402
+from fuzz_programs import fuzz_cases  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
+FUSED = V.VBE_FUSE | V.VBE_PACK | V.VBE_AUTOTUNE
+MODES = {"fused": (FUSED, 1, 0), "fused_graphs": (FUSED | V.VBE_GRAPHS, 2, 0), "fused_staged": (FUSED, 1, 64),
+         "plain": (0, 1, 0)}
+CASES = fuzz_cases(range(80))
+
+
+def _run(program, flags, repeat, staging):
+    old = os.environ.pop("VBE_STAGING", None)
+    if staging:
+        os.environ["VBE_STAGING"] = str(staging)  # read when the context is created
+    try:
+        ex = Executor(flags, cache_dir=CACHE)
+    finally:
+        os.environ.pop("VBE_STAGING", None)
+        if old is not None:
+            os.environ["VBE_STAGING"] = old
+    with ex:
+        L = ex.load(program)
+        for _ in range(repeat):
+            ex.run(L)
+        return {bid: ex.read(L, bid) for bid in program.outputs}
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("case", CASES, ids=[c.name for c in CASES])
+def test_fuzz_parity(case, mode):
+    flags, repeat, staging = MODES[mode]
+    # a second run starts from the state the first left: the oracle runs the
+    # instructions as many times over the same memory
+    mem = oracle.run(case.program, instrs=list(case.program.instrs) * repeat)
+    case.check(_run(case.program, flags, repeat, staging), {bid: mem[bid] for bid in case.program.outputs})
