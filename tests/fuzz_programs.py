@@ -14,6 +14,10 @@ int64 sums), so every result must equal the oracle's bit for bit; the one
 documented relaxation is the sign of a zero chosen by a MIN/MAX reduction
 from tied signed zeros. Reductions write bases that no later instruction
 reads, so no reordering tolerance is needed anywhere.
+
+A second generator (``random_stencil_program``) makes random stencil chains
+that the library turns into tile-fused groups, to be run in every group
+form.
 """
 from __future__ import annotations
 
@@ -125,3 +129,70 @@ def random_program(seed: int):
 
 def fuzz_cases(seeds):
     return [random_program(s) for s in seeds]
+
+
+def random_stencil_program(seed: int):
+    """A random stencil chain that the library fuses into one tile-fused
+    group: 2 to 4 runs, each computing a temporary from the previous one
+    (or the input) read at random row and column shifts of 0 to 3, with
+    random exact operations and constants; later runs may read the input
+    again at a shift; the last run writes a separate output or updates the
+    input in place (renamed while the group reads it around). Temporaries
+    are discarded, and the chain runs twice, so the second pass reads what
+    the first renamed. Sizes are random (23 to 70), float64 or float32."""
+    rng = np.random.default_rng(5000 + seed)
+    dt = ["float64", "float32"][rng.integers(0, 2)]
+    R0, C0 = (int(x) for x in rng.integers(23, 71, 2))
+    b = ProgramBuilder(f"fuzz_stencil{seed}_{dt}")
+    A = b.base(dt, (R0, C0), (rng.standard_normal(R0 * C0) * 2.0).astype(dt))
+    O = b.base(dt, (R0, C0), np.zeros(R0 * C0, dt))
+    nruns = int(rng.integers(2, 5))
+    in_place = bool(rng.random() < 0.5)
+    ops = ["ADD", "SUBTRACT", "MULTIPLY", "MAXIMUM", "MINIMUM", "DIVIDE"]
+    plan = []  # per run: (shift range, ops, extra reads)
+    for j in range(nruns):
+        plan.append(dict(mdr=int(rng.integers(0, 4)), mdc=int(rng.integers(0, 4)),
+                         op1=ops[rng.integers(0, 6)], op2=ops[rng.integers(0, 5)],
+                         s3=(rng.random(), rng.random()), k=float(np.round(rng.uniform(0.5, 2.0), 2)),
+                         second=int(rng.integers(0, 3)), reread=bool(rng.random() < 0.4),
+                         ao=(rng.random(), rng.random())))
+    for _ in range(2):
+        prev, (pr, pc) = A, (R0, C0)
+        temps = []
+        for j, q in enumerate(plan):
+            Rj, Cj = pr - q["mdr"], pc - q["mdc"]
+            last = j == nruns - 1
+            if last:
+                tgt = A if in_place else O
+                a0 = int(q["ao"][0] * (R0 - Rj + 1))
+                c0 = int(q["ao"][1] * (C0 - Cj + 1))
+                out = b.sub2d(tgt, a0, a0 + Rj, c0, c0 + Cj)
+            else:
+                t = b.base(dt, (Rj, Cj))
+                temps.append(t)
+                out = b.whole(t)
+            d3r = int(q["s3"][0] * (q["mdr"] + 1))
+            d3c = int(q["s3"][1] * (q["mdc"] + 1))
+            b.emit(q["op1"], out, b.sub2d(prev, 0, Rj, 0, Cj), b.sub2d(prev, q["mdr"], pr, q["mdc"], pc))
+            if q["second"] == 1:
+                b.emit(q["op2"], out, out, Const(q["k"]))
+            elif q["second"] == 2:
+                b.emit(q["op2"], out, out, b.sub2d(prev, d3r, d3r + Rj, d3c, d3c + Cj))
+            if q["reread"] and j > 0:  # the input again, shifted
+                b.emit("ADD", out, out, b.sub2d(A, d3r, d3r + Rj, d3c, d3c + Cj))
+            prev, (pr, pc) = (t if not last else None), (Rj, Cj)
+        b.discard(*temps)
+    p = b.build([A, O])
+    check = _exact_outputs(p)
+    return Case(p.name, p, check)
+
+
+def _exact_outputs(p):
+    def check(got, want):
+        for bid in p.outputs:
+            assert_exact(got[bid], want[bid], f"{p.name} base {bid}")
+    return check
+
+
+def stencil_cases(seeds):
+    return [random_stencil_program(s) for s in seeds]

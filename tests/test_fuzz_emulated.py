@@ -8,11 +8,15 @@ from paper_1210_7774_b300 import build
 
 build.build()
 
-from fuzz_programs import fuzz_cases  # noqa: E402
+import os  # noqa: E402
+
+from fuzz_programs import fuzz_cases, stencil_cases  # noqa: E402
 from parity_cases import oracle_outputs  # noqa: E402
 from test_emulated_kernels import EMU, MODES, emulate  # noqa: E402
 
 CASES = fuzz_cases(range(4))
+STENCILS = stencil_cases(range(3))
+FORMS = ["8x16", "s32x32", "t32x32", "r32"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,3 +32,15 @@ def _prebuild_fuzz_kernels():
 @pytest.mark.parametrize("case", CASES, ids=[c.name for c in CASES])
 def test_fuzz_emulated(case, mode):
     case.check(emulate(case.program, MODES[mode], (64, 1, 2)), oracle_outputs(case.program))
+
+
+@pytest.mark.parametrize("tile", FORMS)
+@pytest.mark.parametrize("case", STENCILS, ids=[c.name for c in STENCILS])
+def test_fuzz_stencil_emulated(case, tile):
+    """Random stencil chains in each group form (VBE_RECORD_TILE), emulated."""
+    os.environ["VBE_RECORD_TILE"] = tile
+    try:
+        got = emulate(case.program, MODES["fused"], (64, 1, 2))
+    finally:
+        os.environ.pop("VBE_RECORD_TILE")
+    case.check(got, oracle_outputs(case.program))

@@ -16,7 +16,7 @@ from paper_1210_7774_b300 import vbe as V  # noqa: E402
 from paper_1210_7774_b300.runner import Executor  # noqa: E402
 
 import oracle  # noqa: E402
-from fuzz_programs import fuzz_cases  # noqa: E402
+from fuzz_programs import fuzz_cases, stencil_cases  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
@@ -24,18 +24,24 @@ FUSED = V.VBE_FUSE | V.VBE_PACK | V.VBE_AUTOTUNE
 MODES = {"fused": (FUSED, 1, 0), "fused_graphs": (FUSED | V.VBE_GRAPHS, 2, 0), "fused_staged": (FUSED, 1, 64),
          "plain": (0, 1, 0)}
 CASES = fuzz_cases(range(80))
+STENCILS = stencil_cases(range(40))
+# group forms forced by VBE_TILE ("" leaves the choice to the tuner)
+FORMS = ["", "32x32", "s32x32", "t32x32", "r24", "r64"]
 
 
-def _run(program, flags, repeat, staging):
-    old = os.environ.pop("VBE_STAGING", None)
+def _run(program, flags, repeat, staging, tile=""):
+    saved = {k: os.environ.pop(k, None) for k in ("VBE_STAGING", "VBE_TILE")}
     if staging:
-        os.environ["VBE_STAGING"] = str(staging)  # read when the context is created
+        os.environ["VBE_STAGING"] = str(staging)  # both read when the context is created
+    if tile:
+        os.environ["VBE_TILE"] = tile
     try:
         ex = Executor(flags, cache_dir=CACHE)
     finally:
-        os.environ.pop("VBE_STAGING", None)
-        if old is not None:
-            os.environ["VBE_STAGING"] = old
+        for k, v in saved.items():
+            os.environ.pop(k, None)
+            if v is not None:
+                os.environ[k] = v
     with ex:
         L = ex.load(program)
         for _ in range(repeat):
@@ -51,3 +57,14 @@ def test_fuzz_parity(case, mode):
     # instructions as many times over the same memory
     mem = oracle.run(case.program, instrs=list(case.program.instrs) * repeat)
     case.check(_run(case.program, flags, repeat, staging), {bid: mem[bid] for bid in case.program.outputs})
+
+
+@pytest.mark.parametrize("tile", FORMS)
+@pytest.mark.parametrize("case", STENCILS, ids=[c.name for c in STENCILS])
+def test_fuzz_stencil_groups(case, tile):
+    """Random stencil chains (tile-fused into one group, the input renamed
+    when updated in place) in every group form, against the oracle bit for
+    bit; graph replay, so the second pass of each chain replays."""
+    got = _run(case.program, FUSED | V.VBE_GRAPHS, 1, 0, tile)
+    mem = oracle.run(case.program)
+    case.check(got, {bid: mem[bid] for bid in case.program.outputs})
