@@ -257,6 +257,7 @@ int vbe_init(const vbe_config* cfg, vbe_ctx** out) {
     cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   if (!c.host_only || c.record) vbe::init_error_word(&c);
+  vbe::load_tune(&c);
   *out = h.release();
   API_END
 }

@@ -86,6 +86,42 @@ std::vector<char> compile_cached(Ctx* c, const std::string& src, bool* compiled)
   return cubin;
 }
 
+// Tuning choices across processes: "<key> <block> <U> <maxreg> <bulk_chunk>
+// <grid_mult>" lines in <cache_dir>/tune_<device model>_<SMs>.txt, appended
+// as choices are made (later lines win), so a process that meets a kernel
+// signature and size class tuned before skips the timing and launches what
+// was chosen then. Keys hold no spaces (source hashes, size classes).
+void load_tune(Ctx* c) {
+  if (c->host_only || !c->cfg.cache_dir || !*c->cfg.cache_dir) return;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const std::string name(prop.name);
+  c->tune_file = std::string(c->cfg.cache_dir) + "/tune_" + hex64(hash64(name.data(), name.size(), 7)) + "_" +
+                 std::to_string(c->sm_count) + ".txt";
+  std::ifstream f(c->tune_file);
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream ls(line);
+    std::string key;
+    TuneChoice tc;
+    if (ls >> key >> tc.block >> tc.U >> tc.maxreg >> tc.bulk_chunk >> tc.grid_mult) c->tune[key] = tc;
+  }
+}
+
+void remember_tune(Ctx* c, const std::string& key, const TuneChoice& tc) {
+  c->tune[key] = tc;
+  if (c->tune_file.empty()) return;
+  static std::mutex mu;  // contexts of one process append one line at a time
+  std::lock_guard<std::mutex> lk(mu);
+  mkdir(c->cfg.cache_dir, 0755);
+  std::ofstream f(c->tune_file, std::ios::app);
+  f << key << ' ' << tc.block << ' ' << tc.U << ' ' << tc.maxreg << ' ' << tc.bulk_chunk << ' ' << tc.grid_mult
+    << '\n';
+}
+
 // the source a context compiles: with a wait limit set for tests, the
 // limit is defined ahead of the text (and so is part of the cache key)
 static bool with_wait_limit(const Ctx* c, const std::string& src, std::string* src2, std::string* key2) {
@@ -718,7 +754,7 @@ TuneChoice choose(Ctx* c, Exec* ex, Prepared& P, const RunPtrs& ptr, bool may_tu
   }
   if (tile && may_tune && (c->cfg.flags & VBE_AUTOTUNE) && P.canon.total >= (1 << 20)) {
     tc = autotune(c, ex, P, ptr);
-    c->tune[tk] = tc;
+    remember_tune(c, tk, tc);
   }
   return tc;
 }
@@ -1019,7 +1055,7 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
   tc.block = best.th;
   tc.U = best.tw;
   tc.grid_mult = best.form();
-  c->tune[tk] = tc;
+  remember_tune(c, tk, tc);
   return best;
 }
 
@@ -1101,7 +1137,7 @@ bool group_split(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const 
   for (auto& b : bufs) dev_free(c, ex, b.first, b.second);
   TuneChoice tc;
   tc.block = t_sep < t_group ? 1 : 0;
-  c->tune[sk] = tc;
+  remember_tune(c, sk, tc);
   return tc.block == 1;
 }
 

@@ -297,9 +297,11 @@ struct Kernel {
 
 // Long runs (many fused bytecodes) also get tile kernels compiled under a
 // per-thread register cap, as tuning candidates: more resident warps to hide
-// the latency of their long dependency chains, against some spilling.
+// the latency of their long dependency chains, against some spilling
+// (float64 Black-Scholes: 32 registers 1.766 ms against 1.795 ms at 40 and
+// above on one B300; 24 measured no better than 32).
 constexpr int kRegCapMinSteps = 24;
-constexpr int kRegCaps[2] = {40, 48};
+constexpr int kRegCaps[3] = {32, 40, 48};
 inline bool reg_cap_variants(const Run& r) { return (int)r.steps.size() >= kRegCapMinSteps; }
 
 struct TuneChoice {
@@ -369,6 +371,7 @@ struct Ctx {
   // caches
   std::unordered_map<std::string, std::shared_ptr<Kernel>> kernels;  // by source hash
   std::unordered_map<std::string, TuneChoice> tune;                  // by source hash
+  std::string tune_file;  // tuning choices kept across processes (in the cache directory), or empty
   std::unordered_map<uint64_t, CachedBatch> batches;
   // tickets: ticket t is recorded in ring slot t mod kTicketRing; a slot
   // reused by a later submit holds a later point of the same stream, so
@@ -416,6 +419,11 @@ void dev_free(Ctx* c, Exec* ex, void* p, int64_t bytes);
 void ensure_scratch(Ctx* c, Exec* ex, int64_t partials, int64_t counters);
 void release_exec(Ctx* c, Exec* ex);
 void init_error_word(Ctx* c);
+// Tuning choices persist in the cache directory, one file per device model:
+// load_tune reads it when a context is created, remember_tune records a new
+// choice in the context and appends it to the file.
+void load_tune(Ctx* c);
+void remember_tune(Ctx* c, const std::string& key, const TuneChoice& tc);
 void release_error_word(Ctx* c);
 bool take_error_word(Ctx* c);  // true (and cleared) when a staged kernel reported a failed wait
 void check_error_word(Ctx* c);  // fails with VBE_ERR_TIMEOUT when take_error_word is true
