@@ -221,6 +221,53 @@ def test_shallow_water_conserves_mass_and_mirror_symmetry():
     assert np.max(np.abs(U)) > 1e-3  # the droplet has moved
 
 
+def _sw_1d(h, m, steps, g=9.8, dt=0.1, dx=1.0):
+    """Two-step Lax-Wendroff for the 1-D shallow-water equations
+    h_t + (hu)_x = 0, (hu)_t + (hu^2/h + g h^2 / 2)_x = 0, state (h, m = hu),
+    reflective ends (h copied, m negated in the ghost cells)."""
+    h, m = list(h), list(m)
+    N = len(h)
+
+    def flux(hh, mm):
+        return (mm, mm * mm / hh + 0.5 * g * hh * hh)
+
+    for _ in range(steps):
+        h[0], m[0] = h[1], -m[1]
+        h[N - 1], m[N - 1] = h[N - 2], -m[N - 2]
+        half = []
+        for i in range(N - 1):
+            fa, fb = flux(h[i], m[i]), flux(h[i + 1], m[i + 1])
+            hh = (h[i] + h[i + 1]) / 2 - dt / (2 * dx) * (fb[0] - fa[0])
+            mm = (m[i] + m[i + 1]) / 2 - dt / (2 * dx) * (fb[1] - fa[1])
+            half.append(flux(hh, mm))
+        for i in range(1, N - 1):
+            h[i] -= dt / dx * (half[i][0] - half[i - 1][0])
+            m[i] -= dt / dx * (half[i][1] - half[i - 1][1])
+    return np.array(h), np.array(m)
+
+
+def test_shallow_water_y_uniform_state_follows_the_1d_scheme():
+    """A state uniform along axis 1 with V = 0 stays uniform along axis 1
+    with V = 0 (its y fluxes cancel exactly), and its interior follows the
+    1-D scheme along axis 0."""
+    N, steps = 20, 12
+    x = np.arange(N, dtype=np.float64)
+    h1 = 1.0 + 0.4 * np.exp(-((x - 8.3) ** 2) / 8.0)
+    m1 = 0.05 * np.sin(x / 3.0)
+    inp = {"H": np.repeat(h1[:, None], N, axis=1), "U": np.repeat(m1[:, None], N, axis=1), "V": np.zeros((N, N))}
+    p = shallow_water(N, steps, inputs=inp)
+    mem = oracle.run(p)
+    H = mem[p.meta["H"]].reshape(N, N)[:, 1:N - 1]
+    U = mem[p.meta["U"]].reshape(N, N)[:, 1:N - 1]
+    V = mem[p.meta["V"]].reshape(N, N)[1:N - 1, 1:N - 1]
+    assert np.all(V == 0.0)
+    assert np.all(H[1:N - 1] == H[1:N - 1, :1]) and np.all(U[1:N - 1] == U[1:N - 1, :1])
+    bh, bm = _sw_1d(h1, m1, steps)
+    assert np.max(np.abs(H[1:N - 1, 0] - bh[1:N - 1])) <= 1e-13
+    assert np.max(np.abs(U[1:N - 1, 0] - bm[1:N - 1])) <= 1e-13
+    assert np.max(np.abs(U[1:N - 1, 0] - m1[1:N - 1])) > 1e-3  # the state has evolved
+
+
 # ---------------------------------------------------------------- Monte-Carlo pi
 
 
