@@ -845,6 +845,18 @@ def serving_bench(args, V, local):
                      "breakdown_ms": {k: {"p50": float(np.percentile(pa[:, q], 50)),
                                           "p99": float(np.percentile(pa[:, q], 99))}
                                       for q, k in enumerate(("queued", "host_planning", "device_and_copies"))}}
+        # the same per request kind (Jacobi solves, Black-Scholes pricings)
+        by_kind = {}
+        for kind in ("jacobi", "blackscholes"):
+            sel = np.array([m[0] == kind for m in mix])
+            if sel.any():
+                by_kind[kind] = {"requests": int(sel.sum()),
+                                 "latency_ms": {"p50": float(np.percentile(lat[sel], 50)),
+                                                "p99": float(np.percentile(lat[sel], 99))},
+                                 **{k: {"p50": float(np.percentile(pa[sel, q], 50)),
+                                        "p99": float(np.percentile(pa[sel, q], 99))}
+                                    for q, k in enumerate(("queued", "host_planning", "device_and_copies"))}}
+        res[name]["by_kind"] = by_kind
     res["requests"] = n_req
     res["server"] = {"slots": 16, "workers": args.serve_workers, "mem_cap_bytes": 60 << 30, "clients": 64,
                      "rate": "0.7 x the fused capacity, for both paths",

@@ -69,11 +69,36 @@ bool live_after(const std::vector<RInstr>& prog, int64_t base, size_t idx) {
   return true;
 }
 
+LiveIndex::LiveIndex(const std::vector<RInstr>& prog) {
+  for (size_t j = 0; j < prog.size(); ++j) {
+    const RInstr& r = prog[j];
+    if (op_kind(r.op) == K_CONTROL) {
+      ev[r.out.base].push_back({(int64_t)j, r.op == VBE_OP_SYNC ? 1 : 2});
+      continue;
+    }
+    for (int k = 0; k < r.nin; ++k) {
+      if (k == r.const_slot) continue;
+      auto& e = ev[r.in[k].base];
+      if (e.empty() || e.back().first != (int64_t)j) e.push_back({(int64_t)j, 0});
+    }
+  }
+}
+
+bool LiveIndex::live_after(int64_t base, size_t idx) const {
+  auto it = ev.find(base);
+  if (it == ev.end()) return true;  // nothing after it: still live after the batch
+  const auto& e = it->second;
+  auto nx = std::upper_bound(e.begin(), e.end(), std::make_pair((int64_t)idx, 3));
+  if (nx == e.end()) return true;
+  return nx->second != 2;  // a read or a SYNC: live; a DISCARD or FREE: dead
+}
+
 namespace {
 
 struct Builder {
   Ctx* c;
   std::vector<RInstr>& prog;
+  const LiveIndex& live;
   bool fuse;
   Plan plan;
   bool open = false;
@@ -89,7 +114,7 @@ struct Builder {
   std::vector<HostAction> pending;
   int last_instr = -1;
 
-  Builder(Ctx* c_, std::vector<RInstr>& p, bool f) : c(c_), prog(p), fuse(f) {}
+  Builder(Ctx* c_, std::vector<RInstr>& p, const LiveIndex& l, bool f) : c(c_), prog(p), live(l), fuse(f) {}
 
   int new_value(int dt) {
     cur.value_dtype.push_back(dt);
@@ -189,7 +214,7 @@ struct Builder {
       for (size_t j = i + 1; j < written.size(); ++j)
         if (written[j].first.identical(written[i].first)) superseded = true;
       if (superseded) continue;
-      if (!fuse || live_after(prog, written[i].first.base, (size_t)last_instr)) keep.push_back(written[i]);
+      if (!fuse || live.live_after(written[i].first.base, (size_t)last_instr)) keep.push_back(written[i]);
     }
     for (auto& w : keep) {
       cur.stores.push_back(slot_of(w.first, c->bases[w.first.base].dtype));
@@ -278,7 +303,7 @@ struct Builder {
     if (!cur.has_red || r.op != cur.red_op || cur.has_red2) return false;
     if (r.op == VBE_OP_ARGMIN_REDUCE || r.op == VBE_OP_ARGMAX_REDUCE) return false;  // indices do not compose
     if (!r.in[0].identical(red_view)) return false;
-    if (live_after(prog, red_view.base, idx)) return false;
+    if (live.live_after(red_view.base, idx)) return false;
     // the merged output must not touch anything else in the run
     for (auto& l : load_views)
       if (may_overlap(r.out, l)) return false;
@@ -458,10 +483,11 @@ Plan make_plan(Ctx* c, std::vector<RInstr>& prog, bool fuse, bool pack) {
   Plan pre;
   std::vector<RInstr> staged = stage_partial_overlaps(c, prog, &pre);
   prog.swap(staged);
-  Builder b(c, prog, fuse);
+  const LiveIndex live(prog);
+  Builder b(c, prog, live, fuse);
   b.plan.staging = pre.staging;
   b.run_all();
-  if (fuse && !(c->cfg.flags & VBE_NO_TILE_FUSION)) form_groups(c, prog, &b.plan);
+  if (fuse && !(c->cfg.flags & VBE_NO_TILE_FUSION)) form_groups(c, prog, live, &b.plan);
   return std::move(b.plan);
 }
 

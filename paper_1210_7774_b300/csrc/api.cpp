@@ -1,4 +1,5 @@
 // extern "C" entry points of libvbe (declared in include/vbe.h).
+#include <algorithm>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -285,8 +286,7 @@ int vbe_finalize(vbe_ctx* ctx) {
     cudaStreamSynchronize(c.exec.stream);
     vbe::release_exec(&c, &c.exec);
     vbe::release_error_word(&c);
-    for (auto& kv : c.kernels)
-      if (kv.second->lib) cudaLibraryUnload(kv.second->lib);
+    c.kernels.clear();  // modules no other context holds are unloaded
     if (c.own_stream) cudaStreamDestroy(c.exec.stream);
   }
   delete ctx;
@@ -385,7 +385,7 @@ int vbe_view_create(vbe_ctx* ctx, vbe_base base, int64_t offset, int32_t ndim, c
     vbe::fail(VBE_ERR_OUT_OF_BOUNDS, "view reaches [" + std::to_string(v.lo) + ", " + std::to_string(v.hi) +
                                          "] outside a base of " + std::to_string(it->second.nelem) + " elements");
   int64_t h = ctx->c.next_handle++;
-  ctx->c.views[h] = v;
+  vbe::add_view(&ctx->c, h, v);
   *out = h;
   API_END
 }
@@ -393,7 +393,14 @@ int vbe_view_create(vbe_ctx* ctx, vbe_base base, int64_t offset, int32_t ndim, c
 int vbe_view_destroy(vbe_ctx* ctx, vbe_view view) {
   API_BEGIN
   if (!ctx) vbe::fail(VBE_ERR_INVALID, "null context");
-  if (!ctx->c.views.erase(view)) vbe::fail(VBE_ERR_INVALID, "unknown view");
+  auto it = ctx->c.views.find(view);
+  if (it == ctx->c.views.end()) vbe::fail(VBE_ERR_INVALID, "unknown view");
+  auto bt = ctx->c.bases.find(it->second.base);
+  if (bt != ctx->c.bases.end()) {
+    auto& vs = bt->second.views;
+    vs.erase(std::remove(vs.begin(), vs.end(), view), vs.end());
+  }
+  ctx->c.views.erase(it);
   ctx->c.epoch++;
   API_END
 }
@@ -556,10 +563,7 @@ int vbe_free(vbe_ctx* ctx, vbe_base base) {
   if (it == c.bases.end()) vbe::fail(VBE_ERR_INVALID, "unknown base");
   if (it->second.dptr && !it->second.external) vbe::dev_free(&c, &c.exec, it->second.dptr, it->second.bytes());
   if (it->second.shadow) vbe::dev_free(&c, &c.exec, it->second.shadow, it->second.bytes());
-  for (auto v = c.views.begin(); v != c.views.end();) {
-    if (v->second.base == base) v = c.views.erase(v);
-    else ++v;
-  }
+  vbe::erase_views_of(&c, it->second);
   c.bases.erase(it);
   c.epoch++;
   API_END

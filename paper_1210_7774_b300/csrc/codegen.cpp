@@ -1450,31 +1450,29 @@ static std::string generate_source_uncached(const Run& r, const Canon& c, std::s
 
 // Generated sources are memoised by signature: a serving loop or a long
 // batch plans many runs of a few signatures.
-std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix, std::string* key_out) {
-  struct Entry {
-    std::string src, prefix, key;
-  };
+std::shared_ptr<const RunSource> run_source(const Run& r, const Canon& c) {
   static std::mutex mu;
-  static std::unordered_map<std::string, Entry> memo;
+  static std::unordered_map<std::string, std::shared_ptr<const RunSource>> memo;
   const std::string key = signature(r, c);
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = memo.find(key);
-    if (it != memo.end()) {
-      if (entry_prefix) *entry_prefix = it->second.prefix;
-      if (key_out) *key_out = it->second.key;
-      return it->second.src;
-    }
+    if (it != memo.end()) return it->second;
   }
-  Entry e;
-  e.src = generate_source_uncached(r, c, &e.prefix);
-  e.key = src_key(e.src);
-  if (entry_prefix) *entry_prefix = e.prefix;
-  if (key_out) *key_out = e.key;
+  auto e = std::make_shared<RunSource>();
+  e->src = generate_source_uncached(r, c, &e->prefix);
+  e->key = src_key(e->src);
   std::lock_guard<std::mutex> lk(mu);
   if (memo.size() > 4096) memo.clear();
   memo[key] = e;
-  return e.src;
+  return e;
+}
+
+std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix, std::string* key_out) {
+  auto e = run_source(r, c);
+  if (entry_prefix) *entry_prefix = e->prefix;
+  if (key_out) *key_out = e->key;
+  return e->src;
 }
 
 static std::string generate_source_uncached(const Run& r, const Canon& c, std::string* entry_prefix) {
@@ -2518,35 +2516,32 @@ static std::string group_key(const Group& g) {
 static std::string generate_group_source_uncached(const Group& g, std::string* entry_prefix,
                                                   std::vector<TileShape>* shapes_out);
 
-std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes_out,
-                                  std::string* key_out) {
-  struct Entry {
-    std::string src, prefix, key;
-    std::vector<TileShape> shapes;
-  };
+std::shared_ptr<const GroupSource> group_source(const Group& g) {
+  if (g.source) return g.source;
   static std::mutex mu;
-  static std::unordered_map<std::string, Entry> memo;
+  static std::unordered_map<std::string, std::shared_ptr<const GroupSource>> memo;
   const std::string key = group_key(g);
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = memo.find(key);
-    if (it != memo.end()) {
-      if (entry_prefix) *entry_prefix = it->second.prefix;
-      if (shapes_out) *shapes_out = it->second.shapes;
-      if (key_out) *key_out = it->second.key;
-      return it->second.src;
-    }
+    if (it != memo.end()) return g.source = it->second;
   }
-  Entry e;
-  e.src = generate_group_source_uncached(g, &e.prefix, &e.shapes);
-  e.key = src_key(e.src);
-  if (entry_prefix) *entry_prefix = e.prefix;
-  if (shapes_out) *shapes_out = e.shapes;
-  if (key_out) *key_out = e.key;
+  auto e = std::make_shared<GroupSource>();
+  e->src = generate_group_source_uncached(g, &e->prefix, &e->shapes);
+  e->key = src_key(e->src);
   std::lock_guard<std::mutex> lk(mu);
   if (memo.size() > 1024) memo.clear();
   memo[key] = e;
-  return e.src;
+  return g.source = e;
+}
+
+std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes_out,
+                                  std::string* key_out) {
+  auto e = group_source(g);
+  if (entry_prefix) *entry_prefix = e->prefix;
+  if (shapes_out) *shapes_out = e->shapes;
+  if (key_out) *key_out = e->key;
+  return e->src;
 }
 
 static std::string generate_group_source_uncached(const Group& g, std::string* entry_prefix,

@@ -75,7 +75,7 @@ bool shift_of(const Slot& st, const Slot& ld, int64_t* dr, int64_t* dc) {
 
 bool same_slot(const Slot& a, const Slot& b) { return a.base == b.base && a.offset == b.offset && a.st == b.st; }
 
-std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const Plan& plan,
+std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const LiveIndex& live, const Plan& plan,
                                  const std::vector<size_t>& items) {
   const int m = (int)items.size();
   if (m < 2 || m > kMaxGroupRuns) return nullptr;
@@ -105,7 +105,7 @@ std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const 
       int64_t b = g->runs[k].stores[s].base;
       if (prod.count(b)) return nullptr;
       prod[b] = {k, s};
-      if (k < anchor && live_after(prog, b, (size_t)last)) return nullptr;
+      if (k < anchor && live.live_after(b, (size_t)last)) return nullptr;
     }
   // loads served by earlier runs of the group
   g->lds.resize(m);
@@ -202,7 +202,7 @@ std::shared_ptr<Group> try_group(Ctx* c, const std::vector<RInstr>& prog, const 
 
 }  // namespace
 
-void form_groups(Ctx* c, const std::vector<RInstr>& prog, Plan* plan) {
+void form_groups(Ctx* c, const std::vector<RInstr>& prog, const LiveIndex& live, Plan* plan) {
   std::vector<PlanItem>& items = plan->items;
   std::vector<PlanItem> rev;  // output, back to front
   int64_t j = (int64_t)items.size() - 1;
@@ -221,7 +221,7 @@ void form_groups(Ctx* c, const std::vector<RInstr>& prog, Plan* plan) {
       if (p < 0 || items[p].kind != 0) break;
       std::vector<size_t> cand{(size_t)p};
       cand.insert(cand.end(), win.begin(), win.end());
-      auto g = try_group(c, prog, *plan, cand);
+      auto g = try_group(c, prog, live, *plan, cand);
       if (!g) break;
       best = g;
       win = cand;

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <fstream>
 #include <set>
+#include <unordered_set>
 #include <sstream>
 
 #include "vbe_core.h"
@@ -91,31 +92,59 @@ std::vector<char> compile_cached(Ctx* c, const std::string& src, bool* compiled)
 // as choices are made (later lines win), so a process that meets a kernel
 // signature and size class tuned before skips the timing and launches what
 // was chosen then. Keys hold no spaces (source hashes, size classes).
+// Contexts of one process share their choices too (a serving process runs
+// one context per scheduler thread): a choice made by one is found by the
+// others, keyed by the device model and SM count.
+namespace {
+std::mutex g_tune_mu;
+std::unordered_map<std::string, TuneChoice> g_tune;
+}  // namespace
+
 void load_tune(Ctx* c) {
-  if (c->host_only || !c->cfg.cache_dir || !*c->cfg.cache_dir) return;
+  if (c->host_only) return;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
     cudaGetLastError();
     return;
   }
   const std::string name(prop.name);
-  c->tune_file = std::string(c->cfg.cache_dir) + "/tune_" + hex64(hash64(name.data(), name.size(), 7)) + "_" +
-                 std::to_string(c->sm_count) + ".txt";
+  c->tune_device = hex64(hash64(name.data(), name.size(), 7)) + "_" + std::to_string(c->sm_count);
+  if (!c->cfg.cache_dir || !*c->cfg.cache_dir) return;
+  c->tune_file = std::string(c->cfg.cache_dir) + "/tune_" + c->tune_device + ".txt";
   std::ifstream f(c->tune_file);
   std::string line;
   while (std::getline(f, line)) {
     std::istringstream ls(line);
     std::string key;
     TuneChoice tc;
-    if (ls >> key >> tc.block >> tc.U >> tc.maxreg >> tc.bulk_chunk >> tc.grid_mult) c->tune[key] = tc;
+    if (ls >> key >> tc.block >> tc.U >> tc.maxreg >> tc.bulk_chunk >> tc.grid_mult) {
+      c->tune[key] = tc;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune.emplace(c->tune_device + ":" + key, tc);
+    }
   }
+}
+
+bool recall_tune(Ctx* c, const std::string& key, TuneChoice* out) {
+  auto it = c->tune.find(key);
+  if (it != c->tune.end()) {
+    *out = it->second;
+    return true;
+  }
+  if (c->tune_device.empty()) return false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto g = g_tune.find(c->tune_device + ":" + key);
+  if (g == g_tune.end()) return false;
+  c->tune[key] = *out = g->second;
+  return true;
 }
 
 void remember_tune(Ctx* c, const std::string& key, const TuneChoice& tc) {
   c->tune[key] = tc;
+  if (c->tune_device.empty()) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);  // one line at a time from the contexts of this process
+  g_tune[c->tune_device + ":" + key] = tc;
   if (c->tune_file.empty()) return;
-  static std::mutex mu;  // contexts of one process append one line at a time
-  std::lock_guard<std::mutex> lk(mu);
   mkdir(c->cfg.cache_dir, 0755);
   std::ofstream f(c->tune_file, std::ios::app);
   f << key << ' ' << tc.block << ' ' << tc.U << ' ' << tc.maxreg << ' ' << tc.bulk_chunk << ' ' << tc.grid_mult
@@ -131,6 +160,34 @@ static bool with_wait_limit(const Ctx* c, const std::string& src, std::string* s
   return true;
 }
 
+Kernel::~Kernel() {
+  if (lib) cudaLibraryUnload(lib);
+}
+
+namespace {
+std::mutex g_lib_mu;
+std::unordered_map<std::string, std::weak_ptr<Kernel>> g_libs;  // by source key
+
+// the module of this source key if some context of the process holds it
+std::shared_ptr<Kernel> find_library(const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_lib_mu);
+  auto it = g_libs.find(key);
+  return it == g_libs.end() ? nullptr : it->second.lock();
+}
+
+// load a compiled module, unless another thread loaded it meanwhile
+std::shared_ptr<Kernel> load_library(const std::string& key, const std::vector<char>& cubin) {
+  std::lock_guard<std::mutex> lk(g_lib_mu);
+  auto& slot = g_libs[key];
+  if (auto k = slot.lock()) return k;
+  auto k = std::make_shared<Kernel>();
+  cuda_check(cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0),
+             "cudaLibraryLoadData");
+  slot = k;
+  return k;
+}
+}  // namespace
+
 // Compile, in parallel threads, every source not loaded yet (first sight
 // of a batch), then load the modules.
 void precompile(Ctx* c, const std::vector<std::string>& srcs, const std::vector<std::string>* keys) {
@@ -141,6 +198,12 @@ void precompile(Ctx* c, const std::vector<std::string>& srcs, const std::vector<
     const bool adj = with_wait_limit(c, srcs[i], &src2, &key2);
     const std::string k = adj ? key2 : (keys ? (*keys)[i] : src_key(srcs[i]));
     if (c->kernels.count(k) || seen.count(k)) continue;
+    if (!c->host_only) {
+      if (auto shared = find_library(k)) {  // another context of the process loaded it
+        c->kernels[k] = shared;
+        continue;
+      }
+    }
     seen.insert(k);
     todo.push_back(adj ? src2 : srcs[i]);
     todo_keys.push_back(k);
@@ -176,10 +239,7 @@ void precompile(Ctx* c, const std::vector<std::string>& srcs, const std::vector<
   for (size_t i = 0; i < todo.size(); ++i) {
     if (!errs[i].empty()) fail(VBE_ERR_COMPILE, errs[i]);
     if (c->host_only) continue;
-    auto k = std::make_shared<Kernel>();
-    cuda_check(cudaLibraryLoadData(&k->lib, bins[i].data(), nullptr, nullptr, 0, nullptr, nullptr, 0),
-               "cudaLibraryLoadData");
-    c->kernels[todo_keys[i]] = k;
+    c->kernels[todo_keys[i]] = load_library(todo_keys[i], bins[i]);
   }
 }
 
@@ -199,17 +259,15 @@ std::shared_ptr<Kernel> get_kernel(Ctx* c, const std::string& src_in, const std:
     c->kernels[key] = k;
     return k;
   }
-  std::vector<char> cubin = compile_cached(c, src, nullptr);
-  auto k = std::make_shared<Kernel>();
   if (c->host_only) fail(VBE_ERR_NO_DEVICE, "host-only context cannot load kernels");
-  cuda_check(cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0),
-             "cudaLibraryLoadData");
-  c->kernels[key] = k;
-  return k;
+  if (auto k = find_library(key)) return c->kernels[key] = k;
+  std::vector<char> cubin = compile_cached(c, src, nullptr);
+  return c->kernels[key] = load_library(key, cubin);
 }
 
 static cudaKernel_t kernel_fn(Kernel* k, const std::string& name) {
   if (!k->lib) return (cudaKernel_t)(uintptr_t)1;  // recording: never launched
+  std::lock_guard<std::mutex> lk(k->mu);
   auto it = k->fn.find(name);
   if (it != k->fn.end()) return it->second;
   cudaKernel_t f;
@@ -564,10 +622,8 @@ int64_t tiles_of(const Canon& cn, int block, int U) {
 struct Prepared {
   Run* run = nullptr;
   Canon canon;
-  std::string src;
+  std::shared_ptr<const RunSource> rs;  // source, key, kernel name prefix
   std::shared_ptr<Kernel> kern;
-  std::string key;
-  std::string prefix;  // kernel name prefix
 };
 
 std::string tune_key(const std::string& key, const Canon& cn) {
@@ -589,8 +645,8 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
   if (tc.bulk_chunk > 0 && bulk_ok(r, cn, ptr, tc.bulk_chunk)) {
     // inputs staged through shared memory: two stages of CH elements per unit-stride input
     const int64_t CH = tc.bulk_chunk;
-    L.entry = P.prefix + "_bulk";
-    L.key = P.key;
+    L.entry = P.rs->prefix + "_bulk";
+    L.key = P.rs->key;
     L.fn = kernel_fn(P.kern.get(), L.entry);
     L.block = tc.block;
     L.smem = (unsigned)(2 * CH * bulk_bytes_per_elem(r, cn) + 64);
@@ -606,8 +662,8 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
     fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, (uintptr_t)ex->scratch.partials, (uintptr_t)ex->scratch.counters,
                tc.block, 1, &a, CH, (uintptr_t)c->err_word_dev);
   } else if (cn.spec.mode == Mode::ELEM || cn.spec.mode == Mode::FULL) {
-    L.entry = P.prefix + "_u" + std::to_string(tc.U) + (tc.maxreg ? "r" + std::to_string(tc.maxreg) : std::string());
-    L.key = P.key;
+    L.entry = P.rs->prefix + "_u" + std::to_string(tc.U) + (tc.maxreg ? "r" + std::to_string(tc.maxreg) : std::string());
+    L.key = P.rs->key;
     L.fn = kernel_fn(P.kern.get(), L.entry);
     L.block = tc.block;
     int64_t tiles = tiles_of(cn, tc.block, tc.U);
@@ -619,8 +675,8 @@ Launch build_single(Ctx* c, Exec* ex, Prepared& P, const TuneChoice& tc, const R
     fill_words(r, cn, ptr.lp, ptr.sp, ptr.rp, (uintptr_t)ex->scratch.partials, (uintptr_t)ex->scratch.counters,
                tc.block, tc.U, &a, 0, (uintptr_t)c->err_word_dev);
   } else {
-    L.entry = P.prefix + "_axis";
-    L.key = P.key;
+    L.entry = P.rs->prefix + "_axis";
+    L.key = P.rs->key;
     L.fn = kernel_fn(P.kern.get(), L.entry);
     int64_t nout = 1, nred = 1;
     for (int k = 0; k < cn.spec.ndk; ++k) nout *= cn.dims[k];
@@ -741,9 +797,9 @@ TuneChoice choose(Ctx* c, Exec* ex, Prepared& P, const RunPtrs& ptr, bool may_tu
     tc.bulk_chunk = c->force_bulk;
     return tc;
   }
-  std::string tk = tune_key(P.key, P.canon);
-  auto it = c->tune.find(tk);
-  if (it != c->tune.end()) return it->second;
+  std::string tk = tune_key(P.rs->key, P.canon);
+  TuneChoice known;
+  if (recall_tune(c, tk, &known)) return known;
   TuneChoice tc;
   tc.block = 256;
   tc.U = P.canon.total >= (1 << 16) ? 2 : 1;
@@ -801,9 +857,8 @@ bool independent(const Run& a, const Run& b, Ctx* c) {
 
 struct GroupPrepared {
   Group* g = nullptr;
-  std::string src, prefix, key;
+  std::shared_ptr<const GroupSource> gs;  // source, entry prefix, key, tile shapes
   std::shared_ptr<Kernel> kern;
-  std::vector<TileShape> shapes;
 };
 
 struct GroupPtrs {
@@ -928,8 +983,8 @@ bool tma_pointers_ok(const Group& g, const TileShape& ts, const GroupPtrs& ptr) 
 
 Launch build_group(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const GroupPtrs& ptr) {
   Launch L;
-  L.entry = G.prefix + ts.suffix();
-  L.key = G.key;
+  L.entry = G.gs->prefix + ts.suffix();
+  L.key = G.gs->key;
   L.fn = kernel_fn(G.kern.get(), L.entry);
   L.block = (unsigned)(ts.block + (ts.tma ? 32 : 0));  // the tensor-copy form adds a producer warp
   L.smem = (unsigned)ts.smem;
@@ -974,33 +1029,34 @@ std::string group_tune_key(const GroupPrepared& G) {
     n >>= 1;
     ++lg;
   }
-  return G.key + ":" + std::to_string(lg);
+  return G.gs->key + ":" + std::to_string(lg);
 }
 
 // the tile shape: fixed in record mode (VBE_RECORD_TILE=THxTW), else timed
 // per signature and size class with the anchor's in-place targets
 // redirected to scratch buffers
 TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real, bool may_tune) {
-  if (G.shapes.empty()) fail(VBE_ERR_INVALID, "tile-fused group without a tile shape");
+  const std::vector<TileShape>& shapes = G.gs->shapes;
+  if (shapes.empty()) fail(VBE_ERR_INVALID, "tile-fused group without a tile shape");
   // a fixed shape: "THxTW", "sTHxTW" for the staged form, "tTHxTW" for the
   // tensor-copy form, "rR" for the row-sweep form with strips of R rows
   // (VBE_RECORD_TILE when recording, else VBE_TILE)
   const char* e = c->record ? getenv("VBE_RECORD_TILE") : (c->force_tile.empty() ? nullptr : c->force_tile.c_str());
   if (e)
-    for (auto& ts : G.shapes) {
+    for (auto& ts : shapes) {
       const std::string name = ts.letter() + std::to_string(ts.th) + (ts.sweep ? "" : "x" + std::to_string(ts.tw));
       if (name == e && (c->record || !ts.tma || tma_pointers_ok(*G.g, ts, real))) return ts;
     }
-  if (c->record) return G.shapes[0];
+  if (c->record) return shapes[0];
   std::string tk = group_tune_key(G);
-  auto it = c->tune.find(tk);
-  if (it != c->tune.end())
-    for (auto& ts : G.shapes)
-      if (ts.th == it->second.block && ts.tw == it->second.U && ts.form() == it->second.grid_mult &&
+  TuneChoice known;
+  if (recall_tune(c, tk, &known))
+    for (auto& ts : shapes)
+      if (ts.th == known.block && ts.tw == known.U && ts.form() == known.grid_mult &&
           (!ts.tma || tma_pointers_ok(*G.g, ts, real)))
         return ts;
-  TileShape def = G.shapes[0];
-  for (auto& ts : G.shapes)
+  TileShape def = shapes[0];
+  for (auto& ts : shapes)
     if (!ts.staged && !ts.tma && !ts.sweep && ts.th * ts.tw <= 1024 && ts.th * ts.tw >= def.th * def.tw) def = ts;
   const Group& g = *G.g;
   const int anchor = (int)g.runs.size() - 1;
@@ -1030,7 +1086,7 @@ TileShape choose_group(Ctx* c, Exec* ex, GroupPrepared& G, const GroupPtrs& real
   }
   TileShape best = def;
   float best_ms = 1e30f;
-  for (const TileShape& ts : G.shapes) {
+  for (const TileShape& ts : shapes) {
     if (ts.tma && !tma_pointers_ok(g, ts, ptr)) continue;
     Launch L = build_group(c, ex, G, ts, ptr);
     issue(c, ex, L, false);  // warm
@@ -1068,8 +1124,8 @@ bool group_split(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const 
   if (c->record) return getenv("VBE_RECORD_SPLIT") != nullptr;
   if (!c->force_tile.empty()) return false;  // a fixed tile shape runs the group kernel
   const std::string sk = group_tune_key(G) + ":split";
-  auto it = c->tune.find(sk);
-  if (it != c->tune.end()) return it->second.block == 1;
+  TuneChoice known;
+  if (recall_tune(c, sk, &known)) return known.block == 1;
   Group& g = *G.g;
   const int anchor = (int)g.runs.size() - 1;
   if (!(may_tune && (c->cfg.flags & VBE_AUTOTUNE) && g.rows(anchor) * g.cols(anchor) >= (1 << 16))) return false;
@@ -1107,8 +1163,8 @@ bool group_split(Ctx* c, Exec* ex, GroupPrepared& G, const TileShape& ts, const 
     if (k == anchor)
       for (size_t s = 0; s < r.stores.size(); ++s) rp.sp[s] = scratch_for(r.stores[s], r.shape);
     P.canon = canonicalize(r, true, rp.lp, rp.sp, rp.rp);
-    P.src = generate_source(r, P.canon, &P.prefix, &P.key);
-    P.kern = get_kernel(c, P.src, &P.key);
+    P.rs = run_source(r, P.canon);
+    P.kern = get_kernel(c, P.rs->src, &P.rs->key);
     TuneChoice tc = choose(c, ex, P, rp, true);
     sep.push_back(build_single(c, ex, P, tc, rp));
   }
@@ -1163,6 +1219,21 @@ std::vector<std::pair<int64_t, uintptr_t>> fingerprint(Ctx* c, const std::vector
   return f;
 }
 
+}  // namespace
+
+void add_view(Ctx* c, int64_t handle, const ViewDesc& v) {
+  c->views[handle] = v;
+  auto it = c->bases.find(v.base);
+  if (it != c->bases.end()) it->second.views.push_back(handle);
+}
+
+void erase_views_of(Ctx* c, BaseRec& br) {
+  for (int64_t h : br.views) c->views.erase(h);
+  br.views.clear();
+}
+
+namespace {
+
 void do_action(Ctx* c, Exec* ex, const HostAction& a) {
   auto it = c->bases.find(a.base);
   if (it == c->bases.end()) return;
@@ -1180,10 +1251,7 @@ void do_action(Ctx* c, Exec* ex, const HostAction& a) {
   if (a.kind == 0) {  // FREE
     if (it->second.dptr && !it->second.external) dev_free(c, ex, it->second.dptr, it->second.bytes());
     if (it->second.shadow) dev_free(c, ex, it->second.shadow, it->second.bytes());
-    for (auto v = c->views.begin(); v != c->views.end();) {
-      if (v->second.base == a.base) v = c->views.erase(v);
-      else ++v;
-    }
+    erase_views_of(c, it->second);
     c->bases.erase(it);
     c->epoch++;
   }
@@ -1292,8 +1360,10 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
     std::vector<std::string> srcs, keys;
     for (auto& it : plan.items) {
       if (it.kind == 2) {
-        keys.emplace_back();
-        srcs.push_back(generate_group_source(*it.group, nullptr, nullptr, &keys.back()));
+        auto gs = group_source(*it.group);
+        if (c->cwait < 0 && c->kernels.count(gs->key)) continue;  // loaded already
+        keys.push_back(gs->key);
+        srcs.push_back(gs->src);
         continue;
       }
       if (it.kind != 0) continue;
@@ -1301,16 +1371,28 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       for (auto& s : it.run.loads) pp.lp.push_back((uintptr_t)c->bases[s.base].dptr);
       for (auto& s : it.run.stores) pp.sp.push_back((uintptr_t)c->bases[s.base].dptr);
       Canon cn = canonicalize(it.run, true, pp.lp, pp.sp, 0);
-      keys.emplace_back();
-      srcs.push_back(generate_source(it.run, cn, nullptr, &keys.back()));
+      auto rs = run_source(it.run, cn);
+      if (c->cwait < 0 && c->kernels.count(rs->key)) continue;  // loaded already
+      keys.push_back(rs->key);
+      srcs.push_back(rs->src);
     }
     if (!c->record) precompile(c, srcs, &keys);
   }
-  // first pass: allocation order and reads of never-written bases
+  // first pass: allocation order and reads of never-written bases (a base
+  // is available when it has memory or an earlier item of the batch writes
+  // it; only the bases the batch touches are looked at, so the cost does not
+  // grow with the bases other requests keep in the context)
   {
-    std::set<int64_t> avail;
-    for (auto& kv : c->bases)
-      if (kv.second.dptr) avail.insert(kv.first);
+    struct Avail {
+      Ctx* c;
+      std::unordered_set<int64_t> written;
+      size_t count(int64_t b) const {
+        if (written.count(b)) return 1;
+        auto it = c->bases.find(b);
+        return it != c->bases.end() && it->second.dptr ? 1 : 0;
+      }
+      void insert(int64_t b) { written.insert(b); }
+    } avail{c, {}};
     for (auto& it : plan.items) {
       if (it.kind == 2) {
         const Group& g = *it.group;
@@ -1375,8 +1457,8 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       allocate_group(c, ex, g);
       GroupPrepared G;
       G.g = &g;
-      G.src = generate_group_source(g, &G.prefix, &G.shapes, &G.key);
-      G.kern = get_kernel(c, G.src, &G.key);
+      G.gs = group_source(g);
+      G.kern = get_kernel(c, G.gs->src, &G.gs->key);
       GroupPtrs ptr = group_ptrs(c, g);
       TileShape ts = choose_group(c, ex, G, ptr, !capture);
       if (group_split(c, ex, G, ts, ptr, !capture)) {
@@ -1389,8 +1471,8 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
           P.run = &r;
           RunPtrs rp = run_ptrs(c, r);
           P.canon = canonicalize(r, true, rp.lp, rp.sp, rp.rp);
-          P.src = generate_source(r, P.canon, &P.prefix, &P.key);
-          P.kern = get_kernel(c, P.src, &P.key);
+          P.rs = run_source(r, P.canon);
+          P.kern = get_kernel(c, P.rs->src, &P.rs->key);
           TuneChoice tc = choose(c, ex, P, rp, !capture);
           Launch L = build_single(c, ex, P, tc, rp);
           if (capture) {
@@ -1430,8 +1512,8 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
     P.run = &r;
     RunPtrs ptr = run_ptrs(c, r);
     P.canon = canonicalize(r, true, ptr.lp, ptr.sp, ptr.rp);
-    P.src = generate_source(r, P.canon, &P.prefix, &P.key);
-    P.kern = get_kernel(c, P.src, &P.key);
+    P.rs = run_source(r, P.canon);
+    P.kern = get_kernel(c, P.rs->src, &P.rs->key);
     bool tile = P.canon.spec.mode == Mode::ELEM || P.canon.spec.mode == Mode::FULL;
     // packing: following runs with the same kernel that share no data
     std::vector<size_t> group{i};
@@ -1455,7 +1537,7 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
         allocate_outputs(c, ex, r2);
         RunPtrs p2 = run_ptrs(c, r2);
         Canon c2 = canonicalize(r2, true, p2.lp, p2.sp, p2.rp);
-        if (c2.spec.nd != 1 || generate_source(r2, c2, nullptr) != P.src) break;
+        if (c2.spec.nd != 1 || run_source(r2, c2) != P.rs) break;
         group.push_back(j);
         ++j;
       }
@@ -1466,8 +1548,8 @@ void exec_batch(Ctx* c, Exec* ex, const vbe_instr* prog, int64_t n, bool allow_g
       Launch L;
       L.packed = true;
       int U = 4;
-      L.entry = P.prefix + "_pack_u" + std::to_string(U);
-      L.key = P.key;
+      L.entry = P.rs->prefix + "_pack_u" + std::to_string(U);
+      L.key = P.rs->key;
       L.fn = kernel_fn(P.kern.get(), L.entry);
       L.block = 256;
       int64_t total_elems = 0;

@@ -75,6 +75,10 @@ struct Req {
   bool taken = false;    // a client's wait has started taking the results
   bool cb_enqueued = false;  // the results callback is on the stream (it may set ready)
   bool fetched = false;  // ... and is finished with the request (it may be deleted)
+  // its client's wait: woken (under the server's lock) when the results are
+  // ready or the request is done, and only its client, so a completion does
+  // not wake every waiting client
+  std::condition_variable cv;
 };
 
 }  // namespace
@@ -97,7 +101,7 @@ struct vbe_server {
   int64_t used = 0;
   int64_t next_id = 1;
   std::mutex m;
-  std::condition_variable cv_done, cv_work;
+  std::condition_variable cv_work;
   bool stop = false;
   PinnedPool pinned;
   int inflight = 0;  // over all workers
@@ -137,8 +141,8 @@ void CUDART_CB on_results_ready(void* arg) {
     // a request finishing on the same context meanwhile is failed too)
     if (r->err_word && *(volatile const unsigned*)r->err_word) r->res.status = VBE_ERR_TIMEOUT;
     r->ready = true;
+    r->cv.notify_all();  // under the lock: the client cannot delete the request before this returns
   }
-  s->cv_done.notify_all();
 }
 
 // pinned (page-locked) host memory: a result can be copied there directly
@@ -189,7 +193,7 @@ void admit(vbe_server* s, Worker* w, Req* r, int slot) {
       if (d.size() > 0 && (d.lo < 0 || d.hi >= c.bases[d.base].nelem))
         vbe::fail(VBE_ERR_OUT_OF_BOUNDS, "request view out of bounds");
       int64_t h = c.next_handle++;
-      c.views[h] = d;
+      vbe::add_view(&c, h, d);
       r->vh.push_back(h);
     }
     std::vector<vbe_instr> prog = r->instrs;
@@ -303,6 +307,7 @@ void worker_loop(vbe_server* s, Worker* w) {
         r->done = true;
         s->used -= r->footprint;
         if (r->fetched) s->reqs.erase(r->id);  // its client is gone already
+        else r->cv.notify_all();
       }
       for (size_t i = 0; i < admitted.size(); ++i) {
         Req* r = admitted[i];
@@ -312,10 +317,10 @@ void worker_loop(vbe_server* s, Worker* w) {
           w->slot_req[admitted_slot[i]] = nullptr;
           w->inflight--;
           s->inflight--;
+          r->cv.notify_all();
         }
       }
     }
-    s->cv_done.notify_all();
     if (!done.empty()) s->cv_work.notify_all();  // memory freed: other workers may admit
   }
 }
@@ -435,8 +440,8 @@ int vbe_server_wait(vbe_server* s, int64_t id, int64_t timeout_ns, vbe_request_r
   // results in host memory (ready), or finished without them (done: an error)
   auto pred = [&] { return r->ready || r->done; };
   if (timeout_ns < 0) {
-    s->cv_done.wait(lk, pred);
-  } else if (!s->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), pred)) {
+    r->cv.wait(lk, pred);
+  } else if (!r->cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns), pred)) {
     return VBE_ERR_TIMEOUT;
   }
   r->taken = true;

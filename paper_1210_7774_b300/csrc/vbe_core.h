@@ -164,6 +164,8 @@ struct GroupLoad {
   int dr = 0, dc = 0;   // producer point = loader point + (dr, dc)
 };
 
+struct GroupSource;  // generated source of a group (codegen), shared by identical groups
+
 struct Group {
   std::vector<Run> runs;                     // program order; the last is the anchor
   std::vector<std::array<int, 4>> box;       // per run: row lo/hi, col lo/hi margins around the tile
@@ -178,6 +180,9 @@ struct Group {
   std::map<int64_t, int64_t> base_nelem;     // element count of every base the group reads
   int64_t rows(int k) const { return runs[k].shape[0]; }
   int64_t cols(int k) const { return runs[k].shape[1]; }
+  // its source, once looked up (a batch asks for it when it compiles and
+  // again when it launches)
+  mutable std::shared_ptr<const GroupSource> source;
 };
 
 struct PlanItem {
@@ -219,6 +224,12 @@ Canon canonicalize(const Run& r, bool allow_vec, const std::vector<uintptr_t>& l
                    const std::vector<uintptr_t>& store_ptrs, uintptr_t red_ptr);
 // key_out: the source's cache key (src_key), kept with the memoised source
 std::string generate_source(const Run& r, const Canon& c, std::string* entry_prefix, std::string* key_out = nullptr);
+// The memoised source of a run's signature, shared (nothing copied; the memo's
+// lock is held only to look the entry up).
+struct RunSource {
+  std::string src, prefix, key;
+};
+std::shared_ptr<const RunSource> run_source(const Run& r, const Canon& c);
 std::string src_key(const std::string& src);  // two 64-bit hashes of the source text
 std::vector<std::pair<const char*, const char*>> nvrtc_headers();  // (include name, text)
 
@@ -261,6 +272,13 @@ struct TileShape {
   const char* letter() const { return sweep ? "r" : (tma ? "t" : (staged ? "s" : "")); }
   int form() const { return sweep ? 3 : (tma ? 2 : (int)staged); }
 };
+struct GroupSource {
+  std::string src, prefix, key;  // CUDA source, entry prefix, source key
+  std::vector<TileShape> shapes;  // one kernel per shape
+};
+// A group's source, generated once per distinct group (process-wide memo)
+// and kept on the group; nothing is copied.
+std::shared_ptr<const GroupSource> group_source(const Group& g);
 std::string generate_group_source(const Group& g, std::string* entry_prefix, std::vector<TileShape>* shapes,
                                   std::string* key_out = nullptr);
 std::vector<TmaBox> group_tma_boxes(const Group& g, const TileShape& ts);
@@ -287,12 +305,19 @@ struct BaseRec {
   bool dev_valid = true;    // the device copy holds the base's current value
   bool host_valid = false;  // the host mirror holds it
   bool host_write = false;  // the host holds write access (it owns the base)
+  std::vector<int64_t> views;  // handles of the views on this base (erased with it)
   int64_t bytes() const { return nelem * itemsize(dtype); }
 };
 
+// A loaded module. Modules are context-independent (cudaLibrary), so the
+// contexts of a process share one per source: a scheduler thread meeting a
+// kernel that another one loaded does not load it again (loading can wait
+// for the device work in flight). Unloaded when its last user goes.
 struct Kernel {
   cudaLibrary_t lib = nullptr;
+  std::mutex mu;  // fn is filled lazily, from any context's thread
   std::map<std::string, cudaKernel_t> fn;
+  ~Kernel();
 };
 
 // Long runs (many fused bytecodes) also get tile kernels compiled under a
@@ -371,7 +396,8 @@ struct Ctx {
   // caches
   std::unordered_map<std::string, std::shared_ptr<Kernel>> kernels;  // by source hash
   std::unordered_map<std::string, TuneChoice> tune;                  // by source hash
-  std::string tune_file;  // tuning choices kept across processes (in the cache directory), or empty
+  std::string tune_file;    // tuning choices kept across processes (in the cache directory), or empty
+  std::string tune_device;  // the device model and SM count the choices are keyed by (empty: host only)
   std::unordered_map<uint64_t, CachedBatch> batches;
   // tickets: ticket t is recorded in ring slot t mod kTicketRing; a slot
   // reused by a later submit holds a later point of the same stream, so
@@ -404,7 +430,17 @@ struct Ctx {
 
 // analysis
 bool live_after(const std::vector<RInstr>& prog, int64_t base, size_t idx);
-void form_groups(Ctx* c, const std::vector<RInstr>& prog, Plan* plan);  // tile fusion (groups.cpp)
+// The same question answered from an index built once per batch: per base,
+// the positions of the instructions that read it or control it (SYNC,
+// DISCARD, FREE), so each answer is a binary search instead of a scan of
+// the rest of the batch.
+struct LiveIndex {
+  // position, and 0 a read, 1 a SYNC, 2 a DISCARD or FREE
+  std::unordered_map<int64_t, std::vector<std::pair<int64_t, int>>> ev;
+  explicit LiveIndex(const std::vector<RInstr>& prog);
+  bool live_after(int64_t base, size_t idx) const;
+};
+void form_groups(Ctx* c, const std::vector<RInstr>& prog, const LiveIndex& live, Plan* plan);  // tile fusion (groups.cpp)
 std::vector<RInstr> resolve_batch(Ctx* c, const vbe_instr* prog, int64_t n);
 Plan make_plan(Ctx* c, std::vector<RInstr>& prog, bool fuse, bool pack);
 std::string plan_json(Ctx* c, const std::vector<RInstr>& prog, const Plan& p, bool want_source);
@@ -419,10 +455,17 @@ void dev_free(Ctx* c, Exec* ex, void* p, int64_t bytes);
 void ensure_scratch(Ctx* c, Exec* ex, int64_t partials, int64_t counters);
 void release_exec(Ctx* c, Exec* ex);
 void init_error_word(Ctx* c);
-// Tuning choices persist in the cache directory, one file per device model:
-// load_tune reads it when a context is created, remember_tune records a new
-// choice in the context and appends it to the file.
+// views by base: a new view is listed under its base, and freeing a base
+// erases its views without looking at any other
+void add_view(Ctx* c, int64_t handle, const ViewDesc& v);
+void erase_views_of(Ctx* c, BaseRec& br);
+// Tuning choices are shared by the contexts of a process and persist in the
+// cache directory, one file per device model: load_tune reads it when a
+// context is created, recall_tune finds a choice (this context's, another
+// context's, or the file's), remember_tune records a new one and appends it
+// to the file.
 void load_tune(Ctx* c);
+bool recall_tune(Ctx* c, const std::string& key, TuneChoice* out);
 void remember_tune(Ctx* c, const std::string& key, const TuneChoice& tc);
 void release_error_word(Ctx* c);
 bool take_error_word(Ctx* c);  // true (and cleared) when a staged kernel reported a failed wait

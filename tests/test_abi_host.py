@@ -218,6 +218,43 @@ def test_validation_errors(fused):
         assert e.value.code == code
 
 
+def test_views_go_with_their_base(fused):
+    """A base keeps the list of its views: freeing it (vbe_free, or a FREE
+    bytecode in a recorded batch) makes exactly its views unknown; views of
+    other bases keep working, and a destroyed view is gone."""
+    ctx = fused.ctx
+    f = V.vbe_base_create(ctx, V.VBE_FLOAT64, 10)
+    g = V.vbe_base_create(ctx, V.VBE_FLOAT64, 10)
+    vf = [V.vbe_view_create(ctx, f, k, (5,), (1,)) for k in range(3)]
+    vg = V.vbe_view_create(ctx, g, 0, (5,), (1,))
+    vg2 = V.vbe_view_create(ctx, g, 5, (5,), (1,))
+
+    def instr(op, out, *ins):
+        arr = (V.vbe_instr * 1)()
+        arr[0].op = V.OPCODES[op]
+        arr[0].const_slot = -1
+        arr[0].out = out
+        for k, x in enumerate(ins):
+            arr[0].in_[k] = x
+        return arr
+
+    V.vbe_plan(ctx, instr("ADD", vf[0], vf[1], vg), 1)
+    V.vbe_view_destroy(ctx, vg2)
+    with pytest.raises(V.VbeError):
+        V.vbe_view_destroy(ctx, vg2)  # already gone
+    V.vbe_free(ctx, f)
+    for v in vf:
+        with pytest.raises(V.VbeError) as e:
+            V.vbe_plan(ctx, instr("COPY", vg, v), 1)
+        assert e.value.code == -1  # an unknown view
+        with pytest.raises(V.VbeError):
+            V.vbe_view_destroy(ctx, v)
+    V.vbe_plan(ctx, instr("ADD", vg, vg, vg), 1)  # the other base's view is untouched
+    h = V.vbe_view_create(ctx, g, 1, (9,), (1,))  # and the base takes new views
+    V.vbe_plan(ctx, instr("COPY", vg, V.vbe_view_create(ctx, g, 2, (5,), (1,))), 1)
+    V.vbe_view_destroy(ctx, h)
+
+
 def _np_view(buf, v):
     return np.lib.stride_tricks.as_strided(buf[v.offset:], v.shape, tuple(8 * s for s in v.strides))
 

@@ -45,3 +45,17 @@ def test_tuning_choices_reused_across_contexts(tmp_path):
     want = oracle_outputs(sw)
     for bid in sw.outputs:
         assert_exact(first[sw.name][0][bid], want[bid], sw.name)
+
+
+def test_tuning_choices_shared_by_contexts_of_a_process():
+    """Contexts of one process (a server's scheduler threads) share their
+    choices even without a cache directory: the second context tunes
+    nothing and computes the same results."""
+    n = (1 << 23) + 4096  # a size class no other test tunes in this process
+    bs = blackscholes(n, "float64", inputs=bs_inputs(n, "float64"))
+    first, tunes = _run(bs, None)
+    assert tunes > 0
+    second, tunes2 = _run(bs, None)
+    assert tunes2 == 0
+    for bid in bs.outputs:
+        np.testing.assert_array_equal(first[bid], second[bid])
