@@ -89,6 +89,9 @@ struct Worker {
   bool owns_ctx = false;
   std::vector<vbe::Exec> slots;
   std::vector<Req*> slot_req;
+  // one completion event per slot, created with the slot: a slot holds one
+  // request at a time and takes the next only after this event completed
+  std::vector<cudaEvent_t> slot_ev;
   int inflight = 0;
   std::thread th;
 };
@@ -124,8 +127,7 @@ void finish_request(Worker* w, Req* r) {
     c.bases.erase(it);
   }
   c.epoch++;
-  if (r->ev) cudaEventDestroy(r->ev);
-  r->ev = nullptr;
+  r->ev = nullptr;  // the slot's event, kept for its next request
 }
 
 // Stream host callback after a request's result copies: its client may
@@ -225,7 +227,7 @@ void admit(vbe_server* s, Worker* w, Req* r, int slot) {
     }
     // the client is woken by the callback; the event (after it) tells the
     // worker that the slot's work, callback included, is finished
-    vbe::cuda_check(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming), "event");
+    r->ev = w->slot_ev[slot];
     vbe::cuda_check(cudaLaunchHostFunc(ex->stream, on_results_ready, r), "results callback");
     r->cb_enqueued = true;
     vbe::cuda_check(cudaEventRecord(r->ev, ex->stream), "event record");
@@ -354,8 +356,11 @@ int vbe_server_create(vbe_ctx* ctx, const vbe_server_config* cfg, vbe_server** o
       const int ns = cfg->slots / nw + (k < cfg->slots % nw ? 1 : 0);
       w->slots.resize(ns);
       w->slot_req.assign(ns, nullptr);
-      for (auto& e : w->slots) {
+      w->slot_ev.assign(ns, nullptr);
+      for (int q = 0; q < ns; ++q) {
+        vbe::Exec& e = w->slots[q];
         vbe::cuda_check(cudaStreamCreateWithFlags(&e.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        vbe::cuda_check(cudaEventCreateWithFlags(&w->slot_ev[q], cudaEventDisableTiming), "event");
         vbe::ensure_scratch(&w->ctx->c, &e, 1 << 20, 1 << 16);
       }
       s->workers.push_back(std::move(w));
@@ -368,6 +373,8 @@ int vbe_server_create(vbe_ctx* ctx, const vbe_server_config* cfg, vbe_server** o
           vbe::release_exec(&w->ctx->c, &x);
           cudaStreamDestroy(x.stream);
         }
+      for (auto ev : w->slot_ev)
+        if (ev) cudaEventDestroy(ev);
       if (w->owns_ctx) vbe_finalize(w->ctx);
     }
     delete s;
@@ -480,6 +487,8 @@ int vbe_server_destroy(vbe_server* s) {
       vbe::release_exec(&w->ctx->c, &e);
       cudaStreamDestroy(e.stream);
     }
+    for (auto ev : w->slot_ev)
+      if (ev) cudaEventDestroy(ev);
     if (w->owns_ctx) vbe_finalize(w->ctx);
   }
   delete s;
