@@ -189,3 +189,35 @@ def test_pinned_result_buffers_filled_directly():
     for i in range(0, len(reqs), 6):
         reqs[i].results = got[i]
         check_against_oracle(reqs[i])
+
+
+def test_waits_out_of_order_and_timed_out_waits():
+    """Each request wakes only its own waiter: one thread submits many
+    requests and waits for them in reverse order; another waits with a wait
+    limit too short for a large request (VBE_ERR_TIMEOUT, nothing taken),
+    then waits again and gets the same results as a solo run."""
+    progs = [request_program(k, p) for k, p in small_mix(24)]
+    big = request_program("blackscholes", dict(n=1 << 22, dtype="float64", seed=7))
+    ctx = V.vbe_init(0, FLAGS, 0, None, CACHE)
+    srv = V.vbe_server_create(ctx, 4, 8 << 30, FLAGS, workers=2)
+    try:
+        reqs = [Request(p) for p in progs]
+        ids = [V.vbe_server_submit(srv, r.req) for r in reqs]
+        for i in reversed(range(len(ids))):
+            assert V.vbe_server_wait(srv, ids[i], 120_000_000_000).status == 0
+        rb = Request(big)
+        rid = V.vbe_server_submit(srv, rb.req)
+        with pytest.raises(V.VbeError) as e:
+            V.vbe_server_wait(srv, rid, 1000)  # 1 us: the pricing of 4M options is still running
+        assert e.value.code == -8  # VBE_ERR_TIMEOUT
+        assert V.vbe_server_wait(srv, rid, 120_000_000_000).status == 0
+    finally:
+        V.vbe_server_destroy(srv)
+        V.vbe_finalize(ctx)
+    solo_reqs, solo = serve(progs, threads=1)
+    for a, b in zip(reqs, solo_reqs):
+        for bid in a.results:
+            np.testing.assert_array_equal(a.results[bid], b.results[bid])
+    big_solo_reqs, _ = serve([big], threads=1)
+    for bid in rb.results:
+        np.testing.assert_array_equal(rb.results[bid], big_solo_reqs[0].results[bid])
