@@ -399,14 +399,57 @@ def e2e_pipelined(V, Executor, prog, dtype, flags, local, cache, args, torch, wo
         return time.perf_counter() - t0
 
     run_steps(2)  # warm-up (tuning, first launches)
-    steps = max(3, args.steps // 4)
+    steps = max(5, args.steps // 2)
     sec = run_steps(steps) / steps
     for sh in shares:
         sh[0].close()
-    return {"value": cbytes / sec / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "workers": workers,
+    link = link_rates(torch, h2d, d2h)
+    value = cbytes / sec / 1e9
+    return {"value": value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "workers": workers, "steps": steps, "link": link,
+            "frac_of_link": value / link["same_bytes_gbs"],
             "how": f"{workers} contexts, one host thread each, over equal shares of the options: pinned inputs "
                    "uploaded, batch submitted, results synced back, each thread in turn; the threads overlap"}
+
+
+def link_rates(torch, h2d, d2h, reps=5):
+    """The host link's rates for the end-to-end step's copies, measured with
+    plain copies between page-locked host memory and the device: each
+    direction alone, both directions at once with equal sizes, and the
+    step's own bytes (h2d to the device, d2h back, started together on two
+    streams). The last is the bound of any end-to-end step that moves these
+    bytes: ``same_bytes_gbs`` = (h2d + d2h) / its time (best of ``reps``)."""
+    dev = torch.cuda.current_device()
+    hin = torch.empty(h2d, dtype=torch.uint8).pin_memory()
+    hout = torch.empty(d2h, dtype=torch.uint8).pin_memory()
+    din = torch.empty(h2d, dtype=torch.uint8, device=dev)
+    dout = torch.empty(d2h, dtype=torch.uint8, device=dev)
+    s_up, s_down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def timed(up, down):
+        best = None
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if up is not None:
+                with torch.cuda.stream(s_up):
+                    up[0].copy_(up[1], non_blocking=True)
+            if down is not None:
+                with torch.cuda.stream(s_down):
+                    down[0].copy_(down[1], non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        return best
+    m = min(h2d, d2h)
+    r = {"h2d_gbs": h2d / timed((din, hin), None) / 1e9,
+         "d2h_gbs": d2h / timed(None, (hout, dout)) / 1e9,
+         "both_equal_gbs": 2 * m / timed((din[:m], hin[:m]), (hout[:m], dout[:m])) / 1e9,
+         "same_bytes_gbs": (h2d + d2h) / timed((din, hin), (hout, dout)) / 1e9,
+         "how": "plain copies between page-locked host memory and the device, best of %d: each direction "
+                "alone, both at once with equal sizes, and the step's own bytes both ways at once" % reps}
+    del hin, hout, din, dout
+    return r
 
 
 # ------------------------------------------------- per-configuration keys
