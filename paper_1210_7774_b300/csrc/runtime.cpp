@@ -117,7 +117,14 @@ void load_tune(Ctx* c) {
     std::istringstream ls(line);
     std::string key;
     TuneChoice tc;
-    if (ls >> key >> tc.block >> tc.U >> tc.maxreg >> tc.bulk_chunk >> tc.grid_mult) {
+    // a line that does not parse, or whose values lie outside what the
+    // tuner ever writes (a damaged or foreign file), is ignored: its key is
+    // tuned afresh
+    std::string extra;
+    if (ls >> key >> tc.block >> tc.U >> tc.maxreg >> tc.bulk_chunk >> tc.grid_mult && !(ls >> extra) &&
+        tc.block >= 1 && tc.block <= 1024 && tc.U >= 1 && tc.U <= 1024 &&
+        (tc.maxreg == 0 || std::find(std::begin(kRegCaps), std::end(kRegCaps), tc.maxreg) != std::end(kRegCaps)) &&
+        tc.bulk_chunk >= 0 && tc.bulk_chunk <= (1 << 24) && tc.grid_mult >= 0 && tc.grid_mult <= 64) {
       c->tune[key] = tc;
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune.emplace(c->tune_device + ":" + key, tc);

@@ -59,3 +59,51 @@ def test_tuning_choices_shared_by_contexts_of_a_process():
     assert tunes2 == 0
     for bid in bs.outputs:
         np.testing.assert_array_equal(first[bid], second[bid])
+
+
+def _unusual_chain(n):
+    """An elementwise chain no other test builds (its own tuning key)."""
+    from workloads import Const, ProgramBuilder
+    rng = np.random.default_rng(77)
+    b = ProgramBuilder("tune_damage")
+    x = b.base("float32", (n,), rng.standard_normal(n).astype(np.float32))
+    y = b.base("float32", (n,), rng.standard_normal(n).astype(np.float32))
+    o = b.base("float32", (n,), np.zeros(n, np.float32))
+    X, Y, O = b.whole(x), b.whole(y), b.whole(o)
+    b.emit("MAXIMUM", O, X, Y)
+    b.emit("SUBTRACT", O, O, X)
+    b.emit("MULTIPLY", O, O, Const(0.375))
+    b.emit("ABSOLUTE", O, O)
+    b.emit("MINIMUM", O, O, Y)
+    b.emit("ADD", O, O, X)
+    b.emit("NEGATIVE", O, O)
+    return b.build([o])
+
+
+def test_damaged_tuning_lines_are_ignored(tmp_path):
+    """Lines of the tuning file that do not parse, carry an extra field or
+    hold values the tuner never writes (block 0, U 0, an unknown register
+    cap, a negative chunk) are dropped when a context loads the file; the
+    context falls back on the process's own choices and computes the same,
+    exact results."""
+    cache = str(tmp_path)
+    p = _unusual_chain((1 << 21) + 96)
+    first, tunes = _run(p, cache)
+    assert tunes > 0
+    (path,) = glob.glob(os.path.join(cache, "tune_*.txt"))
+    keys = [ln.split()[0] for ln in open(path) if ln.strip()]
+    assert keys
+    with open(path, "w") as f:
+        for k in keys:
+            f.write(f"{k} 0 1 0 0 0\n")       # block 0
+            f.write(f"{k} 256 0 0 0 0\n")     # U 0
+            f.write(f"{k} 256 1 7 0 0\n")     # a register cap the tuner never uses
+            f.write(f"{k} 256 1 0 -16 0\n")   # negative chunk
+            f.write(f"{k} 256 1 0 0 0 9\n")   # an extra field
+            f.write(f"{k} 256\n")             # cut short
+            f.write(f"{k} 2x6 1 0 0 0\n")     # not a number
+    second, tunes2 = _run(p, cache)
+    assert tunes2 == 0
+    np.testing.assert_array_equal(second[p.outputs[0]], first[p.outputs[0]])
+    want = oracle_outputs(p)
+    assert_exact(second[p.outputs[0]], want[p.outputs[0]], p.name)
