@@ -131,6 +131,87 @@ def fuzz_cases(seeds):
     return [random_program(s) for s in seeds]
 
 
+def random_reduce_chain_program(seed: int):
+    """Random programs in which later instructions read what reductions
+    wrote: int64 sums and ARGMIN/ARGMAX indices (exact in any combining
+    order) land in a 64-element int64 base, and later int64 operations,
+    compares, selects and casts read them through row or column broadcasts
+    (stride 0 along one axis) of that base, then feed further reductions.
+    Every reduction result read later is a dependency through a reduction,
+    which fusion must break and packing must not put into one launch with
+    its reader. MIN/MAX values go to a float64 base that nothing reads (the
+    sign of a zero chosen from tied signed zeros is not fixed)."""
+    rng = np.random.default_rng(9000 + seed)
+    b = ProgramBuilder(f"fuzz_redchain{seed}")
+    n = R * C
+    F = [b.base("float64", (R, C), rng.standard_normal(n) * np.exp2(rng.integers(-3, 4, n))) for _ in range(2)]
+    I = [b.base("int64", (R, C), rng.integers(-50, 50, n)) for _ in range(2)]
+    B = b.base("bool", (R, C), rng.random(n) < 0.5)
+    redi = b.base("int64", (64,), rng.integers(-20, 20, 64))
+    redf = b.base("float64", (64,), np.zeros(64))
+
+    def fv(h, w, bc=True):
+        return _view(b, rng, F[rng.integers(0, 2)], h, w, bc)
+
+    def iv(h, w, bc=True):
+        return _view(b, rng, I[rng.integers(0, 2)], h, w, bc)
+
+    def red_out(bid, m):
+        return b.view(bid, int(rng.integers(0, 64 - m + 1)), (m,), (1,))
+
+    def red_in(h, w):
+        """redi read as an (h, w) array: a row repeated down, or a column
+        repeated across"""
+        if rng.random() < 0.5:
+            return b.view(redi, int(rng.integers(0, 64 - w + 1)), (h, w), (0, 1))
+        return b.view(redi, int(rng.integers(0, 64 - h + 1)), (h, w), (1, 0))
+
+    for _ in range(int(rng.integers(10, 24))):
+        h, w = SHAPES[rng.integers(0, len(SHAPES))]
+        k = int(rng.integers(0, 8))
+        if k <= 1:  # int64 sums over either axis into redi
+            ax = int(rng.integers(0, 2))
+            b.emit("ADD_REDUCE", red_out(redi, (h, w)[1 - ax]), iv(h, w), axis=ax)
+        elif k == 2:  # argmin/argmax into redi, sometimes paired with its MIN/MAX
+            ax = int(rng.integers(0, 2))
+            m = (h, w)[1 - ax]
+            x = fv(h, w)
+            if rng.random() < 0.5:
+                b.emit(["MIN_REDUCE", "MAX_REDUCE"][rng.integers(0, 2)], red_out(redf, m), x, axis=ax)
+            b.emit(["ARGMIN_REDUCE", "ARGMAX_REDUCE"][rng.integers(0, 2)], red_out(redi, m), x, axis=ax)
+        elif k <= 4:  # int64 arithmetic on reduction results
+            op = ["ADD", "SUBTRACT", "MAXIMUM", "MINIMUM"][rng.integers(0, 4)]
+            y = red_in(h, w) if rng.random() < 0.6 else iv(h, w)
+            b.emit(op, iv(h, w, False), red_in(h, w) if rng.random() < 0.5 else iv(h, w), y)
+        elif k == 5:  # compare with a reduction result, then select
+            m = _view(b, rng, B, h, w, False)
+            b.emit(["LESS", "GREATER_EQUAL", "EQUAL"][rng.integers(0, 3)], m, iv(h, w), red_in(h, w))
+            b.emit("SELECT", iv(h, w, False), m, red_in(h, w), iv(h, w))
+        elif k == 6:  # a reduction result into float64 arithmetic (exact: small integers)
+            o = fv(h, w, False)
+            b.emit("CAST", o, red_in(h, w))
+            b.emit(["ADD", "MULTIPLY", "SUBTRACT"][rng.integers(0, 3)], o, o, fv(h, w))
+        else:  # in place on redi itself: a slice updated from another slice
+            m = int(rng.integers(1, 12))
+            b.emit(["ADD", "SUBTRACT"][rng.integers(0, 2)], red_out(redi, m), red_out(redi, m), red_out(redi, m))
+    outs = F + I + [B, redi, redf]
+    p = b.build(outs)
+
+    def check(got, want):
+        for bid in outs:
+            if bid == redf:
+                g, wv = np.asarray(got[bid]), np.asarray(want[bid])
+                same = (g == wv) | (np.isnan(g) & np.isnan(wv))
+                assert np.all(same), f"{p.name} MIN/MAX values: got {g[~same][:4]} want {wv[~same][:4]}"
+            else:
+                assert_exact(got[bid], want[bid], f"{p.name} base {bid}")
+    return Case(p.name, p, check)
+
+
+def reduce_chain_cases(seeds):
+    return [random_reduce_chain_program(s) for s in seeds]
+
+
 def random_stencil_program(seed: int):
     """A random stencil chain that the library fuses into one tile-fused
     group: 2 to 4 runs, each computing a temporary from the previous one
