@@ -212,6 +212,138 @@ def reduce_chain_cases(seeds):
     return [random_reduce_chain_program(s) for s in seeds]
 
 
+LAYOUT = (3, 4, 5, 6)  # the n-D generator's bases, row-major
+LSTR = (120, 30, 6, 1)
+
+
+def _nd_view(b, rng, bid, shape, broadcast_ok):
+    """A random view of the given shape (rank 1 to 5) of a LAYOUT base:
+    each dimension walks a distinct base axis (in any order, forwards or
+    backwards, every element or every other one when it fits) or, for
+    inputs, repeats (stride 0); base axes left over sit at a random index."""
+    for _ in range(200):
+        axes = list(rng.permutation(4))
+        off, strides, used = 0, [], []
+        ok = True
+        for n in shape:
+            if broadcast_ok and rng.random() < 0.15:
+                strides.append(0)
+                continue
+            cand = [a for a in axes if a not in used and LAYOUT[a] >= n]
+            if not cand:
+                ok = False
+                break
+            a = int(cand[rng.integers(0, len(cand))])
+            used.append(a)
+            step = 2 if (rng.random() < 0.3 and 2 * (n - 1) < LAYOUT[a]) else 1
+            span = step * (n - 1)
+            start = int(rng.integers(0, LAYOUT[a] - span))
+            if rng.random() < 0.35:  # backwards
+                off += (start + span) * LSTR[a]
+                strides.append(-step * LSTR[a])
+            else:
+                off += start * LSTR[a]
+                strides.append(step * LSTR[a])
+        if not ok:
+            continue
+        for a in range(4):
+            if a not in used:
+                off += int(rng.integers(0, LAYOUT[a])) * LSTR[a]
+        return b.view(bid, off, tuple(shape), tuple(strides))
+    raise AssertionError("no view fits")
+
+
+def random_nd_program(seed: int):
+    """Random exact programs over views of rank 1 to 5 of 3 x 4 x 5 x 6
+    bases: dimensions in any order of the base axes, reversed, strided by
+    two, broadcast (stride 0, inputs only), so the library's merging of
+    dimensions, its general (non-vector) tile path and reductions over
+    inner, middle and outer axes of such views are compared with the
+    oracle bit for bit (int64 sums; MIN/MAX/ARGMIN/ARGMAX; a zero chosen
+    from tied signed zeros by MIN/MAX compared by value)."""
+    rng = np.random.default_rng(13000 + seed)
+    b = ProgramBuilder(f"fuzz_nd{seed}")
+    n = int(np.prod(LAYOUT))
+    F = [b.base("float64", LAYOUT, rng.standard_normal(n) * np.exp2(rng.integers(-3, 4, n))) for _ in range(2)]
+    I = [b.base("int64", LAYOUT, rng.integers(-50, 50, n)) for _ in range(2)]
+    B = b.base("bool", LAYOUT, rng.random(n) < 0.5)
+    red = b.base("float64", (256,), np.zeros(256))
+    redi = b.base("int64", (256,), np.zeros(256, np.int64))
+
+    def shape():
+        r = int(rng.integers(1, 6))
+        return tuple(int(rng.integers(1, 7)) for _ in range(r))
+
+    def fv(S, bc=True):
+        return _nd_view(b, rng, F[rng.integers(0, 2)], S, bc)
+
+    def iv(S, bc=True):
+        return _nd_view(b, rng, I[rng.integers(0, 2)], S, bc)
+
+    def red_out(bid, S):
+        """a contiguous (or, when there are two or more dims, transposed) view of S elements"""
+        m = int(np.prod(S)) if S else 1
+        if m > 256:
+            raise AssertionError("result does not fit")
+        off = int(rng.integers(0, 256 - m + 1))
+        st = [0] * len(S)
+        acc = 1
+        order = list(range(len(S)))[::-1] if rng.random() < 0.7 else list(rng.permutation(len(S)))
+        for k in order:
+            st[k] = acc
+            acc *= S[k]
+        return b.view(bid, off, tuple(S) if S else (1,), tuple(st) if S else (1,))
+
+    for _ in range(int(rng.integers(8, 18))):
+        S = shape()
+        k = int(rng.integers(0, 9))
+        try:
+            if k <= 2:
+                op = ["ADD", "SUBTRACT", "MULTIPLY", "MAXIMUM", "MINIMUM", "DIVIDE"][rng.integers(0, 6)]
+                y = Const(float(np.round(rng.standard_normal(), 3))) if rng.random() < 0.2 else fv(S)
+                b.emit(op, fv(S, False), fv(S), y)
+            elif k == 3:
+                b.emit(["NEGATIVE", "ABSOLUTE", "COPY"][rng.integers(0, 3)], fv(S, False), fv(S))
+            elif k == 4:
+                op = ["ADD", "SUBTRACT", "MAXIMUM", "MINIMUM"][rng.integers(0, 4)]
+                b.emit(op, iv(S, False), iv(S), iv(S))
+            elif k == 5:
+                m = _nd_view(b, rng, B, S, False)
+                b.emit(["LESS", "GREATER", "EQUAL"][rng.integers(0, 3)], m, fv(S), fv(S))
+                b.emit("SELECT", fv(S, False), _nd_view(b, rng, B, S, True), fv(S), fv(S))
+            elif k == 6:
+                b.emit("CAST", fv(S, False), iv(S))
+            elif k == 7 and len(S) >= 2:  # min/max/argmin/argmax over any axis
+                ax = int(rng.integers(0, len(S)))
+                R_ = S[:ax] + S[ax + 1:]
+                x = fv(S)
+                op = ["MIN_REDUCE", "MAX_REDUCE"][rng.integers(0, 2)]
+                b.emit(op, red_out(red, R_), x, axis=ax)
+                if rng.random() < 0.6:
+                    b.emit("ARGMIN_REDUCE" if op == "MIN_REDUCE" else "ARGMAX_REDUCE", red_out(redi, R_), x, axis=ax)
+            elif len(S) >= 2:  # int64 sums over any axis
+                ax = int(rng.integers(0, len(S)))
+                b.emit("ADD_REDUCE", red_out(redi, S[:ax] + S[ax + 1:]), iv(S), axis=ax)
+        except AssertionError:
+            continue  # no view of that shape fits: draw another instruction
+    outs = F + I + [B, red, redi]
+    p = b.build(outs)
+
+    def check(got, want):
+        for bid in outs:
+            if bid == red:
+                g, wv = np.asarray(got[bid]), np.asarray(want[bid])
+                same = (g == wv) | (np.isnan(g) & np.isnan(wv))
+                assert np.all(same), f"{p.name} reductions: got {g[~same][:4]} want {wv[~same][:4]}"
+            else:
+                assert_exact(got[bid], want[bid], f"{p.name} base {bid}")
+    return Case(p.name, p, check)
+
+
+def nd_cases(seeds):
+    return [random_nd_program(s) for s in seeds]
+
+
 def random_stencil_program(seed: int):
     """A random stencil chain that the library fuses into one tile-fused
     group: 2 to 4 runs, each computing a temporary from the previous one

@@ -10,12 +10,13 @@ build.build()
 
 import os  # noqa: E402
 
-from fuzz_programs import fuzz_cases, reduce_chain_cases, stencil_cases  # noqa: E402
+from fuzz_programs import fuzz_cases, nd_cases, reduce_chain_cases, stencil_cases  # noqa: E402
 from parity_cases import oracle_outputs  # noqa: E402
 from test_emulated_kernels import EMU, MODES, emulate  # noqa: E402
 
 CASES = fuzz_cases(range(4))
 REDCHAINS = reduce_chain_cases(range(3))
+ND = nd_cases(range(3))
 STENCILS = stencil_cases(range(3))
 FORMS = ["8x16", "s32x32", "t32x32", "r32"]
 
@@ -23,7 +24,7 @@ FORMS = ["8x16", "s32x32", "t32x32", "r32"]
 @pytest.fixture(scope="module", autouse=True)
 def _prebuild_fuzz_kernels():
     srcs = []
-    for case in CASES + REDCHAINS:
+    for case in CASES + REDCHAINS + ND:
         for mode in ("fused", "plain"):
             srcs += emulate(case.program, MODES[mode], (64, 1, 2), run=False)
     EMU.prebuild(srcs)
@@ -39,6 +40,13 @@ def test_fuzz_emulated(case, mode):
 @pytest.mark.parametrize("case", REDCHAINS, ids=[c.name for c in REDCHAINS])
 def test_fuzz_reduce_chains_emulated(case, mode):
     """Random programs that read reduction results later in the batch."""
+    case.check(emulate(case.program, MODES[mode], (64, 1, 2)), oracle_outputs(case.program))
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+@pytest.mark.parametrize("case", ND, ids=[c.name for c in ND])
+def test_fuzz_nd_emulated(case, mode):
+    """Random programs over views of rank 1 to 5."""
     case.check(emulate(case.program, MODES[mode], (64, 1, 2)), oracle_outputs(case.program))
 
 

@@ -16,7 +16,7 @@ from paper_1210_7774_b300 import vbe as V  # noqa: E402
 from paper_1210_7774_b300.runner import Executor  # noqa: E402
 
 import oracle  # noqa: E402
-from fuzz_programs import fuzz_cases, reduce_chain_cases, stencil_cases  # noqa: E402
+from fuzz_programs import fuzz_cases, nd_cases, reduce_chain_cases, stencil_cases  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
@@ -25,6 +25,7 @@ MODES = {"fused": (FUSED, 1, 0), "fused_graphs": (FUSED | V.VBE_GRAPHS, 2, 0), "
          "plain": (0, 1, 0)}
 CASES = fuzz_cases(range(80))
 REDCHAINS = reduce_chain_cases(range(40))
+ND = nd_cases(range(40))
 STENCILS = stencil_cases(range(40))
 # group forms forced by VBE_TILE ("" leaves the choice to the tuner)
 FORMS = ["", "32x32", "s32x32", "t32x32", "r24", "r64"]
@@ -66,6 +67,16 @@ def test_fuzz_reduce_chains(case, mode):
     """Programs whose later instructions read reduction results (int64 sums,
     argmin/argmax indices) through broadcasts: dependencies through
     reductions across fusion breaks, staging and graph replay."""
+    flags, repeat, staging = MODES[mode]
+    mem = oracle.run(case.program, instrs=list(case.program.instrs) * repeat)
+    case.check(_run(case.program, flags, repeat, staging), {bid: mem[bid] for bid in case.program.outputs})
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("case", ND, ids=[c.name for c in ND])
+def test_fuzz_nd(case, mode):
+    """Programs over views of rank 1 to 5 (axes in any order, reversed,
+    strided, broadcast; reductions over every axis)."""
     flags, repeat, staging = MODES[mode]
     mem = oracle.run(case.program, instrs=list(case.program.instrs) * repeat)
     case.check(_run(case.program, flags, repeat, staging), {bid: mem[bid] for bid in case.program.outputs})
