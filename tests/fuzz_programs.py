@@ -55,14 +55,17 @@ def _view(b, rng, bid, h, w, broadcast_ok):
     raise AssertionError("no view fits")
 
 
-def random_program(seed: int):
+def random_program(seed: int, fdt: str = "float64"):
+    """``fdt`` is the floating type of the float bases (float32 programs
+    draw the same instructions; their divides and square roots are
+    correctly rounded in float32, so they too are exact)."""
     rng = np.random.default_rng(1000 + seed)
-    b = ProgramBuilder(f"fuzz{seed}")
+    b = ProgramBuilder(f"fuzz{seed}" + ("" if fdt == "float64" else "_f32"))
     n = R * C
-    F = [b.base("float64", (R, C), rng.standard_normal(n) * np.exp2(rng.integers(-3, 4, n))) for _ in range(3)]
+    F = [b.base(fdt, (R, C), rng.standard_normal(n) * np.exp2(rng.integers(-3, 4, n))) for _ in range(3)]
     I = [b.base("int64", (R, C), rng.integers(-50, 50, n)) for _ in range(2)]
     B = b.base("bool", (R, C), rng.random(n) < 0.5)
-    red = b.base("float64", (64,), np.zeros(64))
+    red = b.base(fdt, (64,), np.zeros(64))
     redi = b.base("int64", (64,), np.zeros(64, np.int64))
 
     def fv(h, w, bc=True):
@@ -127,8 +130,8 @@ def random_program(seed: int):
     return Case(p.name, p, check)
 
 
-def fuzz_cases(seeds):
-    return [random_program(s) for s in seeds]
+def fuzz_cases(seeds, fdt: str = "float64"):
+    return [random_program(s, fdt) for s in seeds]
 
 
 def random_reduce_chain_program(seed: int):

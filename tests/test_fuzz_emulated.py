@@ -14,7 +14,7 @@ from fuzz_programs import fuzz_cases, nd_cases, reduce_chain_cases, stencil_case
 from parity_cases import oracle_outputs  # noqa: E402
 from test_emulated_kernels import EMU, MODES, emulate  # noqa: E402
 
-CASES = fuzz_cases(range(4))
+CASES = fuzz_cases(range(4)) + fuzz_cases(range(2), "float32")
 REDCHAINS = reduce_chain_cases(range(3))
 ND = nd_cases(range(3))
 STENCILS = stencil_cases(range(3))

@@ -1,9 +1,10 @@
 """Random exact programs (``fuzz_programs``) on the GPU against the oracle,
-bit for bit: fused with packing, fused with graph replay (each program run
-twice, so the second run replays), staged and plain. The views alias, overlap
-in place and partially overlap their own inputs, so every fusion break, the
-staging of overlapping operands and the MIN/ARGMIN pairing are exercised on
-shapes the hand-written cases do not have."""
+bit for bit, float64 and float32: fused with packing, fused with graph
+replay (each program run twice, so the second run replays), staged and
+plain. The views alias, overlap in place and partially overlap their own
+inputs, so every fusion break, the staging of overlapping operands and the
+MIN/ARGMIN pairing are exercised on shapes the hand-written cases do not
+have."""
 import os
 
 import pytest
@@ -23,7 +24,7 @@ CACHE = os.environ.get("VBE_CACHE_DIR", "/tmp/vbe_kernel_cache")
 FUSED = V.VBE_FUSE | V.VBE_PACK | V.VBE_AUTOTUNE
 MODES = {"fused": (FUSED, 1, 0), "fused_graphs": (FUSED | V.VBE_GRAPHS, 2, 0), "fused_staged": (FUSED, 1, 64),
          "plain": (0, 1, 0)}
-CASES = fuzz_cases(range(80))
+CASES = fuzz_cases(range(80)) + fuzz_cases(range(40), "float32")
 REDCHAINS = reduce_chain_cases(range(40))
 ND = nd_cases(range(40))
 STENCILS = stencil_cases(range(40))
