@@ -255,23 +255,35 @@ void admit(vbe_server* s, Worker* w, Req* r, int slot) {
 void worker_loop(vbe_server* s, Worker* w) {
   vbe::cuda_check(cudaSetDevice(w->ctx->c.device), "cudaSetDevice");
   std::vector<Req*> done, admitted;
-  std::vector<int> admitted_slot;
+  std::vector<int> admitted_slot, done_status;
   for (;;) {
     done.clear();
+    done_status.clear();
     admitted.clear();
     admitted_slot.clear();
+    // completions (their device work is finished), found outside the
+    // server's lock: only this worker changes its slots, and a request in a
+    // slot lives until this worker marks it done. The event queries are
+    // driver calls, which can wait behind another thread's driver work
+    // (a module load, the memory pool growing); under the lock such a wait
+    // would also hold up the host callbacks of every stream, which take it
+    // to hand results to their clients.
+    for (size_t k = 0; k < w->slots.size(); ++k) {
+      Req* r = w->slot_req[k];
+      if (!r || !r->ev) continue;
+      cudaError_t e = cudaEventQuery(r->ev);
+      if (e == cudaErrorNotReady) continue;
+      int st = VBE_OK;
+      if (e != cudaSuccess) st = VBE_ERR_CUDA;
+      else if (vbe::take_error_word(&w->ctx->c)) st = VBE_ERR_TIMEOUT;
+      done.push_back(r);
+      done_status.push_back(st);
+      w->slot_req[k] = nullptr;
+    }
     {
       std::unique_lock<std::mutex> lk(s->m);
-      // completions (their device work is finished)
-      for (size_t k = 0; k < w->slots.size(); ++k) {
-        Req* r = w->slot_req[k];
-        if (!r || !r->ev) continue;
-        cudaError_t e = cudaEventQuery(r->ev);
-        if (e == cudaErrorNotReady) continue;
-        if (e != cudaSuccess) r->res.status = VBE_ERR_CUDA;
-        else if (vbe::take_error_word(&w->ctx->c)) r->res.status = VBE_ERR_TIMEOUT;
-        done.push_back(r);
-        w->slot_req[k] = nullptr;
+      for (size_t i = 0; i < done.size(); ++i) {
+        if (done_status[i] != VBE_OK) done[i]->res.status = done_status[i];
         w->inflight--;
         s->inflight--;
       }
