@@ -819,7 +819,7 @@ def serving_bench(args, V, local):
         nb = sum((p.bases[b].nelem * np.dtype(NP_DTYPE[p.bases[b].dtype]).itemsize + 63) // 64 * 64
                  for b in p.outputs)
         need[i % nclients] = max(need[i % nclients], nb)
-    extra_mix = request_mix(1280, seed=1210_7774 + 99)
+    extra_mix = request_mix(256 + 3072, seed=1210_7774 + 99)
     for i, m in enumerate(extra_mix):
         p = request_program(*m)
         nb = sum((p.bases[b].nelem * np.dtype(NP_DTYPE[p.bases[b].dtype]).itemsize + 63) // 64 * 64
@@ -835,7 +835,7 @@ def serving_bench(args, V, local):
         # wait and drop the request (its result memory) when it is done
         reqs = [Request(p) for p in progs_all]
         # capacity: after a pass over 256 requests of the same mix (kernel
-        # compilation), a closed loop of the 64 clients over 1024 further
+        # compilation), a closed loop of the 64 clients over 3072 further
         # requests that have not been seen (another seed), so per-size work is
         # paid as it is in the timed run: each client submits its next
         # request as soon as its previous one is back
