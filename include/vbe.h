@@ -435,6 +435,11 @@ typedef struct vbe_request_result {
                              vbe_server_wait call that fetched them)       */
   double t_issued_ns;     /* the request's kernels and result copies were
                              enqueued (t_issued - t_admit: host planning)  */
+  double t_ready_ns;      /* results in host memory: the stream's host
+                             callback ran (t_ready - t_issued: device work
+                             and copies; t_done - t_ready: waking the
+                             client's thread and staging copies; 0 when
+                             the request failed before that)               */
 } vbe_request_result;
 
 typedef struct vbe_server vbe_server;

@@ -142,6 +142,7 @@ void CUDART_CB on_results_ready(void* arg) {
     // invalid (the word is cleared later by the worker's completion check;
     // a request finishing on the same context meanwhile is failed too)
     if (r->err_word && *(volatile const unsigned*)r->err_word) r->res.status = VBE_ERR_TIMEOUT;
+    r->res.t_ready_ns = now_ns();
     r->ready = true;
     r->cv.notify_all();  // under the lock: the client cannot delete the request before this returns
   }

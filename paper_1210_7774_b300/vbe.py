@@ -83,7 +83,7 @@ class vbe_server_config(Structure):
 class vbe_request_result(Structure):
     _fields_ = [("status", c_int32), ("reserved", c_int32), ("footprint_bytes", c_int64),
                 ("t_arrive_ns", c_double), ("t_admit_ns", c_double), ("t_done_ns", c_double),
-                ("t_issued_ns", c_double)]
+                ("t_issued_ns", c_double), ("t_ready_ns", c_double)]
 
 
 assert ctypes.sizeof(vbe_instr) == 80 and ctypes.sizeof(vbe_config) == 32
