@@ -274,16 +274,16 @@ void worker_loop(vbe_server* s, Worker* w) {
       if (!r || !r->ev) continue;
       cudaError_t e = cudaEventQuery(r->ev);
       if (e == cudaErrorNotReady) continue;
-      int st = VBE_OK;
-      if (e != cudaSuccess) st = VBE_ERR_CUDA;
-      else if (vbe::take_error_word(&w->ctx->c)) st = VBE_ERR_TIMEOUT;
       done.push_back(r);
-      done_status.push_back(st);
+      done_status.push_back(e == cudaSuccess ? VBE_OK : VBE_ERR_CUDA);
       w->slot_req[k] = nullptr;
     }
     {
       std::unique_lock<std::mutex> lk(s->m);
       for (size_t i = 0; i < done.size(); ++i) {
+        // the context's error word is read by the results callbacks under
+        // this lock, so it is taken (and cleared) under it too
+        if (done_status[i] == VBE_OK && vbe::take_error_word(&w->ctx->c)) done_status[i] = VBE_ERR_TIMEOUT;
         if (done_status[i] != VBE_OK) done[i]->res.status = done_status[i];
         w->inflight--;
         s->inflight--;
