@@ -838,7 +838,7 @@ def serving_bench(args, V, local):
     sys.setswitchinterval(1e-4)
     for name, flags in (("fused", V.VBE_FUSE | V.VBE_PACK), ("plain", 0)):
         ctx = V.vbe_init(local, flags, 0, None, cache)
-        srv = V.vbe_server_create(ctx, 16, 60 << 30, flags, workers=args.serve_workers)
+        srv = V.vbe_server_create(ctx, args.serve_slots, 60 << 30, flags, workers=args.serve_workers)
         # every request is built and packed (views, bytecodes, result buffers
         # not yet touched) before the clock starts, so the Python load
         # generator stays off the measured path; the clients only submit,
@@ -917,7 +917,7 @@ def serving_bench(args, V, local):
         res[name]["by_kind"] = by_kind
     sys.setswitchinterval(switch)
     res["requests"] = n_req
-    res["server"] = {"slots": 16, "workers": args.serve_workers, "mem_cap_bytes": 60 << 30, "clients": 64,
+    res["server"] = {"slots": args.serve_slots, "workers": args.serve_workers, "mem_cap_bytes": 60 << 30, "clients": 64,
                      "rate": "0.7 x the fused capacity, for both paths",
                      "results": "each client's results in a page-locked arena of its own (one request in flight "
                                 "per client), filled by the server straight from the device"}
@@ -939,6 +939,7 @@ def main():
     ap.add_argument("--dtypes", default="float64,float32", help="profiling: restrict the dtypes run")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--serve-workers", type=int, default=8, help="serving: scheduler threads of the server")
+    ap.add_argument("--serve-slots", type=int, default=16, help="serving: slots (streams) over all workers")
     ap.add_argument("--e2e-workers", type=int, default=4,
                     help="end-to-end: contexts (and host threads) the options are split over")
     ap.add_argument("--paths", default="fused,plain", help="profiling: restrict the paths run (jacobi: paper_size runs the 7168^2 part alone)")
