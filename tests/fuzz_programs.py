@@ -347,7 +347,7 @@ def nd_cases(seeds):
     return [random_nd_program(s) for s in seeds]
 
 
-def random_stencil_program(seed: int):
+def random_stencil_program(seed: int, reduce: bool = False):
     """A random stencil chain that the library fuses into one tile-fused
     group: 2 to 4 runs, each computing a temporary from the previous one
     (or the input) read at random row and column shifts of 0 to 3, with
@@ -355,13 +355,21 @@ def random_stencil_program(seed: int):
     again at a shift; the last run writes a separate output or updates the
     input in place (renamed while the group reads it around). Temporaries
     are discarded, and the chain runs twice, so the second pass reads what
-    the first renamed. Sizes are random (23 to 70), float64 or float32."""
+    the first renamed. Sizes are random (23 to 70), float64 or float32.
+
+    With ``reduce`` each pass ends, as a Jacobi sweep does, with a MIN or
+    MAX of one of its arrays along the rows and then of those results to a
+    scalar (exact in any order; a zero chosen from tied signed zeros is
+    compared by value). Those choices draw from a second generator, so the
+    chains themselves are the same as without."""
     rng = np.random.default_rng(5000 + seed)
+    rng2 = np.random.default_rng(7000 + seed)
     dt = ["float64", "float32"][rng.integers(0, 2)]
     R0, C0 = (int(x) for x in rng.integers(23, 71, 2))
-    b = ProgramBuilder(f"fuzz_stencil{seed}_{dt}")
+    b = ProgramBuilder(f"fuzz_stencil{seed}_{dt}" + ("_red" if reduce else ""))
     A = b.base(dt, (R0, C0), (rng.standard_normal(R0 * C0) * 2.0).astype(dt))
     O = b.base(dt, (R0, C0), np.zeros(R0 * C0, dt))
+    S = b.base(dt, (4,), np.zeros(4, dt)) if reduce else None
     nruns = int(rng.integers(2, 5))
     in_place = bool(rng.random() < 0.5)
     ops = ["ADD", "SUBTRACT", "MULTIPLY", "MAXIMUM", "MINIMUM", "DIVIDE"]
@@ -372,9 +380,10 @@ def random_stencil_program(seed: int):
                          s3=(rng.random(), rng.random()), k=float(np.round(rng.uniform(0.5, 2.0), 2)),
                          second=int(rng.integers(0, 3)), reread=bool(rng.random() < 0.4),
                          ao=(rng.random(), rng.random())))
-    for _ in range(2):
+    for ps in range(2):
         prev, (pr, pc) = A, (R0, C0)
         temps = []
+        arrays = []  # (view, rows) of every array the pass writes
         for j, q in enumerate(plan):
             Rj, Cj = pr - q["mdr"], pc - q["mdc"]
             last = j == nruns - 1
@@ -396,10 +405,27 @@ def random_stencil_program(seed: int):
                 b.emit(q["op2"], out, out, b.sub2d(prev, d3r, d3r + Rj, d3c, d3c + Cj))
             if q["reread"] and j > 0:  # the input again, shifted
                 b.emit("ADD", out, out, b.sub2d(A, d3r, d3r + Rj, d3c, d3c + Cj))
+            arrays.append((out, Rj))
             prev, (pr, pc) = (t if not last else None), (Rj, Cj)
+        if reduce:
+            x, rows = arrays[int(rng2.integers(0, len(arrays)))]
+            op = ["MIN_REDUCE", "MAX_REDUCE"][rng2.integers(0, 2)]
+            rt = b.base(dt, (rows,))
+            temps.append(rt)
+            b.emit(op, b.whole(rt), x, axis=1)
+            b.emit(op, b.view(S, ps, (), ()), b.whole(rt), axis=0)
         b.discard(*temps)
-    p = b.build([A, O])
-    check = _exact_outputs(p)
+    p = b.build([A, O, S] if reduce else [A, O])
+    exact = _exact_outputs(p)
+
+    def check(got, want):
+        if not reduce:
+            return exact(got, want)
+        for bid in (A, O):
+            assert_exact(got[bid], want[bid], f"{p.name} base {bid}")
+        g, wv = np.asarray(got[S]), np.asarray(want[S])
+        same = (g == wv) | (np.isnan(g) & np.isnan(wv))
+        assert np.all(same), f"{p.name} reductions: got {g} want {wv}"
     return Case(p.name, p, check)
 
 
@@ -410,5 +436,5 @@ def _exact_outputs(p):
     return check
 
 
-def stencil_cases(seeds):
-    return [random_stencil_program(s) for s in seeds]
+def stencil_cases(seeds, reduce: bool = False):
+    return [random_stencil_program(s, reduce) for s in seeds]

@@ -18,6 +18,7 @@ CASES = fuzz_cases(range(4)) + fuzz_cases(range(2), "float32")
 REDCHAINS = reduce_chain_cases(range(3))
 ND = nd_cases(range(3))
 STENCILS = stencil_cases(range(3))
+RED_STENCILS = stencil_cases(range(2), reduce=True)
 FORMS = ["8x16", "s32x32", "t32x32", "r32"]
 
 
@@ -51,7 +52,7 @@ def test_fuzz_nd_emulated(case, mode):
 
 
 @pytest.mark.parametrize("tile", FORMS)
-@pytest.mark.parametrize("case", STENCILS, ids=[c.name for c in STENCILS])
+@pytest.mark.parametrize("case", STENCILS + RED_STENCILS, ids=[c.name for c in STENCILS + RED_STENCILS])
 def test_fuzz_stencil_emulated(case, tile):
     """Random stencil chains in each group form (VBE_RECORD_TILE), emulated."""
     os.environ["VBE_RECORD_TILE"] = tile

@@ -27,7 +27,7 @@ MODES = {"fused": (FUSED, 1, 0), "fused_graphs": (FUSED | V.VBE_GRAPHS, 2, 0), "
 CASES = fuzz_cases(range(80)) + fuzz_cases(range(40), "float32")
 REDCHAINS = reduce_chain_cases(range(40))
 ND = nd_cases(range(40))
-STENCILS = stencil_cases(range(40))
+STENCILS = stencil_cases(range(40)) + stencil_cases(range(12), reduce=True)
 # group forms forced by VBE_TILE ("" leaves the choice to the tuner)
 FORMS = ["", "32x32", "s32x32", "t32x32", "r24", "r64"]
 
