@@ -15,9 +15,13 @@ documented relaxation is the sign of a zero chosen by a MIN/MAX reduction
 from tied signed zeros. Reductions write bases that no later instruction
 reads, so no reordering tolerance is needed anywhere.
 
-A second generator (``random_stencil_program``) makes random stencil chains
-that the library turns into tile-fused groups, to be run in every group
-form.
+The other generators: ``random_stencil_program`` makes random stencil
+chains that the library turns into tile-fused groups, to be run in every
+group form (optionally ending in MIN/MAX reductions, as a Jacobi sweep
+does); ``random_reduce_chain_program`` makes programs whose later
+instructions read reduction results back through broadcasts;
+``random_nd_program`` works on views of rank 1 to 5. ``random_program``
+also draws float32 programs (``fdt``).
 """
 from __future__ import annotations
 
