@@ -260,7 +260,7 @@ def _nd_view(b, rng, bid, shape, broadcast_ok):
     raise AssertionError("no view fits")
 
 
-def random_nd_program(seed: int):
+def random_nd_program(seed: int, fdt: str = "float64"):
     """Random exact programs over views of rank 1 to 5 of 3 x 4 x 5 x 6
     bases: dimensions in any order of the base axes, reversed, strided by
     two, broadcast (stride 0, inputs only), so the library's merging of
@@ -269,12 +269,12 @@ def random_nd_program(seed: int):
     oracle bit for bit (int64 sums; MIN/MAX/ARGMIN/ARGMAX; a zero chosen
     from tied signed zeros by MIN/MAX compared by value)."""
     rng = np.random.default_rng(13000 + seed)
-    b = ProgramBuilder(f"fuzz_nd{seed}")
+    b = ProgramBuilder(f"fuzz_nd{seed}" + ("" if fdt == "float64" else "_f32"))
     n = int(np.prod(LAYOUT))
-    F = [b.base("float64", LAYOUT, rng.standard_normal(n) * np.exp2(rng.integers(-3, 4, n))) for _ in range(2)]
+    F = [b.base(fdt, LAYOUT, rng.standard_normal(n) * np.exp2(rng.integers(-3, 4, n))) for _ in range(2)]
     I = [b.base("int64", LAYOUT, rng.integers(-50, 50, n)) for _ in range(2)]
     B = b.base("bool", LAYOUT, rng.random(n) < 0.5)
-    red = b.base("float64", (256,), np.zeros(256))
+    red = b.base(fdt, (256,), np.zeros(256))
     redi = b.base("int64", (256,), np.zeros(256, np.int64))
 
     def shape():
@@ -347,8 +347,8 @@ def random_nd_program(seed: int):
     return Case(p.name, p, check)
 
 
-def nd_cases(seeds):
-    return [random_nd_program(s) for s in seeds]
+def nd_cases(seeds, fdt: str = "float64"):
+    return [random_nd_program(s, fdt) for s in seeds]
 
 
 def random_stencil_program(seed: int, reduce: bool = False):

@@ -16,7 +16,7 @@ from test_emulated_kernels import EMU, MODES, emulate  # noqa: E402
 
 CASES = fuzz_cases(range(4)) + fuzz_cases(range(2), "float32")
 REDCHAINS = reduce_chain_cases(range(3))
-ND = nd_cases(range(3))
+ND = nd_cases(range(3)) + nd_cases(range(2), "float32")
 STENCILS = stencil_cases(range(3))
 RED_STENCILS = stencil_cases(range(2), reduce=True)
 FORMS = ["8x16", "s32x32", "t32x32", "r32"]
